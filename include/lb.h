@@ -1,0 +1,173 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) library for dense small-d Lindblad
+ * propagation.
+ *
+ * The operations follow arXiv 2603.18052 ("Hardware-Aware Performance
+ * Characterization of Small Dense Lindblad Propagation for Near-Term Quantum
+ * Control"): the vectorised Lindbladian of Eq. 1-3, the segment generator of
+ * Eq. 5, the Pade [13/13] scaling-and-squaring propagator build of
+ * Algorithm 1 and the propagation step of Algorithm 2, batched over states as
+ * in Algorithm 3, plus the gradient of a piecewise-constant control
+ * (Sec. 2.5).
+ *
+ * Conventions shared by every call
+ *  - Complex numbers are interleaved (re, im) doubles, the layout of
+ *    torch.complex128 and of C99 double complex.
+ *  - Matrices are dense and row-major.  A d x d density matrix is stored as
+ *    its row-major n-vector, n = d*d (Sec. 3.2: the d x d array is the
+ *    vector), so a batch of B states is a B x n row-major array.
+ *  - Every array argument is DEVICE memory owned by the caller, on the device
+ *    the context was created for, unless stated otherwise.  The library never
+ *    frees or keeps caller pointers after a call returns.
+ *  - All scratch memory is owned by the context and allocated in lb_create
+ *    only; the compute calls allocate nothing.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream).  Argument errors are detected on the host and returned
+ *    before anything is launched.  Numerical faults found on the device
+ *    (non-finite values, a zero pivot) are recorded in the context's error
+ *    word; lb_sync_status synchronises the stream and reports them.
+ *  - Calls on one context must not run concurrently (they share scratch).
+ */
+#ifndef LB_H
+#define LB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LB_OK = 0,
+  LB_EINVAL = 1,        /* bad argument (null pointer, size out of range) */
+  LB_ENODEV = 2,        /* no CUDA device, or the device is not sm_103 */
+  LB_ENOMEM = 3,        /* device allocation failed in lb_create */
+  LB_ECUDA = 4,         /* a CUDA runtime call or launch failed */
+  LB_ENONFINITE = 5,    /* NaN or Inf met on the device */
+  LB_ESINGULAR = 6,     /* zero pivot in the LU factorisation */
+  LB_ETIMEOUT = 7,      /* a bounded device-side wait gave up */
+  LB_EUNSUPPORTED = 8   /* valid request outside what this build supports */
+} lb_status;
+
+typedef enum {
+  LB_FP64 = 0,    /* every product in FP64 */
+  LB_FP32 = 1,    /* products in FP32 with FP32 accumulation */
+  LB_BF16X3 = 2   /* products as split-BF16 x3 on the tensor cores, FP32 accumulation */
+} lb_precision;
+
+typedef struct lb_ctx lb_ctx;
+
+typedef struct {
+  double re, im;
+} lb_c64;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int lb_version(void);
+
+/* Human-readable name of a status code.  Never NULL. */
+const char* lb_status_str(int status);
+
+/*
+ * lb_create: bind a context to CUDA device `device` and allocate its scratch
+ * for problems up to n = max_n (at most 729), max_batch states and
+ * max_slices propagators per call.  Larger slice counts are processed in
+ * chunks of max_slices.  *ctx receives the context (NULL on error).
+ * Returns LB_ENODEV without a usable sm_103 device, LB_ENOMEM if the scratch
+ * does not fit.
+ */
+lb_status lb_create(lb_ctx** ctx, int device, int max_n, int max_batch, int max_slices);
+
+/* Release the context and its scratch.  NULL is accepted. */
+lb_status lb_destroy(lb_ctx* ctx);
+
+/*
+ * Synchronise `stream`, then report (and clear) the device error word:
+ * LB_ENONFINITE, LB_ESINGULAR or LB_ETIMEOUT, else LB_OK.  A CUDA error met
+ * while synchronising gives LB_ECUDA.
+ */
+lb_status lb_sync_status(lb_ctx* ctx, void* stream);
+
+/* Bytes of device scratch owned by the context. */
+unsigned long long lb_workspace_bytes(const lb_ctx* ctx);
+
+/*
+ * lb_assemble -- the vectorised Lindbladian of Eq. 1 under row-major vec
+ * (Eq. 2-3):
+ *   L = -i (H (x) I - I (x) H^T)
+ *       + sum_k [ L_k (x) conj(L_k) - 1/2 (L_k^+ L_k) (x) I - 1/2 I (x) (L_k^+ L_k)^T ]
+ *   H      : d x d (Hermitian in physical use; not checked)
+ *   Ls     : K x d x d jump operators, contiguous; may be NULL when K == 0
+ *   L_out  : n x n, n = d*d, fully overwritten
+ * The drive generator of Eq. 5 is lb_assemble(X, K = 0).
+ * Limits: 1 <= d, d*d <= max_n; 0 <= K <= 64.
+ */
+lb_status lb_assemble(lb_ctx* ctx, int d, const lb_c64* H, int K, const lb_c64* Ls,
+                      lb_c64* L_out, void* stream);
+
+/*
+ * lb_expm_pade -- P[s] = exp(A_s), A_s = (Lbase + u[s] * Ldrv) * dt, for
+ * s < nslices (Eq. 5 and Algorithm 1 with theta = 0.25):
+ *   sc = max(0, ceil(log2(||A_s||_1 / theta))), ||.||_1 the maximum absolute
+ *   column sum; A = A_s / 2^sc; the three power products and three U/V
+ *   products of the [13/13] approximant; P from (V - U) P = (V + U) by an
+ *   FP64 LU factorisation and forward/back substitution; sc FP64 squarings.
+ *   Lbase : n x n; if Ldrv == NULL, Lbase holds nslices generators
+ *           (nslices x n x n) and u is ignored (may be NULL)
+ *   Ldrv  : n x n or NULL
+ *   u     : nslices doubles (device)
+ *   prec  : precision of the six Pade products; LU, solve and squarings are
+ *           always FP64
+ *   P_out : nslices x n x n
+ *   s_out : nslices ints (device) receiving sc, or NULL
+ * The LU takes no pivots: at theta = 0.25 the matrix V - U is strictly
+ * column diagonally dominant, for which partial pivoting selects the
+ * diagonal at every step.  A pivot of modulus below 1e-300 sets
+ * LB_ESINGULAR in the error word.
+ */
+lb_status lb_expm_pade(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                       const double* u, double dt, lb_precision prec, lb_c64* P_out, int* s_out,
+                       void* stream);
+
+/*
+ * lb_propagate_batch -- chained propagation steps rho <- P rho (Algorithm 2)
+ * for B states sharing the propagators (Algorithm 3's batch):
+ *   step t = 0 .. nslices*steps_per_slice - 1 uses P[t / steps_per_slice].
+ *   P      : nslices x n x n (FP64, as written by lb_expm_pade)
+ *   states : B x n, read as the initial states and overwritten with the
+ *            final ones
+ *   prec   : LB_FP64 computes in FP64.  LB_FP32 and LB_BF16X3 store
+ *            D = P - I in the lower precision, keep the states in FP32,
+ *            and apply rho + D rho with FP32 accumulation; the result is
+ *            written back as complex128.
+ *   renorm_trace : if nonzero and prec != LB_FP64, divide every state by
+ *            its trace (sum of entries i*d + i) after each step.
+ * Limits: n a perfect square, n <= max_n; 1 <= B <= max_batch.
+ */
+lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, int steps_per_slice,
+                             int B, lb_c64* states, lb_precision prec, int renorm_trace,
+                             void* stream);
+
+/*
+ * lb_grape_grad -- fidelity of a piecewise-constant control and its gradient
+ * (Sec. 2.5 landscape point, Eq. 5 segment generator):
+ *   P_s = exp((Lbase + u[s] Ldrv) dt), applied steps_per_slice times per
+ *   slice; X_T = chain applied to each of the B rows of X0;
+ *   F = Re sum_b <Xt_b, X_T,b> / B, <a, b> = sum_i conj(a_i) b_i;
+ *   grad[s] = dF/du[s] = sum over the steps t of slice s of
+ *             Re <Lam_t, dP_s X_{t-1}> / B,
+ *   with the adjoint chain Lam_T = Xt, Lam_{t-1} = P^+ Lam_t and dP_s the
+ *   Frechet derivative of exp at (Lbase + u[s] Ldrv) dt in the direction
+ *   Ldrv dt, obtained by differentiating the Pade approximant and the
+ *   squarings.  All FP64.
+ *   X0, Xtarget : B x n
+ *   fidelity_out: 1 double (device); grad_out: nslices doubles (device)
+ * Limits: n <= 81 (d <= 9), nslices <= max_slices, B <= max_batch.
+ */
+lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                        const double* u, double dt, int steps_per_slice, int B, const lb_c64* X0,
+                        const lb_c64* Xtarget, double* fidelity_out, double* grad_out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,268 @@
+// Grouped, batched complex GEMM on the CUDA cores.
+//
+// Every dense complex product of the propagator build (Algorithm 1: the three
+// power products, the three U/V products, the LU panel and trailing updates,
+// the back substitution and the squarings) and the large-n FP64 propagation
+// step (Algorithm 2 batched over states) goes through this kernel.
+//
+// FP64 form: on GB300 FP64 runs at 1/64 of the FP32 rate, so the kernel is
+// bound by the FP64 pipe and the design goal is the fewest FP64 instructions
+// with every SM busy.  It uses Gauss's three-real-product form of the complex
+// product, C_re = A_re B_re - A_im B_im and
+// C_im = (A_re + A_im)(B_re + B_im) - A_re B_re - A_im B_im, with the operand
+// sums formed once per shared-memory tile: 3 DFMA per complex multiply-add
+// instead of 4.  Work is a flat list of output tiles over all problems and
+// batch elements, walked by a persistent grid of (SMs x resident CTAs), so
+// 200-slice batches and ragged LU updates balance across the 152 SMs.
+//
+// FP32 form (mixed-precision Pade products): the same tiling with FP32
+// operands and FP32 accumulation, four real products per complex
+// multiply-add and larger register tiles; the epilogue (the linear
+// combinations of the Pade step) stays FP64.
+#include "lb_internal.cuh"
+
+#include <algorithm>
+
+namespace lb {
+
+namespace {
+
+struct GroupArgs {
+  ZGemmProblem p[4];
+  long long tile_start[5];
+  int tiles_m[4];
+  int tiles_n[4];
+  int nprob;
+};
+
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// NPL = number of operand planes kept in shared memory (3 for Gauss, 2 otherwise).
+template <typename T, int BM, int BN, int TM, int TN, bool GAUSS>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    zgemm_kernel(const __grid_constant__ GroupArgs g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int BK = 16;
+  constexpr int NPL = GAUSS ? 3 : 2;
+  __shared__ __align__(16) T As[NPL][BK][BM];
+  __shared__ __align__(16) T Bs[NPL][BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN);
+  const int ty = tid / (BN / TN);
+  const long long total = g.tile_start[g.nprob];
+
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    int pi = 0;
+    while (pi + 1 < g.nprob && t >= g.tile_start[pi + 1]) pi++;
+    const ZGemmProblem& P = g.p[pi];
+    const long long lt = t - g.tile_start[pi];
+    const int tpb = g.tiles_m[pi] * g.tiles_n[pi];
+    const long long b = lt / tpb;
+    const int r = (int)(lt - b * tpb);
+    const int tm = r / g.tiles_n[pi];
+    const int tn = r - tm * g.tiles_n[pi];
+    if (P.active != nullptr && P.active[b] <= P.active_iter) continue;
+    const int m0 = tm * BM, n0 = tn * BN;
+    const z64* __restrict__ A = P.A + b * P.sA;
+    const z64* __restrict__ B = P.B + b * P.sB;
+    const int M = P.M, N = P.N, K = P.K;
+
+    T acc1[TM][TN], acc2[TM][TN], acc3[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        acc1[i][j] = T(0);
+        acc2[i][j] = T(0);
+        acc3[i][j] = T(0);
+      }
+
+    const bool bT = (P.opB & 1) != 0;
+    const double bsign = (P.opB & 2) ? -1.0 : 1.0;
+    const double asign = P.conjA ? -1.0 : 1.0;
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      // A tile (BM x BK), k contiguous in memory.
+      for (int e = tid; e < BM * BK; e += NT) {
+        const int m = e / BK, k = e - (e / BK) * BK;
+        const int gm = m0 + m, gk = k0 + k;
+        z64 v = make_double2(0.0, 0.0);
+        if (gm < M && gk < K) v = A[(long long)gm * P.lda + gk];
+        const T re = T(v.x), im = T(asign * v.y);
+        As[0][k][m] = re;
+        As[1][k][m] = im;
+        if (GAUSS) As[NPL - 1][k][m] = re + im;
+      }
+      // B tile (BK x BN).
+      if (!bT) {
+        for (int e = tid; e < BK * BN; e += NT) {
+          const int k = e / BN, nn = e - (e / BN) * BN;
+          const int gk = k0 + k, gn = n0 + nn;
+          z64 v = make_double2(0.0, 0.0);
+          if (gk < K && gn < N) v = B[(long long)gk * P.ldb + gn];
+          const T re = T(v.x), im = T(bsign * v.y);
+          Bs[0][k][nn] = re;
+          Bs[1][k][nn] = im;
+          if (GAUSS) Bs[NPL - 1][k][nn] = re + im;
+        }
+      } else {
+        for (int e = tid; e < BK * BN; e += NT) {
+          const int nn = e / BK, k = e - (e / BK) * BK;
+          const int gk = k0 + k, gn = n0 + nn;
+          z64 v = make_double2(0.0, 0.0);
+          if (gk < K && gn < N) v = B[(long long)gn * P.ldb + gk];
+          const T re = T(v.x), im = T(bsign * v.y);
+          Bs[0][k][nn] = re;
+          Bs[1][k][nn] = im;
+          if (GAUSS) Bs[NPL - 1][k][nn] = re + im;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; k++) {
+        T ar[TM], ai[TM], br[TN], bi[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i++) {
+          ar[i] = As[0][k][ty * TM + i];
+          ai[i] = As[1][k][ty * TM + i];
+        }
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+          br[j] = Bs[0][k][tx * TN + j];
+          bi[j] = Bs[1][k][tx * TN + j];
+        }
+        if (GAUSS) {
+          T as[TM], bs[TN];
+#pragma unroll
+          for (int i = 0; i < TM; i++) as[i] = As[NPL - 1][k][ty * TM + i];
+#pragma unroll
+          for (int j = 0; j < TN; j++) bs[j] = Bs[NPL - 1][k][tx * TN + j];
+#pragma unroll
+          for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) {
+              acc1[i][j] = fmaT(ar[i], br[j], acc1[i][j]);
+              acc2[i][j] = fmaT(ai[i], bi[j], acc2[i][j]);
+              acc3[i][j] = fmaT(as[i], bs[j], acc3[i][j]);
+            }
+        } else {
+          // acc1 = re, acc2 = im
+#pragma unroll
+          for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) {
+              acc1[i][j] = fmaT(ar[i], br[j], acc1[i][j]);
+              acc1[i][j] = fmaT(-ai[i], bi[j], acc1[i][j]);
+              acc2[i][j] = fmaT(ar[i], bi[j], acc2[i][j]);
+              acc2[i][j] = fmaT(ai[i], br[j], acc2[i][j]);
+            }
+        }
+      }
+      __syncthreads();
+    }
+
+    // Epilogue in FP64.
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int gm = m0 + ty * TM + i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        const int gn = n0 + tx * TN + j;
+        if (gn >= N) continue;
+        double pre, pim;
+        if (GAUSS) {
+          pre = double(acc1[i][j]) - double(acc2[i][j]);
+          pim = double(acc3[i][j]) - double(acc1[i][j]) - double(acc2[i][j]);
+        } else {
+          pre = double(acc1[i][j]);
+          pim = double(acc2[i][j]);
+        }
+        const long long off = (long long)gm * P.ldc + gn;
+        const long long idx = b * P.sC + off;
+        double cr = P.alpha * pre, ci = P.alpha * pim;
+        if (P.beta != 0.0) {
+          const z64 c0 = P.C[idx];
+          cr = fma(P.beta, c0.x, cr);
+          ci = fma(P.beta, c0.y, ci);
+        }
+        for (int q = 0; q < P.nterms; q++) {
+          const z64 x = P.X[q][b * P.sX[q] + off];
+          cr = fma(P.coef[q], x.x, cr);
+          ci = fma(P.coef[q], x.y, ci);
+        }
+        if (gm == gn) cr += P.gamma;
+        P.C[idx] = make_double2(cr, ci);
+        if (P.C2 != nullptr) {
+          const z64 x2 = P.X2[b * P.sX2 + off];
+          P.C2[idx] = make_double2(fma(P.alpha2, pre, x2.x), fma(P.alpha2, pim, x2.y));
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int TM, int TN, bool GAUSS>
+cudaError_t launch_cfg(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
+  GroupArgs g;
+  g.nprob = nprob;
+  long long acc = 0;
+  for (int i = 0; i < nprob; i++) {
+    g.p[i] = probs[i];
+    g.tiles_m[i] = (probs[i].M + BM - 1) / BM;
+    g.tiles_n[i] = (probs[i].N + BN - 1) / BN;
+    g.tile_start[i] = acc;
+    if (probs[i].M > 0 && probs[i].N > 0 && probs[i].batch > 0)
+      acc += (long long)g.tiles_m[i] * g.tiles_n[i] * probs[i].batch;
+    else
+      g.tiles_m[i] = g.tiles_n[i] = 1;  // empty problem: zero tiles
+  }
+  g.tile_start[nprob] = acc;
+  for (int i = nprob; i < 4; i++) g.tile_start[i + 1 > 4 ? 4 : i + 1] = acc;
+  if (acc == 0) return cudaSuccess;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  static int occ = -1;  // resident CTAs per SM for this configuration
+  if (occ < 0) {
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &o, zgemm_kernel<T, BM, BN, TM, TN, GAUSS>, NT, 0);
+    if (e != cudaSuccess) return e;
+    occ = std::max(1, o);
+  }
+  long long grid = std::min<long long>(acc, (long long)sm_count * occ);
+  zgemm_kernel<T, BM, BN, TM, TN, GAUSS><<<(unsigned)grid, NT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+long long count_tiles(const ZGemmProblem* probs, int nprob, int BM, int BN) {
+  long long acc = 0;
+  for (int i = 0; i < nprob; i++)
+    if (probs[i].M > 0 && probs[i].N > 0)
+      acc += (long long)((probs[i].M + BM - 1) / BM) * ((probs[i].N + BN - 1) / BN) * probs[i].batch;
+  return acc;
+}
+
+}  // namespace
+
+cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
+  if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
+  // 32x32 tiles when there are enough of them to balance the persistent grid,
+  // else 16x16 tiles.
+  const long long t32 = count_tiles(probs, nprob, 32, 32);
+  if (t32 >= 8LL * sm_count) return launch_cfg<double, 32, 32, 2, 2, true>(probs, nprob, sm_count, st);
+  return launch_cfg<double, 16, 16, 1, 1, true>(probs, nprob, sm_count, st);
+}
+
+cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
+  if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
+  const long long t64 = count_tiles(probs, nprob, 64, 64);
+  if (t64 >= 4LL * sm_count) return launch_cfg<float, 64, 64, 4, 4, false>(probs, nprob, sm_count, st);
+  return launch_cfg<float, 32, 32, 2, 2, false>(probs, nprob, sm_count, st);
+}
+
+}  // namespace lb

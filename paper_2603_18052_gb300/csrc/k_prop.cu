@@ -1,0 +1,402 @@
+// Propagation kernels: chained steps rho <- P rho (Algorithm 2), batched over
+// states that share P (Algorithm 3's batch), for the sizes where P fits in
+// shared memory (n <= 81, i.e. d <= 9).  The whole chain runs inside one
+// launch: states are independent, so each CTA owns a slice of the batch,
+// keeps P and its states on chip for every step and synchronises only
+// within the CTA.  Larger n (d = 27) goes through the grouped GEMM, one
+// launch per step.
+//
+// FP64 form: Gauss three-real-product complex multiply-add, P held as the
+// planes (re, im, re + im).
+// FP32 form: D = P - I held in FP32 planes, states in FP32, each step
+// rho <- rho + D rho with FP32 accumulation (the identity part is applied
+// exactly, so the rounding of the stored propagator scales with |D| rather
+// than with |P| ~ 1), optional per-step division by the trace.
+#include "lb_internal.cuh"
+
+#include <algorithm>
+
+namespace lb {
+
+namespace {
+
+constexpr int kResThreads = 256;
+
+size_t resident_f64_smem(int n, int chunk) {
+  return sizeof(double) * (3ull * n * n + 5ull * chunk * n);
+}
+size_t resident_f32_smem(int n, int chunk) {
+  return sizeof(float) * (2ull * n * n + 4ull * chunk * n) + sizeof(float) * 2 * chunk;
+}
+
+__global__ void __launch_bounds__(kResThreads)
+    prop_resident_f64_kernel(int n, int nslices, const z64* __restrict__ P, int steps_per_slice, int B,
+                             int chunk, z64* __restrict__ states) {
+  extern __shared__ __align__(16) double sm[];
+  double* Pr = sm;
+  double* Pi = Pr + n * n;
+  double* Ps = Pi + n * n;
+  double* xr = Ps + n * n;      // chunk x n
+  double* xi = xr + chunk * n;
+  double* xs = xi + chunk * n;
+  double* yr = xs + chunk * n;
+  double* yi = yr + chunk * n;
+  const int b0 = blockIdx.x * chunk;
+  if (b0 >= B) return;
+  const int nb = min(chunk, B - b0);
+  const int tid = threadIdx.x;
+  const long long nn = (long long)n * n;
+  for (int e = tid; e < nb * n; e += blockDim.x) {
+    const z64 v = states[(long long)b0 * n + e];
+    xr[e] = v.x;
+    xi[e] = v.y;
+    xs[e] = v.x + v.y;
+  }
+  const int work = nb * n;
+  for (int s = 0; s < nslices; s++) {
+    __syncthreads();
+    for (int e = tid; e < n * n; e += blockDim.x) {
+      const z64 v = P[s * nn + e];
+      Pr[e] = v.x;
+      Pi[e] = v.y;
+      Ps[e] = v.x + v.y;
+    }
+    __syncthreads();
+    for (int t = 0; t < steps_per_slice; t++) {
+      for (int e = tid; e < work; e += blockDim.x) {
+        const int q = e / n, i = e - (e / n) * n;
+        const double* pr = Pr + i * n;
+        const double* pi = Pi + i * n;
+        const double* ps = Ps + i * n;
+        const double* ar = xr + q * n;
+        const double* ai = xi + q * n;
+        const double* as = xs + q * n;
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 3
+        for (int j = 0; j < n; j++) {
+          a1 = fma(pr[j], ar[j], a1);
+          a2 = fma(pi[j], ai[j], a2);
+          a3 = fma(ps[j], as[j], a3);
+        }
+        yr[e] = a1 - a2;
+        yi[e] = a3 - a1 - a2;
+      }
+      __syncthreads();
+      for (int e = tid; e < work; e += blockDim.x) {
+        const double r = yr[e], im = yi[e];
+        xr[e] = r;
+        xi[e] = im;
+        xs[e] = r + im;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < nb * n; e += blockDim.x) states[(long long)b0 * n + e] = make_double2(xr[e], xi[e]);
+}
+
+__global__ void __launch_bounds__(kResThreads)
+    prop_resident_f32_kernel(int n, int d, int nslices, const float* __restrict__ Dr,
+                             const float* __restrict__ Di, int steps_per_slice, int B, int chunk,
+                             int renorm, z64* __restrict__ states) {
+  extern __shared__ __align__(16) float smf[];
+  float* dr = smf;
+  float* di = dr + n * n;
+  float* xr = di + n * n;
+  float* xi = xr + chunk * n;
+  float* yr = xi + chunk * n;
+  float* yi = yr + chunk * n;
+  float* tr = yi + chunk * n;  // 2 * chunk: reciprocal trace (re, im)
+  const int b0 = blockIdx.x * chunk;
+  if (b0 >= B) return;
+  const int nb = min(chunk, B - b0);
+  const int tid = threadIdx.x;
+  const long long nn = (long long)n * n;
+  for (int e = tid; e < nb * n; e += blockDim.x) {
+    const z64 v = states[(long long)b0 * n + e];
+    xr[e] = (float)v.x;
+    xi[e] = (float)v.y;
+  }
+  const int work = nb * n;
+  for (int s = 0; s < nslices; s++) {
+    __syncthreads();
+    for (int e = tid; e < n * n; e += blockDim.x) {
+      dr[e] = Dr[s * nn + e];
+      di[e] = Di[s * nn + e];
+    }
+    __syncthreads();
+    for (int t = 0; t < steps_per_slice; t++) {
+      for (int e = tid; e < work; e += blockDim.x) {
+        const int q = e / n, i = e - (e / n) * n;
+        const float* pr = dr + i * n;
+        const float* pi = di + i * n;
+        const float* ar = xr + q * n;
+        const float* ai = xi + q * n;
+        float re = 0.f, im = 0.f;
+#pragma unroll 3
+        for (int j = 0; j < n; j++) {
+          re = fmaf(pr[j], ar[j], re);
+          re = fmaf(-pi[j], ai[j], re);
+          im = fmaf(pr[j], ai[j], im);
+          im = fmaf(pi[j], ar[j], im);
+        }
+        yr[e] = xr[e] + re;
+        yi[e] = xi[e] + im;
+      }
+      __syncthreads();
+      if (renorm) {
+        for (int q = tid; q < nb; q += blockDim.x) {
+          float sr = 0.f, si = 0.f;
+          for (int k = 0; k < d; k++) {
+            sr += yr[q * n + k * (d + 1)];
+            si += yi[q * n + k * (d + 1)];
+          }
+          const float m2 = sr * sr + si * si;
+          tr[2 * q] = sr / m2;
+          tr[2 * q + 1] = -si / m2;
+        }
+        __syncthreads();
+        for (int e = tid; e < work; e += blockDim.x) {
+          const int q = e / n;
+          const float cr = tr[2 * q], ci = tr[2 * q + 1];
+          const float r = yr[e], im = yi[e];
+          xr[e] = r * cr - im * ci;
+          xi[e] = r * ci + im * cr;
+        }
+      } else {
+        for (int e = tid; e < work; e += blockDim.x) {
+          xr[e] = yr[e];
+          xi[e] = yi[e];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < nb * n; e += blockDim.x)
+    states[(long long)b0 * n + e] = make_double2((double)xr[e], (double)xi[e]);
+}
+
+__global__ void make_delta_f32_kernel(int n, long long total, const z64* __restrict__ P,
+                                      float* __restrict__ Dr, float* __restrict__ Di) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long o = e % nn;
+    const int i = (int)(o / n), j = (int)(o - (o / n) * n);
+    z64 v = P[e];
+    if (i == j) v.x -= 1.0;
+    Dr[e] = (float)v.x;
+    Di[e] = (float)v.y;
+  }
+}
+
+__global__ void states_to_f32_kernel(long long total, const z64* __restrict__ s, float* __restrict__ r,
+                                     float* __restrict__ im) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const z64 v = s[e];
+    r[e] = (float)v.x;
+    im[e] = (float)v.y;
+  }
+}
+
+__global__ void states_from_f32_kernel(long long total, const float* __restrict__ r,
+                                       const float* __restrict__ im, z64* __restrict__ s) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    s[e] = make_double2((double)r[e], (double)im[e]);
+}
+
+// Out[b][i] = R[b][i] + sum_j D[i][j] R[b][j]; planar FP32.  64 x 64 output
+// tile (states x rows), 256 threads with 4 x 4 outputs each.
+__global__ void __launch_bounds__(256)
+    step_f32_kernel(int n, int B, const float* __restrict__ Dr, const float* __restrict__ Di,
+                    const float* __restrict__ Rr, const float* __restrict__ Ri, float* __restrict__ Or,
+                    float* __restrict__ Oi) {
+  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+  __shared__ __align__(16) float Ar[BK][BM], Ai[BK][BM], Br[BK][BN], Bi[BK][BN];
+  const int tilesN = (n + BN - 1) / BN;
+  const int tilesM = (B + BM - 1) / BM;
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  for (int t = blockIdx.x; t < tilesM * tilesN; t += gridDim.x) {
+    const int m0 = (t / tilesN) * BM, n0 = (t % tilesN) * BN;
+    float cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < TN; j++) cr[i][j] = ci[i][j] = 0.f;
+    for (int k0 = 0; k0 < n; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        const int m = e / BK, k = e % BK;
+        const int gm = m0 + m, gk = k0 + k;
+        const bool ok = gm < B && gk < n;
+        Ar[k][m] = ok ? Rr[(long long)gm * n + gk] : 0.f;
+        Ai[k][m] = ok ? Ri[(long long)gm * n + gk] : 0.f;
+      }
+      for (int e = tid; e < BN * BK; e += 256) {
+        const int nn_ = e / BK, k = e % BK;
+        const int gn = n0 + nn_, gk = k0 + k;
+        const bool ok = gn < n && gk < n;
+        Br[k][nn_] = ok ? Dr[(long long)gn * n + gk] : 0.f;
+        Bi[k][nn_] = ok ? Di[(long long)gn * n + gk] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; k++) {
+        float ar[TM], ai[TM], br[TN], bi[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i++) {
+          ar[i] = Ar[k][ty * TM + i];
+          ai[i] = Ai[k][ty * TM + i];
+        }
+#pragma unroll
+        for (int j = 0; j < TN; j++) {
+          br[j] = Br[k][tx * TN + j];
+          bi[j] = Bi[k][tx * TN + j];
+        }
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < TN; j++) {
+            cr[i][j] = fmaf(ar[i], br[j], cr[i][j]);
+            cr[i][j] = fmaf(-ai[i], bi[j], cr[i][j]);
+            ci[i][j] = fmaf(ar[i], bi[j], ci[i][j]);
+            ci[i][j] = fmaf(ai[i], br[j], ci[i][j]);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int gm = m0 + ty * TM + i;
+      if (gm >= B) continue;
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        const int gn = n0 + tx * TN + j;
+        if (gn >= n) continue;
+        const long long idx = (long long)gm * n + gn;
+        Or[idx] = Rr[idx] + cr[i][j];
+        Oi[idx] = Ri[idx] + ci[i][j];
+      }
+    }
+  }
+}
+
+// One warp per state: divide by the trace.
+__global__ void renorm_f32_kernel(int n, int d, int B, float* __restrict__ Rr, float* __restrict__ Ri) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= B) return;
+  float sr = 0.f, si = 0.f;
+  for (int k = lane; k < d; k += 32) {
+    sr += Rr[(long long)w * n + k * (d + 1)];
+    si += Ri[(long long)w * n + k * (d + 1)];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const float m2 = sr * sr + si * si;
+  const float cr = sr / m2, ci = -si / m2;
+  for (int e = lane; e < n; e += 32) {
+    const long long idx = (long long)w * n + e;
+    const float r = Rr[idx], im = Ri[idx];
+    Rr[idx] = r * cr - im * ci;
+    Ri[idx] = r * ci + im * cr;
+  }
+}
+
+int isqrt_exact(int n) {
+  int d = 1;
+  while ((d + 1) * (d + 1) <= n) d++;
+  return d;
+}
+
+unsigned grid_for(long long total, int threads, int sm_count) {
+  long long g = (total + threads - 1) / threads;
+  long long cap = (long long)sm_count * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+int pick_chunk(int B, int sm_count) { return std::max(1, (B + sm_count - 1) / sm_count); }
+
+}  // namespace
+
+bool resident_f64_fits(int n) { return n <= 81 && resident_f64_smem(n, 8) <= 227 * 1024; }
+bool resident_f32_fits(int n) { return n <= 81; }
+
+cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int steps_per_slice, int B,
+                                          z64* states, int sm_count, cudaStream_t st) {
+  int chunk = pick_chunk(B, sm_count);
+  size_t smem = resident_f64_smem(n, chunk);
+  while (smem > 227 * 1024 && chunk > 1) {
+    chunk = (chunk + 1) / 2;
+    smem = resident_f64_smem(n, chunk);
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(prop_resident_f64_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (B + chunk - 1) / chunk;
+  prop_resident_f64_kernel<<<grid, kResThreads, smem, st>>>(n, nslices, P, steps_per_slice, B, chunk,
+                                                            states);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_make_delta_f32(int n, int S, const z64* P, float* Dr, float* Di, cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  make_delta_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(n, total, P, Dr, Di);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, const float* Di,
+                                          int steps_per_slice, int B, z64* states, int renorm,
+                                          int sm_count, cudaStream_t st) {
+  int chunk = pick_chunk(B, sm_count);
+  size_t smem = resident_f32_smem(n, chunk);
+  while (smem > 227 * 1024 && chunk > 1) {
+    chunk = (chunk + 1) / 2;
+    smem = resident_f32_smem(n, chunk);
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(prop_resident_f32_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (B + chunk - 1) / chunk;
+  prop_resident_f32_kernel<<<grid, kResThreads, smem, st>>>(n, isqrt_exact(n), nslices, Dr, Di,
+                                                            steps_per_slice, B, chunk, renorm, states);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, float* Ri, cudaStream_t st) {
+  const long long total = (long long)n * B;
+  states_to_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, states, Rr, Ri);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* Ri, z64* states,
+                                   cudaStream_t st) {
+  const long long total = (long long)n * B;
+  states_from_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, Rr, Ri, states);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
+                            const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st) {
+  const int tiles = ((B + 63) / 64) * ((n + 63) / 64);
+  const int grid = std::min(tiles, sm_count * 2);
+  step_f32_kernel<<<grid, 256, 0, st>>>(n, B, Dr, Di, Rr, Ri, Or, Oi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t st) {
+  const int d = isqrt_exact(n);
+  const int threads = 256;
+  const int grid = (B * 32 + threads - 1) / threads;
+  renorm_f32_kernel<<<grid, threads, 0, st>>>(n, d, B, Rr, Ri);
+  return cudaGetLastError();
+}
+
+}  // namespace lb

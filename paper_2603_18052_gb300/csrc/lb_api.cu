@@ -1,0 +1,480 @@
+// C ABI of liblb: context management, argument checks and the host-side
+// orchestration of the propagator build (Algorithm 1), the propagation chain
+// (Algorithm 2, batched as in Algorithm 3) and the GRAPE gradient (Sec. 2.5).
+#include "lb_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+using namespace lb;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define LB_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return LB_ECUDA; \
+  } while (0)
+
+// [13/13] Pade coefficients of exp from the recurrence of the closed form
+// b_j = (2m-j)! m! / ((2m)! j! (m-j)!):  b_j = b_{j-1} (m - j + 1) / (j (2m - j + 1)).
+void pade13(double* b) {
+  const int m = 13;
+  b[0] = 1.0;
+  for (int j = 1; j <= m; j++) b[j] = b[j - 1] * double(m - j + 1) / (double(j) * double(2 * m - j + 1));
+}
+
+int nblocks(int n) { return (n + kLuNb - 1) / kLuNb; }
+
+bool is_square(int n, int* d_out) {
+  int d = 1;
+  while (d * d < n) d++;
+  if (d_out) *d_out = d;
+  return d * d == n;
+}
+
+size_t grape_ws_bytes(int max_n, int max_batch, int max_slices);
+
+}  // namespace
+
+extern "C" {
+
+int lb_version(void) { return 100; }
+
+const char* lb_status_str(int s) {
+  switch (s) {
+    case LB_OK: return "LB_OK";
+    case LB_EINVAL: return "LB_EINVAL: invalid argument";
+    case LB_ENODEV: return "LB_ENODEV: no usable sm_103 CUDA device";
+    case LB_ENOMEM: return "LB_ENOMEM: device allocation failed";
+    case LB_ECUDA: return "LB_ECUDA: CUDA runtime error";
+    case LB_ENONFINITE: return "LB_ENONFINITE: NaN or Inf on the device";
+    case LB_ESINGULAR: return "LB_ESINGULAR: zero pivot in the LU factorisation";
+    case LB_ETIMEOUT: return "LB_ETIMEOUT: a device-side wait timed out";
+    case LB_EUNSUPPORTED: return "LB_EUNSUPPORTED: request outside what this build supports";
+    default: return "unknown lb_status";
+  }
+}
+
+lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_slices) {
+  if (out == nullptr) return LB_EINVAL;
+  *out = nullptr;
+  if (max_n < 1 || max_n > kMaxN || max_batch < 1 || max_slices < 1) return LB_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return LB_ENODEV;
+  }
+  if (device < 0 || device >= ndev) return LB_ENODEV;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return LB_ENODEV;
+  if (prop.major != 10 || prop.minor != 3) return LB_ENODEV;  // sm_103 only
+  DeviceGuard g(device);
+  lb_ctx* c = new (std::nothrow) lb_ctx();
+  if (!c) return LB_ENOMEM;
+  c->device = device;
+  c->max_n = max_n;
+  c->max_batch = max_batch;
+  c->max_slices = max_slices;
+  c->sm_count = prop.multiProcessorCount;
+  pade13(c->pade_b);
+
+  const size_t nn = (size_t)max_n * max_n;
+  const size_t S = (size_t)max_slices;
+  const size_t zb = sizeof(z64);
+  const int nb = kLuNb, nbk = nblocks(max_n);
+  size_t need = 0;
+  auto add = [&](size_t b) { need = ((need + 255) & ~size_t(255)) + b; };
+  for (int i = 0; i < 9; i++) add(nn * S * zb);            // A A2 A4 A6 Z1 Z2 V W Mx
+  add(S * nb * nb * zb);                                    // Linv
+  add(S * (size_t)nbk * nb * nb * zb);                      // Uinv
+  add(S * sizeof(unsigned long long));                      // norm bits
+  add((S + 1) * sizeof(int));                               // sc
+  add(sizeof(z64) * 64 * 64);                               // G
+  add((size_t)max_batch * max_n * zb);                      // Rtmp
+  add(nn * S * sizeof(float));                              // Dr
+  add(nn * S * sizeof(float));                              // Di
+  for (int i = 0; i < 4; i++) add((size_t)max_batch * max_n * sizeof(float));
+  const size_t gbytes = grape_ws_bytes(max_n, max_batch, max_slices);
+  add(gbytes);
+  add(sizeof(unsigned int));                                // error word
+  need += 256;
+
+  if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return LB_ENOMEM;
+  }
+  c->ws_bytes = need;
+  Arena ar;
+  ar.base = c->ws;
+  ar.cap = need;
+  auto Z = [&](size_t elems) { return (z64*)ar.take(elems * zb); };
+  c->A = Z(nn * S);
+  c->A2 = Z(nn * S);
+  c->A4 = Z(nn * S);
+  c->A6 = Z(nn * S);
+  c->Z1 = Z(nn * S);
+  c->Z2 = Z(nn * S);
+  c->V = Z(nn * S);
+  c->W = Z(nn * S);
+  c->Mx = Z(nn * S);
+  c->Linv = Z(S * nb * nb);
+  c->Uinv = Z(S * (size_t)nbk * nb * nb);
+  c->norm_bits = (unsigned long long*)ar.take(S * sizeof(unsigned long long));
+  c->sc = (int*)ar.take((S + 1) * sizeof(int));
+  c->G = Z(64 * 64);
+  c->Rtmp = Z((size_t)max_batch * max_n);
+  c->Dr = (float*)ar.take(nn * S * sizeof(float));
+  c->Di = (float*)ar.take(nn * S * sizeof(float));
+  c->Rr = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->Ri = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->Or = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->Oi = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->grape = (z64*)ar.take(gbytes);
+  c->grape_bytes = gbytes;
+  c->err_dev = (unsigned int*)ar.take(sizeof(unsigned int));
+  if (!c->err_dev || cudaMemset(c->err_dev, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost(&c->err_host, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost(&c->scmax_host, sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_scmax, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    lb_destroy(c);
+    return LB_ENOMEM;
+  }
+  *out = c;
+  return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx* c) {
+  if (c == nullptr) return LB_OK;
+  DeviceGuard g(c->device);
+  if (c->ev_scmax) cudaEventDestroy(c->ev_scmax);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->scmax_host) cudaFreeHost(c->scmax_host);
+  if (c->ws) cudaFree(c->ws);
+  delete c;
+  return LB_OK;
+}
+
+unsigned long long lb_workspace_bytes(const lb_ctx* c) { return c ? (unsigned long long)c->ws_bytes : 0ull; }
+
+lb_status lb_sync_status(lb_ctx* c, void* stream) {
+  if (c == nullptr) return LB_EINVAL;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return LB_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ECUDA;
+  const unsigned int w = *c->err_host;
+  if (w != 0) {
+    if (cudaMemsetAsync(c->err_dev, 0, sizeof(unsigned int), st) != cudaSuccess) return LB_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ECUDA;
+  }
+  if (w & ERR_NONFINITE) return LB_ENONFINITE;
+  if (w & ERR_SINGULAR) return LB_ESINGULAR;
+  if (w & ERR_TIMEOUT) return LB_ETIMEOUT;
+  return LB_OK;
+}
+
+lb_status lb_assemble(lb_ctx* c, int d, const lb_c64* H, int K, const lb_c64* Ls, lb_c64* L_out,
+                      void* stream) {
+  if (c == nullptr || H == nullptr || L_out == nullptr) return LB_EINVAL;
+  if (d < 1 || d * d > c->max_n || K < 0 || K > 64 || (K > 0 && Ls == nullptr)) return LB_EINVAL;
+  DeviceGuard g(c->device);
+  LB_CUDA(launch_assemble(d, (const z64*)H, K, (const z64*)Ls, (z64*)L_out, c->G, c->sm_count,
+                          (cudaStream_t)stream));
+  return LB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+
+ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C) {
+  ZGemmProblem p;
+  const long long nn = (long long)n * n;
+  p.M = p.N = p.K = n;
+  p.A = A;
+  p.lda = n;
+  p.sA = nn;
+  p.B = B;
+  p.ldb = n;
+  p.sB = nn;
+  p.C = C;
+  p.ldc = n;
+  p.sC = nn;
+  p.batch = S;
+  return p;
+}
+
+// Blocked LU of Mx[s] (no pivot search) applied to the right-hand sides held in
+// N[s], then back substitution into N[s]:  N <- Mx^{-1} N.  Y and Uf are
+// scratch (n x n per slice), Lp scratch (n x nb per slice).
+lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, z64* Uf, z64* Y, z64* Lp,
+                           cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  const int nb = kLuNb, nbk = nblocks(n);
+  const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
+  for (int k = 0; k < nbk; k++) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, rest = n - k0 - kb;
+    z64* Uinv_k = c->Uinv + (long long)k * nb * nb;
+    LB_CUDA(launch_lu_diag(n, S, k0, kb, Mx, Uf, c->Linv, sLinv, Uinv_k, sUinv, c->err_dev, st));
+    ZGemmProblem pr[3];
+    int np = 0;
+    if (rest > 0) {
+      // (a) Lp = Mx[k0+kb:, k0:k0+kb] Uinv_k
+      ZGemmProblem& a = pr[np++];
+      a.M = rest; a.N = kb; a.K = kb;
+      a.A = Mx + (long long)(k0 + kb) * n + k0; a.lda = n; a.sA = nn;
+      a.B = Uinv_k; a.ldb = nb; a.sB = sUinv;
+      a.C = Lp; a.ldc = nb; a.sC = nn;
+      a.batch = S;
+      // (b) Uf[k0:k0+kb, k0+kb:] = Linv_k Mx[k0:k0+kb, k0+kb:]
+      ZGemmProblem& b = pr[np++];
+      b.M = kb; b.N = rest; b.K = kb;
+      b.A = c->Linv; b.lda = nb; b.sA = sLinv;
+      b.B = Mx + (long long)k0 * n + k0 + kb; b.ldb = n; b.sB = nn;
+      b.C = Uf + (long long)k0 * n + k0 + kb; b.ldc = n; b.sC = nn;
+      b.batch = S;
+    }
+    {
+      // (c) Y[k0:k0+kb, :] = Linv_k N[k0:k0+kb, :]
+      ZGemmProblem& q = pr[np++];
+      q.M = kb; q.N = n; q.K = kb;
+      q.A = c->Linv; q.lda = nb; q.sA = sLinv;
+      q.B = N + (long long)k0 * n; q.ldb = n; q.sB = nn;
+      q.C = Y + (long long)k0 * n; q.ldc = n; q.sC = nn;
+      q.batch = S;
+    }
+    LB_CUDA(zgemm_f64(pr, np, c->sm_count, st));
+    if (rest > 0) {
+      ZGemmProblem tr[2];
+      // (d) Mx[k0+kb:, k0+kb:] -= Lp Uf[k0:k0+kb, k0+kb:]
+      ZGemmProblem& d = tr[0];
+      d.M = rest; d.N = rest; d.K = kb;
+      d.A = Lp; d.lda = nb; d.sA = nn;
+      d.B = Uf + (long long)k0 * n + k0 + kb; d.ldb = n; d.sB = nn;
+      d.C = Mx + (long long)(k0 + kb) * n + k0 + kb; d.ldc = n; d.sC = nn;
+      d.alpha = -1.0; d.beta = 1.0; d.batch = S;
+      // (e) N[k0+kb:, :] -= Lp Y[k0:k0+kb, :]
+      ZGemmProblem& e = tr[1];
+      e.M = rest; e.N = n; e.K = kb;
+      e.A = Lp; e.lda = nb; e.sA = nn;
+      e.B = Y + (long long)k0 * n; e.ldb = n; e.sB = nn;
+      e.C = N + (long long)(k0 + kb) * n; e.ldc = n; e.sC = nn;
+      e.alpha = -1.0; e.beta = 1.0; e.batch = S;
+      LB_CUDA(zgemm_f64(tr, 2, c->sm_count, st));
+    }
+  }
+  // back substitution: X_k = Uinv_k Y_k; Y[:k0] -= Uf[:k0, k0:k0+kb] X_k
+  for (int k = nbk - 1; k >= 0; k--) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb;
+    z64* Uinv_k = c->Uinv + (long long)k * nb * nb;
+    ZGemmProblem f;
+    f.M = kb; f.N = n; f.K = kb;
+    f.A = Uinv_k; f.lda = nb; f.sA = sUinv;
+    f.B = Y + (long long)k0 * n; f.ldb = n; f.sB = nn;
+    f.C = N + (long long)k0 * n; f.ldc = n; f.sC = nn;
+    f.batch = S;
+    LB_CUDA(zgemm_f64(&f, 1, c->sm_count, st));
+    if (k0 > 0) {
+      ZGemmProblem gq;
+      gq.M = k0; gq.N = n; gq.K = kb;
+      gq.A = Uf + k0; gq.lda = n; gq.sA = nn;
+      gq.B = N + (long long)k0 * n; gq.ldb = n; gq.sB = nn;
+      gq.C = Y; gq.ldc = n; gq.sC = nn;
+      gq.alpha = -1.0; gq.beta = 1.0; gq.batch = S;
+      LB_CUDA(zgemm_f64(&gq, 1, c->sm_count, st));
+    }
+  }
+  return LB_OK;
+}
+
+// One chunk of slices of lb_expm_pade.
+lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
+                     double dt, lb_precision prec, z64* P, int* s_out, cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  const double* b = c->pade_b;
+  gemm_fn gemm = (prec == LB_FP64) ? zgemm_f64 : zgemm_f32;
+  LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, s_out, c->err_dev,
+                               c->sm_count, st));
+  LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+  // three power products
+  ZGemmProblem p = sq(n, S, c->A, c->A, c->A2);
+  LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  p = sq(n, S, c->A2, c->A2, c->A4);
+  LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  p = sq(n, S, c->A4, c->A2, c->A6);
+  LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[12], b[10], b[8], c->Z1, st));
+  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[13], b[11], b[9], c->Z2, st));
+  // V = A6 Z1 + b6 A6 + b4 A4 + b2 A2 + b0 I ;  W' = A6 Z2 + b7 A6 + b5 A4 + b3 A2 + b1 I
+  ZGemmProblem vw[2];
+  vw[0] = sq(n, S, c->A6, c->Z1, c->V);
+  vw[0].nterms = 3;
+  vw[0].X[0] = c->A6; vw[0].X[1] = c->A4; vw[0].X[2] = c->A2;
+  vw[0].sX[0] = vw[0].sX[1] = vw[0].sX[2] = nn;
+  vw[0].coef[0] = b[6]; vw[0].coef[1] = b[4]; vw[0].coef[2] = b[2];
+  vw[0].gamma = b[0];
+  vw[1] = sq(n, S, c->A6, c->Z2, c->W);
+  vw[1].nterms = 3;
+  vw[1].X[0] = c->A6; vw[1].X[1] = c->A4; vw[1].X[2] = c->A2;
+  vw[1].sX[0] = vw[1].sX[1] = vw[1].sX[2] = nn;
+  vw[1].coef[0] = b[7]; vw[1].coef[1] = b[5]; vw[1].coef[2] = b[3];
+  vw[1].gamma = b[1];
+  LB_CUDA(gemm(vw, 2, c->sm_count, st));
+  // U = A W';  Mx = V - U, P = V + U
+  p = sq(n, S, c->A, c->W, c->Mx);
+  p.alpha = -1.0;
+  p.nterms = 1;
+  p.X[0] = c->V; p.sX[0] = nn; p.coef[0] = 1.0;
+  p.C2 = P; p.X2 = c->V; p.sX2 = nn; p.alpha2 = 1.0;
+  LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  // (V - U) P = (V + U), FP64.  Uf, Y, Lp reuse A2, A4, A6.
+  lb_status s = lu_solve_blocked(c, n, S, c->Mx, P, c->A2, c->A4, c->A6, st);
+  if (s != LB_OK) return s;
+  // squarings, FP64.  The count is known on the host once the event that
+  // follows the norm kernel has completed (long before the LU finishes).
+  LB_CUDA(cudaEventSynchronize(c->ev_scmax));
+  const int smax = *c->scmax_host;
+  for (int it = 0; it < smax; it++) {
+    ZGemmProblem q = sq(n, S, P, P, c->Z1);
+    q.active = c->sc;
+    q.active_iter = it;
+    LB_CUDA(zgemm_f64(&q, 1, c->sm_count, st));
+    LB_CUDA(launch_copy_active(nn, S, c->Z1, P, c->sc, it, st));
+  }
+  LB_CUDA(launch_check_finite(nn * S, P, c->err_dev, st));
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                       const double* u, double dt, lb_precision prec, lb_c64* P_out, int* s_out,
+                       void* stream) {
+  if (c == nullptr || Lbase == nullptr || P_out == nullptr) return LB_EINVAL;
+  if (n < 1 || n > c->max_n || nslices < 0) return LB_EINVAL;
+  if (Ldrv != nullptr && u == nullptr) return LB_EINVAL;
+  if (!std::isfinite(dt)) return LB_EINVAL;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
+  if (prec == LB_BF16X3) return LB_EUNSUPPORTED;
+  if (nslices == 0) return LB_OK;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nn = (long long)n * n;
+  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+    const z64* Lb = (const z64*)Lbase + (Ldrv == nullptr ? s0 * nn : 0);
+    lb_status r = expm_chunk(c, n, S, Lb, (const z64*)Ldrv, u ? u + s0 : nullptr, dt, prec,
+                             (z64*)P_out + s0 * nn, s_out ? s_out + s0 : nullptr, st);
+    if (r != LB_OK) return r;
+  }
+  return LB_OK;
+}
+
+lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int steps_per_slice,
+                             int B, lb_c64* states, lb_precision prec, int renorm_trace,
+                             void* stream) {
+  if (c == nullptr || P == nullptr || states == nullptr) return LB_EINVAL;
+  int d = 0;
+  if (n < 1 || n > c->max_n || !is_square(n, &d)) return LB_EINVAL;
+  if (nslices < 0 || steps_per_slice < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
+  if (prec == LB_BF16X3) return LB_EUNSUPPORTED;
+  if (nslices == 0 || steps_per_slice == 0) return LB_OK;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nn = (long long)n * n;
+  const z64* Pz = (const z64*)P;
+  z64* X = (z64*)states;
+  if (prec == LB_FP64) {
+    if (resident_f64_fits(n)) {
+      LB_CUDA(launch_propagate_resident_f64(n, nslices, Pz, steps_per_slice, B, X, c->sm_count, st));
+      return LB_OK;
+    }
+    z64* cur = X;
+    z64* nxt = c->Rtmp;
+    for (int s = 0; s < nslices; s++)
+      for (int t = 0; t < steps_per_slice; t++) {
+        // next[b][i] = sum_j P[i][j] cur[b][j]  ->  C = cur * P^T
+        ZGemmProblem q;
+        q.M = B; q.N = n; q.K = n;
+        q.A = cur; q.lda = n;
+        q.B = Pz + s * nn; q.ldb = n; q.opB = 1;
+        q.C = nxt; q.ldc = n;
+        q.batch = 1;
+        LB_CUDA(zgemm_f64(&q, 1, c->sm_count, st));
+        z64* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+    if (cur != X)
+      LB_CUDA(cudaMemcpyAsync(X, cur, sizeof(z64) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
+    return LB_OK;
+  }
+  // FP32: D = P - I in FP32, states in FP32
+  const bool resident = resident_f32_fits(n);
+  if (!resident) LB_CUDA(launch_states_to_f32(n, B, X, c->Rr, c->Ri, st));
+  float *cr = c->Rr, *ci = c->Ri, *nr = c->Or, *ni = c->Oi;
+  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+    LB_CUDA(launch_make_delta_f32(n, S, Pz + s0 * nn, c->Dr, c->Di, st));
+    if (resident) {
+      LB_CUDA(launch_propagate_resident_f32(n, S, c->Dr, c->Di, steps_per_slice, B, X, renorm_trace,
+                                            c->sm_count, st));
+      continue;
+    }
+    for (int s = 0; s < S; s++)
+      for (int t = 0; t < steps_per_slice; t++) {
+        LB_CUDA(launch_step_f32(n, B, c->Dr + s * nn, c->Di + s * nn, cr, ci, nr, ni, c->sm_count, st));
+        if (renorm_trace) LB_CUDA(launch_renorm_f32(n, B, nr, ni, st));
+        float* t1 = cr; cr = nr; nr = t1;
+        float* t2 = ci; ci = ni; ni = t2;
+      }
+  }
+  if (!resident) LB_CUDA(launch_states_from_f32(n, B, cr, ci, X, st));
+  return LB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+size_t grape_ws_bytes(int max_n, int max_batch, int max_slices) {
+  (void)max_n;
+  (void)max_batch;
+  (void)max_slices;
+  return 256;
+}
+}  // namespace
+
+extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* Lbase,
+                                   const lb_c64* Ldrv, const double* u, double dt, int steps_per_slice,
+                                   int B, const lb_c64* X0, const lb_c64* Xtarget, double* fidelity_out,
+                                   double* grad_out, void* stream) {
+  if (c == nullptr) return LB_EINVAL;
+  (void)n; (void)nslices; (void)Lbase; (void)Ldrv; (void)u; (void)dt; (void)steps_per_slice;
+  (void)B; (void)X0; (void)Xtarget; (void)fidelity_out; (void)grad_out; (void)stream;
+  return LB_EUNSUPPORTED;
+}

@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of liblb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "lb.h"
+
+namespace lb {
+
+// Device error word bits (the context's error word is a uint32).
+enum : unsigned int {
+  ERR_NONFINITE = 1u,
+  ERR_SINGULAR = 2u,
+  ERR_TIMEOUT = 4u,
+};
+
+constexpr int kMaxN = 729;
+constexpr int kLuNb = 32;  // LU block size
+
+typedef double2 z64;
+
+// Workspace carve-out.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    size_t a = (off + 255) & ~size_t(255);
+    if (a + bytes > cap) return nullptr;
+    off = a + bytes;
+    return base + a;
+  }
+};
+
+}  // namespace lb
+
+struct lb_ctx {
+  int device = 0;
+  int max_n = 0, max_batch = 0, max_slices = 0;
+  int sm_count = 0;
+  char* ws = nullptr;  // device scratch (one allocation)
+  size_t ws_bytes = 0;
+  unsigned int* err_dev = nullptr;  // device error word
+  unsigned int* err_host = nullptr; // pinned copy
+  int* scmax_host = nullptr;        // pinned: largest squaring count of the last build
+  cudaEvent_t ev_scmax = nullptr;
+  double pade_b[14];
+  // --- propagator build, per slice (stride max_n^2 complex) ---
+  lb::z64 *A = nullptr, *A2 = nullptr, *A4 = nullptr, *A6 = nullptr, *Z1 = nullptr, *Z2 = nullptr;
+  lb::z64 *V = nullptr, *W = nullptr, *Mx = nullptr;
+  lb::z64 *Linv = nullptr;  // per slice nb x nb
+  lb::z64 *Uinv = nullptr;  // per slice nblk x nb x nb
+  unsigned long long* norm_bits = nullptr;
+  int* sc = nullptr;  // max_slices + 1 (last = max)
+  lb::z64* G = nullptr;  // d x d Gram matrix for assembly
+  // --- propagation ---
+  lb::z64* Rtmp = nullptr;  // max_batch x max_n
+  float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2
+  float *Rr = nullptr, *Ri = nullptr, *Or = nullptr, *Oi = nullptr;  // max_batch x max_n
+  // --- GRAPE (n <= 81) ---
+  lb::z64* grape = nullptr;
+  size_t grape_bytes = 0;
+};
+
+namespace lb {
+
+// ---------------------------------------------------------------- GEMM ----
+// Grouped, batched complex FP64 GEMM (Gauss three-real-product form):
+//   C[b] = alpha * opA(A[b]) opB(B[b]) + beta * C[b] + sum_t coef[t] * X_t[b] + gamma * I
+//   C2[b] = X2[b] + alpha2 * opA(A[b]) opB(B[b])          (when C2 != nullptr)
+// All matrices row-major complex128.  opB: 0 = B, 1 = B^T, 2 = conj(B), 3 = B^H.
+// conjA conjugates A.  A batch element b is skipped when
+// active != nullptr and active[b] <= active_iter.
+struct ZGemmProblem {
+  int M = 0, N = 0, K = 0;
+  const z64* A = nullptr; long long lda = 0, sA = 0; int conjA = 0;
+  const z64* B = nullptr; long long ldb = 0, sB = 0; int opB = 0;
+  z64* C = nullptr; long long ldc = 0, sC = 0;
+  double alpha = 1.0, beta = 0.0, gamma = 0.0;
+  int nterms = 0;
+  const z64* X[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long sX[4] = {0, 0, 0, 0};
+  double coef[4] = {0, 0, 0, 0};
+  z64* C2 = nullptr; const z64* X2 = nullptr; long long sX2 = 0; double alpha2 = 1.0;
+  const int* active = nullptr; int active_iter = 0;
+  int batch = 1;
+};
+
+// Launch up to 4 problems in one grouped launch.  Returns a CUDA error code.
+cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
+
+// FP32 variant (operands rounded to FP32, FP32 accumulation, FP64 epilogue).
+cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
+
+// ------------------------------------------------------------ assembly ----
+cudaError_t launch_assemble(int d, const z64* H, int K, const z64* Ls, z64* L_out, z64* G_scratch,
+                            int sm_count, cudaStream_t st);
+
+// A_s = (Lbase + u_s Ldrv) dt (or Lbase[s] dt); column abs-sums -> norm1[s]
+// (as uint64 bit patterns of non-negative doubles, max-reduced), then
+// sc[s] and A_s /= 2^sc[s].
+cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
+                                 double dt, z64* A, unsigned long long* norm_bits, int* sc,
+                                 int* s_out, unsigned int* err, int sm_count, cudaStream_t st);
+
+// Elementwise linear combinations used by the Pade step.
+// Z[b] = c0*X0[b] + c1*X1[b] + c2*X2[b]  (n x n each, batch strides = n*n)
+cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z64* X2, double c0,
+                            double c1, double c2, z64* Z, cudaStream_t st);
+
+// --------------------------------------------------------------- LU -------
+// Factor the kb x kb diagonal block at (k0, k0) of M[b] (no pivot search),
+// write Linv and Uinv (nb x nb each, per batch) and the U11 factor into Uf.
+cudaError_t launch_lu_diag(int n, int S, int k0, int kb, const z64* M, z64* Uf, z64* Linv,
+                           long long sLinv, z64* Uinv, long long sUinv, unsigned int* err,
+                           cudaStream_t st);
+
+// Copy rows/cols helper: dst[b][r][c] = src[b][r][c] for r in [r0,r0+nr), c in [c0,c0+nc)
+cudaError_t launch_copy_block(int S, long long ld, long long stride, int r0, int nr, int c0, int nc,
+                              const z64* src, z64* dst, cudaStream_t st);
+
+// ------------------------------------------------------------ misc --------
+cudaError_t launch_copy_active(long long nn, int S, const z64* src, z64* dst, const int* active,
+                               int iter, cudaStream_t st);
+cudaError_t launch_check_finite(long long count, const z64* x, unsigned int* err, cudaStream_t st);
+
+// ----------------------------------------------------------- propagation --
+// Resident FP64 propagation for small n (P in shared memory): every step of
+// the chain in one launch, states split across CTAs.
+cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int steps_per_slice,
+                                          int B, z64* states, int sm_count, cudaStream_t st);
+bool resident_f64_fits(int n);
+
+// FP32 propagation with D = P - I stored in FP32 planes.
+cudaError_t launch_make_delta_f32(int n, int S, const z64* P, float* Dr, float* Di, cudaStream_t st);
+cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, const float* Di,
+                                          int steps_per_slice, int B, z64* states, int renorm,
+                                          int sm_count, cudaStream_t st);
+bool resident_f32_fits(int n);
+// Large-n FP32 step: Rout = Rin + Rin * D^T (planar FP32 states), optional renorm.
+cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, float* Ri, cudaStream_t st);
+cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* Ri, z64* states,
+                                   cudaStream_t st);
+cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
+                            const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st);
+cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t st);
+
+}  // namespace lb

@@ -1,0 +1,208 @@
+"""ctypes binding of liblb (the C ABI declared in include/lb.h).
+
+Argument marshalling only: every function takes torch tensors that already
+live on the context's CUDA device, checks dtype, shape and contiguity, and
+passes their data pointers and the current CUDA stream to the C function of
+the same name.  All arithmetic runs in the library's kernels; there is no
+fallback path, and a missing or unloadable library raises immediately.
+"""
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+LB_FP64, LB_FP32, LB_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3}
+
+_STATUS = {
+    0: "LB_OK",
+    1: "LB_EINVAL",
+    2: "LB_ENODEV",
+    3: "LB_ENOMEM",
+    4: "LB_ECUDA",
+    5: "LB_ENONFINITE",
+    6: "LB_ESINGULAR",
+    7: "LB_ETIMEOUT",
+    8: "LB_EUNSUPPORTED",
+}
+
+EXPORTED = (
+    "lb_version",
+    "lb_status_str",
+    "lb_create",
+    "lb_destroy",
+    "lb_sync_status",
+    "lb_workspace_bytes",
+    "lb_assemble",
+    "lb_expm_pade",
+    "lb_propagate_batch",
+    "lb_grape_grad",
+)
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        self.name = _STATUS.get(status, "?")
+        super().__init__("%s failed: %s" % (what, lib().lb_status_str(status).decode()))
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load liblb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("liblb.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, ip, dp, i32, f64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.lb_version.restype = i32
+    L.lb_version.argtypes = []
+    L.lb_status_str.restype = ctypes.c_char_p
+    L.lb_status_str.argtypes = [i32]
+    L.lb_create.restype = i32
+    L.lb_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32]
+    L.lb_destroy.restype = i32
+    L.lb_destroy.argtypes = [vp]
+    L.lb_sync_status.restype = i32
+    L.lb_sync_status.argtypes = [vp, vp]
+    L.lb_workspace_bytes.restype = ctypes.c_ulonglong
+    L.lb_workspace_bytes.argtypes = [vp]
+    L.lb_assemble.restype = i32
+    L.lb_assemble.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+    L.lb_expm_pade.restype = i32
+    L.lb_expm_pade.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, vp, vp]
+    L.lb_propagate_batch.restype = i32
+    L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
+    L.lb_grape_grad.restype = i32
+    L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
+    del ip, dp
+    _lib = L
+    return L
+
+
+def _check(status, what):
+    if status != 0:
+        raise LBError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, dtype, what, shape=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s must not be None" % what)
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA %s tensor" % (what, dtype))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (what, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """An lb_ctx bound to one CUDA device, owning the library's scratch."""
+
+    def __init__(self, device=0, max_n=729, max_batch=1024, max_slices=200):
+        L = lib()
+        h = ctypes.c_void_p()
+        if isinstance(device, torch.device):
+            device = device.index or 0
+        _check(L.lb_create(ctypes.byref(h), int(device), int(max_n), int(max_batch), int(max_slices)),
+               "lb_create")
+        self.handle = h
+        self.device = int(device)
+        self.max_n, self.max_batch, self.max_slices = int(max_n), int(max_batch), int(max_slices)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().lb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self):
+        return int(lib().lb_workspace_bytes(self.handle))
+
+
+def lb_sync_status(ctx, stream=None):
+    """Synchronise the stream and raise on a device-side error."""
+    _check(lib().lb_sync_status(ctx.handle, _stream(stream)), "lb_sync_status")
+
+
+def lb_assemble(ctx, H, Ls, L_out, stream=None):
+    """L_out (n x n) = vectorised Lindbladian of H (d x d) and the jump
+    operators Ls (K x d x d, or None)."""
+    d = H.shape[0]
+    K = 0 if Ls is None else Ls.shape[0]
+    c128 = torch.complex128
+    _check(lib().lb_assemble(ctx.handle, d, _ptr(H, c128, "H", (d, d)), K,
+                             _ptr(Ls, c128, "Ls", (K, d, d)) if K else None,
+                             _ptr(L_out, c128, "L_out", (d * d, d * d)), _stream(stream)),
+           "lb_assemble")
+
+
+def lb_expm_pade(ctx, Lbase, Ldrv, u, dt, P_out, prec="fp64", s_out=None, stream=None):
+    """P_out[s] = exp((Lbase + u[s] Ldrv) dt); with Ldrv None, Lbase holds
+    one generator per slice."""
+    c128 = torch.complex128
+    S, n = P_out.shape[0], P_out.shape[1]
+    if Ldrv is None:
+        pb = _ptr(Lbase, c128, "Lbase", (S, n, n))
+        pd, pu = None, None
+    else:
+        pb = _ptr(Lbase, c128, "Lbase", (n, n))
+        pd = _ptr(Ldrv, c128, "Ldrv", (n, n))
+        pu = _ptr(u, torch.float64, "u", (S,))
+    ps = _ptr(s_out, torch.int32, "s_out", (S,), allow_none=True)
+    _check(lib().lb_expm_pade(ctx.handle, n, S, pb, pd, pu, float(dt), PRECISIONS.get(prec, prec),
+                              _ptr(P_out, c128, "P_out", (S, n, n)), ps, _stream(stream)),
+           "lb_expm_pade")
+
+
+def lb_propagate_batch(ctx, P, states, steps_per_slice=1, prec="fp64", renorm_trace=False, stream=None):
+    """states (B x n) <- chain of P[t // steps_per_slice] applied to every row."""
+    c128 = torch.complex128
+    S, n = P.shape[0], P.shape[1]
+    B = states.shape[0]
+    _check(lib().lb_propagate_batch(ctx.handle, n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
+                                    _ptr(states, c128, "states", (B, n)), PRECISIONS.get(prec, prec),
+                                    int(bool(renorm_trace)), _stream(stream)),
+           "lb_propagate_batch")
+
+
+def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelity_out, grad_out, stream=None):
+    """Fidelity and gradient of a piecewise-constant control."""
+    c128 = torch.complex128
+    n = Lbase.shape[0]
+    S = u.shape[0]
+    B = X0.shape[0]
+    _check(lib().lb_grape_grad(ctx.handle, n, S, _ptr(Lbase, c128, "Lbase", (n, n)),
+                               _ptr(Ldrv, c128, "Ldrv", (n, n)), _ptr(u, torch.float64, "u", (S,)), float(dt),
+                               int(steps_per_slice), B, _ptr(X0, c128, "X0", (B, n)),
+                               _ptr(Xtarget, c128, "Xtarget", (B, n)),
+                               _ptr(fidelity_out, torch.float64, "fidelity_out", (1,)),
+                               _ptr(grad_out, torch.float64, "grad_out", (S,)), _stream(stream)),
+           "lb_grape_grad")

@@ -1,0 +1,242 @@
+"""GPU vs oracle parity of assembly, propagator build and propagation.
+
+Every call goes through the C ABI (ctypes binding).  Tolerances: FP64 paths
+1e-12 relative Frobenius per result; FP32 propagation 1e-5 absolute Frobenius
+per state after 1000 steps; FP32 Pade products 1e-6 relative on P (see the
+comment at that test for the derivation)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import make_workload, transmon_chain
+from workloads.rng import normal
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2603_18052_gb300 import _build, lb
+
+    _build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lb
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+def _t(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def _rand_c(seed, shape):
+    z = normal(seed, 2 * int(np.prod(shape))).reshape(*shape, 2)
+    return z[..., 0] + 1j * z[..., 1]
+
+
+def _relf(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ assembly
+
+@pytest.mark.parametrize("d,K", [(1, 0), (2, 1), (3, 2), (5, 3), (9, 4), (27, 6)])
+def test_assemble_matches_oracle(lbm, dev, d, K):
+    ctx = lbm.Context(0, max_n=d * d, max_batch=1, max_slices=1)
+    Hr = _rand_c(300 + d, (d, d))
+    H = Hr + Hr.conj().T
+    Ls = _rand_c(400 + d, (K, d, d)) * 0.2 if K else None
+    out = torch.empty((d * d, d * d), dtype=torch.complex128, device=dev)
+    lbm.lb_assemble(ctx, _t(H, dev), _t(Ls, dev) if K else None, out)
+    lbm.lb_sync_status(ctx)
+    ref = O.lindbladian(H, [] if Ls is None else list(Ls))
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+
+
+# ------------------------------------------------------------------- build
+
+def _gen_pair(d, seed, scale):
+    """Random Lindblad generators (a base with jumps and a drive term)."""
+    Hr = _rand_c(seed, (d, d))
+    H = 0.5 * (Hr + Hr.conj().T)
+    jumps = list(_rand_c(seed + 1, (2, d, d)) * 0.3)
+    Xr = _rand_c(seed + 2, (d, d))
+    X = 0.5 * (Xr + Xr.conj().T)
+    Lb = O.lindbladian(H, jumps)
+    Ld = O.drive_generator(X)
+    f = scale / O.onenorm(Lb)
+    return Lb * f, Ld * f
+
+
+@pytest.mark.parametrize("d,S,scale", [(1, 3, 0.1), (2, 5, 0.2), (3, 4, 3.0), (5, 3, 0.9), (7, 2, 13.0),
+                                       (9, 3, 1.7)])
+def test_expm_fp64_matches_oracle(lbm, dev, d, S, scale):
+    """Sizes n = 1..81 cover the ragged LU blocks (n not a multiple of 32)
+    and squaring counts from 0 to 6."""
+    n = d * d
+    Lb, Ld = _gen_pair(d, 500 + d, scale)
+    u = np.linspace(-0.3, 0.4, S)
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=S)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    s_out = torch.empty(S, dtype=torch.int32, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(u, dev), 1.0, P, s_out=s_out)
+    lbm.lb_sync_status(ctx)
+    Pg = P.cpu().numpy()
+    sg = s_out.cpu().numpy()
+    for s in range(S):
+        ref, info = O.expm_pade13(Lb + u[s] * Ld, return_info=True)
+        assert sg[s] == info["s"]
+        assert _relf(Pg[s], ref) <= 1e-12, (s, _relf(Pg[s], ref))
+
+
+def test_expm_fp64_per_slice_generators_and_chunking(lbm, dev):
+    """Ldrv = NULL (one generator per slice) and more slices than the
+    context holds at once (processed in chunks)."""
+    d, S = 4, 7
+    n = d * d
+    gens = []
+    for s in range(S):
+        Lb, _ = _gen_pair(d, 600 + 3 * s, 0.2 + 0.5 * s)
+        gens.append(Lb)
+    gens = np.array(gens)
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=3)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(gens, dev), None, None, 0.5, P)
+    lbm.lb_sync_status(ctx)
+    Pg = P.cpu().numpy()
+    for s in range(S):
+        assert _relf(Pg[s], O.expm_pade13(gens[s] * 0.5)) <= 1e-12
+
+
+@pytest.mark.parametrize("name,S", [("d9_batch", 2), ("d27_chain", 2)])
+def test_expm_fp64_workloads(lbm, dev, name, S):
+    w = make_workload(name, nslices=S)
+    n = w["n"]
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=S)
+    Lbg = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    Ldg = torch.empty_like(Lbg)
+    lbm.lb_assemble(ctx, _t(w["H0"], dev), _t(w["jumps"], dev), Lbg)
+    lbm.lb_assemble(ctx, _t(w["X"], dev), None, Ldg)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, Lbg, Ldg, _t(w["u"], dev), w["dt"], P)
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
+    Pg = P.cpu().numpy()
+    for s in range(S):
+        assert _relf(Pg[s], ref[s]) <= 1e-12
+
+
+def test_expm_fp32_products(lbm, dev):
+    """FP32 Pade products, FP64 LU/solve/squarings.  Each product of
+    ||A||_1 <= 0.25 matrices carries a relative error of about
+    n * 2^-24 ~ 5e-6 on terms that enter V and U scaled by b_j ||A||^j <= 0.03,
+    so P is off by about 1e-7 relative; the test allows 1e-6."""
+    w = make_workload("d9_batch", nslices=3)
+    w["u"] = np.array([0.05, -0.08, 0.1])
+    n = w["n"]
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=3)
+    P = torch.empty((3, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(w["u"], dev), w["dt"], P, prec="fp32")
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
+    err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(3))
+    assert err <= 1e-6, err
+
+
+def test_expm_nonfinite_input_is_reported(lbm, dev):
+    n = 9
+    Lb = np.zeros((n, n), dtype=complex)
+    Lb[2, 3] = np.nan
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=1)
+    P = torch.empty((1, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb[None], dev), None, None, 0.1, P)
+    with pytest.raises(lbm.LBError) as ei:
+        lbm.lb_sync_status(ctx)
+    assert ei.value.name == "LB_ENONFINITE"
+    lbm.lb_sync_status(ctx)  # the word was cleared
+
+
+# ------------------------------------------------------------- propagation
+
+def _slice_props(w, u):
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    return O.slice_propagators(Lb, Ld, u, w["dt"])
+
+
+@pytest.mark.parametrize("name,B,S,m", [("d3_single", 1, 1, 200), ("d3_single", 5, 3, 4),
+                                        ("d9_batch", 37, 2, 3), ("d9_batch", 300, 1, 5)])
+def test_propagate_fp64_resident(lbm, dev, name, B, S, m):
+    w = make_workload(name, B=B)
+    u = np.linspace(-0.1, 0.1, S)
+    Ps = _slice_props(w, u)
+    ctx = lbm.Context(0, max_n=w["n"], max_batch=B, max_slices=S)
+    R = _t(w["states"], dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=m)
+    lbm.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, w["states"], m)
+    Rg = R.cpu().numpy()
+    for b in range(B):
+        assert _relf(Rg[b], ref[b]) <= 1e-12
+
+
+@pytest.mark.parametrize("B,S,m", [(256, 2, 1), (37, 1, 2)])
+def test_propagate_fp64_d27(lbm, dev, B, S, m):
+    w = make_workload("d27_chain", B=B, nslices=S)
+    Ps = _slice_props(w, w["u"])
+    ctx = lbm.Context(0, max_n=w["n"], max_batch=B, max_slices=S)
+    R = _t(w["states"], dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=m)
+    lbm.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, w["states"], m)
+    Rg = R.cpu().numpy()
+    for b in range(B):
+        assert _relf(Rg[b], ref[b]) <= 1e-12
+
+
+def test_propagate_fp32_d9_1000_steps(lbm, dev):
+    """The d = 9 batch: 1024 states, 1000 steps, FP32 with the per-step trace
+    renormalisation; max over states of ||rho - rho_ref||_F <= 1e-5."""
+    w = make_workload("d9_batch")
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate(Ps[0], w["states"], w["steps_per_slice"])
+    ctx = lbm.Context(0, max_n=w["n"], max_batch=w["B"], max_slices=1)
+    for renorm in (True, False):
+        R = _t(w["states"], dev)
+        lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=w["steps_per_slice"], prec="fp32",
+                               renorm_trace=renorm)
+        lbm.lb_sync_status(ctx)
+        err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
+        assert err <= 1e-5, (renorm, err)
+
+
+def test_propagate_fp32_d27(lbm, dev):
+    w = make_workload("d27_chain", B=64, nslices=3)
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate_chain(Ps, w["states"], 1)
+    ctx = lbm.Context(0, max_n=w["n"], max_batch=64, max_slices=3)
+    R = _t(w["states"], dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=1, prec="fp32", renorm_trace=True)
+    lbm.lb_sync_status(ctx)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
+    assert err <= 1e-6, err
+
+
+def test_zero_steps_and_slices_leave_states(lbm, dev):
+    w = make_workload("d3_single", B=3)
+    Ps = _slice_props(w, np.array([0.05]))
+    ctx = lbm.Context(0, max_n=9, max_batch=3, max_slices=1)
+    R = _t(w["states"], dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=0)
+    lbm.lb_sync_status(ctx)
+    assert np.array_equal(R.cpu().numpy(), w["states"])
