@@ -88,6 +88,28 @@ lb_status lb_sync_status(lb_ctx* ctx, void* stream);
 /* Bytes of device scratch owned by the context. */
 unsigned long long lb_workspace_bytes(const lb_ctx* ctx);
 
+/* Number of kernel launches the library has issued in this process (all
+ * contexts).  For accounting in benchmarks. */
+unsigned long long lb_launch_count(void);
+
+/*
+ * Stage timers of lb_expm_pade, following the stages of Algorithm 1 (the
+ * paper's build-time breakdown).  lb_set_stage_timing(ctx, 1) clears the
+ * totals and makes every later lb_expm_pade record CUDA events on its stream
+ * around each stage, without synchronising (a ring of 16 event sets; the
+ * host waits only when more than 16 chunks of slices are in flight).
+ * lb_stage_times waits for the recorded events and returns in ms_out (host,
+ * 5 doubles) the totals since the last lb_set_stage_timing call:
+ *   ms_out[0] generator, 1-norm, squaring count and scaling
+ *   ms_out[1] the six Pade products (three powers, V, W, U)
+ *   ms_out[2] LU factorisation and solve of (V - U) P = (V + U)
+ *   ms_out[3] squarings
+ *   ms_out[4] final non-finite check
+ * and in *chunks_out (may be NULL) the number of slice chunks timed.
+ */
+lb_status lb_set_stage_timing(lb_ctx* ctx, int enable);
+lb_status lb_stage_times(lb_ctx* ctx, double* ms_out, long long* chunks_out);
+
 /*
  * lb_assemble -- the vectorised Lindbladian of Eq. 1 under row-major vec
  * (Eq. 2-3):

@@ -332,11 +332,13 @@ inline unsigned grid_for(long long total, int threads, int sm_count) {
 cudaError_t launch_assemble(int d, const z64* H, int K, const z64* Ls, z64* L_out, z64* G_scratch,
                             int sm_count, cudaStream_t st) {
   if (K > 0) {
+    count_launch();
     gram_kernel<<<1, 256, 0, st>>>(d, K, Ls, G_scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   const long long nn = (long long)d * d * d * d;
+  count_launch();
   assemble_kernel<<<grid_for(nn, 256, sm_count), 256, 0, st>>>(d, H, K, Ls, G_scratch, L_out);
   return cudaGetLastError();
 }
@@ -350,13 +352,16 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
   e = cudaMemsetAsync(sc + S, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   dim3 g1((n + 127) / 128, S);
+  count_launch();
   colnorm_kernel<<<g1, 128, 0, st>>>(n, Lbase, Ldrv, u, dt, norm_bits);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  count_launch();
   squaring_count_kernel<<<(S + 127) / 128, 128, 0, st>>>(S, norm_bits, sc, s_out, sc + S, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long total = (long long)n * n * S;
+  count_launch();
   scale_kernel<<<grid_for(total, 256, sm_count), 256, 0, st>>>(n, S, Lbase, Ldrv, u, dt, sc, A);
   return cudaGetLastError();
 }
@@ -364,6 +369,7 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
 cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z64* X2, double c0,
                             double c1, double c2, z64* Z, cudaStream_t st) {
   const long long total = (long long)nn * S;
+  count_launch();
   lincomb3_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, X0, X1, X2, c0, c1, c2, Z);
   return cudaGetLastError();
 }
@@ -371,6 +377,7 @@ cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z
 cudaError_t launch_lu_diag(int n, int S, int k0, int kb, const z64* M, z64* Uf, z64* Linv,
                            long long sLinv, z64* Uinv, long long sUinv, unsigned int* err,
                            cudaStream_t st) {
+  count_launch();
   lu_diag_kernel<<<S, 256, 0, st>>>(n, k0, kb, M, Uf, Linv, sLinv, Uinv, sUinv, err);
   return cudaGetLastError();
 }
@@ -379,6 +386,7 @@ cudaError_t launch_copy_block(int S, long long ld, long long stride, int r0, int
                               const z64* src, z64* dst, cudaStream_t st) {
   const long long total = (long long)nr * nc * S;
   if (total == 0) return cudaSuccess;
+  count_launch();
   copy_block_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(S, ld, stride, r0, nr, c0, nc, src, dst);
   return cudaGetLastError();
 }
@@ -386,11 +394,13 @@ cudaError_t launch_copy_block(int S, long long ld, long long stride, int r0, int
 cudaError_t launch_copy_active(long long nn, int S, const z64* src, z64* dst, const int* active,
                                int iter, cudaStream_t st) {
   const long long total = nn * S;
+  count_launch();
   copy_active_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(nn, S, src, dst, active, iter);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_finite(long long count, const z64* x, unsigned int* err, cudaStream_t st) {
+  count_launch();
   check_finite_kernel<<<grid_for(count, 256, 152), 256, 0, st>>>(count, x, err);
   return cudaGetLastError();
 }

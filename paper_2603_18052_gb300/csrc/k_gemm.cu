@@ -235,6 +235,7 @@ cudaError_t launch_cfg(const ZGemmProblem* probs, int nprob, int sm_count, cudaS
     occ = std::max(1, o);
   }
   long long grid = std::min<long long>(acc, (long long)sm_count * occ);
+  count_launch();
   zgemm_kernel<T, BM, BN, TM, TN, GAUSS><<<(unsigned)grid, NT, 0, st>>>(g);
   return cudaGetLastError();
 }

@@ -340,6 +340,7 @@ cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int 
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (B + chunk - 1) / chunk;
+  count_launch();
   prop_resident_f64_kernel<<<grid, kResThreads, smem, st>>>(n, nslices, P, steps_per_slice, B, chunk,
                                                             states);
   return cudaGetLastError();
@@ -347,6 +348,7 @@ cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int 
 
 cudaError_t launch_make_delta_f32(int n, int S, const z64* P, float* Dr, float* Di, cudaStream_t st) {
   const long long total = (long long)n * n * S;
+  count_launch();
   make_delta_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(n, total, P, Dr, Di);
   return cudaGetLastError();
 }
@@ -365,6 +367,7 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (B + chunk - 1) / chunk;
+  count_launch();
   prop_resident_f32_kernel<<<grid, kResThreads, smem, st>>>(n, isqrt_exact(n), nslices, Dr, Di,
                                                             steps_per_slice, B, chunk, renorm, states);
   return cudaGetLastError();
@@ -372,6 +375,7 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
 
 cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, float* Ri, cudaStream_t st) {
   const long long total = (long long)n * B;
+  count_launch();
   states_to_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, states, Rr, Ri);
   return cudaGetLastError();
 }
@@ -379,6 +383,7 @@ cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, flo
 cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* Ri, z64* states,
                                    cudaStream_t st) {
   const long long total = (long long)n * B;
+  count_launch();
   states_from_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, Rr, Ri, states);
   return cudaGetLastError();
 }
@@ -387,6 +392,7 @@ cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, cons
                             const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st) {
   const int tiles = ((B + 63) / 64) * ((n + 63) / 64);
   const int grid = std::min(tiles, sm_count * 2);
+  count_launch();
   step_f32_kernel<<<grid, 256, 0, st>>>(n, B, Dr, Di, Rr, Ri, Or, Oi);
   return cudaGetLastError();
 }
@@ -395,6 +401,7 @@ cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t s
   const int d = isqrt_exact(n);
   const int threads = 256;
   const int grid = (B * 32 + threads - 1) / threads;
+  count_launch();
   renorm_f32_kernel<<<grid, threads, 0, st>>>(n, d, B, Rr, Ri);
   return cudaGetLastError();
 }

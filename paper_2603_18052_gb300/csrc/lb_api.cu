@@ -3,12 +3,18 @@
 // (Algorithm 2, batched as in Algorithm 3) and the GRAPE gradient (Sec. 2.5).
 #include "lb_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 
 using namespace lb;
+
+namespace lb {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace lb
 
 namespace {
 
@@ -39,6 +45,22 @@ void pade13(double* b) {
 }
 
 int nblocks(int n) { return (n + kLuNb - 1) / kLuNb; }
+
+// Fold the stage times of one ring slot into the totals (waits for its last event).
+cudaError_t accumulate_slot(lb_ctx* c, int r) {
+  if (!c->ring_used[r]) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(c->ev_stage[r][5]);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 5; i++) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, c->ev_stage[r][i], c->ev_stage[r][i + 1]);
+    if (e != cudaSuccess) return e;
+    c->stage_ms[i] += ms;
+  }
+  c->stage_chunks++;
+  c->ring_used[r] = 0;
+  return cudaSuccess;
+}
 
 bool is_square(int n, int* d_out) {
   int d = 1;
@@ -156,6 +178,14 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
     lb_destroy(c);
     return LB_ENOMEM;
   }
+  for (int r = 0; r < lb_ctx::kRing; r++)
+    for (int i = 0; i < 6; i++) {
+      if (cudaEventCreate(&c->ev_stage[r][i]) != cudaSuccess) {
+        cudaGetLastError();
+        lb_destroy(c);
+        return LB_ENOMEM;
+      }
+    }
   *out = c;
   return LB_OK;
 }
@@ -164,6 +194,9 @@ lb_status lb_destroy(lb_ctx* c) {
   if (c == nullptr) return LB_OK;
   DeviceGuard g(c->device);
   if (c->ev_scmax) cudaEventDestroy(c->ev_scmax);
+  for (int r = 0; r < lb_ctx::kRing; r++)
+    for (int i = 0; i < 6; i++)
+      if (c->ev_stage[r][i]) cudaEventDestroy(c->ev_stage[r][i]);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->scmax_host) cudaFreeHost(c->scmax_host);
   if (c->ws) cudaFree(c->ws);
@@ -172,6 +205,29 @@ lb_status lb_destroy(lb_ctx* c) {
 }
 
 unsigned long long lb_workspace_bytes(const lb_ctx* c) { return c ? (unsigned long long)c->ws_bytes : 0ull; }
+
+unsigned long long lb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+lb_status lb_set_stage_timing(lb_ctx* c, int enable) {
+  if (c == nullptr) return LB_EINVAL;
+  DeviceGuard g(c->device);
+  for (int r = 0; r < lb_ctx::kRing; r++)
+    if (accumulate_slot(c, r) != cudaSuccess) return LB_ECUDA;
+  c->timing = enable ? 1 : 0;
+  for (int i = 0; i < 5; i++) c->stage_ms[i] = 0.0;
+  c->stage_chunks = 0;
+  return LB_OK;
+}
+
+lb_status lb_stage_times(lb_ctx* c, double* ms_out, long long* chunks_out) {
+  if (c == nullptr || ms_out == nullptr) return LB_EINVAL;
+  DeviceGuard g(c->device);
+  for (int r = 0; r < lb_ctx::kRing; r++)
+    if (accumulate_slot(c, r) != cudaSuccess) return LB_ECUDA;
+  for (int i = 0; i < 5; i++) ms_out[i] = c->stage_ms[i];
+  if (chunks_out) *chunks_out = c->stage_chunks;
+  return LB_OK;
+}
 
 lb_status lb_sync_status(lb_ctx* c, void* stream) {
   if (c == nullptr) return LB_EINVAL;
@@ -314,10 +370,20 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   const long long nn = (long long)n * n;
   const double* b = c->pade_b;
   gemm_fn gemm = (prec == LB_FP64) ? zgemm_f64 : zgemm_f32;
+  cudaEvent_t* ev = nullptr;
+  if (c->timing) {
+    const int r = c->ring_next;
+    c->ring_next = (r + 1) % lb_ctx::kRing;
+    LB_CUDA(accumulate_slot(c, r));  // only waits if the ring has wrapped
+    ev = c->ev_stage[r];
+    c->ring_used[r] = 1;
+    LB_CUDA(cudaEventRecord(ev[0], st));
+  }
   LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, s_out, c->err_dev,
                                c->sm_count, st));
   LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
   LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+  if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
   // three power products
   ZGemmProblem p = sq(n, S, c->A, c->A, c->A2);
   LB_CUDA(gemm(&p, 1, c->sm_count, st));
@@ -349,9 +415,11 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   p.X[0] = c->V; p.sX[0] = nn; p.coef[0] = 1.0;
   p.C2 = P; p.X2 = c->V; p.sX2 = nn; p.alpha2 = 1.0;
   LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
   // (V - U) P = (V + U), FP64.  Uf, Y, Lp reuse A2, A4, A6.
   lb_status s = lu_solve_blocked(c, n, S, c->Mx, P, c->A2, c->A4, c->A6, st);
   if (s != LB_OK) return s;
+  if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
   // squarings, FP64.  The count is known on the host once the event that
   // follows the norm kernel has completed (long before the LU finishes).
   LB_CUDA(cudaEventSynchronize(c->ev_scmax));
@@ -363,7 +431,9 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
     LB_CUDA(zgemm_f64(&q, 1, c->sm_count, st));
     LB_CUDA(launch_copy_active(nn, S, c->Z1, P, c->sc, it, st));
   }
+  if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
   LB_CUDA(launch_check_finite(nn * S, P, c->err_dev, st));
+  if (ev) LB_CUDA(cudaEventRecord(ev[5], st));
   return LB_OK;
 }
 

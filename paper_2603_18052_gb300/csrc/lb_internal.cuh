@@ -34,6 +34,9 @@ struct Arena {
   }
 };
 
+// Process-wide count of kernel launches issued by the library.
+void count_launch();
+
 }  // namespace lb
 
 struct lb_ctx {
@@ -47,6 +50,14 @@ struct lb_ctx {
   int* scmax_host = nullptr;        // pinned: largest squaring count of the last build
   cudaEvent_t ev_scmax = nullptr;
   double pade_b[14];
+  // --- stage timers of lb_expm_pade (CUDA events in a ring, optional) ---
+  int timing = 0;
+  static constexpr int kRing = 16;
+  cudaEvent_t ev_stage[kRing][6] = {};
+  int ring_used[kRing] = {};  // slot holds events not yet accumulated
+  int ring_next = 0;
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  long long stage_chunks = 0;
   // --- propagator build, per slice (stride max_n^2 complex) ---
   lb::z64 *A = nullptr, *A2 = nullptr, *A4 = nullptr, *A6 = nullptr, *Z1 = nullptr, *Z2 = nullptr;
   lb::z64 *V = nullptr, *W = nullptr, *Mx = nullptr;

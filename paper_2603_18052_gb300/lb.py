@@ -36,6 +36,9 @@ EXPORTED = (
     "lb_destroy",
     "lb_sync_status",
     "lb_workspace_bytes",
+    "lb_launch_count",
+    "lb_set_stage_timing",
+    "lb_stage_times",
     "lb_assemble",
     "lb_expm_pade",
     "lb_propagate_batch",
@@ -79,6 +82,12 @@ def lib():
     L.lb_sync_status.argtypes = [vp, vp]
     L.lb_workspace_bytes.restype = ctypes.c_ulonglong
     L.lb_workspace_bytes.argtypes = [vp]
+    L.lb_launch_count.restype = ctypes.c_ulonglong
+    L.lb_launch_count.argtypes = []
+    L.lb_set_stage_timing.restype = i32
+    L.lb_set_stage_timing.argtypes = [vp, i32]
+    L.lb_stage_times.restype = i32
+    L.lb_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     L.lb_assemble.restype = i32
     L.lb_assemble.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     L.lb_expm_pade.restype = i32
@@ -145,6 +154,29 @@ class Context:
     @property
     def workspace_bytes(self):
         return int(lib().lb_workspace_bytes(self.handle))
+
+
+def lb_launch_count():
+    """Kernel launches issued by the library so far in this process."""
+    return int(lib().lb_launch_count())
+
+
+def lb_set_stage_timing(ctx, enable=True):
+    """Clear the stage totals and switch the per-stage CUDA events of
+    lb_expm_pade on or off."""
+    _check(lib().lb_set_stage_timing(ctx.handle, int(bool(enable))), "lb_set_stage_timing")
+
+
+STAGES = ("prepare", "pade_products", "lu_solve", "squarings", "check")
+
+
+def lb_stage_times(ctx):
+    """Stage totals (ms) since the last lb_set_stage_timing, and the number
+    of slice chunks they cover."""
+    out = (ctypes.c_double * 5)()
+    chunks = ctypes.c_longlong(0)
+    _check(lib().lb_stage_times(ctx.handle, out, ctypes.byref(chunks)), "lb_stage_times")
+    return dict(zip(STAGES, list(out))), int(chunks.value)
 
 
 def lb_sync_status(ctx, stream=None):
