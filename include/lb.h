@@ -188,6 +188,30 @@ lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, co
                         const lb_c64* Xtarget, double* fidelity_out, double* grad_out,
                         void* stream);
 
+/*
+ * lb_propagate_batch_static -- the FP64 form of lb_propagate_batch for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this exists for applications whose device memory is already owned by their
+ * own allocator, and for loops that must not risk the device-wide
+ * synchronisation and unbounded latency of cudaMalloc.  It needs no lb_ctx,
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call),
+ * and runs on the CURRENT CUDA device, which must hold P and states.
+ *   Same arguments and results as lb_propagate_batch with prec = LB_FP64:
+ *   step t uses P[t / steps_per_slice]; states (B x n) are overwritten.
+ *   Limit: B * n <= 262144 (4 MiB of complex128); larger requests return
+ *   LB_EUNSUPPORTED before any work is queued.
+ *   The intermediate states live in one 4 MiB array in device memory that
+ *   the library reserves on every GPU where its device code is loaded, kept
+ *   until the process exits.  All calls share it: two calls running on the
+ *   GPU at the same time (different streams or threads) race and must be
+ *   serialised by the caller.  Nothing in it needs clearing between calls.
+ *   The first call on each device looks up the array's device address (which
+ *   can load the library's device code on that device); make that first call
+ *   before any stream capture.
+ */
+lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64* P, int steps_per_slice, int B,
+                                    lb_c64* states, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,7 @@ EXPORTED = (
     "lb_expm_pade",
     "lb_propagate_batch",
     "lb_grape_grad",
+    "lb_propagate_batch_static",
 )
 
 
@@ -94,6 +95,8 @@ def lib():
     L.lb_expm_pade.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, vp, vp]
     L.lb_propagate_batch.restype = i32
     L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
+    L.lb_propagate_batch_static.restype = i32
+    L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
     del ip, dp
@@ -238,3 +241,15 @@ def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelit
                                _ptr(fidelity_out, torch.float64, "fidelity_out", (1,)),
                                _ptr(grad_out, torch.float64, "grad_out", (S,)), _stream(stream)),
            "lb_grape_grad")
+
+
+def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
+    """FP64 propagation with no context and no device allocation (the
+    intermediate states use a 4 MiB array reserved by the library; calls
+    must not overlap on the GPU).  Runs on the current CUDA device."""
+    c128 = torch.complex128
+    S, n = P.shape[0], P.shape[1]
+    B = states.shape[0]
+    _check(lib().lb_propagate_batch_static(n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
+                                           _ptr(states, c128, "states", (B, n)), _stream(stream)),
+           "lb_propagate_batch_static")
