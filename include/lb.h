@@ -181,7 +181,11 @@ lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, i
  *   squarings.  All FP64.
  *   X0, Xtarget : B x n
  *   fidelity_out: 1 double (device); grad_out: nslices doubles (device)
- * Limits: n <= 81 (d <= 9), nslices <= max_slices, B <= max_batch.
+ * Limits: the context must have been created with max_n <= 81 (its GRAPE
+ * scratch is sized then); n <= max_n; B <= min(max_batch, 64);
+ * nslices <= max_slices; steps_per_slice <= 20.  Other sizes return
+ * LB_EUNSUPPORTED.  The call waits on the host for the small copy of the
+ * largest squaring count (made right after the norm kernel).
  */
 lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
                         const double* u, double dt, int steps_per_slice, int B, const lb_c64* X0,

@@ -124,8 +124,9 @@ __global__ void colnorm_kernel(int n, const z64* __restrict__ Lb, const z64* __r
 // sc = max(0, ceil(log2(norm / theta))), theta = 0.25.  Non-finite norms
 // set the error word and use sc = 0.
 __global__ void squaring_count_kernel(int S, const unsigned long long* __restrict__ norm_bits,
-                                      int* __restrict__ sc, int* __restrict__ s_out,
-                                      int* __restrict__ sc_max, unsigned int* err) {
+                                      int* __restrict__ sc, int* __restrict__ kmix,
+                                      int* __restrict__ s_out, int* __restrict__ sc_max,
+                                      unsigned int* err) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const double nrm = __longlong_as_double((long long)norm_bits[s]);
@@ -140,6 +141,14 @@ __global__ void squaring_count_kernel(int S, const unsigned long long* __restric
     if (k > 1000) k = 1000;
   }
   sc[s] = k;
+  if (kmix != nullptr) {
+    // squaring j acts on P = exp(A 2^j / 2^k); keep the D-form while
+    // ||A||_1 2^(j-k) <= 1, i.e. while ||P - I|| stays of order ||A||
+    int m = 0;
+    if (isfinite(nrm))
+      while (m < k && ldexp(nrm, m - k) <= 1.0) m++;
+    kmix[s] = m;
+  }
   if (s_out != nullptr) s_out[s] = k;
   atomicMax(sc_max, k);
 }
@@ -345,7 +354,8 @@ cudaError_t launch_assemble(int d, const z64* H, int K, const z64* Ls, z64* L_ou
 
 cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
                                  double dt, z64* A, unsigned long long* norm_bits, int* sc,
-                                 int* s_out, unsigned int* err, int sm_count, cudaStream_t st) {
+                                 int* kmix, int* s_out, unsigned int* err, int sm_count,
+                                 cudaStream_t st) {
   // norm_bits[0..S) and sc_max (stored right after sc[S]) must start at zero
   cudaError_t e = cudaMemsetAsync(norm_bits, 0, sizeof(unsigned long long) * S, st);
   if (e != cudaSuccess) return e;
@@ -357,7 +367,7 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launch();
-  squaring_count_kernel<<<(S + 127) / 128, 128, 0, st>>>(S, norm_bits, sc, s_out, sc + S, err);
+  squaring_count_kernel<<<(S + 127) / 128, 128, 0, st>>>(S, norm_bits, sc, kmix, s_out, sc + S, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long total = (long long)n * n * S;

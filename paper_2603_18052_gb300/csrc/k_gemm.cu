@@ -67,6 +67,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const int tm = r / g.tiles_n[pi];
     const int tn = r - tm * g.tiles_n[pi];
     if (P.active != nullptr && P.active[b] <= P.active_iter) continue;
+    if (P.active_lo != nullptr && P.active_lo[b] > P.active_iter) continue;
     const int m0 = tm * BM, n0 = tn * BN;
     const z64* __restrict__ A = P.A + b * P.sA;
     const z64* __restrict__ B = P.B + b * P.sB;
@@ -92,7 +93,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int m = e / BK, k = e - (e / BK) * BK;
         const int gm = m0 + m, gk = k0 + k;
         z64 v = make_double2(0.0, 0.0);
-        if (gm < M && gk < K) v = A[(long long)gm * P.lda + gk];
+        if (gm < M && gk < K) {
+          v = A[(long long)gm * P.lda + gk];
+          if (gm == gk) v.x -= P.shiftA;
+        }
         const T re = T(v.x), im = T(asign * v.y);
         As[0][k][m] = re;
         As[1][k][m] = im;
@@ -104,7 +108,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
           const int k = e / BN, nn = e - (e / BN) * BN;
           const int gk = k0 + k, gn = n0 + nn;
           z64 v = make_double2(0.0, 0.0);
-          if (gk < K && gn < N) v = B[(long long)gk * P.ldb + gn];
+          if (gk < K && gn < N) {
+            v = B[(long long)gk * P.ldb + gn];
+            if (gk == gn) v.x -= P.shiftB;
+          }
           const T re = T(v.x), im = T(bsign * v.y);
           Bs[0][k][nn] = re;
           Bs[1][k][nn] = im;
@@ -115,7 +122,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
           const int nn = e / BK, k = e - (e / BK) * BK;
           const int gk = k0 + k, gn = n0 + nn;
           z64 v = make_double2(0.0, 0.0);
-          if (gk < K && gn < N) v = B[(long long)gn * P.ldb + gk];
+          if (gk < K && gn < N) {
+            v = B[(long long)gn * P.ldb + gk];
+            if (gk == gn) v.x -= P.shiftB;
+          }
           const T re = T(v.x), im = T(bsign * v.y);
           Bs[0][k][nn] = re;
           Bs[1][k][nn] = im;

@@ -1,0 +1,300 @@
+// GRAPE landscape point: fidelity of a piecewise-constant control and its
+// gradient (Sec. 2.5; the segment generator of Eq. 5; one Pade-13 build per
+// segment, Algorithm 1, applied steps_per_slice times, Algorithm 2).
+//
+//   P_s  = exp(A_s),  A_s = (Lbase + u_s Ldrv) dt
+//   dP_s = Frechet derivative of exp at A_s in the direction E = Ldrv dt,
+//          obtained by differentiating every step of the Pade build:
+//          M2 = A E + E A, M4 = A2 M2 + M2 A2, M6 = A4 M2 + M4 A2,
+//          dV and dW' from the same linear combinations as V and W',
+//          dU = E W' + A dW', then, with the same LU of V - U,
+//          dR = (V-U)^{-1}(dV + dU) - (V-U)^{-1}(dV - dU) R, and through each
+//          squaring dR <- R dR + dR R, R <- R R (all on the scaled A, E).
+//   forward chain X_t = P X_{t-1}, adjoint chain Lam_{t-1} = P^+ Lam_t,
+//   F = Re sum <Xt, X_T> / B,  g_s = sum_{t in s} Re <Lam_t, dP_s X_{t-1}> / B.
+// The gradient of slice s is a GEMM of the stacked states of its steps with
+// dP_s^T followed by a deterministic reduction.  All FP64.
+#include "lb_internal.cuh"
+
+#include <algorithm>
+
+namespace lb {
+
+namespace {
+
+__global__ void combine_kernel(int n, long long total, double c0, const z64* __restrict__ X0, long long ld0,
+                               long long s0, double c1, const z64* __restrict__ X1, long long ld1,
+                               long long s1, z64* __restrict__ dst, long long ldd, long long sd) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / nn;
+    const long long o = e - s * nn;
+    const long long i = o / n, j = o - (o / n) * n;
+    const z64 a = X0[s * s0 + i * ld0 + j];
+    z64 r = make_double2(c0 * a.x, c0 * a.y);
+    if (X1 != nullptr) {
+      const z64 b = X1[s * s1 + i * ld1 + j];
+      r.x = fma(c1, b.x, r.x);
+      r.y = fma(c1, b.y, r.y);
+    }
+    dst[s * sd + i * ldd + j] = r;
+  }
+}
+
+__global__ void scale_bcast_kernel(int n, long long total, const z64* __restrict__ Ld, double dt,
+                                   const int* __restrict__ sc, z64* __restrict__ E) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / nn);
+    const z64 v = Ld[e - s * nn];
+    E[e] = make_double2(ldexp(v.x * dt, -sc[s]), ldexp(v.y * dt, -sc[s]));
+  }
+}
+
+// One CTA per slice; fixed-order tree reduction (deterministic).
+__global__ void __launch_bounds__(256) redot_kernel(long long len, const z64* __restrict__ L, long long sL,
+                                                    const z64* __restrict__ Y, long long sY, double scale,
+                                                    double* __restrict__ out) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < len; e += blockDim.x) {
+    const z64 a = L[s * sL + e], b = Y[s * sY + e];
+    acc = fma(a.x, b.x, fma(a.y, b.y, acc));  // Re(conj(a) b)
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[s] = red[0] * scale;
+}
+
+unsigned grid_for(long long total) {
+  long long g = (total + 255) / 256;
+  return (unsigned)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
+}
+
+struct GrapeWs {
+  z64 *E, *M2, *M4, *M6, *dZ1, *dZ2, *dV, *dW, *R, *dR, *T1, *T2, *RHS, *Y3, *Xh, *Lh, *Yg, *S0, *S1;
+};
+
+size_t hist_elems(int nG, int Bg, int S) {
+  return ((size_t)S * kGrapeMaxStepsPerSlice + 1) * Bg * nG;
+}
+
+GrapeWs carve(lb_ctx* c) {
+  const int nG = std::min(c->max_n, kGrapeMaxN);
+  const size_t nn = (size_t)nG * nG, S = c->max_slices;
+  const int Bg = std::min(c->max_batch, kGrapeMaxB);
+  z64* p = c->grape;
+  auto take = [&](size_t e) {
+    z64* r = p;
+    p += (e + 15) & ~size_t(15);
+    return r;
+  };
+  GrapeWs w;
+  w.E = take(nn * S); w.M2 = take(nn * S); w.M4 = take(nn * S); w.M6 = take(nn * S);
+  w.dZ1 = take(nn * S); w.dZ2 = take(nn * S); w.dV = take(nn * S); w.dW = take(nn * S);
+  w.R = take(nn * S); w.dR = take(nn * S); w.T1 = take(nn * S); w.T2 = take(nn * S);
+  w.RHS = take(3 * nn * S); w.Y3 = take(3 * nn * S);
+  const size_t h = hist_elems(nG, Bg, (int)S);
+  w.Xh = take(h); w.Lh = take(h); w.Yg = take(h);
+  w.S0 = take((size_t)Bg * nG); w.S1 = take((size_t)Bg * nG);
+  return w;
+}
+
+}  // namespace
+
+size_t grape_ws_bytes(int max_n, int max_batch, int max_slices) {
+  if (max_n > kGrapeMaxN) return 256;
+  const size_t nn = (size_t)max_n * max_n, S = max_slices;
+  const int Bg = std::min(max_batch, kGrapeMaxB);
+  const size_t elems = 18 * nn * S + 3 * hist_elems(max_n, Bg, max_slices) + 2 * (size_t)Bg * max_n + 16 * 24;
+  return elems * sizeof(z64);
+}
+
+cudaError_t launch_combine(int n, int S, double c0, const z64* X0, long long ld0, long long s0, double c1,
+                           const z64* X1, long long ld1, long long s1, z64* dst, long long ldd, long long sd,
+                           cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  combine_kernel<<<grid_for(total), 256, 0, st>>>(n, total, c0, X0, ld0, s0, c1, X1, ld1, s1, dst, ldd, sd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_bcast(int n, int S, const z64* Ldrv, double dt, const int* sc, z64* E, cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  scale_bcast_kernel<<<grid_for(total), 256, 0, st>>>(n, total, Ldrv, dt, sc, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_redot(int S, long long len, const z64* L, long long sL, const z64* Y, long long sY,
+                         double scale, double* out, cudaStream_t st) {
+  count_launch();
+  redot_kernel<<<S, 256, 0, st>>>(len, L, sL, Y, sY, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lb
+
+using namespace lb;
+
+#define LB_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return LB_ECUDA; \
+  } while (0)
+
+extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                                   const double* u, double dt, int steps_per_slice, int B, const lb_c64* X0,
+                                   const lb_c64* Xtarget, double* fidelity_out, double* grad_out,
+                                   void* stream) {
+  if (c == nullptr || Lbase == nullptr || Ldrv == nullptr || u == nullptr || X0 == nullptr ||
+      Xtarget == nullptr || fidelity_out == nullptr || grad_out == nullptr)
+    return LB_EINVAL;
+  if (n < 1 || n > c->max_n || nslices < 1 || steps_per_slice < 1 || B < 1 || B > c->max_batch) return LB_EINVAL;
+  int d = 1;
+  while (d * d < n) d++;
+  if (d * d != n) return LB_EINVAL;
+  if (c->max_n > kGrapeMaxN || n > kGrapeMaxN || B > kGrapeMaxB || nslices > c->max_slices ||
+      steps_per_slice > kGrapeMaxStepsPerSlice)
+    return LB_EUNSUPPORTED;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = nslices, m = steps_per_slice;
+  const long long nn = (long long)n * n;
+  const double* b = c->pade_b;
+  GrapeWs w = carve(c);
+  const z64* Lb = (const z64*)Lbase;
+  const z64* Ld = (const z64*)Ldrv;
+
+  lb_status rs = [&]() -> lb_status {
+    // scaled A and E, s per slice
+    LB_CUDA(launch_slice_prepare(n, S, Lb, Ld, u, dt, c->A, c->norm_bits, c->sc, nullptr, nullptr, c->err_dev,
+                                 c->sm_count, st));
+    LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+    LB_CUDA(launch_scale_bcast(n, S, Ld, dt, c->sc, w.E, st));
+    // powers and their derivatives
+    ZGemmProblem p = sq(n, S, c->A, c->A, c->A2);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A, w.E, w.M2);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, w.E, c->A, w.M2);
+    p.beta = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A2, c->A2, c->A4);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A2, w.M2, w.M4);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, w.M2, c->A2, w.M4);
+    p.beta = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A4, c->A2, c->A6);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A4, w.M2, w.M6);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, w.M4, c->A2, w.M6);
+    p.beta = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[12], b[10], b[8], c->Z1, st));
+    LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[13], b[11], b[9], c->Z2, st));
+    LB_CUDA(launch_lincomb3((int)nn, S, w.M6, w.M4, w.M2, b[12], b[10], b[8], w.dZ1, st));
+    LB_CUDA(launch_lincomb3((int)nn, S, w.M6, w.M4, w.M2, b[13], b[11], b[9], w.dZ2, st));
+    // V, W' and dV, dW'
+    auto with3 = [&](ZGemmProblem q, const z64* x0, const z64* x1, const z64* x2, double c0, double c1, double c2,
+                     double gamma) {
+      q.nterms = 3;
+      q.X[0] = x0; q.X[1] = x1; q.X[2] = x2;
+      q.sX[0] = q.sX[1] = q.sX[2] = nn;
+      q.coef[0] = c0; q.coef[1] = c1; q.coef[2] = c2;
+      q.gamma = gamma;
+      return q;
+    };
+    ZGemmProblem g4[4];
+    g4[0] = with3(sq(n, S, c->A6, c->Z1, c->V), c->A6, c->A4, c->A2, b[6], b[4], b[2], b[0]);
+    g4[1] = with3(sq(n, S, c->A6, c->Z2, c->W), c->A6, c->A4, c->A2, b[7], b[5], b[3], b[1]);
+    g4[2] = with3(sq(n, S, c->A6, w.dZ1, w.dV), w.M6, w.M4, w.M2, b[6], b[4], b[2], 0.0);
+    g4[3] = with3(sq(n, S, c->A6, w.dZ2, w.dW), w.M6, w.M4, w.M2, b[7], b[5], b[3], 0.0);
+    LB_CUDA(zgemm_f64(g4, 4, c->sm_count, st));
+    ZGemmProblem g2[2];
+    g2[0] = sq(n, S, w.M6, c->Z1, w.dV);
+    g2[0].beta = 1.0;
+    g2[1] = sq(n, S, w.M6, c->Z2, w.dW);
+    g2[1].beta = 1.0;
+    LB_CUDA(zgemm_f64(g2, 2, c->sm_count, st));
+    // Mx = V - A W' ;  dU = E W' + A dW' (in T1)
+    p = sq(n, S, c->A, c->W, c->Mx);
+    p.alpha = -1.0;
+    p.nterms = 1;
+    p.X[0] = c->V; p.sX[0] = nn; p.coef[0] = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, w.E, c->W, w.T1);
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    p = sq(n, S, c->A, w.dW, w.T1);
+    p.beta = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    // RHS = [V + U | dV + dU | dV - dU]  (n x 3n per slice), V + U = 2V - Mx
+    const long long ld3 = 3LL * n, s3 = 3 * nn;
+    LB_CUDA(launch_combine(n, S, 2.0, c->V, n, nn, -1.0, c->Mx, n, nn, w.RHS, ld3, s3, st));
+    LB_CUDA(launch_combine(n, S, 1.0, w.dV, n, nn, 1.0, w.T1, n, nn, w.RHS + n, ld3, s3, st));
+    LB_CUDA(launch_combine(n, S, 1.0, w.dV, n, nn, -1.0, w.T1, n, nn, w.RHS + 2 * n, ld3, s3, st));
+    lb_status ls = lu_solve_blocked(c, n, S, c->Mx, w.RHS, 3 * n, ld3, s3, c->A2, w.Y3, c->A4, st);
+    if (ls != LB_OK) return ls;
+    // R = RHS[:, 0:n];  dR = RHS[:, n:2n] - RHS[:, 2n:3n] R
+    LB_CUDA(launch_combine(n, S, 1.0, w.RHS, ld3, s3, 0.0, nullptr, 0, 0, w.R, n, nn, st));
+    LB_CUDA(launch_combine(n, S, 1.0, w.RHS + n, ld3, s3, 0.0, nullptr, 0, 0, w.T2, n, nn, st));
+    p = sq(n, S, w.RHS + 2 * n, w.R, w.dR);
+    p.lda = ld3; p.sA = s3;
+    p.alpha = -1.0;
+    p.nterms = 1;
+    p.X[0] = w.T2; p.sX[0] = nn; p.coef[0] = 1.0;
+    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    // squarings with their derivative
+    LB_CUDA(cudaEventSynchronize(c->ev_scmax));
+    const int smax = *c->scmax_host;
+    for (int it = 0; it < smax; it++) {
+      ZGemmProblem q[2];
+      q[0] = sq(n, S, w.R, w.dR, w.T1);
+      q[1] = sq(n, S, w.R, w.R, w.T2);
+      q[0].active = q[1].active = c->sc;
+      q[0].active_iter = q[1].active_iter = it;
+      LB_CUDA(zgemm_f64(q, 2, c->sm_count, st));
+      ZGemmProblem q2 = sq(n, S, w.dR, w.R, w.T1);
+      q2.beta = 1.0;
+      q2.active = c->sc;
+      q2.active_iter = it;
+      LB_CUDA(zgemm_f64(&q2, 1, c->sm_count, st));
+      LB_CUDA(launch_copy_active(nn, S, w.T1, w.dR, c->sc, it, st));
+      LB_CUDA(launch_copy_active(nn, S, w.T2, w.R, c->sc, it, st));
+    }
+    // forward and adjoint chains with history
+    const long long T = (long long)S * m;
+    const long long bn = (long long)B * n;
+    LB_CUDA(cudaMemcpyAsync(w.S0, X0, sizeof(z64) * bn, cudaMemcpyDeviceToDevice, st));
+    LB_CUDA(launch_propagate_resident_f64_hist(n, S, w.R, m, B, w.S0, 0, w.Xh, c->sm_count, st));
+    LB_CUDA(cudaMemcpyAsync(w.S1, Xtarget, sizeof(z64) * bn, cudaMemcpyDeviceToDevice, st));
+    LB_CUDA(launch_propagate_resident_f64_hist(n, S, w.R, m, B, w.S1, 1, w.Lh, c->sm_count, st));
+    // Yg[s] = (stacked X_{t-1}, t in slice s) dP_s^T
+    ZGemmProblem y;
+    y.M = (int)(m * B); y.N = n; y.K = n;
+    y.A = w.Xh; y.lda = n; y.sA = m * bn;
+    y.B = w.dR; y.ldb = n; y.sB = nn; y.opB = 1;
+    y.C = w.Yg; y.ldc = n; y.sC = m * bn;
+    y.batch = S;
+    LB_CUDA(zgemm_f64(&y, 1, c->sm_count, st));
+    // g_s = Re <Lam block of slice s, Yg[s]> / B ;  F = Re <Xt, X_T> / B
+    LB_CUDA(launch_redot(S, m * bn, w.Lh + bn, m * bn, w.Yg, m * bn, 1.0 / B, grad_out, st));
+    LB_CUDA(launch_redot(1, bn, (const z64*)Xtarget, 0, w.Xh + T * bn, 0, 1.0 / B, fidelity_out, st));
+    return LB_OK;
+  }();
+  if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+  return rs;
+}

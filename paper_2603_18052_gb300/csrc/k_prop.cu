@@ -29,9 +29,12 @@ size_t resident_f32_smem(int n, int chunk) {
   return sizeof(float) * (2ull * n * n + 4ull * chunk * n) + sizeof(float) * 2 * chunk;
 }
 
+// adjoint: apply P^+ (load conj(P[j][i]) as row i) with the slices in reverse
+// order.  hist (optional): the states before the first step and after every
+// step, indexed t = 0..T forward or T - k after k adjoint steps.
 __global__ void __launch_bounds__(kResThreads)
     prop_resident_f64_kernel(int n, int nslices, const z64* __restrict__ P, int steps_per_slice, int B,
-                             int chunk, z64* __restrict__ states) {
+                             int chunk, z64* __restrict__ states, int adjoint, z64* __restrict__ hist) {
   extern __shared__ __align__(16) double sm[];
   double* Pr = sm;
   double* Pi = Pr + n * n;
@@ -53,10 +56,23 @@ __global__ void __launch_bounds__(kResThreads)
     xs[e] = v.x + v.y;
   }
   const int work = nb * n;
-  for (int s = 0; s < nslices; s++) {
+  const long long T = (long long)nslices * steps_per_slice;
+  long long hidx = adjoint ? T : 0;
+  if (hist != nullptr)
+    for (int e = tid; e < work; e += blockDim.x)
+      hist[(hidx * B + b0) * n + e] = states[(long long)b0 * n + e];
+  for (int si = 0; si < nslices; si++) {
+    const int s = adjoint ? nslices - 1 - si : si;
     __syncthreads();
     for (int e = tid; e < n * n; e += blockDim.x) {
-      const z64 v = P[s * nn + e];
+      z64 v;
+      if (adjoint) {
+        const int i = e / n, j = e - (e / n) * n;
+        v = P[s * nn + (long long)j * n + i];
+        v.y = -v.y;
+      } else {
+        v = P[s * nn + e];
+      }
       Pr[e] = v.x;
       Pi[e] = v.y;
       Ps[e] = v.x + v.y;
@@ -82,11 +98,13 @@ __global__ void __launch_bounds__(kResThreads)
         yi[e] = a3 - a1 - a2;
       }
       __syncthreads();
+      hidx += adjoint ? -1 : 1;
       for (int e = tid; e < work; e += blockDim.x) {
         const double r = yr[e], im = yi[e];
         xr[e] = r;
         xi[e] = im;
         xs[e] = r + im;
+        if (hist != nullptr) hist[(hidx * B + b0) * n + e] = make_double2(r, im);
       }
       __syncthreads();
     }
@@ -329,6 +347,12 @@ bool resident_f32_fits(int n) { return n <= 81; }
 
 cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int steps_per_slice, int B,
                                           z64* states, int sm_count, cudaStream_t st) {
+  return launch_propagate_resident_f64_hist(n, nslices, P, steps_per_slice, B, states, 0, nullptr, sm_count, st);
+}
+
+cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P, int steps_per_slice, int B,
+                                               z64* states, int adjoint, z64* hist, int sm_count,
+                                               cudaStream_t st) {
   int chunk = pick_chunk(B, sm_count);
   size_t smem = resident_f64_smem(n, chunk);
   while (smem > 227 * 1024 && chunk > 1) {
@@ -342,7 +366,7 @@ cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int 
   const int grid = (B + chunk - 1) / chunk;
   count_launch();
   prop_resident_f64_kernel<<<grid, kResThreads, smem, st>>>(n, nslices, P, steps_per_slice, B, chunk,
-                                                            states);
+                                                            states, adjoint, hist);
   return cudaGetLastError();
 }
 

@@ -69,8 +69,6 @@ bool is_square(int n, int* d_out) {
   return d * d == n;
 }
 
-size_t grape_ws_bytes(int max_n, int max_batch, int max_slices);
-
 }  // namespace
 
 extern "C" {
@@ -126,6 +124,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add(S * (size_t)nbk * nb * nb * zb);                      // Uinv
   add(S * sizeof(unsigned long long));                      // norm bits
   add((S + 1) * sizeof(int));                               // sc
+  add(S * sizeof(int));                                     // kmix
   add(sizeof(z64) * 64 * 64);                               // G
   add((size_t)max_batch * max_n * zb);                      // Rtmp
   add(nn * S * sizeof(float));                              // Dr
@@ -159,6 +158,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->Uinv = Z(S * (size_t)nbk * nb * nb);
   c->norm_bits = (unsigned long long*)ar.take(S * sizeof(unsigned long long));
   c->sc = (int*)ar.take((S + 1) * sizeof(int));
+  c->kmix = (int*)ar.take(S * sizeof(int));
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
   c->Dr = (float*)ar.take(nn * S * sizeof(float));
@@ -260,9 +260,7 @@ lb_status lb_assemble(lb_ctx* c, int d, const lb_c64* H, int K, const lb_c64* Ls
 
 }  // extern "C"
 
-namespace {
-
-typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+namespace lb {
 
 ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C) {
   ZGemmProblem p;
@@ -282,10 +280,11 @@ ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C) {
 }
 
 // Blocked LU of Mx[s] (no pivot search) applied to the right-hand sides held in
-// N[s], then back substitution into N[s]:  N <- Mx^{-1} N.  Y and Uf are
-// scratch (n x n per slice), Lp scratch (n x nb per slice).
-lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, z64* Uf, z64* Y, z64* Lp,
-                           cudaStream_t st) {
+// N[s] (n x nrhs, leading dimension ldN, slice stride sN), then back
+// substitution into N[s]:  N <- Mx^{-1} N.  Y (same shape as N) and Uf (n x n
+// per slice) are scratch, Lp scratch (n x nb per slice, stride n*n).
+lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, int nrhs, long long ldN, long long sN,
+                           z64* Uf, z64* Y, z64* Lp, cudaStream_t st) {
   const long long nn = (long long)n * n;
   const int nb = kLuNb, nbk = nblocks(n);
   const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
@@ -314,10 +313,10 @@ lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, z64* Uf, z6
     {
       // (c) Y[k0:k0+kb, :] = Linv_k N[k0:k0+kb, :]
       ZGemmProblem& q = pr[np++];
-      q.M = kb; q.N = n; q.K = kb;
+      q.M = kb; q.N = nrhs; q.K = kb;
       q.A = c->Linv; q.lda = nb; q.sA = sLinv;
-      q.B = N + (long long)k0 * n; q.ldb = n; q.sB = nn;
-      q.C = Y + (long long)k0 * n; q.ldc = n; q.sC = nn;
+      q.B = N + (long long)k0 * ldN; q.ldb = ldN; q.sB = sN;
+      q.C = Y + (long long)k0 * ldN; q.ldc = ldN; q.sC = sN;
       q.batch = S;
     }
     LB_CUDA(zgemm_f64(pr, np, c->sm_count, st));
@@ -332,10 +331,10 @@ lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, z64* Uf, z6
       d.alpha = -1.0; d.beta = 1.0; d.batch = S;
       // (e) N[k0+kb:, :] -= Lp Y[k0:k0+kb, :]
       ZGemmProblem& e = tr[1];
-      e.M = rest; e.N = n; e.K = kb;
+      e.M = rest; e.N = nrhs; e.K = kb;
       e.A = Lp; e.lda = nb; e.sA = nn;
-      e.B = Y + (long long)k0 * n; e.ldb = n; e.sB = nn;
-      e.C = N + (long long)(k0 + kb) * n; e.ldc = n; e.sC = nn;
+      e.B = Y + (long long)k0 * ldN; e.ldb = ldN; e.sB = sN;
+      e.C = N + (long long)(k0 + kb) * ldN; e.ldc = ldN; e.sC = sN;
       e.alpha = -1.0; e.beta = 1.0; e.batch = S;
       LB_CUDA(zgemm_f64(tr, 2, c->sm_count, st));
     }
@@ -345,24 +344,30 @@ lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, z64* Uf, z6
     const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb;
     z64* Uinv_k = c->Uinv + (long long)k * nb * nb;
     ZGemmProblem f;
-    f.M = kb; f.N = n; f.K = kb;
+    f.M = kb; f.N = nrhs; f.K = kb;
     f.A = Uinv_k; f.lda = nb; f.sA = sUinv;
-    f.B = Y + (long long)k0 * n; f.ldb = n; f.sB = nn;
-    f.C = N + (long long)k0 * n; f.ldc = n; f.sC = nn;
+    f.B = Y + (long long)k0 * ldN; f.ldb = ldN; f.sB = sN;
+    f.C = N + (long long)k0 * ldN; f.ldc = ldN; f.sC = sN;
     f.batch = S;
     LB_CUDA(zgemm_f64(&f, 1, c->sm_count, st));
     if (k0 > 0) {
       ZGemmProblem gq;
-      gq.M = k0; gq.N = n; gq.K = kb;
+      gq.M = k0; gq.N = nrhs; gq.K = kb;
       gq.A = Uf + k0; gq.lda = n; gq.sA = nn;
-      gq.B = N + (long long)k0 * n; gq.ldb = n; gq.sB = nn;
-      gq.C = Y; gq.ldc = n; gq.sC = nn;
+      gq.B = N + (long long)k0 * ldN; gq.ldb = ldN; gq.sB = sN;
+      gq.C = Y; gq.ldc = ldN; gq.sC = sN;
       gq.alpha = -1.0; gq.beta = 1.0; gq.batch = S;
       LB_CUDA(zgemm_f64(&gq, 1, c->sm_count, st));
     }
   }
   return LB_OK;
 }
+
+}  // namespace lb
+
+namespace {
+
+typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
 
 // One chunk of slices of lb_expm_pade.
 lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
@@ -379,8 +384,8 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
     c->ring_used[r] = 1;
     LB_CUDA(cudaEventRecord(ev[0], st));
   }
-  LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, s_out, c->err_dev,
-                               c->sm_count, st));
+  LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, c->kmix, s_out,
+                               c->err_dev, c->sm_count, st));
   LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
   LB_CUDA(cudaEventRecord(c->ev_scmax, st));
   if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
@@ -417,17 +422,32 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   LB_CUDA(gemm(&p, 1, c->sm_count, st));
   if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
   // (V - U) P = (V + U), FP64.  Uf, Y, Lp reuse A2, A4, A6.
-  lb_status s = lu_solve_blocked(c, n, S, c->Mx, P, c->A2, c->A4, c->A6, st);
+  lb_status s = lu_solve_blocked(c, n, S, c->Mx, P, n, n, nn, c->A2, c->A4, c->A6, st);
   if (s != LB_OK) return s;
   if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
   // squarings, FP64.  The count is known on the host once the event that
   // follows the norm kernel has completed (long before the LU finishes).
   LB_CUDA(cudaEventSynchronize(c->ev_scmax));
   const int smax = *c->scmax_host;
+  // In the mixed forms a squaring whose operand is still close to I (the
+  // leading kmix[s] ones, while ||A||_1 2^(j-s) <= 1) runs on D = P - I:
+  // P^2 = 2P - I + D D, with only D D in the product precision; later
+  // squarings (large ||L dt||) stay FP64.
   for (int it = 0; it < smax; it++) {
     ZGemmProblem q = sq(n, S, P, P, c->Z1);
     q.active = c->sc;
     q.active_iter = it;
+    if (prec != LB_FP64) {
+      ZGemmProblem qm = sq(n, S, P, P, c->Z1);
+      qm.shiftA = qm.shiftB = 1.0;
+      qm.nterms = 1;
+      qm.X[0] = P; qm.sX[0] = nn; qm.coef[0] = 2.0;
+      qm.gamma = -1.0;
+      qm.active = c->kmix;
+      qm.active_iter = it;
+      LB_CUDA(gemm(&qm, 1, c->sm_count, st));
+      q.active_lo = c->kmix;
+    }
     LB_CUDA(zgemm_f64(&q, 1, c->sm_count, st));
     LB_CUDA(launch_copy_active(nn, S, c->Z1, P, c->sc, it, st));
   }
@@ -530,21 +550,3 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
 
 }  // extern "C"
 
-namespace {
-size_t grape_ws_bytes(int max_n, int max_batch, int max_slices) {
-  (void)max_n;
-  (void)max_batch;
-  (void)max_slices;
-  return 256;
-}
-}  // namespace
-
-extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* Lbase,
-                                   const lb_c64* Ldrv, const double* u, double dt, int steps_per_slice,
-                                   int B, const lb_c64* X0, const lb_c64* Xtarget, double* fidelity_out,
-                                   double* grad_out, void* stream) {
-  if (c == nullptr) return LB_EINVAL;
-  (void)n; (void)nslices; (void)Lbase; (void)Ldrv; (void)u; (void)dt; (void)steps_per_slice;
-  (void)B; (void)X0; (void)Xtarget; (void)fidelity_out; (void)grad_out; (void)stream;
-  return LB_EUNSUPPORTED;
-}

@@ -65,12 +65,13 @@ struct lb_ctx {
   lb::z64 *Uinv = nullptr;  // per slice nblk x nb x nb
   unsigned long long* norm_bits = nullptr;
   int* sc = nullptr;  // max_slices + 1 (last = max)
+  int* kmix = nullptr;  // max_slices
   lb::z64* G = nullptr;  // d x d Gram matrix for assembly
   // --- propagation ---
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
   float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2
   float *Rr = nullptr, *Ri = nullptr, *Or = nullptr, *Oi = nullptr;  // max_batch x max_n
-  // --- GRAPE (n <= 81) ---
+  // --- GRAPE (contexts with max_n <= 81) ---
   lb::z64* grape = nullptr;
   size_t grape_bytes = 0;
 };
@@ -96,6 +97,8 @@ struct ZGemmProblem {
   double coef[4] = {0, 0, 0, 0};
   z64* C2 = nullptr; const z64* X2 = nullptr; long long sX2 = 0; double alpha2 = 1.0;
   const int* active = nullptr; int active_iter = 0;
+  const int* active_lo = nullptr;  // also skip b when active_lo[b] > active_iter
+  double shiftA = 0.0, shiftB = 0.0;  // subtracted from the diagonals of A and B as loaded
   int batch = 1;
 };
 
@@ -112,9 +115,12 @@ cudaError_t launch_assemble(int d, const z64* H, int K, const z64* Ls, z64* L_ou
 // A_s = (Lbase + u_s Ldrv) dt (or Lbase[s] dt); column abs-sums -> norm1[s]
 // (as uint64 bit patterns of non-negative doubles, max-reduced), then
 // sc[s] and A_s /= 2^sc[s].
+// kmix[s] (may be null) receives how many of the leading squarings of slice s
+// keep ||P - I|| small enough for the mixed D-form (scaled norm * 2^k <= 1).
 cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
                                  double dt, z64* A, unsigned long long* norm_bits, int* sc,
-                                 int* s_out, unsigned int* err, int sm_count, cudaStream_t st);
+                                 int* kmix, int* s_out, unsigned int* err, int sm_count,
+                                 cudaStream_t st);
 
 // Elementwise linear combinations used by the Pade step.
 // Z[b] = c0*X0[b] + c1*X1[b] + c2*X2[b]  (n x n each, batch strides = n*n)
@@ -157,5 +163,36 @@ cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* R
 cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
                             const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st);
 cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t st);
+
+// n x n square problem, batch S, slice stride n*n (helper for the build).
+ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C);
+
+// Blocked LU (no pivot search) of Mx[s] and solve for the nrhs columns of N[s].
+lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, int nrhs, long long ldN, long long sN,
+                           z64* Uf, z64* Y, z64* Lp, cudaStream_t st);
+
+// GRAPE scratch (bytes) for a context of these limits; 0 when max_n > 81.
+size_t grape_ws_bytes(int max_n, int max_batch, int max_slices);
+constexpr int kGrapeMaxN = 81;
+constexpr int kGrapeMaxB = 64;
+constexpr int kGrapeMaxStepsPerSlice = 20;
+
+// Resident FP64 chain with optional history and adjoint (conjugate transpose,
+// slices in reverse order).  hist (may be null) receives the states before the
+// first step and after every step: forward index t = 0..T, adjoint index T - k
+// after k steps (T = nslices * steps_per_slice).
+cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P, int steps_per_slice, int B,
+                                               z64* states, int adjoint, z64* hist, int sm_count,
+                                               cudaStream_t st);
+
+// dst[s](ld_d, col off_d) = c0 X0[s](ld_0, off_0) + c1 X1[s](ld_1, off_1), n x n blocks.
+cudaError_t launch_combine(int n, int S, double c0, const z64* X0, long long ld0, long long s0, double c1,
+                           const z64* X1, long long ld1, long long s1, z64* dst, long long ldd, long long sd,
+                           cudaStream_t st);
+// E[s] = Ldrv * dt / 2^sc[s]
+cudaError_t launch_scale_bcast(int n, int S, const z64* Ldrv, double dt, const int* sc, z64* E, cudaStream_t st);
+// out[s] = scale * Re sum_e conj(L[s][e]) Y[s][e], e < len, slice strides sL, sY (deterministic).
+cudaError_t launch_redot(int S, long long len, const z64* L, long long sL, const z64* Y, long long sY,
+                         double scale, double* out, cudaStream_t st);
 
 }  // namespace lb

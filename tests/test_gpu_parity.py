@@ -240,3 +240,93 @@ def test_zero_steps_and_slices_leave_states(lbm, dev):
     lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=0)
     lbm.lb_sync_status(ctx)
     assert np.array_equal(R.cpu().numpy(), w["states"])
+
+
+# -------------------------------------------------------------------- GRAPE
+
+def _gate_problem(nq, S, seed, B=4):
+    m = transmon_chain(nq)
+    d, n = m.d, m.d * m.d
+    Lb = O.lindbladian(m.H0, m.jumps)
+    Ld = O.drive_generator(m.X)
+    u = 0.3 * normal(seed, S)
+    X0 = np.zeros((B, n), dtype=complex)
+    Xt = np.zeros((B, n), dtype=complex)
+    basis = [(0, 0), (0, 1), (1, 0), (1, 1)][:B]
+    th = 0.7
+    Ux = np.eye(d, dtype=complex)
+    Ux[:2, :2] = [[np.cos(th / 2), -1j * np.sin(th / 2)], [-1j * np.sin(th / 2), np.cos(th / 2)]]
+    for b, (i, j) in enumerate(basis):
+        E = np.zeros((d, d), dtype=complex)
+        E[i, j] = 1.0
+        X0[b] = O.vec(E)
+        Xt[b] = O.vec(Ux @ E @ Ux.conj().T)
+    return Lb, Ld, u, m.dt, X0, Xt
+
+
+@pytest.mark.parametrize("nq,S,m,dtscale", [(1, 7, 1, 1.0), (1, 4, 3, 20.0), (2, 5, 2, 1.0), (2, 3, 1, 30.0)])
+def test_grape_matches_oracle(lbm, dev, nq, S, m, dtscale):
+    """F and dF/du against the oracle (Van Loan block Frechet derivative);
+    dtscale > 1 forces several squarings.  Both sides are exact to rounding
+    plus the Pade truncation (~1e-13 relative): F within 1e-12, gradient
+    within 1e-9 of max |g|."""
+    Lb, Ld, u, dt, X0, Xt = _gate_problem(nq, S, 900 + S)
+    dt = dt * dtscale
+    F_ref, g_ref = O.grape_fidelity_grad(Lb, Ld, u, dt, m, X0, Xt)
+    n = Lb.shape[0]
+    ctx = lbm.Context(0, max_n=n, max_batch=4, max_slices=S)
+    Fo = torch.zeros(1, dtype=torch.float64, device=dev)
+    go = torch.zeros(S, dtype=torch.float64, device=dev)
+    lbm.lb_grape_grad(ctx, _t(Lb, dev), _t(Ld, dev), _t(u, dev), dt, m, _t(X0, dev), _t(Xt, dev), Fo, go)
+    lbm.lb_sync_status(ctx)
+    F = float(Fo.item())
+    g = go.cpu().numpy()
+    assert abs(F - F_ref) <= 1e-12 * max(1.0, abs(F_ref)), (F, F_ref)
+    assert np.max(np.abs(g - g_ref)) <= 1e-9 * max(1e-6, np.max(np.abs(g_ref))), (g, g_ref)
+
+
+def test_grape_rejects_large_contexts(lbm, dev):
+    ctx = lbm.Context(0, max_n=729, max_batch=4, max_slices=2)
+    z = torch.zeros((9, 9), dtype=torch.complex128, device=dev)
+    x = torch.zeros((1, 9), dtype=torch.complex128, device=dev)
+    with pytest.raises(lbm.LBError) as ei:
+        lbm.lb_grape_grad(ctx, z, z, torch.zeros(2, dtype=torch.float64, device=dev), 0.1, 1, x, x,
+                          torch.zeros(1, dtype=torch.float64, device=dev),
+                          torch.zeros(2, dtype=torch.float64, device=dev))
+    assert ei.value.name == "LB_EUNSUPPORTED"
+
+
+def test_expm_fp32_mixed_squarings_paper_model(lbm, dev):
+    """Mixed build on the paper's d = 9 model (||L dt||_1 ~ 4, s = 5): four
+    squarings on D = P - I in FP32, the last in FP64.  The FP32 error of the
+    scaled approximant (~1e-8) grows by about 2^s through the squarings; the
+    test allows 1e-6 relative."""
+    from workloads import paper_grape_model
+
+    m = paper_grape_model(9)
+    Lb = O.lindbladian(m.H0, m.jumps)
+    Ld = O.drive_generator(m.X)
+    u = np.array([0.0, 0.05, -0.1])
+    n = 81
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=3)
+    P = torch.empty((3, n, n), dtype=torch.complex128, device=dev)
+    s_out = torch.empty(3, dtype=torch.int32, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(u, dev), m.dt, P, prec="fp32", s_out=s_out)
+    lbm.lb_sync_status(ctx)
+    assert list(s_out.cpu().numpy()) == [5, 5, 5]
+    ref = O.slice_propagators(Lb, Ld, u, m.dt)
+    err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(3))
+    assert err <= 1e-6, err
+
+
+def test_expm_fp32_d27(lbm, dev):
+    w = make_workload("d27_chain", nslices=2)
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    ctx = lbm.Context(0, max_n=729, max_batch=1, max_slices=2)
+    P = torch.empty((2, 729, 729), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(w["u"], dev), w["dt"], P, prec="fp32")
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
+    err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(2))
+    assert err <= 1e-6, err
