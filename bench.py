@@ -171,6 +171,84 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours ---
 
+def other_workloads(lb, accounting, dev, stream, reps=5):
+    """Secondary measurements on the smaller workloads: the d = 3 single-state
+    chain (latency per step), the d = 9 batch (FP64 and FP32 throughput), and
+    one d = 9 GRAPE landscape point (100 slices, 4 basis operators)."""
+    import numpy as np
+    import torch
+
+    from workloads import make_workload, transmon_chain
+
+    def dput(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def time_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = {}
+    ctx = lb.Context(dev.index or 0, max_n=81, max_batch=1024, max_slices=100)
+
+    def props(w):
+        n = w["n"]
+        Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+        Ld = torch.empty_like(Lb)
+        lb.lb_assemble(ctx, dput(w["H0"]), dput(w["jumps"]), Lb)
+        lb.lb_assemble(ctx, dput(w["X"]), None, Ld)
+        P = torch.empty((w["nslices"], n, n), dtype=torch.complex128, device=dev)
+        lb.lb_expm_pade(ctx, Lb, Ld, dput(w["u"]), w["dt"], P)
+        return Lb, Ld, P
+
+    # d = 3, one state, 10^4 steps, FP64 (Algorithm 2 latency)
+    w = make_workload("d3_single")
+    _, _, P = props(w)
+    R = dput(w["states"])
+    N = w["steps_per_slice"]
+    ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N))
+    out["d3_single"] = {"workload": "d=3, 1 state, 10^4 chained FP64 steps", "ns_per_step": 1e6 * ms / N,
+                        "state_steps_per_s": N / (ms / 1e3), "paper_context_ns_per_step": 309.5}
+    # d = 9, 1024 states, 1000 steps
+    w = make_workload("d9_batch")
+    _, _, P = props(w)
+    N, B, n = w["steps_per_slice"], w["B"], w["n"]
+    for prec, renorm in (("fp64", False), ("fp32", True)):
+        R = dput(w["states"])
+        ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N, prec=prec, renorm_trace=renorm))
+        fl = B * N * accounting.state_step_flops(n) / (ms / 1e3)
+        peak = FP64_PEAK if prec == "fp64" else FP32_PEAK
+        out["d9_batch_" + prec] = {"workload": "d=9, 1024 states, 1000 steps, %s" % prec, "ms": ms,
+                                   "state_steps_per_s": B * N / (ms / 1e3),
+                                   "roofline": {"bound": "alu", "achieved": fl / 1e12, "peak": peak / 1e12,
+                                                "unit": "TFLOP/s", "frac": fl / peak}}
+    # one GRAPE landscape point at d = 9
+    m = transmon_chain(2)
+    S, Bg, n = 100, 4, 81
+    wl = {"H0": m.H0, "jumps": m.jumps, "X": m.X, "u": 0.05 * np.sin(np.arange(S) * 0.3), "dt": m.dt,
+          "nslices": S, "n": n}
+    Lb, Ld, _ = props(wl)
+    X0 = np.zeros((Bg, n), dtype=complex)
+    for b, (i, j) in enumerate([(0, 0), (0, 1), (1, 0), (1, 1)]):
+        X0[b, i * 9 + j] = 1.0
+    X0d = dput(X0)
+    Fo = torch.zeros(1, dtype=torch.float64, device=dev)
+    go = torch.zeros(S, dtype=torch.float64, device=dev)
+    ud = dput(wl["u"])
+    ms = time_ms(lambda: lb.lb_grape_grad(ctx, Lb, Ld, ud, m.dt, 1, X0d, X0d, Fo, go))
+    out["d9_grape"] = {"workload": "d=9 GRAPE landscape point: 100 slices, 100 Pade builds + Frechet "
+                                   "derivatives, forward/adjoint chains of 4 basis operators", "ms": ms}
+    ctx.close()
+    return out
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -345,6 +423,7 @@ def run_ours(args):
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
     }
+    line["other_workloads"] = other_workloads(lb, accounting, dev, stream)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, 6)
     if rank == 0:

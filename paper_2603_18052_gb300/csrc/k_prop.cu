@@ -224,13 +224,16 @@ __global__ void states_from_f32_kernel(long long total, const float* __restrict_
     s[e] = make_double2((double)r[e], (double)im[e]);
 }
 
-// Out[b][i] = R[b][i] + sum_j D[i][j] R[b][j]; planar FP32.  64 x 64 output
-// tile (states x rows), 256 threads with 4 x 4 outputs each.
-__global__ void __launch_bounds__(256)
+// Out[b][i] = R[b][i] + sum_j D[i][j] R[b][j]; planar FP32.  BM x BN output
+// tile (states x rows), TM x TN outputs per thread.  32 x 32 tiles give 184
+// CTAs for 256 states x 729 rows, all resident at once on 152 SMs.
+template <int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
     step_f32_kernel(int n, int B, const float* __restrict__ Dr, const float* __restrict__ Di,
                     const float* __restrict__ Rr, const float* __restrict__ Ri, float* __restrict__ Or,
                     float* __restrict__ Oi) {
-  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+  constexpr int BK = 16;
+  constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ __align__(16) float Ar[BK][BM], Ai[BK][BM], Br[BK][BN], Bi[BK][BN];
   const int tilesN = (n + BN - 1) / BN;
   const int tilesM = (B + BM - 1) / BM;
@@ -244,14 +247,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int j = 0; j < TN; j++) cr[i][j] = ci[i][j] = 0.f;
     for (int k0 = 0; k0 < n; k0 += BK) {
-      for (int e = tid; e < BM * BK; e += 256) {
+      for (int e = tid; e < BM * BK; e += NT) {
         const int m = e / BK, k = e % BK;
         const int gm = m0 + m, gk = k0 + k;
         const bool ok = gm < B && gk < n;
         Ar[k][m] = ok ? Rr[(long long)gm * n + gk] : 0.f;
         Ai[k][m] = ok ? Ri[(long long)gm * n + gk] : 0.f;
       }
-      for (int e = tid; e < BN * BK; e += 256) {
+      for (int e = tid; e < BN * BK; e += NT) {
         const int nn_ = e / BK, k = e % BK;
         const int gn = n0 + nn_, gk = k0 + k;
         const bool ok = gn < n && gk < n;
@@ -414,10 +417,10 @@ cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* R
 
 cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
                             const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st) {
-  const int tiles = ((B + 63) / 64) * ((n + 63) / 64);
-  const int grid = std::min(tiles, sm_count * 2);
+  const int tiles = ((B + 31) / 32) * ((n + 31) / 32);
+  const int grid = std::min(tiles, sm_count * 8);
   count_launch();
-  step_f32_kernel<<<grid, 256, 0, st>>>(n, B, Dr, Di, Rr, Ri, Or, Oi);
+  step_f32_kernel<32, 32, 4, 4><<<grid, 64, 0, st>>>(n, B, Dr, Di, Rr, Ri, Or, Oi);
   return cudaGetLastError();
 }
 
