@@ -1,0 +1,438 @@
+// Batched complex GEMM on the 5th-generation tensor cores (tcgen05), in the
+// split-BF16 x3 form:  every FP64 operand x is stored as two BF16 numbers,
+// x ~ hi + lo (hi = bf16(x), lo = bf16(x - hi)), and a real product is
+// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in TMEM.  A
+// complex product takes the four real products of (Ar + i Ai)(Br + i Bi),
+// 12 BF16 MMAs per K step, two TMEM accumulators (re, im); the minus sign of
+// Ai Bi is the instruction's negate-A bit.
+//
+// Operands are pre-split "plane" tensors: for a batch of S complex R x K
+// matrices, bf16 [S][4][R][ld] with planes (re_hi, re_lo, im_hi, im_lo) and
+// K contiguous (K-major).  For C = X Y the A operand is X and the B operand
+// is Y^T (both K-major).  TMA loads 64-wide K blocks with the 128-byte swizzle
+// into a two-stage shared-memory ring: warp 0 issues the copies, one thread of
+// warp 1 issues the MMAs, and after the last K block all four warps read the
+// 128 x BN accumulator tile out of TMEM and apply the FP64 epilogue
+//   C  = alpha acc + sum_t coef_t X_t + gamma I + beta C
+//   C2 = alpha2 acc + sum_t coef2_t X_t + gamma2 I          (optional)
+// and optionally write the split planes of C (row-major and/or transposed)
+// for the next product.  Every mbarrier wait is bounded; a wait that gives up
+// sets the error word and the CTA still frees its TMEM.
+#include "lb_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace lb {
+
+namespace {
+
+constexpr int TBM = 128;           // rows per tile (M of one MMA)
+constexpr int TBK = 64;            // K per stage (128 bytes of BF16)
+constexpr int NSTAGE = 2;
+constexpr int A_PLANE = TBM * 128;  // bytes per A plane per stage
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// Shared memory of one configuration: NPA / NPB BF16 pieces per real value of
+// the A / B operand (re and im planes each), BN columns per tile.
+template <int NPA, int NPB, int BN>
+struct TcCfg {
+  static constexpr int B_PLANE = BN * 128;
+  static constexpr int STAGE_BYTES = 2 * NPA * A_PLANE + 2 * NPB * B_PLANE;
+  static constexpr int SMEM = NSTAGE * STAGE_BYTES + 1024;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t ph) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(ph)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t ph) {
+  if (mbar_try(bar, ph)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, ph))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__host__ __device__ constexpr uint32_t idesc(int negA, int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)negA << 13) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(TBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+}
+
+// Products kept: pieces (i, j) with i + j < max(NPA, NPB): for two pieces
+// each, hi*hi + hi*lo + lo*hi; for a three-piece B also the two products
+// that carry B's third piece.
+template <int NPA, int NPB, int TBN>
+__global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                       const __grid_constant__ CUtensorMap mapB,
+                                                       const __grid_constant__ TcProblem P) {
+  using Cfg = TcCfg<NPA, NPB, TBN>;
+  constexpr int B_PLANE = Cfg::B_PLANE;
+  constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
+  constexpr int NPMAX = NPA > NPB ? NPA : NPB;
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], acc_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int give_up;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM, b = blockIdx.z;
+  const int nk = (P.K + TBK - 1) / TBK;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; s++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty_bar[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    give_up = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(2 * TBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tacc = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA copies of the K blocks into the ring
+    for (int kb = 0; kb < nk; kb++) {
+      const int s = kb % NSTAGE;
+      if (kb >= NSTAGE && !mbar_wait(su32(&empty_bar[s]), ((kb - NSTAGE) / NSTAGE) & 1)) {
+        atomicOr(P.err, ERR_TIMEOUT);
+        give_up = 1;
+        break;
+      }
+      const uint32_t base = su32(sm + s * STAGE_BYTES);
+      const uint32_t fb = su32(&full_bar[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
+      for (int p = 0; p < 2 * NPA; p++) tma3(base + p * A_PLANE, &mapA, kb * TBK, m0, b * 2 * NPA + p, fb);
+      for (int p = 0; p < 2 * NPB; p++)
+        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, kb * TBK, n0, b * 2 * NPB + p, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t tre = tacc, tim = tacc + TBN;
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; kb++) {
+      const int s = kb % NSTAGE;
+      if (!mbar_wait(su32(&full_bar[s]), (kb / NSTAGE) & 1)) {
+        atomicOr(P.err, ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = su32(sm + s * STAGE_BYTES);
+      const uint32_t bb = base + 2 * NPA * A_PLANE;
+#pragma unroll
+      for (int k = 0; k < TBK / 16; k++) {
+        const uint32_t o = k * 32;
+        const uint32_t first = (kb > 0 || k > 0) ? 1u : 0u;
+        bool started = false;
+#pragma unroll
+        for (int i = 0; i < NPA; i++)
+#pragma unroll
+          for (int j = 0; j < NPB; j++) {
+            if (i + j >= NPMAX) continue;
+            const uint64_t Ar = desc_sw128(base + i * A_PLANE + o), Ai = desc_sw128(base + (NPA + i) * A_PLANE + o);
+            const uint64_t Br = desc_sw128(bb + j * B_PLANE + o), Bi = desc_sw128(bb + (NPB + j) * B_PLANE + o);
+            const uint32_t acc = started ? 1u : first;
+            mma(tre, Ar, Br, idesc(0, TBN), acc);
+            mma(tre, Ai, Bi, idesc(1, TBN), 1);
+            mma(tim, Ar, Bi, idesc(0, TBN), acc);
+            mma(tim, Ai, Br, idesc(0, TBN), 1);
+            started = true;
+          }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&empty_bar[s]))
+                   : "memory");
+    }
+    if (!ok) give_up = 1;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&acc_bar))
+                 : "memory");
+  }
+  __syncwarp();
+  // all warps: wait for the accumulator
+  const bool have = mbar_wait(su32(&acc_bar), 0);
+  if (!have && tid == 0) atomicOr(P.err, ERR_TIMEOUT);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool good = have && !give_up;
+  // the producer may still have copies in flight after a give-up: wait for
+  // them (bounded) before the shared memory is released
+  if (!good && tid == 0) {
+    for (int s = 0; s < NSTAGE; s++) {
+      const int uses = (nk - s + NSTAGE - 1) / NSTAGE;
+      if (uses > 0) mbar_wait(su32(&full_bar[s]), (uses - 1) & 1);
+    }
+  }
+  if (good) {
+    const int row = m0 + warp * 32 + lane;
+    const long long bs = (long long)b;
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      float vr[16], vi[16];
+      const uint32_t ta = tacc + ((uint32_t)(warp * 32) << 16) + c0;
+      tmem_ld16(ta, vr);
+      tmem_ld16(ta + TBN, vi);
+      if (row >= P.M) continue;
+#pragma unroll 4
+      for (int j = 0; j < 16; j++) {
+        const int col = n0 + c0 + j;
+        if (col >= P.N) break;
+        const double ar = (double)vr[j], ai = (double)vi[j];
+        const long long off = P.transC ? (long long)col * P.ldc + row : (long long)row * P.ldc + col;
+        double cr = P.alpha * ar, ci = P.alpha * ai;
+        double dr = P.alpha2 * ar, di = P.alpha2 * ai;
+        if (P.beta != 0.0) {
+          const z64 c0v = P.C[bs * P.sC + off];
+          cr = fma(P.beta, c0v.x, cr);
+          ci = fma(P.beta, c0v.y, ci);
+        }
+        for (int q = 0; q < P.nterms; q++) {
+          const z64 x = P.X[q][bs * P.sX[q] + off];
+          cr = fma(P.coef[q], x.x, cr);
+          ci = fma(P.coef[q], x.y, ci);
+          dr = fma(P.coef2[q], x.x, dr);
+          di = fma(P.coef2[q], x.y, di);
+        }
+        if (row == col) {
+          cr += P.gamma;
+          dr += P.gamma2;
+        }
+        P.C[bs * P.sC + off] = make_double2(cr, ci);
+        if (P.C2 != nullptr) P.C2[bs * P.sC + off] = make_double2(dr, di);
+        if (P.sp != nullptr) {  // row-major split planes of C (A-operand layout)
+          __nv_bfloat16 h, l;
+          const long long pb = bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col;
+          const double vr2 = (row == col) ? cr - P.sp_shift : cr;
+          split2(vr2, h, l);
+          P.sp[pb] = h;
+          P.sp[pb + P.sp_plane] = l;
+          split2(ci, h, l);
+          P.sp[pb + 2 * P.sp_plane] = h;
+          P.sp[pb + 3 * P.sp_plane] = l;
+        }
+        if (P.spT != nullptr) {  // transposed split planes (B-operand layout)
+          __nv_bfloat16 h, l;
+          const long long pb = bs * 4 * P.spT_plane + (long long)col * P.spT_ld + row;
+          const double vr2 = (row == col) ? cr - P.spT_shift : cr;
+          split2(vr2, h, l);
+          P.spT[pb] = h;
+          P.spT[pb + P.spT_plane] = l;
+          split2(ci, h, l);
+          P.spT[pb + 2 * P.spT_plane] = h;
+          P.spT[pb + 3 * P.spT_plane] = l;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(2 * TBN));
+}
+
+// Split planes of a batch of complex matrices: dst[s][p][r][c] for the
+// row-major form, or of the transpose (dst[s][p][c][r]) when trans != 0,
+// with `shift` subtracted from the diagonal first.
+__global__ void split_kernel(int R, int Kc, long long total, const z64* __restrict__ src, long long lds,
+                             long long ss, double shift, int trans, __nv_bfloat16* __restrict__ dst, long long ldd,
+                             long long plane, int np) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long per = (long long)R * Kc;
+    const long long s = e / per;
+    const long long o = e - s * per;
+    long long r, c;
+    if (trans) {  // consecutive threads along r: coalesced writes of the transpose
+      c = o / R;
+      r = o - c * R;
+    } else {
+      r = o / Kc;
+      c = o - r * Kc;
+    }
+    z64 v = src[s * ss + r * lds + c];
+    if (r == c) v.x -= shift;
+    const long long d = s * 2 * np * plane + (trans ? c * ldd + r : r * ldd + c);
+    double xr = v.x, xi = v.y;
+    for (int p = 0; p < np; p++) {  // x = sum of np BF16 pieces, each the rounding of what is left
+      const __nv_bfloat16 hr = __double2bfloat16(xr), hi = __double2bfloat16(xi);
+      dst[d + p * plane] = hr;
+      dst[d + (np + p) * plane] = hi;
+      xr -= (double)__bfloat162float(hr);
+      xi -= (double)__bfloat162float(hi);
+    }
+  }
+}
+
+// One warp per state: divide by the trace (when renorm) and write the state's
+// split planes (row b of the [4][B][ld] plane tensor).
+__global__ void renorm_split_kernel(int n, int d, int B, int renorm, z64* __restrict__ X,
+                                    __nv_bfloat16* __restrict__ planes, long long ld, long long plane) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= B) return;
+  z64* x = X + (long long)w * n;
+  double cr = 1.0, ci = 0.0;
+  if (renorm) {
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k < d; k += 32) {
+      sr += x[k * (d + 1)].x;
+      si += x[k * (d + 1)].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    const double m2 = sr * sr + si * si;
+    cr = sr / m2;
+    ci = -si / m2;
+  }
+  for (int e = lane; e < n; e += 32) {
+    z64 v = x[e];
+    if (renorm) {
+      v = make_double2(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
+      x[e] = v;
+    }
+    const long long o = (long long)w * ld + e;
+    __nv_bfloat16 h, l;
+    split2(v.x, h, l);
+    planes[o] = h;
+    planes[o + plane] = l;
+    split2(v.y, h, l);
+    planes[o + 2 * plane] = h;
+    planes[o + 3 * plane] = l;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool encode_planes(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, long long ld, long long plane,
+                   int nplanes, int box_rows) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    else
+      cudaGetLastError();
+  });
+  if (g_encode == nullptr) return false;
+  if ((ld * 2) % 16 != 0 || (plane * 2) % 16 != 0 || ((uintptr_t)base & 15) != 0) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(plane * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+long long plane_ld(int K) { return ((long long)K + 7) / 8 * 8; }
+
+cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, long long ss, double shift, int trans,
+                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np) {
+  const long long total = (long long)R * Kc * S;
+  long long g = (total + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  count_launch();
+  split_kernel<<<(unsigned)g, 256, 0, st>>>(R, Kc, total, src, lds, ss, shift, trans, dst, ldd, plane, np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, z64* X, __nv_bfloat16* planes, long long ld,
+                                long long plane, cudaStream_t st) {
+  const int grid = (B * 32 + 255) / 256;
+  count_launch();
+  renorm_split_kernel<<<grid, 256, 0, st>>>(n, d, B, renorm, X, planes, ld, plane);
+  return cudaGetLastError();
+}
+
+namespace {
+template <int NPA, int NPB, int BN>
+cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
+  using Cfg = TcCfg<NPA, NPB, BN>;
+  static_assert(Cfg::SMEM <= 232448, "shared memory");
+  CUtensorMap ma, mb;
+  if (!encode_planes(&ma, p.Aop, p.M, p.K, p.a_ld, p.a_plane, 2 * NPA * p.batch, TBM) ||
+      !encode_planes(&mb, p.Bop, p.N, p.K, p.b_ld, p.b_plane, 2 * NPB * p.batch, BN))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(zgemm_tc_kernel<NPA, NPB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((p.N + BN - 1) / BN, (p.M + TBM - 1) / TBM, p.batch);
+  count_launch();
+  zgemm_tc_kernel<NPA, NPB, BN><<<grid, 128, Cfg::SMEM, st>>>(ma, mb, p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st) {
+  if (p.M <= 0 || p.N <= 0 || p.batch <= 0) return cudaSuccess;
+  if (p.npa == 2 && p.npb == 2) return launch_tc<2, 2, 64>(p, st);
+  if (p.npa == 2 && p.npb == 3) return launch_tc<2, 3, 32>(p, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lb

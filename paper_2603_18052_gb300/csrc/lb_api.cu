@@ -127,6 +127,9 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add(S * sizeof(int));                                     // kmix
   add(sizeof(z64) * 64 * 64);                               // G
   add((size_t)max_batch * max_n * zb);                      // Rtmp
+  const size_t plane_elems = (size_t)max_n * (size_t)plane_ld(max_n);
+  for (int i = 0; i < 9; i++) add((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));  // split planes
+  for (int i = 0; i < 2; i++) add(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
   add(nn * S * sizeof(float));                              // Dr
   add(nn * S * sizeof(float));                              // Di
   for (int i = 0; i < 4; i++) add((size_t)max_batch * max_n * sizeof(float));
@@ -161,6 +164,10 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->kmix = (int*)ar.take(S * sizeof(int));
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
+  for (int i = 0; i < 9; i++)
+    c->sp[i] = (__nv_bfloat16*)ar.take((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));
+  for (int i = 0; i < 2; i++)
+    c->spR[i] = (__nv_bfloat16*)ar.take(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
   c->Dr = (float*)ar.take(nn * S * sizeof(float));
   c->Di = (float*)ar.take(nn * S * sizeof(float));
   c->Rr = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
@@ -369,6 +376,67 @@ namespace {
 
 typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
 
+// The six Pade products in split-BF16 x3 on the tensor cores.  U is taken as
+// A (W' - b1 I) + b1 A so that the BF16 rounding touches only the small part
+// of W' = b1 I + O(A^2); V - U and V + U are formed in FP64 in the epilogue.
+lb_status pade_products_tc(lb_ctx* c, int n, int S, z64* P, cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  const double* b = c->pade_b;
+  const long long ld = plane_ld(n), pl = (long long)n * ld;
+  __nv_bfloat16 *Aop = c->sp[0], *AopT = c->sp[1], *A2op = c->sp[2], *A2opT = c->sp[3], *A4op = c->sp[4],
+                *A6op = c->sp[5], *Z1T = c->sp[6], *Z2T = c->sp[7], *WT = c->sp[8];
+  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 0, Aop, ld, pl, st));
+  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 1, AopT, ld, pl, st));
+  auto prob = [&](const __nv_bfloat16* a, const __nv_bfloat16* bo, z64* C) {
+    TcProblem t;
+    t.M = t.N = t.K = n;
+    t.batch = S;
+    t.Aop = a; t.a_ld = ld; t.a_plane = pl;
+    t.Bop = bo; t.b_ld = ld; t.b_plane = pl;
+    t.C = C; t.ldc = n; t.sC = nn;
+    t.err = c->err_dev;
+    return t;
+  };
+  TcProblem t = prob(Aop, AopT, c->A2);
+  t.sp = A2op; t.sp_ld = ld; t.sp_plane = pl;
+  t.spT = A2opT; t.spT_ld = ld; t.spT_plane = pl;
+  LB_CUDA(zgemm_tc(t, st));
+  t = prob(A2op, A2opT, c->A4);
+  t.sp = A4op; t.sp_ld = ld; t.sp_plane = pl;
+  LB_CUDA(zgemm_tc(t, st));
+  t = prob(A4op, A2opT, c->A6);
+  t.sp = A6op; t.sp_ld = ld; t.sp_plane = pl;
+  LB_CUDA(zgemm_tc(t, st));
+  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[12], b[10], b[8], c->Z1, st));
+  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[13], b[11], b[9], c->Z2, st));
+  LB_CUDA(launch_split(n, n, S, c->Z1, n, nn, 0.0, 1, Z1T, ld, pl, st));
+  LB_CUDA(launch_split(n, n, S, c->Z2, n, nn, 0.0, 1, Z2T, ld, pl, st));
+  auto with3 = [&](TcProblem q, double c0, double c1, double c2, double gamma) {
+    q.nterms = 3;
+    q.X[0] = c->A6; q.X[1] = c->A4; q.X[2] = c->A2;
+    q.sX[0] = q.sX[1] = q.sX[2] = nn;
+    q.coef[0] = c0; q.coef[1] = c1; q.coef[2] = c2;
+    q.gamma = gamma;
+    return q;
+  };
+  t = with3(prob(A6op, Z1T, c->V), b[6], b[4], b[2], b[0]);
+  LB_CUDA(zgemm_tc(t, st));
+  t = with3(prob(A6op, Z2T, c->W), b[7], b[5], b[3], b[1]);
+  t.spT = WT; t.spT_ld = ld; t.spT_plane = pl; t.spT_shift = b[1];
+  LB_CUDA(zgemm_tc(t, st));
+  // acc = A (W' - b1 I):  Mx = V - b1 A - acc,  P = V + b1 A + acc
+  t = prob(Aop, WT, c->Mx);
+  t.alpha = -1.0;
+  t.nterms = 2;
+  t.X[0] = c->V; t.X[1] = c->A;
+  t.sX[0] = t.sX[1] = nn;
+  t.coef[0] = 1.0; t.coef[1] = -b[1];
+  t.C2 = P; t.alpha2 = 1.0;
+  t.coef2[0] = 1.0; t.coef2[1] = b[1];
+  LB_CUDA(zgemm_tc(t, st));
+  return LB_OK;
+}
+
 // One chunk of slices of lb_expm_pade.
 lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u,
                      double dt, lb_precision prec, z64* P, int* s_out, cudaStream_t st) {
@@ -389,6 +457,10 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
   LB_CUDA(cudaEventRecord(c->ev_scmax, st));
   if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
+  if (prec == LB_BF16X3) {
+    lb_status r = pade_products_tc(c, n, S, P, st);
+    if (r != LB_OK) return r;
+  } else {
   // three power products
   ZGemmProblem p = sq(n, S, c->A, c->A, c->A2);
   LB_CUDA(gemm(&p, 1, c->sm_count, st));
@@ -420,6 +492,7 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   p.X[0] = c->V; p.sX[0] = nn; p.coef[0] = 1.0;
   p.C2 = P; p.X2 = c->V; p.sX2 = nn; p.alpha2 = 1.0;
   LB_CUDA(gemm(&p, 1, c->sm_count, st));
+  }
   if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
   // (V - U) P = (V + U), FP64.  Uf, Y, Lp reuse A2, A4, A6.
   lb_status s = lu_solve_blocked(c, n, S, c->Mx, P, n, n, nn, c->A2, c->A4, c->A6, st);
@@ -445,7 +518,7 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
       qm.gamma = -1.0;
       qm.active = c->kmix;
       qm.active_iter = it;
-      LB_CUDA(gemm(&qm, 1, c->sm_count, st));
+      LB_CUDA((prec == LB_FP32 ? gemm : zgemm_f32)(&qm, 1, c->sm_count, st));
       q.active_lo = c->kmix;
     }
     LB_CUDA(zgemm_f64(&q, 1, c->sm_count, st));
@@ -469,7 +542,6 @@ lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const
   if (Ldrv != nullptr && u == nullptr) return LB_EINVAL;
   if (!std::isfinite(dt)) return LB_EINVAL;
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
-  if (prec == LB_BF16X3) return LB_EUNSUPPORTED;
   if (nslices == 0) return LB_OK;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -492,7 +564,6 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   if (n < 1 || n > c->max_n || !is_square(n, &d)) return LB_EINVAL;
   if (nslices < 0 || steps_per_slice < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
-  if (prec == LB_BF16X3) return LB_EUNSUPPORTED;
   if (nslices == 0 || steps_per_slice == 0) return LB_OK;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -520,6 +591,44 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
         cur = nxt;
         nxt = tmp;
       }
+    if (cur != X)
+      LB_CUDA(cudaMemcpyAsync(X, cur, sizeof(z64) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
+    return LB_OK;
+  }
+  if (prec == LB_BF16X3) {
+    // Split BF16 on the tensor cores: next = cur + D cur with D = P - I.  The
+    // states (A operand, rows = states) keep two BF16 pieces and are held in
+    // FP64 between steps; D (B operand) keeps three pieces, because its
+    // rounding repeats identically at every step and would otherwise add up
+    // coherently over long chains; five BF16 products per real product.
+    const long long ld = plane_ld(n), dpl = (long long)n * ld, rpl = (long long)B * ld;
+    z64* cur = X;
+    z64* nxt = c->Rtmp;
+    __nv_bfloat16* pc = c->spR[0];
+    __nv_bfloat16* pn = c->spR[1];
+    LB_CUDA(launch_renorm_split(n, d, B, 0, cur, pc, ld, rpl, st));
+    for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+      const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+      LB_CUDA(launch_split(n, n, S, Pz + s0 * nn, n, nn, 1.0, 0, c->sp[0], ld, dpl, st, 3));
+      for (int s = 0; s < S; s++)
+        for (int t = 0; t < steps_per_slice; t++) {
+          TcProblem q;
+          q.M = B; q.N = n; q.K = n; q.batch = 1;
+          q.npa = 2; q.npb = 3;
+          q.Aop = pc; q.a_ld = ld; q.a_plane = rpl;
+          q.Bop = c->sp[0] + (long long)s * 6 * dpl; q.b_ld = ld; q.b_plane = dpl;
+          q.C = nxt; q.ldc = n;
+          q.nterms = 1; q.X[0] = cur; q.coef[0] = 1.0;
+          q.err = c->err_dev;
+          if (!renorm_trace) {
+            q.sp = pn; q.sp_ld = ld; q.sp_plane = rpl;
+          }
+          LB_CUDA(zgemm_tc(q, st));
+          if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, nxt, pn, ld, rpl, st));
+          z64* t1 = cur; cur = nxt; nxt = t1;
+          __nv_bfloat16* t2 = pc; pc = pn; pn = t2;
+        }
+    }
     if (cur != X)
       LB_CUDA(cudaMemcpyAsync(X, cur, sizeof(z64) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
     return LB_OK;

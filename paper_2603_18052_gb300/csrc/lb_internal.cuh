@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
 
@@ -67,6 +68,9 @@ struct lb_ctx {
   int* sc = nullptr;  // max_slices + 1 (last = max)
   int* kmix = nullptr;  // max_slices
   lb::z64* G = nullptr;  // d x d Gram matrix for assembly
+  // --- split-BF16 planes for the tensor-core products (per slice 4 x n x ld) ---
+  __nv_bfloat16* sp[9] = {};
+  __nv_bfloat16* spR[2] = {};  // state planes, 4 x max_batch x ld each
   // --- propagation ---
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
   float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2
@@ -195,4 +199,37 @@ cudaError_t launch_scale_bcast(int n, int S, const z64* Ldrv, double dt, const i
 cudaError_t launch_redot(int S, long long len, const z64* L, long long sL, const z64* Y, long long sY,
                          double scale, double* out, cudaStream_t st);
 
+// ------------------------------------------------------ tensor cores ----
+// Complex GEMM in split-BF16 x3 on tcgen05 (see k_tc.cu).  Operands are plane
+// tensors bf16 [batch][4][rows][ld] (re_hi, re_lo, im_hi, im_lo), K-major:
+// A operand = X (M x K), B operand = Y^T (N x K) for C = X Y.
+struct TcProblem {
+  int M = 0, N = 0, K = 0, batch = 1;
+  int npa = 2, npb = 2;  // BF16 pieces per value of A / B: (2, 2) or (2, 3); planes = 2 * pieces
+  const __nv_bfloat16* Aop = nullptr; long long a_ld = 0, a_plane = 0;
+  const __nv_bfloat16* Bop = nullptr; long long b_ld = 0, b_plane = 0;
+  z64* C = nullptr; long long ldc = 0, sC = 0;
+  int transC = 0;  // C (and the X terms) indexed [col][row] instead of [row][col]
+  double alpha = 1.0, beta = 0.0, gamma = 0.0;
+  int nterms = 0;
+  const z64* X[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long sX[4] = {0, 0, 0, 0};
+  double coef[4] = {0, 0, 0, 0};
+  z64* C2 = nullptr; double alpha2 = 0.0, gamma2 = 0.0;
+  double coef2[4] = {0, 0, 0, 0};
+  __nv_bfloat16* sp = nullptr; long long sp_ld = 0, sp_plane = 0; double sp_shift = 0.0;
+  __nv_bfloat16* spT = nullptr; long long spT_ld = 0, spT_plane = 0; double spT_shift = 0.0;
+  unsigned int* err = nullptr;
+};
+cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
+// per state: optional division by the trace, then the row's split planes
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, z64* X, __nv_bfloat16* planes, long long ld,
+                                long long plane, cudaStream_t st);
+long long plane_ld(int K);
+// planes of src (R x Kc per slice) or of its transpose, diagonal shifted
+// np BF16 pieces per value: planes [S][2 np][..] (re pieces, then im pieces)
+cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, long long ss, double shift, int trans,
+                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np = 2);
+
 }  // namespace lb
+

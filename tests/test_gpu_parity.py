@@ -330,3 +330,87 @@ def test_expm_fp32_d27(lbm, dev):
     ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
     err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(2))
     assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("name,S,tol", [("d9_batch", 3, 1e-6), ("d27_chain", 2, 1e-6)])
+def test_expm_bf16x3_products(lbm, dev, name, S, tol):
+    """Split-BF16 x3 Pade products on the tensor cores.  Each operand keeps
+    about 16 significant bits (relative rounding 2^-17), so A^2 is off by
+    ~1e-6 relative; it enters P through b_2 A^2 (b_2 = 0.12, ||A^2|| <= 0.06)
+    and U is formed as A (W' - b_1 I) + b_1 A so that only its O(A^3) part is
+    rounded: P is off by ~1e-7; the test allows `tol`."""
+    w = make_workload(name, nslices=S)
+    n = w["n"]
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=S)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(w["u"], dev), w["dt"], P, prec="bf16x3")
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
+    err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(S))
+    assert err <= tol, err
+
+
+def test_expm_bf16x3_paper_model_squarings(lbm, dev):
+    """s = 5 (four FP32 D-form squarings and one FP64): the ~1e-7 error of
+    the scaled approximant grows by about 2^s; the test allows 1e-5."""
+    from workloads import paper_grape_model
+
+    m = paper_grape_model(9)
+    Lb = O.lindbladian(m.H0, m.jumps)
+    Ld = O.drive_generator(m.X)
+    u = np.array([0.0, 0.05, -0.1])
+    ctx = lbm.Context(0, max_n=81, max_batch=1, max_slices=3)
+    P = torch.empty((3, 81, 81), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(u, dev), m.dt, P, prec="bf16x3")
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, u, m.dt)
+    err = max(_relf(P.cpu().numpy()[s], ref[s]) for s in range(3))
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("d,S,scale", [(2, 3, 0.2), (5, 2, 0.9), (7, 2, 3.0)])
+def test_expm_bf16x3_ragged_sizes(lbm, dev, d, S, scale):
+    """n = 4, 25, 49: tiles far from full (M, N, K < 128) exercise the
+    zero-filled TMA boxes."""
+    n = d * d
+    Lb, Ld = _gen_pair(d, 700 + d, scale)
+    u = np.linspace(-0.2, 0.3, S)
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=S)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(u, dev), 1.0, P, prec="bf16x3")
+    lbm.lb_sync_status(ctx)
+    for s in range(S):
+        ref = O.expm_pade13(Lb + u[s] * Ld)
+        assert _relf(P.cpu().numpy()[s], ref) <= 1e-5
+
+
+def test_propagate_bf16x3_d9_1000_steps(lbm, dev):
+    """The d = 9 batch in split-BF16 x3 on the tensor cores: max over states
+    of ||rho - rho_ref||_F after 1000 steps <= 1e-4 (with and without the
+    trace renormalisation)."""
+    w = make_workload("d9_batch")
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate(Ps[0], w["states"], w["steps_per_slice"])
+    ctx = lbm.Context(0, max_n=w["n"], max_batch=w["B"], max_slices=1)
+    for renorm in (True, False):
+        R = _t(w["states"], dev)
+        lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=w["steps_per_slice"], prec="bf16x3",
+                               renorm_trace=renorm)
+        lbm.lb_sync_status(ctx)
+        err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
+        assert err <= 1e-4, (renorm, err)
+
+
+@pytest.mark.parametrize("B,S,m", [(256, 3, 1), (37, 2, 2)])
+def test_propagate_bf16x3_d27(lbm, dev, B, S, m):
+    w = make_workload("d27_chain", B=B, nslices=S)
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate_chain(Ps, w["states"], m)
+    ctx = lbm.Context(0, max_n=729, max_batch=B, max_slices=S)
+    R = _t(w["states"], dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=m, prec="bf16x3", renorm_trace=True)
+    lbm.lb_sync_status(ctx)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
+    assert err <= 1e-5, err
