@@ -44,6 +44,7 @@ struct TcCfg {
   static constexpr int B_PLANE = BN * 128;
   static constexpr int STAGE_BYTES = 2 * NPA * A_PLANE + 2 * NPB * B_PLANE;
   static constexpr int SMEM = NSTAGE * STAGE_BYTES + 1024;
+  static_assert(TBM * (BN + 1) * 8 <= NSTAGE * STAGE_BYTES, "epilogue tile must fit in the ring");
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,9 +103,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __double2bfloat16(x);
-  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+// x ~ hi + lo, both BF16, computed in FP32 (the residual x - hi is exact).
+__device__ __forceinline__ void split2f(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Exact FP32 -> FP64 widening with integer operations only (FP64 arithmetic
+// runs at 1/64 of the FP32 rate on this part).  FP32 subnormals become 0.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  const uint64_t man = (uint64_t)(u & 0x7FFFFFu) << 29;
+  uint64_t d;
+  if (ex == 0)
+    d = sign;
+  else if (ex == 255)
+    d = sign | 0x7FF0000000000000ull | man;
+  else
+    d = sign | ((uint64_t)(ex + 896) << 52) | man;
+  return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ void put_planes(__nv_bfloat16* base, long long idx, long long plane, float re, float im) {
+  __nv_bfloat16 h, l;
+  split2f(re, h, l);
+  base[idx] = h;
+  base[idx + plane] = l;
+  split2f(im, h, l);
+  base[idx + 2 * plane] = h;
+  base[idx + 3 * plane] = l;
 }
 
 // Products kept: pieces (i, j) with i + j < max(NPA, NPB): for two pieces
@@ -209,8 +238,7 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
   const bool have = mbar_wait(su32(&acc_bar), 0);
   if (!have && tid == 0) atomicOr(P.err, ERR_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  const bool good = have && !give_up;
+  const bool good = __syncthreads_and(have ? 1 : 0) && !give_up;  // uniform across the CTA
   // the producer may still have copies in flight after a give-up: wait for
   // them (bounded) before the shared memory is released
   if (!good && tid == 0) {
@@ -220,62 +248,59 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     }
   }
   if (good) {
-    const int row = m0 + warp * 32 + lane;
-    const long long bs = (long long)b;
+    // The shared-memory ring is idle now (every copy was consumed by an MMA
+    // that has completed).  Stage the accumulator tile through it so that the
+    // global reads and writes of the epilogue are coalesced.
+    constexpr int LDS = TBN + 1;  // padded row of float2
+    float2* tile = (float2*)sm;
     for (int c0 = 0; c0 < TBN; c0 += 16) {
       float vr[16], vi[16];
       const uint32_t ta = tacc + ((uint32_t)(warp * 32) << 16) + c0;
       tmem_ld16(ta, vr);
       tmem_ld16(ta + TBN, vi);
-      if (row >= P.M) continue;
-#pragma unroll 4
-      for (int j = 0; j < 16; j++) {
-        const int col = n0 + c0 + j;
-        if (col >= P.N) break;
-        const double ar = (double)vr[j], ai = (double)vi[j];
-        const long long off = P.transC ? (long long)col * P.ldc + row : (long long)row * P.ldc + col;
-        double cr = P.alpha * ar, ci = P.alpha * ai;
-        double dr = P.alpha2 * ar, di = P.alpha2 * ai;
-        if (P.beta != 0.0) {
-          const z64 c0v = P.C[bs * P.sC + off];
-          cr = fma(P.beta, c0v.x, cr);
-          ci = fma(P.beta, c0v.y, ci);
-        }
-        for (int q = 0; q < P.nterms; q++) {
-          const z64 x = P.X[q][bs * P.sX[q] + off];
-          cr = fma(P.coef[q], x.x, cr);
-          ci = fma(P.coef[q], x.y, ci);
-          dr = fma(P.coef2[q], x.x, dr);
-          di = fma(P.coef2[q], x.y, di);
-        }
-        if (row == col) {
-          cr += P.gamma;
-          dr += P.gamma2;
-        }
-        P.C[bs * P.sC + off] = make_double2(cr, ci);
-        if (P.C2 != nullptr) P.C2[bs * P.sC + off] = make_double2(dr, di);
-        if (P.sp != nullptr) {  // row-major split planes of C (A-operand layout)
-          __nv_bfloat16 h, l;
-          const long long pb = bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col;
-          const double vr2 = (row == col) ? cr - P.sp_shift : cr;
-          split2(vr2, h, l);
-          P.sp[pb] = h;
-          P.sp[pb + P.sp_plane] = l;
-          split2(ci, h, l);
-          P.sp[pb + 2 * P.sp_plane] = h;
-          P.sp[pb + 3 * P.sp_plane] = l;
-        }
-        if (P.spT != nullptr) {  // transposed split planes (B-operand layout)
-          __nv_bfloat16 h, l;
-          const long long pb = bs * 4 * P.spT_plane + (long long)col * P.spT_ld + row;
-          const double vr2 = (row == col) ? cr - P.spT_shift : cr;
-          split2(vr2, h, l);
-          P.spT[pb] = h;
-          P.spT[pb + P.spT_plane] = l;
-          split2(ci, h, l);
-          P.spT[pb + 2 * P.spT_plane] = h;
-          P.spT[pb + 3 * P.spT_plane] = l;
-        }
+      const int r = warp * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < 16; j++) tile[r * LDS + c0 + j] = make_float2(vr[j], vi[j]);
+    }
+    __syncthreads();
+    const long long bs = (long long)b;
+    // row-major pass: consecutive threads take consecutive columns.  FP32
+    // arithmetic only; FP64 outputs are exact widenings plus the FP64
+    // diagonal term.
+    for (int e = tid; e < TBM * TBN; e += 128) {
+      const int r = e / TBN, cc = e - (e / TBN) * TBN;
+      const int row = m0 + r, col = n0 + cc;
+      if (row >= P.M || col >= P.N) continue;
+      const float2 a2 = tile[r * LDS + cc];
+      const long long off = bs * P.sC + (long long)row * P.ldc + col;
+      float cr = P.alpha * a2.x, ci = P.alpha * a2.y;
+      float dr = P.alpha2 * a2.x, di = P.alpha2 * a2.y;
+      for (int q = 0; q < P.nterms; q++) {
+        const float2 x = P.X[q][bs * P.sX[q] + (long long)row * P.ldc + col];
+        cr = fmaf(P.coef[q], x.x, cr);
+        ci = fmaf(P.coef[q], x.y, ci);
+        dr = fmaf(P.coef2[q], x.x, dr);
+        di = fmaf(P.coef2[q], x.y, di);
+      }
+      if (P.Cf != nullptr) P.Cf[off] = make_float2(cr, ci);
+      if (P.Cd != nullptr) P.Cd[off] = make_double2(row == col ? widen(cr) + P.gamma : widen(cr), widen(ci));
+      if (P.C2d != nullptr)
+        P.C2d[off] = make_double2(row == col ? widen(dr) + P.gamma2 : widen(dr), widen(di));
+      if (P.sp != nullptr)
+        put_planes(P.sp, bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col, P.sp_plane,
+                   row == col ? cr - P.sp_shift : cr, ci);
+      if (P.spT != nullptr) tile[r * LDS + cc] = make_float2(row == col ? cr - P.spT_shift : cr, ci);
+    }
+    if (P.spT != nullptr) {
+      // transposed planes (B-operand layout): consecutive threads take
+      // consecutive rows, which are contiguous in the transpose
+      __syncthreads();
+      for (int e = tid; e < TBM * TBN; e += 128) {
+        const int cc = e / TBM, r = e - (e / TBM) * TBM;
+        const int row = m0 + r, col = n0 + cc;
+        if (row >= P.M || col >= P.N) continue;
+        const float2 v = tile[r * LDS + cc];
+        put_planes(P.spT, bs * 4 * P.spT_plane + (long long)col * P.spT_ld + row, P.spT_plane, v.x, v.y);
       }
     }
   }
@@ -284,12 +309,14 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(2 * TBN));
 }
 
-// Split planes of a batch of complex matrices: dst[s][p][r][c] for the
+// Split planes of a batch of complex FP64 matrices: dst[s][p][r][c] for the
 // row-major form, or of the transpose (dst[s][p][c][r]) when trans != 0,
-// with `shift` subtracted from the diagonal first.
+// with `shift` subtracted from the diagonal first; np BF16 pieces per value
+// (the value is rounded to FP32 once, then split in FP32).  f32 (optional)
+// receives the FP32 copy, row-major.
 __global__ void split_kernel(int R, int Kc, long long total, const z64* __restrict__ src, long long lds,
                              long long ss, double shift, int trans, __nv_bfloat16* __restrict__ dst, long long ldd,
-                             long long plane, int np) {
+                             long long plane, int np, float2* __restrict__ f32) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long per = (long long)R * Kc;
@@ -305,29 +332,48 @@ __global__ void split_kernel(int R, int Kc, long long total, const z64* __restri
     }
     z64 v = src[s * ss + r * lds + c];
     if (r == c) v.x -= shift;
+    float xr = (float)v.x, xi = (float)v.y;
+    if (f32 != nullptr) f32[s * per + r * Kc + c] = make_float2(xr, xi);
     const long long d = s * 2 * np * plane + (trans ? c * ldd + r : r * ldd + c);
-    double xr = v.x, xi = v.y;
     for (int p = 0; p < np; p++) {  // x = sum of np BF16 pieces, each the rounding of what is left
-      const __nv_bfloat16 hr = __double2bfloat16(xr), hi = __double2bfloat16(xi);
+      const __nv_bfloat16 hr = __float2bfloat16_rn(xr), hi = __float2bfloat16_rn(xi);
       dst[d + p * plane] = hr;
       dst[d + (np + p) * plane] = hi;
-      xr -= (double)__bfloat162float(hr);
-      xi -= (double)__bfloat162float(hi);
+      xr -= __bfloat162float(hr);
+      xi -= __bfloat162float(hi);
     }
   }
 }
 
-// One warp per state: divide by the trace (when renorm) and write the state's
-// split planes (row b of the [4][B][ld] plane tensor).
-__global__ void renorm_split_kernel(int n, int d, int B, int renorm, z64* __restrict__ X,
+// Z = c0 X0 + c1 X1 + c2 X2 (FP32, n x n per slice), written only as the
+// two-piece planes of its transpose (B-operand layout).
+__global__ void lincomb_splitT_kernel(int n, long long total, const float2* __restrict__ X0,
+                                      const float2* __restrict__ X1, const float2* __restrict__ X2, float c0, float c1,
+                                      float c2, __nv_bfloat16* __restrict__ dst, long long ldd, long long plane) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / nn;
+    const long long o = e - s * nn;
+    const long long c = o / n, r = o - (o / n) * n;  // consecutive threads along r
+    const long long i = s * nn + r * n + c;
+    const float2 a = X0[i], b = X1[i], g = X2[i];
+    const float zr = fmaf(c0, a.x, fmaf(c1, b.x, c2 * g.x)), zi = fmaf(c0, a.y, fmaf(c1, b.y, c2 * g.y));
+    put_planes(dst, s * 4 * plane + c * ldd + r, plane, zr, zi);
+  }
+}
+
+// One warp per state (FP32): optional division by the trace, then the
+// state's two-piece planes (row b of the [4][B][ld] plane tensor).
+__global__ void renorm_split_kernel(int n, int d, int B, int renorm, float2* __restrict__ X,
                                     __nv_bfloat16* __restrict__ planes, long long ld, long long plane) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= B) return;
-  z64* x = X + (long long)w * n;
-  double cr = 1.0, ci = 0.0;
+  float2* x = X + (long long)w * n;
+  float cr = 1.f, ci = 0.f;
   if (renorm) {
-    double sr = 0.0, si = 0.0;
+    float sr = 0.f, si = 0.f;
     for (int k = lane; k < d; k += 32) {
       sr += x[k * (d + 1)].x;
       si += x[k * (d + 1)].y;
@@ -336,25 +382,35 @@ __global__ void renorm_split_kernel(int n, int d, int B, int renorm, z64* __rest
       sr += __shfl_xor_sync(0xffffffffu, sr, o);
       si += __shfl_xor_sync(0xffffffffu, si, o);
     }
-    const double m2 = sr * sr + si * si;
+    const float m2 = sr * sr + si * si;
     cr = sr / m2;
     ci = -si / m2;
   }
   for (int e = lane; e < n; e += 32) {
-    z64 v = x[e];
+    float2 v = x[e];
     if (renorm) {
-      v = make_double2(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
+      v = make_float2(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
       x[e] = v;
     }
-    const long long o = (long long)w * ld + e;
-    __nv_bfloat16 h, l;
-    split2(v.x, h, l);
-    planes[o] = h;
-    planes[o + plane] = l;
-    split2(v.y, h, l);
-    planes[o + 2 * plane] = h;
-    planes[o + 3 * plane] = l;
+    put_planes(planes, (long long)w * ld + e, plane, v.x, v.y);
   }
+}
+
+__global__ void states_c64_to_f32_kernel(long long total, const z64* __restrict__ a, float2* __restrict__ b) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+__global__ void states_f32_to_c64_kernel(long long total, const float2* __restrict__ a, z64* __restrict__ b) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    b[e] = make_double2(widen(a[e].x), widen(a[e].y));
+}
+
+unsigned grid_for(long long total) {
+  long long g = (total + 255) / 256;
+  return (unsigned)(g > 152LL * 16 ? 152LL * 16 : (g < 1 ? 1 : g));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -388,20 +444,39 @@ bool encode_planes(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, l
 long long plane_ld(int K) { return ((long long)K + 7) / 8 * 8; }
 
 cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, long long ss, double shift, int trans,
-                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np) {
+                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np, float2* f32) {
   const long long total = (long long)R * Kc * S;
-  long long g = (total + 255) / 256;
-  if (g > 152LL * 16) g = 152LL * 16;
   count_launch();
-  split_kernel<<<(unsigned)g, 256, 0, st>>>(R, Kc, total, src, lds, ss, shift, trans, dst, ldd, plane, np);
+  split_kernel<<<grid_for(total), 256, 0, st>>>(R, Kc, total, src, lds, ss, shift, trans, dst, ldd, plane, np, f32);
   return cudaGetLastError();
 }
 
-cudaError_t launch_renorm_split(int n, int d, int B, int renorm, z64* X, __nv_bfloat16* planes, long long ld,
+cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* X1, const float2* X2, float c0,
+                                  float c1, float c2, __nv_bfloat16* dst, long long ldd, long long plane,
+                                  cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  lincomb_splitT_kernel<<<grid_for(total), 256, 0, st>>>(n, total, X0, X1, X2, c0, c1, c2, dst, ldd, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, __nv_bfloat16* planes, long long ld,
                                 long long plane, cudaStream_t st) {
   const int grid = (B * 32 + 255) / 256;
   count_launch();
   renorm_split_kernel<<<grid, 256, 0, st>>>(n, d, B, renorm, X, planes, ld, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_states_c64_f32(long long count, const z64* a, float2* b, cudaStream_t st) {
+  count_launch();
+  states_c64_to_f32_kernel<<<grid_for(count), 256, 0, st>>>(count, a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_states_f32_c64(long long count, const float2* a, z64* b, cudaStream_t st) {
+  count_launch();
+  states_f32_to_c64_kernel<<<grid_for(count), 256, 0, st>>>(count, a, b);
   return cudaGetLastError();
 }
 

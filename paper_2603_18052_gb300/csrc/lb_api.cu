@@ -376,63 +376,71 @@ namespace {
 
 typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
 
-// The six Pade products in split-BF16 x3 on the tensor cores.  U is taken as
-// A (W' - b1 I) + b1 A so that the BF16 rounding touches only the small part
-// of W' = b1 I + O(A^2); V - U and V + U are formed in FP64 in the epilogue.
+// The six Pade products in split-BF16 x3 on the tensor cores, with every
+// intermediate kept in FP32 (FP64 arithmetic is 1/64 rate here):
+//   A2, A4, A6 = powers (FP32 copies + planes),  V = I + Vs,  W' = b1 I + Ws,
+//   Vs = A6 Z1 + b6 A6 + b4 A4 + b2 A2,  Ws = A6 Z2 + b7 A6 + b5 A4 + b3 A2,
+//   U = b1 A + A Ws, so the BF16 rounding touches only the O(A^3) part of U;
+//   V - U and V + U are written in FP64 with the identity added in FP64.
 lb_status pade_products_tc(lb_ctx* c, int n, int S, z64* P, cudaStream_t st) {
   const long long nn = (long long)n * n;
   const double* b = c->pade_b;
   const long long ld = plane_ld(n), pl = (long long)n * ld;
   __nv_bfloat16 *Aop = c->sp[0], *AopT = c->sp[1], *A2op = c->sp[2], *A2opT = c->sp[3], *A4op = c->sp[4],
                 *A6op = c->sp[5], *Z1T = c->sp[6], *Z2T = c->sp[7], *WT = c->sp[8];
-  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 0, Aop, ld, pl, st));
-  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 1, AopT, ld, pl, st));
-  auto prob = [&](const __nv_bfloat16* a, const __nv_bfloat16* bo, z64* C) {
+  // FP32 copies live in the (unused here) FP64 buffers
+  float2 *Af = (float2*)c->Z1, *A2f = (float2*)c->A2, *A4f = (float2*)c->A4, *A6f = (float2*)c->A6,
+         *Vsf = (float2*)c->V;
+  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 0, Aop, ld, pl, st, 2, Af));
+  LB_CUDA(launch_split(n, n, S, c->A, n, nn, 0.0, 1, AopT, ld, pl, st, 2));
+  auto prob = [&](const __nv_bfloat16* a, const __nv_bfloat16* bo) {
     TcProblem t;
     t.M = t.N = t.K = n;
     t.batch = S;
     t.Aop = a; t.a_ld = ld; t.a_plane = pl;
     t.Bop = bo; t.b_ld = ld; t.b_plane = pl;
-    t.C = C; t.ldc = n; t.sC = nn;
+    t.ldc = n; t.sC = nn;
     t.err = c->err_dev;
     return t;
   };
-  TcProblem t = prob(Aop, AopT, c->A2);
+  TcProblem t = prob(Aop, AopT);
+  t.Cf = A2f;
   t.sp = A2op; t.sp_ld = ld; t.sp_plane = pl;
   t.spT = A2opT; t.spT_ld = ld; t.spT_plane = pl;
   LB_CUDA(zgemm_tc(t, st));
-  t = prob(A2op, A2opT, c->A4);
+  t = prob(A2op, A2opT);
+  t.Cf = A4f;
   t.sp = A4op; t.sp_ld = ld; t.sp_plane = pl;
   LB_CUDA(zgemm_tc(t, st));
-  t = prob(A4op, A2opT, c->A6);
+  t = prob(A4op, A2opT);
+  t.Cf = A6f;
   t.sp = A6op; t.sp_ld = ld; t.sp_plane = pl;
   LB_CUDA(zgemm_tc(t, st));
-  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[12], b[10], b[8], c->Z1, st));
-  LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[13], b[11], b[9], c->Z2, st));
-  LB_CUDA(launch_split(n, n, S, c->Z1, n, nn, 0.0, 1, Z1T, ld, pl, st));
-  LB_CUDA(launch_split(n, n, S, c->Z2, n, nn, 0.0, 1, Z2T, ld, pl, st));
-  auto with3 = [&](TcProblem q, double c0, double c1, double c2, double gamma) {
+  LB_CUDA(launch_lincomb_splitT(n, S, A6f, A4f, A2f, (float)b[12], (float)b[10], (float)b[8], Z1T, ld, pl, st));
+  LB_CUDA(launch_lincomb_splitT(n, S, A6f, A4f, A2f, (float)b[13], (float)b[11], (float)b[9], Z2T, ld, pl, st));
+  auto with3 = [&](TcProblem q, double c0, double c1, double c2) {
     q.nterms = 3;
-    q.X[0] = c->A6; q.X[1] = c->A4; q.X[2] = c->A2;
+    q.X[0] = A6f; q.X[1] = A4f; q.X[2] = A2f;
     q.sX[0] = q.sX[1] = q.sX[2] = nn;
-    q.coef[0] = c0; q.coef[1] = c1; q.coef[2] = c2;
-    q.gamma = gamma;
+    q.coef[0] = (float)c0; q.coef[1] = (float)c1; q.coef[2] = (float)c2;
     return q;
   };
-  t = with3(prob(A6op, Z1T, c->V), b[6], b[4], b[2], b[0]);
+  t = with3(prob(A6op, Z1T), b[6], b[4], b[2]);
+  t.Cf = Vsf;
   LB_CUDA(zgemm_tc(t, st));
-  t = with3(prob(A6op, Z2T, c->W), b[7], b[5], b[3], b[1]);
-  t.spT = WT; t.spT_ld = ld; t.spT_plane = pl; t.spT_shift = b[1];
+  t = with3(prob(A6op, Z2T), b[7], b[5], b[3]);
+  t.spT = WT; t.spT_ld = ld; t.spT_plane = pl;
   LB_CUDA(zgemm_tc(t, st));
-  // acc = A (W' - b1 I):  Mx = V - b1 A - acc,  P = V + b1 A + acc
-  t = prob(Aop, WT, c->Mx);
-  t.alpha = -1.0;
+  // acc = A Ws:  V - U = b0 I + Vs - b1 A - acc,  V + U = b0 I + Vs + b1 A + acc
+  t = prob(Aop, WT);
+  t.alpha = -1.f; t.alpha2 = 1.f;
   t.nterms = 2;
-  t.X[0] = c->V; t.X[1] = c->A;
+  t.X[0] = Vsf; t.X[1] = Af;
   t.sX[0] = t.sX[1] = nn;
-  t.coef[0] = 1.0; t.coef[1] = -b[1];
-  t.C2 = P; t.alpha2 = 1.0;
-  t.coef2[0] = 1.0; t.coef2[1] = b[1];
+  t.coef[0] = 1.f; t.coef[1] = (float)(-b[1]);
+  t.coef2[0] = 1.f; t.coef2[1] = (float)b[1];
+  t.Cd = c->Mx; t.gamma = b[0];
+  t.C2d = P; t.gamma2 = b[0];
   LB_CUDA(zgemm_tc(t, st));
   return LB_OK;
 }
@@ -597,15 +605,16 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   }
   if (prec == LB_BF16X3) {
     // Split BF16 on the tensor cores: next = cur + D cur with D = P - I.  The
-    // states (A operand, rows = states) keep two BF16 pieces and are held in
-    // FP64 between steps; D (B operand) keeps three pieces, because its
-    // rounding repeats identically at every step and would otherwise add up
-    // coherently over long chains; five BF16 products per real product.
+    // states (A operand, rows = states) are FP32 and enter as two BF16
+    // pieces; D (B operand) keeps three pieces, because its rounding repeats
+    // identically at every step and would otherwise add up coherently over
+    // long chains; five BF16 products per real product, FP32 accumulation.
     const long long ld = plane_ld(n), dpl = (long long)n * ld, rpl = (long long)B * ld;
-    z64* cur = X;
-    z64* nxt = c->Rtmp;
+    float2* cur = (float2*)c->Rtmp;  // the FP64 scratch holds two FP32 state buffers
+    float2* nxt = cur + (long long)B * n;
     __nv_bfloat16* pc = c->spR[0];
     __nv_bfloat16* pn = c->spR[1];
+    LB_CUDA(launch_states_c64_f32((long long)B * n, X, cur, st));
     LB_CUDA(launch_renorm_split(n, d, B, 0, cur, pc, ld, rpl, st));
     for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
       const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
@@ -617,20 +626,20 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
           q.npa = 2; q.npb = 3;
           q.Aop = pc; q.a_ld = ld; q.a_plane = rpl;
           q.Bop = c->sp[0] + (long long)s * 6 * dpl; q.b_ld = ld; q.b_plane = dpl;
-          q.C = nxt; q.ldc = n;
-          q.nterms = 1; q.X[0] = cur; q.coef[0] = 1.0;
+          q.ldc = n;
+          q.nterms = 1; q.X[0] = cur; q.coef[0] = 1.f;
+          q.Cf = nxt;
           q.err = c->err_dev;
           if (!renorm_trace) {
             q.sp = pn; q.sp_ld = ld; q.sp_plane = rpl;
           }
           LB_CUDA(zgemm_tc(q, st));
           if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, nxt, pn, ld, rpl, st));
-          z64* t1 = cur; cur = nxt; nxt = t1;
+          float2* t1 = cur; cur = nxt; nxt = t1;
           __nv_bfloat16* t2 = pc; pc = pn; pn = t2;
         }
     }
-    if (cur != X)
-      LB_CUDA(cudaMemcpyAsync(X, cur, sizeof(z64) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
+    LB_CUDA(launch_states_f32_c64((long long)B * n, cur, X, st));
     return LB_OK;
   }
   // FP32: D = P - I in FP32, states in FP32

@@ -208,28 +208,39 @@ struct TcProblem {
   int npa = 2, npb = 2;  // BF16 pieces per value of A / B: (2, 2) or (2, 3); planes = 2 * pieces
   const __nv_bfloat16* Aop = nullptr; long long a_ld = 0, a_plane = 0;
   const __nv_bfloat16* Bop = nullptr; long long b_ld = 0, b_plane = 0;
-  z64* C = nullptr; long long ldc = 0, sC = 0;
-  int transC = 0;  // C (and the X terms) indexed [col][row] instead of [row][col]
-  double alpha = 1.0, beta = 0.0, gamma = 0.0;
+  // every output and X term is row-major [row][col] with leading dimension
+  // ldc and batch stride sC (sX for the X terms)
+  long long ldc = 0, sC = 0;
+  // r = alpha acc + sum_t coef_t X_t,  r2 = alpha2 acc + sum_t coef2_t X_t  (FP32)
+  float alpha = 1.f, alpha2 = 0.f;
   int nterms = 0;
-  const z64* X[4] = {nullptr, nullptr, nullptr, nullptr};
+  const float2* X[4] = {nullptr, nullptr, nullptr, nullptr};
   long long sX[4] = {0, 0, 0, 0};
-  double coef[4] = {0, 0, 0, 0};
-  z64* C2 = nullptr; double alpha2 = 0.0, gamma2 = 0.0;
-  double coef2[4] = {0, 0, 0, 0};
-  __nv_bfloat16* sp = nullptr; long long sp_ld = 0, sp_plane = 0; double sp_shift = 0.0;
-  __nv_bfloat16* spT = nullptr; long long spT_ld = 0, spT_plane = 0; double spT_shift = 0.0;
+  float coef[4] = {0, 0, 0, 0}, coef2[4] = {0, 0, 0, 0};
+  float2* Cf = nullptr;                  // r in FP32
+  z64* Cd = nullptr; double gamma = 0;   // r widened to FP64, + gamma on the diagonal
+  z64* C2d = nullptr; double gamma2 = 0; // r2 widened to FP64, + gamma2 on the diagonal
+  __nv_bfloat16* sp = nullptr; long long sp_ld = 0, sp_plane = 0; float sp_shift = 0.f;    // planes of r
+  __nv_bfloat16* spT = nullptr; long long spT_ld = 0, spT_plane = 0; float spT_shift = 0.f;  // of r^T
   unsigned int* err = nullptr;
 };
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
-// per state: optional division by the trace, then the row's split planes
-cudaError_t launch_renorm_split(int n, int d, int B, int renorm, z64* X, __nv_bfloat16* planes, long long ld,
+// Z = c0 X0 + c1 X1 + c2 X2 (FP32) written as the two-piece planes of Z^T
+cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* X1, const float2* X2, float c0,
+                                  float c1, float c2, __nv_bfloat16* dst, long long ldd, long long plane,
+                                  cudaStream_t st);
+// per FP32 state: optional division by the trace, then the row's two-piece planes
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, __nv_bfloat16* planes, long long ld,
                                 long long plane, cudaStream_t st);
+cudaError_t launch_states_c64_f32(long long count, const z64* a, float2* b, cudaStream_t st);
+cudaError_t launch_states_f32_c64(long long count, const float2* a, z64* b, cudaStream_t st);
 long long plane_ld(int K);
 // planes of src (R x Kc per slice) or of its transpose, diagonal shifted
 // np BF16 pieces per value: planes [S][2 np][..] (re pieces, then im pieces)
+// (f32, optional: FP32 copy of the shifted source, row-major R x Kc per slice)
 cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, long long ss, double shift, int trans,
-                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np = 2);
+                         __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np = 2,
+                         float2* f32 = nullptr);
 
 }  // namespace lb
 
