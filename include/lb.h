@@ -193,6 +193,38 @@ lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, co
                         void* stream);
 
 /*
+ * lb_run_instances -- many independent problems of mixed size in one call:
+ * for every instance i, its slice propagators
+ *   P_{i,s} = exp((Lbase_i + u_i[s] Ldrv_i) dt)      (Eq. 5, Algorithm 1)
+ * are built and its B_i states are propagated through its slices, each slice
+ * applied steps_per_slice times (Algorithm 2); states are overwritten.
+ * Instances are grouped by n = d*d and packed into chunks of whole instances
+ * of at most max_slices slices; each chunk's propagators are built in one
+ * batched pass, and for n <= 81 one launch propagates every instance of the
+ * chunk (one CTA per instance and group of up to 8 states).
+ *   inst  : HOST array of count descriptors; the pointers in it are device
+ *           memory (n x n generators, nslices controls, B x n states)
+ *   prec  : precision of the Pade products and of the propagation, as in
+ *           lb_expm_pade and lb_propagate_batch (for n <= 81 the reduced
+ *           forms propagate in FP32 with D = P - I)
+ *   renorm_trace : as in lb_propagate_batch (reduced forms only)
+ * Limits: n <= max_n; nslices <= max_slices per instance; for n > 81,
+ * B <= max_batch; at most 262144 slices and 262144 state groups per call
+ * (LB_EUNSUPPORTED beyond).  The host waits on the upload of the previous
+ * call's tables and on the squaring count of each chunk.
+ */
+typedef struct {
+  int d, nslices, steps_per_slice, B;
+  const lb_c64* Lbase;
+  const lb_c64* Ldrv;
+  const double* u;
+  lb_c64* states;
+} lb_instance;
+
+lb_status lb_run_instances(lb_ctx* ctx, const lb_instance* inst, int count, double dt, lb_precision prec,
+                           int renorm_trace, void* stream);
+
+/*
  * lb_propagate_batch_static -- the FP64 form of lb_propagate_batch for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this exists for applications whose device memory is already owned by their

@@ -133,6 +133,9 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add(nn * S * sizeof(float));                              // Dr
   add(nn * S * sizeof(float));                              // Di
   for (int i = 0; i < 4; i++) add((size_t)max_batch * max_n * sizeof(float));
+  add(nn * S * zb);                                          // Ginst
+  add(nn * S * zb);                                          // Pinst
+  add(inst_table_bytes());                                   // instance tables
   const size_t gbytes = grape_ws_bytes(max_n, max_batch, max_slices);
   add(gbytes);
   add(sizeof(unsigned int));                                // error word
@@ -174,13 +177,20 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->Ri = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
   c->Or = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
   c->Oi = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->Ginst = Z(nn * S);
+  c->Pinst = Z(nn * S);
+  c->inst_tab_bytes = inst_table_bytes();
+  c->inst_tab_dev = ar.take(c->inst_tab_bytes);
   c->grape = (z64*)ar.take(gbytes);
   c->grape_bytes = gbytes;
   c->err_dev = (unsigned int*)ar.take(sizeof(unsigned int));
   if (!c->err_dev || cudaMemset(c->err_dev, 0, sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&c->err_host, sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&c->scmax_host, sizeof(int)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_scmax, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_scmax, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tab, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(c->ev_tab, 0) != cudaSuccess ||
+      cudaMallocHost(&c->inst_tab_host, c->inst_tab_bytes) != cudaSuccess) {
     cudaGetLastError();
     lb_destroy(c);
     return LB_ENOMEM;
@@ -201,6 +211,8 @@ lb_status lb_destroy(lb_ctx* c) {
   if (c == nullptr) return LB_OK;
   DeviceGuard g(c->device);
   if (c->ev_scmax) cudaEventDestroy(c->ev_scmax);
+  if (c->ev_tab) cudaEventDestroy(c->ev_tab);
+  if (c->inst_tab_host) cudaFreeHost(c->inst_tab_host);
   for (int r = 0; r < lb_ctx::kRing; r++)
     for (int i = 0; i < 6; i++)
       if (c->ev_stage[r][i]) cudaEventDestroy(c->ev_stage[r][i]);
@@ -574,10 +586,19 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
   if (nslices == 0 || steps_per_slice == 0) return LB_OK;
   DeviceGuard g(c->device);
-  cudaStream_t st = (cudaStream_t)stream;
+  return lb::propagate_impl(c, n, nslices, (const z64*)P, steps_per_slice, B, (z64*)states, prec, renorm_trace,
+                            (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace lb {
+
+lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps_per_slice, int B, z64* X,
+                         lb_precision prec, int renorm_trace, cudaStream_t st) {
+  int d = 0;
+  is_square(n, &d);
   const long long nn = (long long)n * n;
-  const z64* Pz = (const z64*)P;
-  z64* X = (z64*)states;
   if (prec == LB_FP64) {
     if (resident_f64_fits(n)) {
       LB_CUDA(launch_propagate_resident_f64(n, nslices, Pz, steps_per_slice, B, X, c->sm_count, st));
@@ -666,5 +687,10 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   return LB_OK;
 }
 
-}  // extern "C"
+lb_status expm_chunk_public(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
+                            lb_precision prec, z64* P, int* s_out, cudaStream_t st) {
+  return expm_chunk(c, n, S, Lbase, Ldrv, u, dt, prec, P, s_out, st);
+}
+
+}  // namespace lb
 

@@ -75,6 +75,13 @@ struct lb_ctx {
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
   float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2
   float *Rr = nullptr, *Ri = nullptr, *Or = nullptr, *Oi = nullptr;  // max_batch x max_n
+  // --- many-instance batching (lb_run_instances) ---
+  lb::z64* Ginst = nullptr;  // per-slice generators, max_slices x max_n^2
+  lb::z64* Pinst = nullptr;  // their propagators
+  void* inst_tab_dev = nullptr;   // slice and work-item tables
+  void* inst_tab_host = nullptr;  // pinned staging of the tables
+  size_t inst_tab_bytes = 0;
+  cudaEvent_t ev_tab = nullptr;   // the last table upload
   // --- GRAPE (contexts with max_n <= 81) ---
   lb::z64* grape = nullptr;
   size_t grape_bytes = 0;
@@ -242,5 +249,13 @@ cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, lo
                          __nv_bfloat16* dst, long long ldd, long long plane, cudaStream_t st, int np = 2,
                          float2* f32 = nullptr);
 
+// Internal entry points shared by the C ABI functions.
+lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
+                         lb_precision prec, int renorm_trace, cudaStream_t st);
+size_t inst_table_bytes();
+lb_status expm_chunk_public(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
+                            lb_precision prec, z64* P, int* s_out, cudaStream_t st);
+
 }  // namespace lb
+
 

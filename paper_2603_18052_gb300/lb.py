@@ -44,7 +44,16 @@ EXPORTED = (
     "lb_propagate_batch",
     "lb_grape_grad",
     "lb_propagate_batch_static",
+    "lb_run_instances",
 )
+
+
+class Instance(ctypes.Structure):
+    """lb_instance: one problem of lb_run_instances (device pointers)."""
+
+    _fields_ = [("d", ctypes.c_int), ("nslices", ctypes.c_int), ("steps_per_slice", ctypes.c_int),
+                ("B", ctypes.c_int), ("Lbase", ctypes.c_void_p), ("Ldrv", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("states", ctypes.c_void_p)]
 
 
 class LBError(RuntimeError):
@@ -97,6 +106,8 @@ def lib():
     L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
     L.lb_propagate_batch_static.restype = i32
     L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
+    L.lb_run_instances.restype = i32
+    L.lb_run_instances.argtypes = [vp, ctypes.POINTER(Instance), i32, f64, i32, i32, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
     del ip, dp
@@ -253,3 +264,21 @@ def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
     _check(lib().lb_propagate_batch_static(n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
                                            _ptr(states, c128, "states", (B, n)), _stream(stream)),
            "lb_propagate_batch_static")
+
+
+def lb_run_instances(ctx, instances, dt, prec="fp64", renorm_trace=False, stream=None):
+    """Run many independent problems: ``instances`` is a list of dicts with
+    keys Lbase, Ldrv (n x n), u (nslices,), states (B x n, overwritten) and
+    optional steps_per_slice (default 1).  Tensors stay alive during the call."""
+    c128 = torch.complex128
+    arr = (Instance * len(instances))()
+    for i, x in enumerate(instances):
+        n = x["Lbase"].shape[0]
+        d = int(round(n ** 0.5))
+        S = x["u"].shape[0]
+        B = x["states"].shape[0]
+        arr[i] = Instance(d, S, int(x.get("steps_per_slice", 1)), B,
+                          _ptr(x["Lbase"], c128, "Lbase", (n, n)), _ptr(x["Ldrv"], c128, "Ldrv", (n, n)),
+                          _ptr(x["u"], torch.float64, "u", (S,)), _ptr(x["states"], c128, "states", (B, n)))
+    _check(lib().lb_run_instances(ctx.handle, arr, len(instances), float(dt), PRECISIONS.get(prec, prec),
+                                  int(bool(renorm_trace)), _stream(stream)), "lb_run_instances")

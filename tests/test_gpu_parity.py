@@ -414,3 +414,45 @@ def test_propagate_bf16x3_d27(lbm, dev, B, S, m):
     lbm.lb_sync_status(ctx)
     err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
     assert err <= 1e-5, err
+
+
+# --------------------------------------------------------- many instances
+
+def _instance_set(seed, spec):
+    """spec: list of (nq, nslices, B, steps_per_slice)."""
+    from workloads.rng import uniform01, stream_seed, ginibre_states
+
+    out = []
+    for k, (nq, S, B, m) in enumerate(spec):
+        mdl = transmon_chain(nq)
+        u = (2.0 * uniform01(stream_seed(seed, "u%d" % k), S) - 1.0) * 0.1
+        st = ginibre_states(stream_seed(seed, "s%d" % k), mdl.d, B)
+        out.append(dict(model=mdl, u=u, states=st, steps=m))
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_run_instances_matches_oracle(lbm, dev, prec, tol):
+    """Mixed d = 3 / 9 / 27 instances in one call, with chunks that hold
+    several whole instances (max_slices = 6), more than 8 states per
+    instance and several steps per slice."""
+    spec = [(1, 3, 1, 2), (2, 2, 11, 1), (1, 5, 9, 3), (3, 2, 5, 1), (2, 4, 3, 2), (1, 1, 20, 1), (2, 6, 2, 1)]
+    inst = _instance_set(0x5EED0003, spec)
+    ctx = lbm.Context(0, max_n=729, max_batch=32, max_slices=6)
+    keep, arg = [], []
+    for x in inst:
+        m = x["model"]
+        Lb = O.lindbladian(m.H0, m.jumps)
+        Ld = O.drive_generator(m.X)
+        t = dict(Lbase=_t(Lb, dev), Ldrv=_t(Ld, dev), u=_t(x["u"], dev), states=_t(x["states"], dev),
+                 steps_per_slice=x["steps"])
+        keep.append((Lb, Ld, t))
+        arg.append(t)
+    lbm.lb_run_instances(ctx, arg, 0.1, prec=prec, renorm_trace=(prec != "fp64"))
+    lbm.lb_sync_status(ctx)
+    for x, (Lb, Ld, t) in zip(inst, keep):
+        Ps = O.slice_propagators(Lb, Ld, x["u"], 0.1)
+        ref = O.propagate_chain(Ps, x["states"], x["steps"])
+        got = t["states"].cpu().numpy()
+        err = np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1))
+        assert err <= tol, (x["model"].d, err)
