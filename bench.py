@@ -192,6 +192,77 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours ---
 
+def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
+    """The mixed-size batch (d = 3 / 9 / 27 in ratio 8:4:1, 50 slices and
+    1..64 states each), scaled to ``count`` instances: one lb_run_instances
+    call (split-BF16 and FP64) against a loop of per-instance FP64
+    lb_expm_pade + lb_propagate_batch calls."""
+    import numpy as np
+    import torch
+
+    from workloads.configs import make_instances
+
+    inst, models = make_instances(count)
+
+    def dput(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    gens = {}
+    for q, m in models.items():
+        n = m.d * m.d
+        Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+        Ld = torch.empty_like(Lb)
+        lb.lb_assemble(ctx, dput(m.H0), dput(m.jumps), Lb)
+        lb.lb_assemble(ctx, dput(m.X), None, Ld)
+        gens[q] = (Lb, Ld)
+    dt = models[1].dt
+    us = [dput(x["u"]) for x in inst]
+    s0 = [dput(x["states"]) for x in inst]
+    st = [x.clone() for x in s0]
+    arg = [dict(Lbase=gens[x["nq"]][0], Ldrv=gens[x["nq"]][1], u=us[i], states=st[i]) for i, x in enumerate(inst)]
+
+    def reset():
+        for a, b in zip(st, s0):
+            a.copy_(b)
+
+    def timed(fn):
+        reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        lb.lb_sync_status(ctx)
+        return a.elapsed_time(b)
+
+    def per_instance():
+        for i, x in enumerate(inst):
+            S = len(x["u"])
+            n = x["d"] * x["d"]
+            Pv = Pbuf.view(-1)[: S * n * n].view(S, n, n)
+            lb.lb_expm_pade(ctx, gens[x["nq"]][0], gens[x["nq"]][1], us[i], dt, Pv, prec="fp64")
+            lb.lb_propagate_batch(ctx, Pv, st[i], steps_per_slice=1, prec="fp64")
+
+    lb.lb_run_instances(ctx, arg[:8], dt, prec="bf16x3", renorm_trace=True)  # warm-up
+    ms_mixed = timed(lambda: lb.lb_run_instances(ctx, arg, dt, prec="bf16x3", renorm_trace=True))
+    ms_fp64 = timed(lambda: lb.lb_run_instances(ctx, arg, dt, prec="fp64"))
+    ms_loop = timed(per_instance)
+    builds = sum(len(x["u"]) for x in inst)
+    ssteps = sum(len(x["u"]) * x["states"].shape[0] for x in inst)
+    import collections
+
+    counts = collections.Counter(x["d"] for x in inst)
+    res = {"workload": "%d instances (d=3/9/27: %d/%d/%d), 50 slices each, B~U{1..64}; %d builds, %d state-steps"
+                       % (count, counts[3], counts[9], counts[27], builds, ssteps)}
+    for k, ms in (("run_instances_bf16x3", ms_mixed), ("run_instances_fp64", ms_fp64),
+                  ("per_instance_fp64_launches", ms_loop)):
+        res[k] = {"ms": ms, "builds_per_s": builds / (ms / 1e3), "state_steps_per_s": ssteps / (ms / 1e3)}
+    res["speedup_fp64_batched_vs_per_instance"] = ms_loop / ms_fp64
+    res["speedup_bf16x3_batched_vs_per_instance_fp64"] = ms_loop / ms_mixed
+    return res
+
+
 def other_workloads(lb, accounting, dev, stream, reps=5):
     """Secondary measurements on the smaller workloads: the d = 3 single-state
     chain (latency per step), the d = 9 batch (FP64 and FP32 throughput), and
@@ -449,6 +520,7 @@ def run_ours(args):
         "clocks": mixed["clocks"],
     }
     line["other_workloads"] = other_workloads(lb, accounting, dev, stream)
+    line["other_workloads"]["mixed_instances"] = mixed_instances(lb, ctx, P, dev, stream, 128)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, 6)
     if rank == 0:

@@ -225,6 +225,36 @@ lb_status lb_run_instances(lb_ctx* ctx, const lb_instance* inst, int count, doub
                            int renorm_trace, void* stream);
 
 /*
+ * Warm-start network (GRAPE application of Sec. 2.5): a dense MLP with ReLU
+ * hidden layers and a linear output layer, BF16 weights and FP32
+ * accumulation.  Layer l maps dims[l] -> dims[l+1] (dims: HOST array of
+ * nlayers + 1 ints); its weights W_l (dims[l+1] x dims[l], row-major, BF16)
+ * and biases b_l (FP32) are packed back to back in W and b.  All arrays are
+ * device memory, row-major, batch rows.
+ *   lb_mlp_forward : acts (batch x sum_{l>=1} dims[l]) receives every layer's
+ *                    output, hidden layers after the ReLU; the last block is
+ *                    the network output.
+ *   lb_mlp_backward: from dy = dLoss/doutput (batch x dims[nlayers]) writes
+ *                    gW (FP32, packed like W) and gb; scratch holds
+ *                    2 * batch * max(dims) floats.
+ *   lb_mse_loss_grad: dy = 2 (y - t) / count and *loss = mean (y - t)^2
+ *                    (loss may be NULL).
+ *   lb_adam_step   : Adam with bias correction on FP32 parameters; p_bf16
+ *                    (optional) receives the BF16 copy used by the forward.
+ *   lb_adam_step_f64: the same on FP64 parameters; ascend != 0 maximises.
+ * These allocate nothing and return LB_EINVAL for bad sizes or pointers.
+ */
+lb_status lb_mlp_forward(int nlayers, const int* dims, int batch, const void* W, const float* b, const float* x,
+                         float* acts, void* stream);
+lb_status lb_mlp_backward(int nlayers, const int* dims, int batch, const void* W, const float* x, const float* acts,
+                          const float* dy, float* gW, float* gb, float* scratch, void* stream);
+lb_status lb_mse_loss_grad(long long count, const float* y, const float* t, float* dy, float* loss, void* stream);
+lb_status lb_adam_step(long long count, float* p, const float* g, float* m, float* v, void* p_bf16, float lr,
+                       float beta1, float beta2, float eps, int step, void* stream);
+lb_status lb_adam_step_f64(long long count, double* p, const double* g, double* m, double* v, double lr,
+                           double beta1, double beta2, double eps, int step, int ascend, void* stream);
+
+/*
  * lb_propagate_batch_static -- the FP64 form of lb_propagate_batch for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this exists for applications whose device memory is already owned by their

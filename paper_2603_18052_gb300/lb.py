@@ -45,6 +45,11 @@ EXPORTED = (
     "lb_grape_grad",
     "lb_propagate_batch_static",
     "lb_run_instances",
+    "lb_mlp_forward",
+    "lb_mlp_backward",
+    "lb_mse_loss_grad",
+    "lb_adam_step",
+    "lb_adam_step_f64",
 )
 
 
@@ -108,6 +113,18 @@ def lib():
     L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
     L.lb_run_instances.restype = i32
     L.lb_run_instances.argtypes = [vp, ctypes.POINTER(Instance), i32, f64, i32, i32, vp]
+    f32 = ctypes.c_float
+    ll = ctypes.c_longlong
+    L.lb_mlp_forward.restype = i32
+    L.lb_mlp_forward.argtypes = [i32, ctypes.POINTER(ctypes.c_int), i32, vp, vp, vp, vp, vp]
+    L.lb_mlp_backward.restype = i32
+    L.lb_mlp_backward.argtypes = [i32, ctypes.POINTER(ctypes.c_int), i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.lb_mse_loss_grad.restype = i32
+    L.lb_mse_loss_grad.argtypes = [ll, vp, vp, vp, vp, vp]
+    L.lb_adam_step.restype = i32
+    L.lb_adam_step.argtypes = [ll, vp, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]
+    L.lb_adam_step_f64.restype = i32
+    L.lb_adam_step_f64.argtypes = [ll, vp, vp, vp, vp, f64, f64, f64, f64, i32, i32, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
     del ip, dp
@@ -282,3 +299,46 @@ def lb_run_instances(ctx, instances, dt, prec="fp64", renorm_trace=False, stream
                           _ptr(x["u"], torch.float64, "u", (S,)), _ptr(x["states"], c128, "states", (B, n)))
     _check(lib().lb_run_instances(ctx.handle, arr, len(instances), float(dt), PRECISIONS.get(prec, prec),
                                   int(bool(renorm_trace)), _stream(stream)), "lb_run_instances")
+
+
+def _dims(dims):
+    return (ctypes.c_int * len(dims))(*[int(x) for x in dims])
+
+
+def lb_mlp_forward(dims, W_bf16, b, x, acts, stream=None):
+    """acts <- outputs of every layer (see include/lb.h)."""
+    nl = len(dims) - 1
+    batch = x.shape[0]
+    _check(lib().lb_mlp_forward(nl, _dims(dims), batch, _ptr(W_bf16, torch.bfloat16, "W"),
+                                _ptr(b, torch.float32, "b"), _ptr(x, torch.float32, "x"),
+                                _ptr(acts, torch.float32, "acts"), _stream(stream)), "lb_mlp_forward")
+
+
+def lb_mlp_backward(dims, W_bf16, x, acts, dy, gW, gb, scratch, stream=None):
+    nl = len(dims) - 1
+    batch = x.shape[0]
+    _check(lib().lb_mlp_backward(nl, _dims(dims), batch, _ptr(W_bf16, torch.bfloat16, "W"),
+                                 _ptr(x, torch.float32, "x"), _ptr(acts, torch.float32, "acts"),
+                                 _ptr(dy, torch.float32, "dy"), _ptr(gW, torch.float32, "gW"),
+                                 _ptr(gb, torch.float32, "gb"), _ptr(scratch, torch.float32, "scratch"),
+                                 _stream(stream)), "lb_mlp_backward")
+
+
+def lb_mse_loss_grad(y, t, dy, loss=None, stream=None):
+    _check(lib().lb_mse_loss_grad(y.numel(), _ptr(y, torch.float32, "y"), _ptr(t, torch.float32, "t"),
+                                  _ptr(dy, torch.float32, "dy"), _ptr(loss, torch.float32, "loss", allow_none=True),
+                                  _stream(stream)), "lb_mse_loss_grad")
+
+
+def lb_adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=None, stream=None):
+    _check(lib().lb_adam_step(p.numel(), _ptr(p, torch.float32, "p"), _ptr(g, torch.float32, "g"),
+                              _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
+                              _ptr(p_bf16, torch.bfloat16, "p_bf16", allow_none=True), float(lr), float(beta1),
+                              float(beta2), float(eps), int(step), _stream(stream)), "lb_adam_step")
+
+
+def lb_adam_step_f64(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, ascend=False, stream=None):
+    _check(lib().lb_adam_step_f64(p.numel(), _ptr(p, torch.float64, "p"), _ptr(g, torch.float64, "g"),
+                                  _ptr(m, torch.float64, "m"), _ptr(v, torch.float64, "v"), float(lr), float(beta1),
+                                  float(beta2), float(eps), int(step), int(bool(ascend)), _stream(stream)),
+           "lb_adam_step_f64")

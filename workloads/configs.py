@@ -50,3 +50,36 @@ def make_workload(name, B=None, nslices=None, steps_per_slice=None, seed=None):
                 jumps=model.jumps, u=u, states=states, nslices=S,
                 steps_per_slice=cfg["steps_per_slice"], B=cfg["B"], seed=cfg["seed"],
                 model=model)
+
+
+MIXED_INSTANCES = dict(count=4096, ratio=(8, 4, 1), nslices=50, Bmax=64, u_range=0.1, seed=SEED_BASE + 3)
+
+
+def make_instances(count=None, seed=None):
+    """The mixed-size batch: instances with d drawn from {3, 9, 27} in ratio
+    8:4:1 (exact counts by rounding, shuffled by the seed), 50 control slices
+    each with u ~ U(-0.1, 0.1), and B ~ U{1..64} Ginibre states.
+
+    Returns a list of dicts (nq, d, u, states) and the shared transmon models
+    per nq."""
+    cfg = dict(MIXED_INSTANCES)
+    if count is not None:
+        cfg["count"] = count
+    if seed is not None:
+        cfg["seed"] = seed
+    N, r = cfg["count"], cfg["ratio"]
+    tot = sum(r)
+    counts = [int(round(N * x / tot)) for x in r]
+    counts[0] += N - sum(counts)
+    nqs = np.concatenate([np.full(c, q) for q, c in zip((1, 2, 3), counts)]).astype(int)
+    perm = np.argsort(uniform01(stream_seed(cfg["seed"], "order"), N), kind="stable")
+    nqs = nqs[perm]
+    models = {q: transmon_chain(q) for q in (1, 2, 3)}
+    Bs = 1 + (uniform01(stream_seed(cfg["seed"], "batch"), N) * cfg["Bmax"]).astype(int)
+    out = []
+    for i in range(N):
+        q = int(nqs[i])
+        u = (2.0 * uniform01(stream_seed(cfg["seed"], "u%d" % i), cfg["nslices"]) - 1.0) * cfg["u_range"]
+        st = ginibre_states(stream_seed(cfg["seed"], "s%d" % i), models[q].d, int(Bs[i]))
+        out.append(dict(nq=q, d=models[q].d, u=u, states=st))
+    return out, models
