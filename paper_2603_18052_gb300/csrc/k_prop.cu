@@ -112,6 +112,81 @@ __global__ void __launch_bounds__(kResThreads)
   for (int e = tid; e < nb * n; e += blockDim.x) states[(long long)b0 * n + e] = make_double2(xr[e], xi[e]);
 }
 
+// Latency form for tiny n (n <= 16, d <= 4): one warp per state, no shared
+// memory and no block barrier in the step loop.  K = 32 / n lanes share a
+// row of P, each holding C = ceil(n / K) of its entries in registers (three
+// planes for the Gauss form); a step is C chained FMAs, a K-lane shuffle sum
+// and a shuffle broadcast of the new state to the lanes that need it.
+template <int MAXC>
+__global__ void __launch_bounds__(128)
+    prop_warp_f64_kernel(int n, int nslices, const z64* __restrict__ P, int steps_per_slice, int B,
+                         z64* __restrict__ states) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= B) return;  // whole warps leave together
+  const int K = 32 / n, C = (n + K - 1) / K;
+  const int r = lane / K, part = lane - (lane / K) * K;
+  const bool rowok = r < n;
+  const int j0 = part * C;
+  z64* x = states + (long long)w * n;
+  const long long nn = (long long)n * n;
+  double xr[MAXC], xi[MAXC], xs[MAXC], pr[MAXC], pi[MAXC], ps[MAXC];
+#pragma unroll
+  for (int c = 0; c < MAXC; c++) {
+    const int j = j0 + c;
+    z64 v = make_double2(0.0, 0.0);
+    if (c < C && j < n) v = x[j];
+    xr[c] = v.x;
+    xi[c] = v.y;
+    xs[c] = v.x + v.y;
+  }
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < nslices; s++) {
+#pragma unroll
+    for (int c = 0; c < MAXC; c++) {
+      const int j = j0 + c;
+      z64 v = make_double2(0.0, 0.0);
+      if (rowok && c < C && j < n) v = P[s * nn + (long long)r * n + j];
+      pr[c] = v.x;
+      pi[c] = v.y;
+      ps[c] = v.x + v.y;
+    }
+    for (int t = 0; t < steps_per_slice; t++) {
+      double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+      for (int c = 0; c < MAXC; c++) {
+        if (c < C) {
+          a1 = fma(pr[c], xr[c], a1);
+          a2 = fma(pi[c], xi[c], a2);
+          a3 = fma(ps[c], xs[c], a3);
+        }
+      }
+      double vr = a1 - a2, vi = a3 - a1 - a2;
+      // sum of the K parts of the row, at the row's first lane
+      re = vr;
+      im = vi;
+      for (int q = 1; q < K; q++) {
+        re += __shfl_down_sync(FULL, vr, q);
+        im += __shfl_down_sync(FULL, vi, q);
+      }
+      // every lane fetches the new entries of its columns from their rows' first lanes
+#pragma unroll
+      for (int c = 0; c < MAXC; c++) {
+        if (c < C) {
+          const int j = j0 + c;
+          const int src = (j < n ? j : 0) * K;
+          const double nr = __shfl_sync(FULL, re, src), ni = __shfl_sync(FULL, im, src);
+          xr[c] = (j < n) ? nr : 0.0;
+          xi[c] = (j < n) ? ni : 0.0;
+          xs[c] = xr[c] + xi[c];
+        }
+      }
+    }
+  }
+  if (rowok && part == 0 && (long long)nslices * steps_per_slice > 0) x[r] = make_double2(re, im);
+}
+
 __global__ void __launch_bounds__(kResThreads)
     prop_resident_f32_kernel(int n, int d, int nslices, const float* __restrict__ Dr,
                              const float* __restrict__ Di, int steps_per_slice, int B, int chunk,
@@ -356,6 +431,18 @@ cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int 
 cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P, int steps_per_slice, int B,
                                                z64* states, int adjoint, z64* hist, int sm_count,
                                                cudaStream_t st) {
+  if (n <= 16 && !adjoint && hist == nullptr) {
+    const int grid = (B * 32 + 127) / 128;
+    const int K = 32 / n, C = (n + K - 1) / K;
+    count_launch();
+    if (C <= 1)
+      prop_warp_f64_kernel<1><<<grid, 128, 0, st>>>(n, nslices, P, steps_per_slice, B, states);
+    else if (C <= 3)
+      prop_warp_f64_kernel<3><<<grid, 128, 0, st>>>(n, nslices, P, steps_per_slice, B, states);
+    else
+      prop_warp_f64_kernel<8><<<grid, 128, 0, st>>>(n, nslices, P, steps_per_slice, B, states);
+    return cudaGetLastError();
+  }
   int chunk = pick_chunk(B, sm_count);
   size_t smem = resident_f64_smem(n, chunk);
   while (smem > 227 * 1024 && chunk > 1) {

@@ -456,3 +456,24 @@ def test_run_instances_matches_oracle(lbm, dev, prec, tol):
         got = t["states"].cpu().numpy()
         err = np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1))
         assert err <= tol, (x["model"].d, err)
+
+
+@pytest.mark.parametrize("d,B,S,m", [(1, 3, 2, 5), (2, 1, 3, 50), (3, 7, 2, 10), (4, 33, 2, 4), (5, 2, 1, 6)])
+def test_propagate_fp64_small_n_forms(lbm, dev, d, B, S, m):
+    """n = 1, 4, 9, 16 take the one-warp latency kernel, n = 25 the shared
+    memory kernel."""
+    from workloads.rng import ginibre_states
+
+    n = d * d
+    Lb, Ld = _gen_pair(d, 800 + d, 0.3)
+    u = np.linspace(-0.2, 0.2, S)
+    Ps = np.array([O.expm_pade13(Lb + us * Ld) for us in u])
+    states = ginibre_states(900 + d, d, B)
+    ctx = lbm.Context(0, max_n=n, max_batch=B, max_slices=S)
+    R = _t(states, dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=m)
+    lbm.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, states, m)
+    Rg = R.cpu().numpy()
+    for b in range(B):
+        assert _relf(Rg[b], ref[b]) <= 1e-12
