@@ -73,6 +73,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const z64* __restrict__ B = P.B + b * P.sB;
     const int M = P.M, N = P.N, K = P.K;
 
+    // C +- A B with nothing else in the epilogue (the LU updates): start the
+    // Gauss accumulators from C and fold the sign into A, so the epilogue is
+    // the plain recombination (fewer FP64 instructions on a 1/64-rate pipe).
+    const bool fastC = GAUSS && P.beta == 1.0 && (P.alpha == 1.0 || P.alpha == -1.0) && P.nterms == 0 &&
+                       P.C2 == nullptr && P.gamma == 0.0;
     T acc1[TM][TN], acc2[TM][TN], acc3[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; i++)
@@ -81,11 +86,22 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         acc1[i][j] = T(0);
         acc2[i][j] = T(0);
         acc3[i][j] = T(0);
+        if (fastC) {
+          const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
+          if (gm < M && gn < N) {
+            const z64 c0 = P.C[b * P.sC + (long long)gm * P.ldc + gn];
+            acc1[i][j] = T(c0.x);
+            acc3[i][j] = T(c0.x + c0.y);
+          }
+        }
       }
 
+    // signs applied by flipping the sign bit (integer work, no FP64 multiply)
+    const unsigned long long SGN = 0x8000000000000000ull;
     const bool bT = (P.opB & 1) != 0;
-    const double bsign = (P.opB & 2) ? -1.0 : 1.0;
-    const double asign = P.conjA ? -1.0 : 1.0;
+    const unsigned long long bneg_im = (P.opB & 2) ? SGN : 0ull;
+    const unsigned long long aneg_re = (fastC && P.alpha < 0.0) ? SGN : 0ull;
+    const unsigned long long aneg_im = aneg_re ^ (P.conjA ? SGN : 0ull);
 
     for (int k0 = 0; k0 < K; k0 += BK) {
       // A tile (BM x BK), k contiguous in memory.
@@ -97,7 +113,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
           v = A[(long long)gm * P.lda + gk];
           if (gm == gk) v.x -= P.shiftA;
         }
-        const T re = T(v.x), im = T(asign * v.y);
+        const T re = T(__longlong_as_double(__double_as_longlong(v.x) ^ aneg_re));
+        const T im = T(__longlong_as_double(__double_as_longlong(v.y) ^ aneg_im));
         As[0][k][m] = re;
         As[1][k][m] = im;
         if (GAUSS) As[NPL - 1][k][m] = re + im;
@@ -112,7 +129,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
             v = B[(long long)gk * P.ldb + gn];
             if (gk == gn) v.x -= P.shiftB;
           }
-          const T re = T(v.x), im = T(bsign * v.y);
+          const T re = T(v.x), im = T(__longlong_as_double(__double_as_longlong(v.y) ^ bneg_im));
           Bs[0][k][nn] = re;
           Bs[1][k][nn] = im;
           if (GAUSS) Bs[NPL - 1][k][nn] = re + im;
@@ -126,7 +143,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
             v = B[(long long)gn * P.ldb + gk];
             if (gk == gn) v.x -= P.shiftB;
           }
-          const T re = T(v.x), im = T(bsign * v.y);
+          const T re = T(v.x), im = T(__longlong_as_double(__double_as_longlong(v.y) ^ bneg_im));
           Bs[0][k][nn] = re;
           Bs[1][k][nn] = im;
           if (GAUSS) Bs[NPL - 1][k][nn] = re + im;
@@ -195,6 +212,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         }
         const long long off = (long long)gm * P.ldc + gn;
         const long long idx = b * P.sC + off;
+        if (fastC) {  // C was folded into the accumulators
+          P.C[idx] = make_double2(pre, pim);
+          continue;
+        }
         double cr = P.alpha * pre, ci = P.alpha * pim;
         if (P.beta != 0.0) {
           const z64 c0 = P.C[idx];

@@ -97,9 +97,10 @@ class GateProblem:
         return (self.dc * F + 1.0) / (self.dc + 1.0)
 
 
-def grape(ctx, prob, u0, target=0.999, max_iter=300, lr=0.01):
+def grape(ctx, prob, u0, target=0.999, max_iter=300, lr=0.01, history=None):
     """Adam ascent of F from u0 (device float64, modified in place).  Returns
-    (iterations to reach F_avg >= target or max_iter, best F_avg, seconds)."""
+    (iterations to reach F_avg >= target or max_iter, best F_avg, seconds);
+    `history` (a list) receives F_avg of every iteration."""
     dev = u0.device
     u = u0
     g = torch.zeros_like(u)
@@ -113,6 +114,8 @@ def grape(ctx, prob, u0, target=0.999, max_iter=300, lr=0.01):
         lb.lb_grape_grad(ctx, prob.Lb, prob.Ld, u, DT, 1, prob.X0, prob.Xt, F, g)
         fa = prob.f_avg(float(F.item()))
         best = max(best, fa)
+        if history is not None:
+            history.append(fa)
         if fa >= target:
             break
         lb.lb_adam_step_f64(u, g, m, v, it, lr=lr, ascend=True)
@@ -199,7 +202,9 @@ def experiment(nq=1, n_train=128, n_test=8, max_iter=300, target=0.999, seed=0x5
                epochs=400, log=print):
     """Generate GRAPE solutions with the library, train the network on them,
     then compare iterations and wall time to the target fidelity from the
-    network's proposal and from a random start on held-out problems."""
+    network's proposal and from a random start on held-out problems.  Where
+    plain GRAPE does not reach the target within max_iter, the instance's
+    threshold is its best plain F_avg minus 1e-4."""
     dev = dev or torch.device("cuda:0")
     d = 3 ** nq
     ctx = lb.Context(dev.index or 0, max_n=d * d, max_batch=(2 ** nq) ** 2, max_slices=NSLICES)
@@ -226,23 +231,30 @@ def experiment(nq=1, n_train=128, n_test=8, max_iter=300, target=0.999, seed=0x5
     test = sample_problems(ctx, stream_seed(seed, "test"), n_test, nq, dev)
     rows = []
     for k, p in enumerate(test):
+        # plain GRAPE from a random start, run to max_iter: its best F_avg sets
+        # the instance's threshold min(target, F*_plain - 1e-4)
+        u_rand = random_u(stream_seed(seed, "test_u%d" % k), dev)
+        hist = []
+        _, best_r, t_full = grape(ctx, p, u_rand, target=2.0, max_iter=max_iter, history=hist)
+        thr = min(target, best_r - 1e-4)
+        it_r = next(i + 1 for i, f in enumerate(hist) if f >= thr)
+        t_r = t_full * it_r / len(hist)
         xin = torch.from_numpy(p.features()[None, :]).to(dev)
         u_warm = (net.predict(xin)[0].double() * U_SCALE).contiguous()
-        it_w, best_w, t_w = grape(ctx, p, u_warm, target=target, max_iter=max_iter)
-        u_rand = random_u(stream_seed(seed, "test_u%d" % k), dev)
-        it_r, best_r, t_r = grape(ctx, p, u_rand, target=target, max_iter=max_iter)
-        rows.append(dict(theta=p.theta, gamma1=p.gamma1, gamma_phi=p.gamma_phi, warm_iters=it_w, warm_best=best_w,
-                         warm_s=t_w, random_iters=it_r, random_best=best_r, random_s=t_r))
-        log("test %d: warm %d it (F_avg %.5f, %.2f s)  random %d it (F_avg %.5f, %.2f s)"
-            % (k, it_w, best_w, t_w, it_r, best_r, t_r))
+        it_w, best_w, t_w = grape(ctx, p, u_warm, target=thr, max_iter=max_iter)
+        rows.append(dict(theta=p.theta, gamma1=p.gamma1, gamma_phi=p.gamma_phi, threshold=thr, warm_iters=it_w,
+                         warm_best=best_w, warm_s=t_w, random_iters=it_r, random_best=best_r, random_s=t_r))
+        log("test %d: threshold %.5f  warm %d it (%.2f s)  random %d it (%.2f s)"
+            % (k, thr, it_w, t_w, it_r, t_r))
     ctx.close()
     med = lambda key: float(np.median([r[key] for r in rows]))
     return dict(nq=nq, d=d, nslices=NSLICES, dt=DT, target_f_avg=target, max_iter=max_iter, n_train=n_train,
                 n_test=n_test, dataset_seconds=t_data, train_seconds=t_train, final_loss=losses[-1],
                 median_warm_iters=med("warm_iters"), median_random_iters=med("random_iters"),
                 median_warm_seconds=med("warm_s"), median_random_seconds=med("random_s"),
-                warm_reached=sum(r["warm_best"] >= target for r in rows),
-                random_reached=sum(r["random_best"] >= target for r in rows), tests=rows)
+                warm_reached=sum(r["warm_best"] >= r["threshold"] for r in rows),
+                random_reached=sum(r["random_best"] >= r["threshold"] for r in rows),
+                target_reached_plain=sum(r["random_best"] >= target for r in rows), tests=rows)
 
 
 def main():
