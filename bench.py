@@ -52,7 +52,7 @@ DTYPES = {"bf16x3": "bf16 split (x3 build, x5 propagation) + f64", "fp32": "f32+
 PRECISION_DESC = {
     "bf16x3": "split-BF16 on tcgen05 tensor cores with FP32 accumulation: Pade products as hi+lo pieces "
               "(3 products per real product), propagation with D = P - I in three pieces and states in two "
-              "(5 products), FP64 states and per-step trace renormalisation; FP32 D-form squarings; FP64 norm, "
+              "(5 products), FP32 states and per-step trace renormalisation; FP32 D-form squarings; FP64 norm, "
               "LU and solve",
     "fp32": "FP32 Pade products, FP32 D-form squarings and FP32 propagation (D = P - I, per-step trace "
             "renormalisation); FP64 norm, LU and solve",
@@ -432,6 +432,9 @@ def run_ours(args):
         return dict(ms_per_step=total_ms / args.steps, phases=ph, build_stages_ms=stages,
                     launches=n1 - n0, clocks=clocks)
 
+    t_tune = time.perf_counter()
+    tuned = lb.lb_autotune(ctx, n, S, B)
+    t_tune = time.perf_counter() - t_tune
     sampler = ClockSampler(local)
     res = {"bf16x3": timed("bf16x3", sampler), "fp32": timed("fp32"), "fp64": timed("fp64")}
     head = min(("bf16x3", "fp32"), key=lambda f: res[f]["ms_per_step"])
@@ -516,6 +519,7 @@ def run_ours(args):
             "fp64": prop_roof("fp64", FP64_PEAK, "8 n^2 FLOP per state-step against the DFMA peak")},
         "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": "state-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "autotune": {"shapes": tuned, "seconds": t_tune},
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
     }

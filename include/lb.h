@@ -80,10 +80,41 @@ lb_status lb_destroy(lb_ctx* ctx);
 
 /*
  * Synchronise `stream`, then report (and clear) the device error word:
- * LB_ENONFINITE, LB_ESINGULAR or LB_ETIMEOUT, else LB_OK.  A CUDA error met
+ * LB_ENONFINITE, LB_ESINGULAR, LB_ETIMEOUT, or LB_EUNSUPPORTED (a squaring
+ * count above the bound of lb_set_max_squarings), else LB_OK.  A CUDA error met
  * while synchronising gives LB_ECUDA.
  */
 lb_status lb_sync_status(lb_ctx* ctx, void* stream);
+
+/*
+ * lb_set_max_squarings: with bound >= 0, every later lb_expm_pade and
+ * lb_run_instances runs exactly `bound` masked squaring rounds (slices that
+ * need fewer skip the extra ones on the device) instead of reading the
+ * largest squaring count back to the host.  This makes those calls free of
+ * host waits, so they can be captured in a CUDA graph.  A slice that needs
+ * more than `bound` squarings sets the error word: lb_sync_status then
+ * returns LB_EUNSUPPORTED (and that slice's P is not valid).  bound < 0
+ * restores the default.  Without a bound, lb_expm_pade and
+ * lb_run_instances return LB_EUNSUPPORTED when the stream is capturing.
+ * While capturing lb_run_instances, its tables are uploaded from the
+ * context's pinned staging buffer when the graph runs: do not replay such a
+ * graph after another lb_run_instances call on the same context.  Limits:
+ * bound <= 64.
+ */
+lb_status lb_set_max_squarings(lb_ctx* ctx, int bound);
+
+/*
+ * lb_autotune: choose the GEMM tile configuration for every launch shape of
+ * an n-sized propagator build over nslices slices (its LU updates, back
+ * substitution and FP32 products) and of a B-state FP64 propagation step:
+ * each such launch is run once per candidate configuration on the context's
+ * scratch, timed with CUDA events, and the fastest is recorded in a
+ * process-wide table that later calls of the same shape use (other shapes
+ * keep the tile-count rule).  Synchronises `stream`; takes a few seconds for
+ * n = 729 and 200 slices; must not be called while capturing.
+ * *shapes_out (may be NULL) receives the number of recorded shapes.
+ */
+lb_status lb_autotune(lb_ctx* ctx, int n, int nslices, int B, int* shapes_out, void* stream);
 
 /* Bytes of device scratch owned by the context. */
 unsigned long long lb_workspace_bytes(const lb_ctx* ctx);

@@ -328,6 +328,10 @@ __global__ void __launch_bounds__(256) lu_diag_kernel(int n, int k0, int kb, con
   }
 }
 
+__global__ void check_bound_kernel(const int* __restrict__ sc_max, int bound, unsigned int* err) {
+  if (threadIdx.x == 0 && *sc_max > bound) atomicOr(err, ERR_SQUARING_BOUND);
+}
+
 inline unsigned grid_for(long long total, int threads, int sm_count) {
   long long g = (total + threads - 1) / threads;
   long long cap = (long long)sm_count * 16;
@@ -412,6 +416,12 @@ cudaError_t launch_copy_active(long long nn, int S, const z64* src, z64* dst, co
 cudaError_t launch_check_finite(long long count, const z64* x, unsigned int* err, cudaStream_t st) {
   count_launch();
   check_finite_kernel<<<grid_for(count, 256, 152), 256, 0, st>>>(count, x, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_bound(const int* sc_max, int bound, unsigned int* err, cudaStream_t st) {
+  count_launch();
+  check_bound_kernel<<<1, 32, 0, st>>>(sc_max, bound, err);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,9 @@
 #include "lb_internal.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace lb {
 
@@ -281,20 +284,101 @@ long long count_tiles(const ZGemmProblem* probs, int nprob, int BM, int BN) {
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------------------------ autotuner --
+// A launch "shape" is the precision, the number of problems and each
+// problem's (M, N, K, batch, opB, beta).  In tuning mode every launch times
+// each candidate tile configuration (CUDA events, host wait) and records the
+// fastest for its shape; afterwards launches of a recorded shape use it, and
+// other shapes use the tile-count heuristic.
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int,
+                   int, int>
+    ShapeKey;
+std::mutex g_tune_mu;
+std::map<ShapeKey, int> g_tune;
+bool g_tuning = false;
+
+ShapeKey shape_key(int prec, const ZGemmProblem* p, int np) {
+  int v[20] = {0};
+  for (int i = 0; i < np && i < 4; i++) {
+    v[5 * i] = p[i].M;
+    v[5 * i + 1] = p[i].N;
+    v[5 * i + 2] = p[i].K;
+    v[5 * i + 3] = p[i].batch;
+    v[5 * i + 4] = p[i].opB * 4 + (p[i].beta != 0.0 ? 2 : 0) + (p[i].active != nullptr ? 1 : 0);
+  }
+  return ShapeKey(prec, np, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11], v[12], v[13],
+                  v[14], v[15], v[16], v[17], v[18], v[19]);
+}
+
+typedef cudaError_t (*cfg_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+
+cudaError_t run_tuned(int prec, const cfg_fn* cands, int ncand, int heuristic, const ZGemmProblem* probs, int nprob,
+                      int sm_count, cudaStream_t st) {
+  const ShapeKey key = shape_key(prec, probs, nprob);
+  bool tuning;
+  int choice = heuristic;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tuning = g_tuning;
+    auto it = g_tune.find(key);
+    if (!tuning && it != g_tune.end()) choice = it->second;
+  }
+  if (!tuning) return cands[choice](probs, nprob, sm_count, st);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+  float best = 1e30f;
+  int besti = heuristic;
+  for (int c = 0; c < ncand; c++) {
+    cudaError_t e = cands[c](probs, nprob, sm_count, st);  // warm-up
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(e0, st);
+    e = cands[c](probs, nprob, sm_count, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess) return e;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return cudaErrorUnknown;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      besti = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = besti;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+void set_tuning(bool on) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuning = on;
+}
+
+int tuned_shapes() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
+
 cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
-  // 32x32 tiles when there are enough of them to balance the persistent grid,
-  // else 16x16 tiles.
+  static const cfg_fn cands[3] = {launch_cfg<double, 16, 16, 1, 1, true>, launch_cfg<double, 32, 32, 2, 2, true>,
+                                  launch_cfg<double, 64, 64, 4, 4, true>};
+  // heuristic: 32x32 tiles when there are enough of them to balance the
+  // persistent grid, else 16x16 tiles
   const long long t32 = count_tiles(probs, nprob, 32, 32);
-  if (t32 >= 8LL * sm_count) return launch_cfg<double, 32, 32, 2, 2, true>(probs, nprob, sm_count, st);
-  return launch_cfg<double, 16, 16, 1, 1, true>(probs, nprob, sm_count, st);
+  return run_tuned(64, cands, 3, t32 >= 8LL * sm_count ? 1 : 0, probs, nprob, sm_count, st);
 }
 
 cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
+  static const cfg_fn cands[2] = {launch_cfg<float, 32, 32, 2, 2, false>, launch_cfg<float, 64, 64, 4, 4, false>};
   const long long t64 = count_tiles(probs, nprob, 64, 64);
-  if (t64 >= 4LL * sm_count) return launch_cfg<float, 64, 64, 4, 4, false>(probs, nprob, sm_count, st);
-  return launch_cfg<float, 32, 32, 2, 2, false>(probs, nprob, sm_count, st);
+  return run_tuned(32, cands, 2, t64 >= 4LL * sm_count ? 1 : 0, probs, nprob, sm_count, st);
 }
 
 }  // namespace lb

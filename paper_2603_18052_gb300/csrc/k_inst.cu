@@ -213,7 +213,12 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
   cudaStream_t st = (cudaStream_t)stream;
   lb_status rs = [&]() -> lb_status {
     // the pinned staging of the previous call must have reached the device
-    LB_CUDA(cudaEventSynchronize(c->ev_tab));
+    // (while capturing, the upload is a graph node that reads the staging at
+    // replay, and the host may not wait)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    if (capturing && c->max_squarings < 0) return LB_EUNSUPPORTED;
+    if (!capturing) LB_CUDA(cudaEventSynchronize(c->ev_tab));
     GenEntry* htab = (GenEntry*)c->inst_tab_host;
     WorkItem* hitem = (WorkItem*)((char*)c->inst_tab_host + (size_t)kMaxEntries * sizeof(GenEntry));
     GenEntry* dtab = (GenEntry*)c->inst_tab_dev;
@@ -262,7 +267,7 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
     }
     LB_CUDA(cudaMemcpyAsync(dtab, htab, sizeof(GenEntry) * te, cudaMemcpyHostToDevice, st));
     if (ti > 0) LB_CUDA(cudaMemcpyAsync(ditem, hitem, sizeof(WorkItem) * ti, cudaMemcpyHostToDevice, st));
-    LB_CUDA(cudaEventRecord(c->ev_tab, st));
+    if (!capturing) LB_CUDA(cudaEventRecord(c->ev_tab, st));
     for (const Chunk& ch : chunks) {
       if (ch.S == 0) continue;
       const int n = ch.n;
@@ -281,11 +286,11 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
         const bool f32 = prec != LB_FP64;
         const size_t smem = worklist_smem(n, 8, f32);
         if (f32) {
-          LB_CUDA(cudaFuncSetAttribute(worklist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          LB_CUDA(set_smem_once((const void*)worklist_kernel<true>, smem));
           count_launch();
           worklist_kernel<true><<<ch.items, 256, smem, st>>>(n, d, 8, ditem + ch.item0, renorm_trace);
         } else {
-          LB_CUDA(cudaFuncSetAttribute(worklist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          LB_CUDA(set_smem_once((const void*)worklist_kernel<false>, smem));
           count_launch();
           worklist_kernel<false><<<ch.items, 256, smem, st>>>(n, d, 8, ditem + ch.item0, 0);
         }

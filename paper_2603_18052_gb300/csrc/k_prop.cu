@@ -450,8 +450,7 @@ cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P,
     smem = resident_f64_smem(n, chunk);
   }
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(prop_resident_f64_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once((const void*)prop_resident_f64_kernel, smem);
   if (e != cudaSuccess) return e;
   const int grid = (B + chunk - 1) / chunk;
   count_launch();
@@ -477,8 +476,7 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
     smem = resident_f32_smem(n, chunk);
   }
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(prop_resident_f32_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once((const void*)prop_resident_f32_kernel, smem);
   if (e != cudaSuccess) return e;
   const int grid = (B + chunk - 1) / chunk;
   count_launch();

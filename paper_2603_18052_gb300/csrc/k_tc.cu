@@ -489,13 +489,8 @@ cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
   if (!encode_planes(&ma, p.Aop, p.M, p.K, p.a_ld, p.a_plane, 2 * NPA * p.batch, TBM) ||
       !encode_planes(&mb, p.Bop, p.N, p.K, p.b_ld, p.b_plane, 2 * NPB * p.batch, BN))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zgemm_tc_kernel<NPA, NPB, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = set_smem_once((const void*)zgemm_tc_kernel<NPA, NPB, BN>, Cfg::SMEM);
+  if (e != cudaSuccess) return e;
   dim3 grid((p.N + BN - 1) / BN, (p.M + TBM - 1) / TBM, p.batch);
   count_launch();
   zgemm_tc_kernel<NPA, NPB, BN><<<grid, 128, Cfg::SMEM, st>>>(ma, mb, p);

@@ -11,9 +11,25 @@
 
 using namespace lb;
 
+#include <map>
+#include <mutex>
+
 namespace lb {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t set_smem_once(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[std::make_pair(dev, kernel)];
+  if (bytes <= cur) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 }  // namespace lb
 
 namespace {
@@ -264,6 +280,21 @@ lb_status lb_sync_status(lb_ctx* c, void* stream) {
   if (w & ERR_NONFINITE) return LB_ENONFINITE;
   if (w & ERR_SINGULAR) return LB_ESINGULAR;
   if (w & ERR_TIMEOUT) return LB_ETIMEOUT;
+  if (w & ERR_SQUARING_BOUND) return LB_EUNSUPPORTED;
+  return LB_OK;
+}
+
+lb_status lb_autotune(lb_ctx* c, int n, int nslices, int B, int* shapes_out, void* stream) {
+  if (c == nullptr || n < 1 || n > c->max_n || nslices < 1 || nslices > c->max_slices || B < 1 ||
+      B > c->max_batch)
+    return LB_EINVAL;
+  DeviceGuard g(c->device);
+  return lb::autotune_impl(c, n, nslices, B, (cudaStream_t)stream, shapes_out);
+}
+
+lb_status lb_set_max_squarings(lb_ctx* c, int bound) {
+  if (c == nullptr || bound > 64) return LB_EINVAL;
+  c->max_squarings = bound < 0 ? -1 : bound;
   return LB_OK;
 }
 
@@ -474,8 +505,12 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   }
   LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, c->kmix, s_out,
                                c->err_dev, c->sm_count, st));
-  LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+  if (c->max_squarings < 0) {
+    LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+  } else {
+    LB_CUDA(launch_check_bound(c->sc + S, c->max_squarings, c->err_dev, st));
+  }
   if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
   if (prec == LB_BF16X3) {
     lb_status r = pade_products_tc(c, n, S, P, st);
@@ -520,8 +555,11 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
   // squarings, FP64.  The count is known on the host once the event that
   // follows the norm kernel has completed (long before the LU finishes).
-  LB_CUDA(cudaEventSynchronize(c->ev_scmax));
-  const int smax = *c->scmax_host;
+  int smax = c->max_squarings;
+  if (smax < 0) {
+    LB_CUDA(cudaEventSynchronize(c->ev_scmax));
+    smax = *c->scmax_host;
+  }
   // In the mixed forms a squaring whose operand is still close to I (the
   // leading kmix[s] ones, while ||A||_1 2^(j-s) <= 1) runs on D = P - I:
   // P^2 = 2P - I + D D, with only D D in the product precision; later
@@ -565,6 +603,11 @@ lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const
   if (nslices == 0) return LB_OK;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->max_squarings < 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return LB_EUNSUPPORTED;  // the host read of the squaring count cannot be captured
+  }
   const long long nn = (long long)n * n;
   for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
     const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
@@ -685,6 +728,25 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   }
   if (!resident) LB_CUDA(launch_states_from_f32(n, B, cr, ci, X, st));
   return LB_OK;
+}
+
+lb_status autotune_impl(lb_ctx* c, int n, int nslices, int B, cudaStream_t st, int* shapes_out) {
+  const long long nn = (long long)n * n;
+  // zero generators: A = 0, so s = 0 and V - U = I; the values do not matter,
+  // only the launch shapes (every tuned launch runs several times)
+  LB_CUDA(cudaMemsetAsync(c->Ginst, 0, sizeof(z64) * nn * nslices, st));
+  set_tuning(true);
+  lb_status r = expm_chunk(c, n, nslices, c->Ginst, nullptr, nullptr, 1.0, LB_FP32, c->Pinst, nullptr, st);
+  if (r == LB_OK && n > 81 && (long long)B * n <= nn * c->max_slices) {
+    LB_CUDA(cudaMemsetAsync(c->W, 0, sizeof(z64) * B * n, st));
+    r = propagate_impl(c, n, 1, c->Pinst, 1, B, c->W, LB_FP64, 0, st);
+  }
+  set_tuning(false);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ECUDA;
+  LB_CUDA(cudaMemsetAsync(c->err_dev, 0, sizeof(unsigned int), st));
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ECUDA;
+  if (shapes_out) *shapes_out = tuned_shapes();
+  return r;
 }
 
 lb_status expm_chunk_public(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,

@@ -15,6 +15,7 @@ enum : unsigned int {
   ERR_NONFINITE = 1u,
   ERR_SINGULAR = 2u,
   ERR_TIMEOUT = 4u,
+  ERR_SQUARING_BOUND = 8u,  // a slice needed more squarings than the fixed bound
 };
 
 constexpr int kMaxN = 729;
@@ -50,6 +51,7 @@ struct lb_ctx {
   unsigned int* err_host = nullptr; // pinned copy
   int* scmax_host = nullptr;        // pinned: largest squaring count of the last build
   cudaEvent_t ev_scmax = nullptr;
+  int max_squarings = -1;  // >= 0: fixed squaring rounds, no host read (graph capture)
   double pade_b[14];
   // --- stage timers of lb_expm_pade (CUDA events in a ring, optional) ---
   int timing = 0;
@@ -115,6 +117,11 @@ struct ZGemmProblem {
 
 // Launch up to 4 problems in one grouped launch.  Returns a CUDA error code.
 cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
+
+// Autotuner: in tuning mode every GEMM launch times its candidate tile
+// configurations and records the fastest for its shape (see k_gemm.cu).
+void set_tuning(bool on);
+int tuned_shapes();
 
 // FP32 variant (operands rounded to FP32, FP32 accumulation, FP64 epilogue).
 cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
@@ -253,8 +260,16 @@ cudaError_t launch_split(int R, int Kc, int S, const z64* src, long long lds, lo
 lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
                          lb_precision prec, int renorm_trace, cudaStream_t st);
 size_t inst_table_bytes();
+lb_status autotune_impl(lb_ctx* c, int n, int nslices, int B, cudaStream_t st, int* shapes_out);
 lb_status expm_chunk_public(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
                             lb_precision prec, z64* P, int* s_out, cudaStream_t st);
+
+// err |= ERR_SQUARING_BOUND when *sc_max > bound
+cudaError_t launch_check_bound(const int* sc_max, int bound, unsigned int* err, cudaStream_t st);
+
+// Raise a kernel's dynamic shared-memory limit only when a larger size is
+// needed (no host API call on repeated launches, e.g. during graph capture).
+cudaError_t set_smem_once(const void* kernel, size_t bytes);
 
 }  // namespace lb
 

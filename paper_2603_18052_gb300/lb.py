@@ -37,6 +37,8 @@ EXPORTED = (
     "lb_sync_status",
     "lb_workspace_bytes",
     "lb_launch_count",
+    "lb_set_max_squarings",
+    "lb_autotune",
     "lb_set_stage_timing",
     "lb_stage_times",
     "lb_assemble",
@@ -97,6 +99,10 @@ def lib():
     L.lb_sync_status.argtypes = [vp, vp]
     L.lb_workspace_bytes.restype = ctypes.c_ulonglong
     L.lb_workspace_bytes.argtypes = [vp]
+    L.lb_autotune.restype = i32
+    L.lb_autotune.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_int), vp]
+    L.lb_set_max_squarings.restype = i32
+    L.lb_set_max_squarings.argtypes = [vp, i32]
     L.lb_launch_count.restype = ctypes.c_ulonglong
     L.lb_launch_count.argtypes = []
     L.lb_set_stage_timing.restype = i32
@@ -185,6 +191,21 @@ class Context:
     @property
     def workspace_bytes(self):
         return int(lib().lb_workspace_bytes(self.handle))
+
+
+def lb_autotune(ctx, n, nslices, B, stream=None):
+    """Tune GEMM tiles for the launch shapes of an n-sized build over nslices
+    slices and a B-state propagation step; returns the number of tuned shapes."""
+    k = ctypes.c_int(0)
+    _check(lib().lb_autotune(ctx.handle, int(n), int(nslices), int(B), ctypes.byref(k), _stream(stream)),
+           "lb_autotune")
+    return int(k.value)
+
+
+def lb_set_max_squarings(ctx, bound):
+    """Fixed number of squaring rounds (>= 0) so that builds can be captured
+    in a CUDA graph; -1 restores the host read of the squaring count."""
+    _check(lib().lb_set_max_squarings(ctx.handle, int(bound)), "lb_set_max_squarings")
 
 
 def lb_launch_count():

@@ -1,0 +1,115 @@
+"""CUDA-graph capture of the build and the propagation (fixed squaring
+bound, no host waits): a replayed graph gives the same states as the
+uncaptured calls; without a bound the calls refuse to be captured; a slice
+that needs more squarings than the bound is reported."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2603_18052_gb300 import _build, lb
+
+    _build.build()
+    assert torch.cuda.is_available()
+    return lb
+
+
+def _setup(lbm, prec):
+    dev = torch.device("cuda:0")
+    w = make_workload("d9_batch", B=16, nslices=3, steps_per_slice=4)
+    w["u"] = np.array([0.05, -0.07, 0.09])
+    n = w["n"]
+    ctx = lbm.Context(0, max_n=n, max_batch=16, max_slices=3)
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Lb = put(O.lindbladian(w["H0"], w["jumps"]))
+    Ld = put(O.drive_generator(w["X"]))
+    u = put(w["u"])
+    P = torch.empty((3, n, n), dtype=torch.complex128, device=dev)
+    s0 = put(w["states"])
+    return ctx, w, Lb, Ld, u, P, s0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_captured_build_and_propagation_replay(lbm, prec):
+    ctx, w, Lb, Ld, u, P, s0 = _setup(lbm, prec)
+    lbm.lb_set_max_squarings(ctx, 4)
+
+    def step(R):
+        lbm.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P, prec=prec)
+        lbm.lb_propagate_batch(ctx, P, R, steps_per_slice=4, prec=prec, renorm_trace=(prec != "fp64"))
+
+    ref = s0.clone()
+    step(ref)  # uncaptured (also initialises the library's lazy state)
+    lbm.lb_sync_status(ctx)
+    R = s0.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(R)
+    for _ in range(2):
+        R.copy_(s0)
+        g.replay()
+        torch.cuda.synchronize()
+        lbm.lb_sync_status(ctx)
+        assert torch.equal(R, ref)
+    Ps = O.slice_propagators(O.lindbladian(w["H0"], w["jumps"]), O.drive_generator(w["X"]), w["u"], w["dt"])
+    exact = O.propagate_chain(Ps, w["states"], 4)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - exact, axis=1))
+    assert err <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_capture_without_bound_is_refused(lbm):
+    ctx, w, Lb, Ld, u, P, s0 = _setup(lbm, "fp64")
+    lbm.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P)  # initialise outside the capture
+    lbm.lb_sync_status(ctx)
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(lbm.LBError) as ei:
+        with torch.cuda.graph(g):
+            lbm.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P)
+    assert ei.value.name == "LB_EUNSUPPORTED"
+
+
+def test_squaring_bound_exceeded_is_reported(lbm):
+    ctx, w, Lb, Ld, u, P, s0 = _setup(lbm, "fp64")
+    lbm.lb_set_max_squarings(ctx, 0)  # the d = 9 slices need one squaring
+    lbm.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P)
+    with pytest.raises(lbm.LBError) as ei:
+        lbm.lb_sync_status(ctx)
+    assert ei.value.name == "LB_EUNSUPPORTED"
+
+
+def test_captured_mixed_instances_replay(lbm):
+    dev = torch.device("cuda:0")
+    from workloads.configs import make_instances
+
+    inst, models = make_instances(24)
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ctx = lbm.Context(0, max_n=729, max_batch=64, max_slices=100)
+    lbm.lb_set_max_squarings(ctx, 3)
+    gens = {q: (put(O.lindbladian(m.H0, m.jumps)), put(O.drive_generator(m.X))) for q, m in models.items()}
+    s0 = [put(x["states"]) for x in inst]
+    arg = [dict(Lbase=gens[x["nq"]][0], Ldrv=gens[x["nq"]][1], u=put(x["u"]), states=s0[i].clone())
+           for i, x in enumerate(inst)]
+    lbm.lb_run_instances(ctx, arg, 0.1, prec="fp64")
+    lbm.lb_sync_status(ctx)
+    ref = [a["states"].clone() for a in arg]
+    for a, s in zip(arg, s0):
+        a["states"].copy_(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lbm.lb_run_instances(ctx, arg, 0.1, prec="fp64")
+    for a, s in zip(arg, s0):
+        a["states"].copy_(s)
+    g.replay()
+    torch.cuda.synchronize()
+    lbm.lb_sync_status(ctx)
+    for a, r in zip(arg, ref):
+        assert torch.equal(a["states"], r)

@@ -477,3 +477,24 @@ def test_propagate_fp64_small_n_forms(lbm, dev, d, B, S, m):
     Rg = R.cpu().numpy()
     for b in range(B):
         assert _relf(Rg[b], ref[b]) <= 1e-12
+
+
+def test_autotune_keeps_results(lbm, dev):
+    """Tile choices change only the work split: the FP64 build is equal to
+    rounding before and after tuning, and matches the oracle."""
+    w = make_workload("d9_batch", nslices=4)
+    n = w["n"]
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    ctx = lbm.Context(0, max_n=n, max_batch=8, max_slices=4)
+    P1 = torch.empty((4, n, n), dtype=torch.complex128, device=dev)
+    P2 = torch.empty_like(P1)
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(w["u"], dev), w["dt"], P1)
+    shapes = lbm.lb_autotune(ctx, n, 4, 8)
+    assert shapes > 0
+    lbm.lb_expm_pade(ctx, _t(Lb, dev), _t(Ld, dev), _t(w["u"], dev), w["dt"], P2)
+    lbm.lb_sync_status(ctx)
+    ref = O.slice_propagators(Lb, Ld, w["u"], w["dt"])
+    for s in range(4):
+        assert _relf(P2.cpu().numpy()[s], ref[s]) <= 1e-12
+        assert _relf(P2.cpu().numpy()[s], P1.cpu().numpy()[s]) <= 1e-13
