@@ -100,7 +100,7 @@ def squaring_count(A, theta=THETA):
 
 
 def lu_gepp(M):
-    """LU with partial pivoting (Algorithm 1, line 6): P M = L U.
+    """LU with partial pivoting (Algorithm 1, the LU solve of the Padé denominator): P M = L U.
 
     Gaussian elimination column by column; the pivot is the first entry of
     largest modulus in the column.  Returns (L, U, perm, nswaps) with
@@ -127,7 +127,7 @@ def lu_gepp(M):
 
 def lu_solve(L, U, perm, B):
     """Solve (L U) X = B[perm] by forward then back substitution, all columns
-    of B at once (Algorithm 1, line 6)."""
+    of B at once (Algorithm 1, the LU solve of the Padé denominator)."""
     Y = np.array(B[perm], dtype=np.complex128, copy=True)
     n = L.shape[0]
     for i in range(n):
