@@ -1,0 +1,401 @@
+// FP32 propagation of a batch of states through a chain of propagators for
+// n > 81 (Alg. 2 applied to every state, Sec. 3.2), in the reduced form
+//   R_{t+1} = c_t (R_t + R_t D_t^T),   D_t = P_t - I,
+// where c_t = 1 / Tr(R_t) when the trace is renormalised (deferred by one
+// step: the trace of R_t is read at the start of step t + 1 and applied in its
+// epilogue, which is the same state up to rounding) and c_t = 1 otherwise.
+//
+// Layout ("planes", FP32, K-major so that tiles stream with 16-byte async
+// copies and no transposition in the loop):
+//   D^T of every slice   Dt[s][2][Kp][Np]  planes Re, Im, (k, j)
+//   states               Rt[2][Kp][Bp]     planes Re, Im, (k, b)
+// Kp = n rounded up to 16, Np = n rounded up to 64, Bp = B rounded up to 64;
+// padding rows and columns hold zeros (the step keeps them zero).
+//
+// The step is a complex GEMM  O[b][j] = sum_k R[b][k] D[j][k]  in Gauss's
+// three-real-product form (t1 = Re Re, t2 = Im Im, t3 = (Re+Im)(Re+Im);
+// Re = t1 - t2, Im = t3 - t1 - t2; the operand sums are formed in registers,
+// which keeps shared-memory traffic at two planes): 64 x 64 output tiles, 256 threads with
+// 4 x 4 complex outputs each (fragments double-buffered in registers), a
+// four-stage cp.async ring of 16-deep K blocks, two CTAs per SM.  When there
+// are fewer tiles than two per SM the K range is split over
+// CTAs; each writes its partial tile to global scratch and the CTA that
+// arrives last (atomic ticket, no waiting) sums the partials in split order,
+// so the result does not depend on arrival order.
+#include "lb_internal.cuh"
+
+#include <algorithm>
+
+namespace lb {
+
+namespace {
+
+constexpr int CB = 64;        // tile rows (states) and columns (outputs)
+constexpr int CK = 16;        // K per stage
+constexpr int CSTAGE = 4;     // cp.async ring depth
+constexpr int CTHREADS = 256;
+constexpr int NPL = 2;                         // planes per operand (Re, Im)
+constexpr int OPER_FLOATS = NPL * CK * CB;     // one operand
+constexpr int STAGE_FLOATS = 2 * OPER_FLOATS;  // A (states) and B (D^T)
+constexpr size_t STEP_SMEM = (size_t)CSTAGE * STAGE_FLOATS * sizeof(float);
+
+struct ChainDims {
+  int n, d, B, Kp, Np, Bp;
+};
+
+__device__ __forceinline__ void cp16(float* s, const float* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Output of four consecutive states b..b+3 at output index j: add the
+// residual R[b][j], multiply by the per-state factor, store both planes.
+__device__ __forceinline__ void chain_finish(const ChainDims& g, const float* __restrict__ Rt,
+                                             float* __restrict__ Ot, const float2* cs, int j, int b, float4 ar,
+                                             float4 ai) {
+  if (j >= g.Kp) return;
+  const long long pl = (long long)g.Kp * g.Bp;
+  const long long idx = (long long)j * g.Bp + b;
+  const float4 rr = f4add(ar, *(const float4*)(Rt + idx));
+  const float4 ri = f4add(ai, *(const float4*)(Rt + pl + idx));
+  const float vr[4] = {rr.x, rr.y, rr.z, rr.w}, vi[4] = {ri.x, ri.y, ri.z, ri.w};
+  float orr[4], oii[4];
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const float2 c = cs[e];
+    orr[e] = vr[e] * c.x - vi[e] * c.y;
+    oii[e] = vr[e] * c.y + vi[e] * c.x;
+  }
+  *(float4*)(Ot + idx) = make_float4(orr[0], orr[1], orr[2], orr[3]);
+  *(float4*)(Ot + pl + idx) = make_float4(oii[0], oii[1], oii[2], oii[3]);
+}
+
+template <bool RENORM>
+__global__ void __launch_bounds__(CTHREADS, 2)
+    chain32_step_kernel(ChainDims g, int kps, const float* __restrict__ Dt, const float* __restrict__ Rt,
+                        float* __restrict__ Ot, float* __restrict__ part, unsigned* __restrict__ cnt) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float2 cs[CB];
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * CB, m0 = blockIdx.y * CB, z = blockIdx.z, splits = gridDim.z;
+  const int kt0 = z * kps;
+  const int kt1 = min(g.Kp / CK, kt0 + kps);
+  const int nkt = kt1 - kt0;
+  const long long pA = (long long)g.Kp * g.Bp, pB = (long long)g.Kp * g.Np;
+
+  auto load = [&](int stage, int kt) {
+    float* sA = sm + stage * STAGE_FLOATS;
+    float* sB = sA + OPER_FLOATS;
+    const int k0 = kt * CK;
+    for (int c = tid; c < NPL * CK * (CB / 4); c += CTHREADS) {
+      const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
+      cp16(sA + (p * CK + r) * CB + 4 * q, Rt + p * pA + (long long)(k0 + r) * g.Bp + m0 + 4 * q);
+      cp16(sB + (p * CK + r) * CB + 4 * q, Dt + p * pB + (long long)(k0 + r) * g.Np + j0 + 4 * q);
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < CSTAGE - 1; s++) {
+    if (s < nkt) load(s, kt0 + s);
+    cp_commit();
+  }
+  // per-state factor: 1 / Tr(R_b) (complex), 0 for padding states
+  if (tid < CB) {
+    float2 c = make_float2(0.f, 0.f);
+    const int b = m0 + tid;
+    if (b < g.B) {
+      if (RENORM) {
+        float tr = 0.f, ti = 0.f;
+        for (int i = 0; i < g.d; i++) {
+          const long long k = (long long)i * (g.d + 1) * g.Bp + b;
+          tr += Rt[k];
+          ti += Rt[pA + k];
+        }
+        const float m2 = tr * tr + ti * ti;
+        c = make_float2(tr / m2, -ti / m2);
+      } else {
+        c = make_float2(1.f, 0.f);
+      }
+    }
+    cs[tid] = c;
+  }
+
+  const int w = tid >> 5, l = tid & 31;
+  const int am = (w >> 2) * 32 + (l & 7) * 4;  // this thread's 4 states
+  const int bn = (w & 3) * 16 + (l >> 3) * 4;  // this thread's 4 outputs
+  float t1[4][4], t2[4][4], t3[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) t1[i][j] = t2[i][j] = t3[i][j] = 0.f;
+
+  for (int it = 0; it < nkt; it++) {
+    cp_wait<CSTAGE - 2>();
+    __syncthreads();
+    {
+      const int nx = it + CSTAGE - 1;
+      if (nx < nkt) load(nx % CSTAGE, kt0 + nx);
+      cp_commit();
+    }
+    const float* sA = sm + (it % CSTAGE) * STAGE_FLOATS;
+    const float* sB = sA + OPER_FLOATS;
+    // fragments of step k + 1 are read while step k multiplies
+    float4 fa[2][NPL], fb[2][NPL];
+#pragma unroll
+    for (int p = 0; p < NPL; p++) {
+      fa[0][p] = *(const float4*)(sA + (p * CK) * CB + am);
+      fb[0][p] = *(const float4*)(sB + (p * CK) * CB + bn);
+    }
+#pragma unroll
+    for (int k = 0; k < CK; k++) {
+      const int cur = k & 1;
+      if (k + 1 < CK) {
+#pragma unroll
+        for (int p = 0; p < NPL; p++) {
+          fa[cur ^ 1][p] = *(const float4*)(sA + (p * CK + k + 1) * CB + am);
+          fb[cur ^ 1][p] = *(const float4*)(sB + (p * CK + k + 1) * CB + bn);
+        }
+      }
+      const float ar[4] = {fa[cur][0].x, fa[cur][0].y, fa[cur][0].z, fa[cur][0].w};
+      const float ai[4] = {fa[cur][1].x, fa[cur][1].y, fa[cur][1].z, fa[cur][1].w};
+      const float as[4] = {ar[0] + ai[0], ar[1] + ai[1], ar[2] + ai[2], ar[3] + ai[3]};
+      const float br[4] = {fb[cur][0].x, fb[cur][0].y, fb[cur][0].z, fb[cur][0].w};
+      const float bi[4] = {fb[cur][1].x, fb[cur][1].y, fb[cur][1].z, fb[cur][1].w};
+      const float bs[4] = {br[0] + bi[0], br[1] + bi[1], br[2] + bi[2], br[3] + bi[3]};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          t1[i][j] = fmaf(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fmaf(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fmaf(as[i], bs[j], t3[i][j]);
+        }
+    }
+  }
+  cp_wait<0>();
+  __syncthreads();
+
+  float re[4][4], im[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      re[i][j] = t1[i][j] - t2[i][j];
+      im[i][j] = t3[i][j] - t1[i][j] - t2[i][j];
+    }
+
+  if (splits == 1) {
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      chain_finish(g, Rt, Ot, cs + am, j0 + bn + j, m0 + am, make_float4(re[0][j], re[1][j], re[2][j], re[3][j]),
+                   make_float4(im[0][j], im[1][j], im[2][j], im[3][j]));
+    return;
+  }
+  // split K: partial tile [2][CB (j)][CB (b)] to scratch, last CTA reduces
+  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+  float* P = part + ((long long)tile * splits + z) * 2 * CB * CB;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    *(float4*)(P + (bn + j) * CB + am) = make_float4(re[0][j], re[1][j], re[2][j], re[3][j]);
+    *(float4*)(P + CB * CB + (bn + j) * CB + am) = make_float4(im[0][j], im[1][j], im[2][j], im[3][j]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = atomicAdd(&cnt[tile], 1u) == (unsigned)(splits - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const float* P0 = part + (long long)tile * splits * 2 * CB * CB;
+  for (int q = tid; q < CB * CB / 4; q += CTHREADS) {
+    const int jl = q / (CB / 4), b4 = (q % (CB / 4)) * 4;
+    float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
+    for (int zz = 0; zz < splits; zz++) {
+      const float* Pz = P0 + (long long)zz * 2 * CB * CB;
+      sr = f4add(sr, __ldcg((const float4*)(Pz + jl * CB + b4)));
+      si = f4add(si, __ldcg((const float4*)(Pz + CB * CB + jl * CB + b4)));
+    }
+    chain_finish(g, Rt, Ot, cs + b4, j0 + jl, m0 + b4, sr, si);
+  }
+  if (tid == 0) cnt[tile] = 0u;  // ready for the next launch
+}
+
+// D^T planes of S propagators: Dt[s][p][k][j] = (P_s - I)[j][k], zero padding.
+__global__ void chain32_dplanes_kernel(int n, int Kp, int Np, const z64* __restrict__ P, float* __restrict__ Dt) {
+  __shared__ float tr[32][33], ti[32][33];
+  const long long nn = (long long)n * n;
+  const z64* Ps = P + blockIdx.z * nn;
+  float* D = Dt + (long long)blockIdx.z * NPL * Kp * Np;
+  const long long pl = (long long)Kp * Np;
+  const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, k = k0 + tx;
+    double vr = 0.0, vi = 0.0;
+    if (j < n && k < n) {
+      const z64 v = Ps[(long long)j * n + k];
+      vr = v.x - (j == k ? 1.0 : 0.0);
+      vi = v.y;
+    }
+    tr[r][tx] = (float)vr;
+    ti[r][tx] = (float)vi;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, j = j0 + tx;
+    if (k >= Kp || j >= Np) continue;
+    const float a = tr[tx][r], b = ti[tx][r];
+    const long long idx = (long long)k * Np + j;
+    D[idx] = a;
+    D[pl + idx] = b;
+  }
+}
+
+// states (B x n, complex128) -> Rt planes, every element of [2][Kp][Bp] written.
+__global__ void chain32_states_in_kernel(int n, int B, int Kp, int Bp, const z64* __restrict__ X,
+                                         float* __restrict__ Rt) {
+  __shared__ float tr[32][33], ti[32][33];
+  const long long pl = (long long)Kp * Bp;
+  const int b0 = blockIdx.x * 32, k0 = blockIdx.y * 32, tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int b = b0 + r, k = k0 + tx;
+    z64 v = make_double2(0.0, 0.0);
+    if (b < B && k < n) v = X[(long long)b * n + k];
+    tr[r][tx] = (float)v.x;
+    ti[r][tx] = (float)v.y;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, b = b0 + tx;
+    if (k >= Kp || b >= Bp) continue;
+    const float a = tr[tx][r], c = ti[tx][r];
+    const long long idx = (long long)k * Bp + b;
+    Rt[idx] = a;
+    Rt[pl + idx] = c;
+  }
+}
+
+// Rt planes -> states (B x n, complex128), divided by the trace if asked.
+__global__ void chain32_states_out_kernel(int n, int d, int B, int Kp, int Bp, int renorm,
+                                          const float* __restrict__ Rt, z64* __restrict__ X) {
+  __shared__ float tr[32][33], ti[32][33];
+  __shared__ float2 cs[32];
+  const long long pl = (long long)Kp * Bp;
+  const int b0 = blockIdx.x * 32, k0 = blockIdx.y * 32, tx = threadIdx.x;
+  if (threadIdx.y == 0) {
+    float2 c = make_float2(1.f, 0.f);
+    const int b = b0 + tx;
+    if (renorm && b < B) {
+      float sr = 0.f, si = 0.f;
+      for (int i = 0; i < d; i++) {
+        const long long k = (long long)i * (d + 1) * Bp + b;
+        sr += Rt[k];
+        si += Rt[pl + k];
+      }
+      const float m2 = sr * sr + si * si;
+      c = make_float2(sr / m2, -si / m2);
+    }
+    cs[tx] = c;
+  }
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, b = b0 + tx;
+    float a = 0.f, c = 0.f;
+    if (k < n && b < B) {
+      a = Rt[(long long)k * Bp + b];
+      c = Rt[pl + (long long)k * Bp + b];
+    }
+    tr[r][tx] = a;
+    ti[r][tx] = c;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int b = b0 + r, k = k0 + tx;
+    if (b >= B || k >= n) continue;
+    const float a = tr[tx][r], c = ti[tx][r];
+    const float2 s = cs[r];
+    X[(long long)b * n + k] = make_double2((double)(a * s.x - c * s.y), (double)(a * s.y + c * s.x));
+  }
+}
+
+int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+int chain_isqrt(int n) {
+  int d = 1;
+  while ((d + 1) * (d + 1) <= n) d++;
+  return d;
+}
+
+}  // namespace
+
+size_t chain32_dplane_floats(int n) { return (size_t)NPL * rup(n, CK) * rup(n, CB); }
+size_t chain32_state_floats(int n, int B) { return (size_t)NPL * rup(n, CK) * rup(B, CB); }
+size_t chain32_part_floats(int sm_count) { return (size_t)2 * sm_count * 2 * CB * CB; }
+
+cudaError_t launch_chain32_dplanes(int n, int S, const z64* P, float* Dt, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  const int Kp = rup(n, CK), Np = rup(n, CB);
+  dim3 grid(Np / 32, (Kp + 31) / 32, S), block(32, 8);
+  count_launch();
+  chain32_dplanes_kernel<<<grid, block, 0, st>>>(n, Kp, Np, P, Dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain32_states_in(int n, int B, const z64* X, float* Rt, cudaStream_t st) {
+  const int Kp = rup(n, CK), Bp = rup(B, CB);
+  dim3 grid(Bp / 32, (Kp + 31) / 32), block(32, 8);
+  count_launch();
+  chain32_states_in_kernel<<<grid, block, 0, st>>>(n, B, Kp, Bp, X, Rt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt, z64* X, cudaStream_t st) {
+  const int Kp = rup(n, CK), Bp = rup(B, CB);
+  dim3 grid(Bp / 32, (n + 31) / 32), block(32, 8);
+  count_launch();
+  chain32_states_out_kernel<<<grid, block, 0, st>>>(n, chain_isqrt(n), B, Kp, Bp, renorm, Rt, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
+                                unsigned* cnt, int sm_count, cudaStream_t st) {
+  ChainDims g;
+  g.n = n;
+  g.d = chain_isqrt(n);
+  g.B = B;
+  g.Kp = rup(n, CK);
+  g.Np = rup(n, CB);
+  g.Bp = rup(B, CB);
+  const int tilesN = g.Np / CB, tilesM = g.Bp / CB, tiles = tilesN * tilesM;
+  const int ktiles = g.Kp / CK;
+  // two CTAs fit on an SM: split K until the grid fills them (at least four
+  // K blocks per split)
+  int splits = 1;
+  if (tiles < 2 * sm_count) splits = std::max(1, std::min({2 * sm_count / tiles, ktiles / 4, 8}));
+  const int kps = (ktiles + splits - 1) / splits;
+  splits = (ktiles + kps - 1) / kps;
+  if (splits > 1 && (tiles * splits > 2 * sm_count || tiles > sm_count))
+    return cudaErrorInvalidValue;  // scratch is sized for 2 x sm_count partial tiles, sm_count tickets
+  dim3 grid(tilesN, tilesM, splits);
+  cudaError_t e;
+  if (renorm) {
+    e = set_smem_once((const void*)chain32_step_kernel<true>, STEP_SMEM);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    chain32_step_kernel<true><<<grid, CTHREADS, STEP_SMEM, st>>>(g, kps, Dt, Rt, Ot, part, cnt);
+  } else {
+    e = set_smem_once((const void*)chain32_step_kernel<false>, STEP_SMEM);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    chain32_step_kernel<false><<<grid, CTHREADS, STEP_SMEM, st>>>(g, kps, Dt, Rt, Ot, part, cnt);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lb

@@ -282,125 +282,12 @@ __global__ void make_delta_f32_kernel(int n, long long total, const z64* __restr
   }
 }
 
-__global__ void states_to_f32_kernel(long long total, const z64* __restrict__ s, float* __restrict__ r,
-                                     float* __restrict__ im) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const z64 v = s[e];
-    r[e] = (float)v.x;
-    im[e] = (float)v.y;
-  }
-}
 
-__global__ void states_from_f32_kernel(long long total, const float* __restrict__ r,
-                                       const float* __restrict__ im, z64* __restrict__ s) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    s[e] = make_double2((double)r[e], (double)im[e]);
-}
 
 // Out[b][i] = R[b][i] + sum_j D[i][j] R[b][j]; planar FP32.  BM x BN output
 // tile (states x rows), TM x TN outputs per thread.  32 x 32 tiles give 184
 // CTAs for 256 states x 729 rows, all resident at once on 152 SMs.
-template <int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    step_f32_kernel(int n, int B, const float* __restrict__ Dr, const float* __restrict__ Di,
-                    const float* __restrict__ Rr, const float* __restrict__ Ri, float* __restrict__ Or,
-                    float* __restrict__ Oi) {
-  constexpr int BK = 16;
-  constexpr int NT = (BM / TM) * (BN / TN);
-  __shared__ __align__(16) float Ar[BK][BM], Ai[BK][BM], Br[BK][BN], Bi[BK][BN];
-  const int tilesN = (n + BN - 1) / BN;
-  const int tilesM = (B + BM - 1) / BM;
-  const int tid = threadIdx.x;
-  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
-  for (int t = blockIdx.x; t < tilesM * tilesN; t += gridDim.x) {
-    const int m0 = (t / tilesN) * BM, n0 = (t % tilesN) * BN;
-    float cr[TM][TN], ci[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; i++)
-#pragma unroll
-      for (int j = 0; j < TN; j++) cr[i][j] = ci[i][j] = 0.f;
-    for (int k0 = 0; k0 < n; k0 += BK) {
-      for (int e = tid; e < BM * BK; e += NT) {
-        const int m = e / BK, k = e % BK;
-        const int gm = m0 + m, gk = k0 + k;
-        const bool ok = gm < B && gk < n;
-        Ar[k][m] = ok ? Rr[(long long)gm * n + gk] : 0.f;
-        Ai[k][m] = ok ? Ri[(long long)gm * n + gk] : 0.f;
-      }
-      for (int e = tid; e < BN * BK; e += NT) {
-        const int nn_ = e / BK, k = e % BK;
-        const int gn = n0 + nn_, gk = k0 + k;
-        const bool ok = gn < n && gk < n;
-        Br[k][nn_] = ok ? Dr[(long long)gn * n + gk] : 0.f;
-        Bi[k][nn_] = ok ? Di[(long long)gn * n + gk] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < BK; k++) {
-        float ar[TM], ai[TM], br[TN], bi[TN];
-#pragma unroll
-        for (int i = 0; i < TM; i++) {
-          ar[i] = Ar[k][ty * TM + i];
-          ai[i] = Ai[k][ty * TM + i];
-        }
-#pragma unroll
-        for (int j = 0; j < TN; j++) {
-          br[j] = Br[k][tx * TN + j];
-          bi[j] = Bi[k][tx * TN + j];
-        }
-#pragma unroll
-        for (int i = 0; i < TM; i++)
-#pragma unroll
-          for (int j = 0; j < TN; j++) {
-            cr[i][j] = fmaf(ar[i], br[j], cr[i][j]);
-            cr[i][j] = fmaf(-ai[i], bi[j], cr[i][j]);
-            ci[i][j] = fmaf(ar[i], bi[j], ci[i][j]);
-            ci[i][j] = fmaf(ai[i], br[j], ci[i][j]);
-          }
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < TM; i++) {
-      const int gm = m0 + ty * TM + i;
-      if (gm >= B) continue;
-#pragma unroll
-      for (int j = 0; j < TN; j++) {
-        const int gn = n0 + tx * TN + j;
-        if (gn >= n) continue;
-        const long long idx = (long long)gm * n + gn;
-        Or[idx] = Rr[idx] + cr[i][j];
-        Oi[idx] = Ri[idx] + ci[i][j];
-      }
-    }
-  }
-}
 
-// One warp per state: divide by the trace.
-__global__ void renorm_f32_kernel(int n, int d, int B, float* __restrict__ Rr, float* __restrict__ Ri) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= B) return;
-  float sr = 0.f, si = 0.f;
-  for (int k = lane; k < d; k += 32) {
-    sr += Rr[(long long)w * n + k * (d + 1)];
-    si += Ri[(long long)w * n + k * (d + 1)];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-    si += __shfl_xor_sync(0xffffffffu, si, o);
-  }
-  const float m2 = sr * sr + si * si;
-  const float cr = sr / m2, ci = -si / m2;
-  for (int e = lane; e < n; e += 32) {
-    const long long idx = (long long)w * n + e;
-    const float r = Rr[idx], im = Ri[idx];
-    Rr[idx] = r * cr - im * ci;
-    Ri[idx] = r * ci + im * cr;
-  }
-}
 
 int isqrt_exact(int n) {
   int d = 1;
@@ -485,37 +372,8 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, float* Ri, cudaStream_t st) {
-  const long long total = (long long)n * B;
-  count_launch();
-  states_to_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, states, Rr, Ri);
-  return cudaGetLastError();
-}
 
-cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* Ri, z64* states,
-                                   cudaStream_t st) {
-  const long long total = (long long)n * B;
-  count_launch();
-  states_from_f32_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, Rr, Ri, states);
-  return cudaGetLastError();
-}
 
-cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
-                            const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st) {
-  const int tiles = ((B + 31) / 32) * ((n + 31) / 32);
-  const int grid = std::min(tiles, sm_count * 8);
-  count_launch();
-  step_f32_kernel<32, 32, 4, 4><<<grid, 64, 0, st>>>(n, B, Dr, Di, Rr, Ri, Or, Oi);
-  return cudaGetLastError();
-}
 
-cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t st) {
-  const int d = isqrt_exact(n);
-  const int threads = 256;
-  const int grid = (B * 32 + threads - 1) / threads;
-  count_launch();
-  renorm_f32_kernel<<<grid, threads, 0, st>>>(n, d, B, Rr, Ri);
-  return cudaGetLastError();
-}
 
 }  // namespace lb

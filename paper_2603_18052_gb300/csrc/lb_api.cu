@@ -146,9 +146,11 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   const size_t plane_elems = (size_t)max_n * (size_t)plane_ld(max_n);
   for (int i = 0; i < 9; i++) add((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));  // split planes
   for (int i = 0; i < 2; i++) add(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
-  add(nn * S * sizeof(float));                              // Dr
-  add(nn * S * sizeof(float));                              // Di
-  for (int i = 0; i < 4; i++) add((size_t)max_batch * max_n * sizeof(float));
+  const size_t dpl = std::max(chain32_dplane_floats(max_n), 2 * nn) * S;
+  add(dpl * sizeof(float));                                 // Dpl (Dr, Di inside)
+  for (int i = 0; i < 2; i++) add(chain32_state_floats(max_n, max_batch) * sizeof(float));  // C32a, C32b
+  add(chain32_part_floats(prop.multiProcessorCount) * sizeof(float));                       // part32
+  add((size_t)prop.multiProcessorCount * sizeof(unsigned));                                 // cnt32
   add(nn * S * zb);                                          // Ginst
   add(nn * S * zb);                                          // Pinst
   add(inst_table_bytes());                                   // instance tables
@@ -187,12 +189,13 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
     c->sp[i] = (__nv_bfloat16*)ar.take((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));
   for (int i = 0; i < 2; i++)
     c->spR[i] = (__nv_bfloat16*)ar.take(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
-  c->Dr = (float*)ar.take(nn * S * sizeof(float));
-  c->Di = (float*)ar.take(nn * S * sizeof(float));
-  c->Rr = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
-  c->Ri = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
-  c->Or = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
-  c->Oi = (float*)ar.take((size_t)max_batch * max_n * sizeof(float));
+  c->Dpl = (float*)ar.take(dpl * sizeof(float));
+  c->Dr = c->Dpl;
+  c->Di = c->Dpl + nn * S;
+  c->C32a = (float*)ar.take(chain32_state_floats(max_n, max_batch) * sizeof(float));
+  c->C32b = (float*)ar.take(chain32_state_floats(max_n, max_batch) * sizeof(float));
+  c->part32 = (float*)ar.take(chain32_part_floats(c->sm_count) * sizeof(float));
+  c->cnt32 = (unsigned*)ar.take((size_t)c->sm_count * sizeof(unsigned));
   c->Ginst = Z(nn * S);
   c->Pinst = Z(nn * S);
   c->inst_tab_bytes = inst_table_bytes();
@@ -201,6 +204,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->grape_bytes = gbytes;
   c->err_dev = (unsigned int*)ar.take(sizeof(unsigned int));
   if (!c->err_dev || cudaMemset(c->err_dev, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(c->cnt32, 0, (size_t)c->sm_count * sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&c->err_host, sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&c->scmax_host, sizeof(int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_scmax, cudaEventDisableTiming) != cudaSuccess ||
@@ -707,26 +711,34 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
     return LB_OK;
   }
   // FP32: D = P - I in FP32, states in FP32
-  const bool resident = resident_f32_fits(n);
-  if (!resident) LB_CUDA(launch_states_to_f32(n, B, X, c->Rr, c->Ri, st));
-  float *cr = c->Rr, *ci = c->Ri, *nr = c->Or, *ni = c->Oi;
+  if (resident_f32_fits(n)) {
+    for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+      const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+      LB_CUDA(launch_make_delta_f32(n, S, Pz + s0 * nn, c->Dr, c->Di, st));
+      LB_CUDA(launch_propagate_resident_f32(n, S, c->Dr, c->Di, steps_per_slice, B, X, renorm_trace, c->sm_count,
+                                            st));
+    }
+    return LB_OK;
+  }
+  // n > 81: one split-K GEMM launch per step on K-major planes, the trace
+  // renormalisation deferred into the next step's epilogue
+  const size_t dpl = chain32_dplane_floats(n);
+  float* cur = c->C32a;
+  float* nxt = c->C32b;
+  LB_CUDA(launch_chain32_states_in(n, B, X, cur, st));
   for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
     const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
-    LB_CUDA(launch_make_delta_f32(n, S, Pz + s0 * nn, c->Dr, c->Di, st));
-    if (resident) {
-      LB_CUDA(launch_propagate_resident_f32(n, S, c->Dr, c->Di, steps_per_slice, B, X, renorm_trace,
-                                            c->sm_count, st));
-      continue;
-    }
+    LB_CUDA(launch_chain32_dplanes(n, S, Pz + s0 * nn, c->Dpl, st));
     for (int s = 0; s < S; s++)
       for (int t = 0; t < steps_per_slice; t++) {
-        LB_CUDA(launch_step_f32(n, B, c->Dr + s * nn, c->Di + s * nn, cr, ci, nr, ni, c->sm_count, st));
-        if (renorm_trace) LB_CUDA(launch_renorm_f32(n, B, nr, ni, st));
-        float* t1 = cr; cr = nr; nr = t1;
-        float* t2 = ci; ci = ni; ni = t2;
+        LB_CUDA(launch_chain32_step(n, B, renorm_trace, c->Dpl + s * dpl, cur, nxt, c->part32, c->cnt32,
+                                    c->sm_count, st));
+        float* t1 = cur;
+        cur = nxt;
+        nxt = t1;
       }
   }
-  if (!resident) LB_CUDA(launch_states_from_f32(n, B, cr, ci, X, st));
+  LB_CUDA(launch_chain32_states_out(n, B, renorm_trace, cur, X, st));
   return LB_OK;
 }
 

@@ -75,8 +75,11 @@ struct lb_ctx {
   __nv_bfloat16* spR[2] = {};  // state planes, 4 x max_batch x ld each
   // --- propagation ---
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
-  float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2
-  float *Rr = nullptr, *Ri = nullptr, *Or = nullptr, *Oi = nullptr;  // max_batch x max_n
+  float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2 (n <= 81), inside Dpl
+  float* Dpl = nullptr;                // FP32 D^T planes of the chain, per slice chain32_dplane_floats
+  float *C32a = nullptr, *C32b = nullptr;  // FP32 state planes, chain32_state_floats(max_n, max_batch)
+  float* part32 = nullptr;             // split-K partial tiles, chain32_part_floats(sm_count)
+  unsigned* cnt32 = nullptr;           // split-K tickets, sm_count (zero between launches)
   // --- many-instance batching (lb_run_instances) ---
   lb::z64* Ginst = nullptr;  // per-slice generators, max_slices x max_n^2
   lb::z64* Pinst = nullptr;  // their propagators
@@ -175,12 +178,15 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
                                           int sm_count, cudaStream_t st);
 bool resident_f32_fits(int n);
 // Large-n FP32 step: Rout = Rin + Rin * D^T (planar FP32 states), optional renorm.
-cudaError_t launch_states_to_f32(int n, int B, const z64* states, float* Rr, float* Ri, cudaStream_t st);
-cudaError_t launch_states_from_f32(int n, int B, const float* Rr, const float* Ri, z64* states,
-                                   cudaStream_t st);
-cudaError_t launch_step_f32(int n, int B, const float* Dr, const float* Di, const float* Rr,
-                            const float* Ri, float* Or, float* Oi, int sm_count, cudaStream_t st);
-cudaError_t launch_renorm_f32(int n, int B, float* Rr, float* Ri, cudaStream_t st);
+// FP32 chain for n > 81 (k_chain32.cu)
+size_t chain32_dplane_floats(int n);
+size_t chain32_state_floats(int n, int B);
+size_t chain32_part_floats(int sm_count);
+cudaError_t launch_chain32_dplanes(int n, int S, const z64* P, float* Dt, cudaStream_t st);
+cudaError_t launch_chain32_states_in(int n, int B, const z64* X, float* Rt, cudaStream_t st);
+cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt, z64* X, cudaStream_t st);
+cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
+                                unsigned* cnt, int sm_count, cudaStream_t st);
 
 // n x n square problem, batch S, slice stride n*n (helper for the build).
 ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C);

@@ -232,6 +232,68 @@ def test_propagate_fp32_d27(lbm, dev):
     assert err <= 1e-6, err
 
 
+def _random_model(seed, d):
+    """A random open system of dimension d: Hermitian H and drive X, two jump
+    operators, scaled like the transmon generators (||L dt|| well below 1)."""
+    H = _rand_c(seed, (d, d))
+    H = 0.5 * (H + H.conj().T) / d
+    X = _rand_c(seed + 1, (d, d))
+    X = 0.5 * (X + X.conj().T) / d
+    jumps = 0.05 * np.stack([_rand_c(seed + 2, (d, d)), _rand_c(seed + 3, (d, d))]) / d
+    return O.lindbladian(H, jumps), O.drive_generator(X)
+
+
+@pytest.mark.parametrize("d,B,S,m,renorm", [
+    (27, 256, 2, 1, True),    # 4 x 12 tiles, K split in 3
+    (27, 37, 2, 2, False),    # ragged batch, K split in 8
+    (27, 37, 1, 3, True),
+    (10, 70, 3, 1, True),     # n = 100: ragged K and N, no split
+    (11, 200, 2, 2, False),   # n = 121, 4 x 2 tiles
+])
+def test_propagate_fp32_chain_shapes(lbm, dev, d, B, S, m, renorm):
+    """FP32 chain kernel for n > 81 (split-K, padding, deferred trace
+    renormalisation) against the oracle chain; 1e-6 absolute Frobenius per
+    state for these short chains."""
+    from workloads.rng import ginibre_states
+
+    n = d * d
+    if d == 27:
+        w = make_workload("d27_chain", B=B, nslices=S)
+        Ps = _slice_props(w, w["u"])
+        X0 = w["states"]
+    else:
+        Lb, Ld = _random_model(0x5EED0100 + d, d)
+        u = np.linspace(-0.1, 0.1, S)
+        Ps = O.slice_propagators(Lb, Ld, u, 0.1)
+        X0 = ginibre_states(0x5EED0200 + d, d, B)
+    ref = O.propagate_chain(Ps, X0, m)
+    ctx = lbm.Context(0, max_n=n, max_batch=B, max_slices=S)
+    R = _t(X0, dev)
+    lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=m, prec="fp32", renorm_trace=renorm)
+    lbm.lb_sync_status(ctx)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - ref, axis=1))
+    assert err <= 1e-6, err
+
+
+def test_propagate_fp32_d27_200_steps(lbm, dev):
+    """Long FP32 chain at d = 27 (200 steps, the length of the 200-slice
+    workload), renormalised: <= 1e-5 absolute Frobenius per state; run twice
+    to check that the split-K tickets are reset between launches."""
+    w = make_workload("d27_chain", B=16, nslices=2)
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate_chain(Ps, w["states"], 100)
+    ctx = lbm.Context(0, max_n=729, max_batch=16, max_slices=2)
+    out = []
+    for _ in range(2):
+        R = _t(w["states"], dev)
+        lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=100, prec="fp32", renorm_trace=True)
+        lbm.lb_sync_status(ctx)
+        out.append(R.cpu().numpy())
+        err = np.max(np.linalg.norm(out[-1] - ref, axis=1))
+        assert err <= 1e-5, err
+    assert np.array_equal(out[0], out[1])
+
+
 def test_zero_steps_and_slices_leave_states(lbm, dev):
     w = make_workload("d3_single", B=3)
     Ps = _slice_props(w, np.array([0.05]))
