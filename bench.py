@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the split-BF16 form and print its launch count per step (for a "
+                         "profiler's launch list); no other forms, end-to-end run or side workloads")
     return ap.parse_args()
 
 
@@ -436,6 +439,14 @@ def run_ours(args):
     tuned = lb.lb_autotune(ctx, n, S, B)
     t_tune = time.perf_counter() - t_tune
     sampler = ClockSampler(local)
+    if args.headline_only:
+        r = timed("bf16x3")
+        if rank == 0:
+            print(json.dumps({"headline_only": True, "form": "bf16x3", "ms_per_step": r["ms_per_step"],
+                              "steps": args.steps, "warmup": args.warmup,
+                              "launches_per_step": r["launches"] // max(args.steps, 1)}), flush=True)
+        ctx.close()
+        return
     res = {"bf16x3": timed("bf16x3", sampler), "fp32": timed("fp32"), "fp64": timed("fp64")}
     head = min(("bf16x3", "fp32"), key=lambda f: res[f]["ms_per_step"])
     mixed, fp64 = res[head], res["fp64"]

@@ -142,7 +142,7 @@ __device__ __forceinline__ void put_planes(__nv_bfloat16* base, long long idx, l
 template <int NPA, int NPB, int TBN>
 __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                        const __grid_constant__ CUtensorMap mapB,
-                                                       const __grid_constant__ TcProblem P) {
+                                                       const __grid_constant__ TcProblem P, int ksplit, int kbps) {
   using Cfg = TcCfg<NPA, NPB, TBN>;
   constexpr int B_PLANE = Cfg::B_PLANE;
   constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
@@ -151,10 +151,13 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
   uint8_t* sm = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], acc_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int give_up;
+  __shared__ int give_up, last_cta;
+  __shared__ float2 rscale[TBM];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM, b = blockIdx.z;
-  const int nk = (P.K + TBK - 1) / TBK;
+  const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM, b = blockIdx.z / ksplit, zs = blockIdx.z % ksplit;
+  const int nkt = (P.K + TBK - 1) / TBK;
+  const int kb0 = zs * kbps;                           // this CTA's K blocks [kb0, kb0 + nk)
+  const int nk = min(nkt, kb0 + kbps) - kb0;
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; s++) {
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     // producer: TMA copies of the K blocks into the ring
     for (int kb = 0; kb < nk; kb++) {
       const int s = kb % NSTAGE;
+      const int kx = (kb0 + kb) * TBK;
       if (kb >= NSTAGE && !mbar_wait(su32(&empty_bar[s]), ((kb - NSTAGE) / NSTAGE) & 1)) {
         atomicOr(P.err, ERR_TIMEOUT);
         give_up = 1;
@@ -187,9 +191,9 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
       const uint32_t base = su32(sm + s * STAGE_BYTES);
       const uint32_t fb = su32(&full_bar[s]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
-      for (int p = 0; p < 2 * NPA; p++) tma3(base + p * A_PLANE, &mapA, kb * TBK, m0, b * 2 * NPA + p, fb);
+      for (int p = 0; p < 2 * NPA; p++) tma3(base + p * A_PLANE, &mapA, kx, m0, b * 2 * NPA + p, fb);
       for (int p = 0; p < 2 * NPB; p++)
-        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, kb * TBK, n0, b * 2 * NPB + p, fb);
+        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, kx, n0, b * 2 * NPB + p, fb);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -233,6 +237,34 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&acc_bar))
                  : "memory");
   }
+  if (warp >= 2 && P.rs_src != nullptr) {
+    // per-row factor 1 / Tr (rows m0 .. m0 + 127), computed by the two warps
+    // that are idle while the K loop runs
+    for (int r = tid - 64; r < TBM; r += 64) {
+      float2 c = make_float2(1.f, 0.f);
+      const int row = m0 + r;
+      if (row < P.M) {
+        const float2* x = P.rs_src + (long long)b * P.sC + (long long)row * P.ldc;
+        const int step = P.rs_d + 1;
+        float sr = 0.f, si = 0.f;
+        int i = 0;
+        for (; i + 4 <= P.rs_d; i += 4) {
+          const float2 v0 = __ldg(x + i * step), v1 = __ldg(x + (i + 1) * step);
+          const float2 v2 = __ldg(x + (i + 2) * step), v3 = __ldg(x + (i + 3) * step);
+          sr += (v0.x + v1.x) + (v2.x + v3.x);
+          si += (v0.y + v1.y) + (v2.y + v3.y);
+        }
+        for (; i < P.rs_d; i++) {
+          const float2 v = __ldg(x + i * step);
+          sr += v.x;
+          si += v.y;
+        }
+        const float m2 = sr * sr + si * si;
+        c = make_float2(sr / m2, -si / m2);
+      }
+      rscale[r] = c;
+    }
+  }
   __syncwarp();
   // all warps: wait for the accumulator
   const bool have = mbar_wait(su32(&acc_bar), 0);
@@ -263,33 +295,108 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
       for (int j = 0; j < 16; j++) tile[r * LDS + c0 + j] = make_float2(vr[j], vi[j]);
     }
     __syncthreads();
+  }
+  bool emit = good;
+  if (ksplit > 1) {
+    // split K: every CTA of the tile leaves its partial; the one that takes
+    // the last ticket sums them in split order (independent of arrival order)
+    constexpr int LDS = TBN + 1;
+    float2* tile = (float2*)sm;
+    const int tile_id = (b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float2* part = P.part + (long long)tile_id * ksplit * TBM * TBN;
+    if (good) {
+      float4* mine = (float4*)(part + (long long)zs * TBM * TBN);
+      for (int e = tid; e < TBM * TBN / 2; e += 128) {
+        const float2 u = tile[(2 * e / TBN) * LDS + (2 * e) % TBN], v = tile[(2 * e / TBN) * LDS + (2 * e) % TBN + 1];
+        mine[e] = make_float4(u.x, u.y, v.x, v.y);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_cta = atomicAdd(&P.cnt[tile_id], 1u) == (unsigned)(ksplit - 1);
+    __syncthreads();
+    emit = good && last_cta;
+    if (last_cta) {
+      __threadfence();
+      if (good) {
+        const float4* p4 = (const float4*)part;
+        constexpr int E4 = TBM * TBN / 2;  // float4 (two complex values) per partial tile
+#pragma unroll 4
+        for (int e = tid; e < E4; e += 128) {
+          float4 a = __ldcg(p4 + e);
+          for (int z = 1; z < ksplit; z++) {
+            const float4 v = __ldcg(p4 + (long long)z * E4 + e);
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+            a.w += v.w;
+          }
+          const int r = 2 * e / TBN, cc = (2 * e) % TBN;
+          tile[r * LDS + cc] = make_float2(a.x, a.y);
+          tile[r * LDS + cc + 1] = make_float2(a.z, a.w);
+        }
+      }
+      if (tid == 0) P.cnt[tile_id] = 0u;
+      __syncthreads();
+    }
+  }
+  if (emit) {
+    constexpr int LDS = TBN + 1;
+    float2* tile = (float2*)sm;
     const long long bs = (long long)b;
     // row-major pass: consecutive threads take consecutive columns.  FP32
     // arithmetic only; FP64 outputs are exact widenings plus the FP64
-    // diagonal term.
-    for (int e = tid; e < TBM * TBN; e += 128) {
-      const int r = e / TBN, cc = e - (e / TBN) * TBN;
-      const int row = m0 + r, col = n0 + cc;
-      if (row >= P.M || col >= P.N) continue;
-      const float2 a2 = tile[r * LDS + cc];
-      const long long off = bs * P.sC + (long long)row * P.ldc + col;
-      float cr = P.alpha * a2.x, ci = P.alpha * a2.y;
-      float dr = P.alpha2 * a2.x, di = P.alpha2 * a2.y;
-      for (int q = 0; q < P.nterms; q++) {
-        const float2 x = P.X[q][bs * P.sX[q] + (long long)row * P.ldc + col];
-        cr = fmaf(P.coef[q], x.x, cr);
-        ci = fmaf(P.coef[q], x.y, ci);
-        dr = fmaf(P.coef2[q], x.x, dr);
-        di = fmaf(P.coef2[q], x.y, di);
+    // diagonal term.  The X terms of EU elements are loaded before any of
+    // them is stored (the outputs may alias nothing the compiler can prove),
+    // so one L2 round trip covers EU elements.
+    constexpr int EU = 8;
+    static_assert((TBM * TBN) % (128 * EU) == 0, "epilogue batches");
+    for (int e0 = tid; e0 < TBM * TBN; e0 += 128 * EU) {
+      float2 xv[4][EU];
+#pragma unroll
+      for (int u = 0; u < EU; u++) {
+        const int e = e0 + 128 * u;
+        const int r = e / TBN, cc = e - (e / TBN) * TBN;
+        const int row = m0 + r, col = n0 + cc;
+        const bool in = row < P.M && col < P.N;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          xv[q][u] = (q < P.nterms && in) ? __ldg(P.X[q] + bs * P.sX[q] + (long long)row * P.ldc + col)
+                                          : make_float2(0.f, 0.f);
       }
-      if (P.Cf != nullptr) P.Cf[off] = make_float2(cr, ci);
-      if (P.Cd != nullptr) P.Cd[off] = make_double2(row == col ? widen(cr) + P.gamma : widen(cr), widen(ci));
-      if (P.C2d != nullptr)
-        P.C2d[off] = make_double2(row == col ? widen(dr) + P.gamma2 : widen(dr), widen(di));
-      if (P.sp != nullptr)
-        put_planes(P.sp, bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col, P.sp_plane,
-                   row == col ? cr - P.sp_shift : cr, ci);
-      if (P.spT != nullptr) tile[r * LDS + cc] = make_float2(row == col ? cr - P.spT_shift : cr, ci);
+#pragma unroll
+      for (int u = 0; u < EU; u++) {
+        const int e = e0 + 128 * u;
+        const int r = e / TBN, cc = e - (e / TBN) * TBN;
+        const int row = m0 + r, col = n0 + cc;
+        if (row >= P.M || col >= P.N) continue;
+        const float2 a2 = tile[r * LDS + cc];
+        const long long off = bs * P.sC + (long long)row * P.ldc + col;
+        float cr = P.alpha * a2.x, ci = P.alpha * a2.y;
+        float dr = P.alpha2 * a2.x, di = P.alpha2 * a2.y;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (q >= P.nterms) break;
+          cr = fmaf(P.coef[q], xv[q][u].x, cr);
+          ci = fmaf(P.coef[q], xv[q][u].y, ci);
+          dr = fmaf(P.coef2[q], xv[q][u].x, dr);
+          di = fmaf(P.coef2[q], xv[q][u].y, di);
+        }
+        if (P.rs_src != nullptr) {
+          const float2 c = rscale[r];
+          const float t = cr * c.x - ci * c.y;
+          ci = cr * c.y + ci * c.x;
+          cr = t;
+        }
+        if (P.Cf != nullptr) P.Cf[off] = make_float2(cr, ci);
+        if (P.Cd != nullptr) P.Cd[off] = make_double2(row == col ? widen(cr) + P.gamma : widen(cr), widen(ci));
+        if (P.C2d != nullptr)
+          P.C2d[off] = make_double2(row == col ? widen(dr) + P.gamma2 : widen(dr), widen(di));
+        if (P.sp != nullptr)
+          put_planes(P.sp, bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col, P.sp_plane,
+                     row == col ? cr - P.sp_shift : cr, ci);
+        if (P.spT != nullptr) tile[r * LDS + cc] = make_float2(row == col ? cr - P.spT_shift : cr, ci);
+      }
     }
     if (P.spT != nullptr) {
       // transposed planes (B-operand layout): consecutive threads take
@@ -491,9 +598,16 @@ cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   cudaError_t e = set_smem_once((const void*)zgemm_tc_kernel<NPA, NPB, BN>, Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid((p.N + BN - 1) / BN, (p.M + TBM - 1) / TBM, p.batch);
+  const int gx = (p.N + BN - 1) / BN, gy = (p.M + TBM - 1) / TBM;
+  const int tiles = gx * gy * p.batch, nk = (p.K + TBK - 1) / TBK;
+  int ksplit = 1;
+  if (p.part != nullptr && p.cnt != nullptr && tiles < p.max_ctas)
+    ksplit = std::max(1, std::min({p.max_ctas / tiles, nk / 2, 8}));
+  const int kbps = (nk + ksplit - 1) / ksplit;
+  ksplit = (nk + kbps - 1) / kbps;
+  dim3 grid(gx, gy, p.batch * ksplit);
   count_launch();
-  zgemm_tc_kernel<NPA, NPB, BN><<<grid, 128, Cfg::SMEM, st>>>(ma, mb, p);
+  zgemm_tc_kernel<NPA, NPB, BN><<<grid, 128, Cfg::SMEM, st>>>(ma, mb, p, ksplit, kbps);
   return cudaGetLastError();
 }
 }  // namespace

@@ -672,11 +672,14 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
     return LB_OK;
   }
   if (prec == LB_BF16X3) {
-    // Split BF16 on the tensor cores: next = cur + D cur with D = P - I.  The
-    // states (A operand, rows = states) are FP32 and enter as two BF16
-    // pieces; D (B operand) keeps three pieces, because its rounding repeats
-    // identically at every step and would otherwise add up coherently over
-    // long chains; five BF16 products per real product, FP32 accumulation.
+    // Split BF16 on the tensor cores: next = c (cur + D cur) with D = P - I
+    // and c = 1 / Tr(cur) when renormalising (deferred by one step and
+    // applied in the epilogue).  The states (A operand, rows = states) are
+    // FP32 and enter as two BF16 pieces; D (B operand) keeps three pieces,
+    // because its rounding repeats identically at every step and would
+    // otherwise add up coherently over long chains; five BF16 products per
+    // real product, FP32 accumulation, K split over CTAs when the tiles do
+    // not fill the GPU.
     const long long ld = plane_ld(n), dpl = (long long)n * ld, rpl = (long long)B * ld;
     float2* cur = (float2*)c->Rtmp;  // the FP64 scratch holds two FP32 state buffers
     float2* nxt = cur + (long long)B * n;
@@ -697,16 +700,20 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
           q.ldc = n;
           q.nterms = 1; q.X[0] = cur; q.coef[0] = 1.f;
           q.Cf = nxt;
-          q.err = c->err_dev;
-          if (!renorm_trace) {
-            q.sp = pn; q.sp_ld = ld; q.sp_plane = rpl;
+          q.sp = pn; q.sp_ld = ld; q.sp_plane = rpl;
+          if (renorm_trace) {
+            q.rs_src = cur;
+            q.rs_d = d;
           }
+          q.part = (float2*)c->part32; q.cnt = c->cnt32; q.max_ctas = c->sm_count;
+          q.err = c->err_dev;
           LB_CUDA(zgemm_tc(q, st));
-          if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, nxt, pn, ld, rpl, st));
           float2* t1 = cur; cur = nxt; nxt = t1;
           __nv_bfloat16* t2 = pc; pc = pn; pn = t2;
         }
     }
+    // the last step's trace factor (the others were applied one step late)
+    if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, cur, pn, ld, rpl, st));
     LB_CUDA(launch_states_f32_c64((long long)B * n, cur, X, st));
     return LB_OK;
   }

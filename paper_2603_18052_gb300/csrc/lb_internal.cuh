@@ -242,6 +242,13 @@ struct TcProblem {
   z64* C2d = nullptr; double gamma2 = 0; // r2 widened to FP64, + gamma2 on the diagonal
   __nv_bfloat16* sp = nullptr; long long sp_ld = 0, sp_plane = 0; float sp_shift = 0.f;    // planes of r
   __nv_bfloat16* spT = nullptr; long long spT_ld = 0, spT_plane = 0; float spT_shift = 0.f;  // of r^T
+  // optional per-row factor 1 / Tr(row of rs_src) (a row read as a d x d
+  // matrix, leading dimension ldc) applied to r before it is written
+  const float2* rs_src = nullptr; int rs_d = 0;
+  // optional split of K over up to max_ctas / tiles CTAs: FP32 partial tiles
+  // in part (max_ctas x 128 x 64 float2), one ticket per tile in cnt
+  // (zero between launches); the last CTA of a tile sums them in split order
+  float2* part = nullptr; unsigned* cnt = nullptr; int max_ctas = 0;
   unsigned int* err = nullptr;
 };
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
