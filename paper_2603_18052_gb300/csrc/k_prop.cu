@@ -187,6 +187,97 @@ __global__ void __launch_bounds__(128)
   if (rowok && part == 0 && (long long)nslices * steps_per_slice > 0) x[r] = make_double2(re, im);
 }
 
+// Latency form for one state per CTA (n <= 16, few states).  FP64 runs at
+// 1/64 of the FP32 rate here: a warp-wide FP64 instruction occupies its SM
+// sub-partition for 64 cycles however many lanes are active, so the step time
+// is the number of FP64 instructions a warp issues.  The 2n real outputs
+// (Re and Im of each row) each sum 2n real products; an output is split over
+// K lanes of one warp with C products each (C FMAs), the K partial sums meet
+// in a log2(K)-level shuffle tree, and the outputs are spread over four warps
+// (one per sub-partition).  The new state goes through shared memory (double
+// buffered, one barrier per step).  n = 9: C = 3, K = 6, six FP64
+// instructions per warp per step instead of about twenty for one warp.
+template <int CMAX>
+__global__ void __launch_bounds__(128)
+    prop_lat_f64_kernel(int n, int C, int K, int nslices, const z64* __restrict__ P, int steps_per_slice,
+                        z64* __restrict__ states) {
+  __shared__ double X[2][32];  // [xr(0..n-1), xi(0..n-1)], double buffered
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n2 = 2 * n;
+  const int gpw = 32 / K;                 // output groups per warp
+  const int g = lane / K, part = lane - g * K;
+  const int o = g * 4 + warp;             // this lane's output (round robin over the warps)
+  const bool active = g < gpw && o < n2;
+  z64* x = states + (long long)blockIdx.x * n;
+  if (tid < n) {
+    const z64 v = x[tid];
+    X[0][tid] = v.x;
+    X[0][n + tid] = v.y;
+  }
+  // coefficient and state index of each of this lane's C terms
+  const int i = o < n ? o : o - n;
+  int xidx[CMAX];
+  double cf[CMAX];
+  const long long nn = (long long)n * n;
+  int cur = 0;
+  __syncthreads();
+  for (int s = 0; s < nslices; s++) {
+#pragma unroll
+    for (int k = 0; k < CMAX; k++) {
+      const int t = part * C + k;
+      double c = 0.0;
+      int xi_ = 0;
+      if (active && k < C && t < n2) {
+        const int j = t < n ? t : t - n;
+        const z64 pv = P[s * nn + (long long)i * n + j];
+        if (o < n) {  // Re_i = sum_j pr xr - pi xi
+          c = t < n ? pv.x : -pv.y;
+          xi_ = t;
+        } else {      // Im_i = sum_j pr xi + pi xr
+          c = t < n ? pv.x : pv.y;
+          xi_ = t < n ? n + t : t - n;
+        }
+      }
+      cf[k] = c;
+      xidx[k] = xi_;
+    }
+    for (int st = 0; st < steps_per_slice; st++) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < CMAX; k++)
+        if (k < C) acc = fma(cf[k], X[cur][xidx[k]], acc);
+      // segmented tree over the K lanes of the group; the first lane ends with the sum
+      for (int off = 1; off < K; off <<= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, acc, off);
+        if (part + off < K) acc += v;
+      }
+      if (active && part == 0) X[cur ^ 1][o] = acc;
+      __syncthreads();
+      cur ^= 1;
+    }
+  }
+  if (tid < n && (long long)nslices * steps_per_slice > 0) x[tid] = make_double2(X[cur][tid], X[cur][n + tid]);
+}
+
+// Split of 2n products per output for the latency form: C products per lane,
+// K = ceil(2n / C) lanes per output, at most four warps of 32 lanes; the
+// choice minimises C + ceil(log2 K) (FP64 instructions per step).
+bool lat_split(int n, int* C, int* K) {
+  int best = 1 << 30;
+  for (int c = 1; c <= 8; c++) {
+    const int k = (2 * n + c - 1) / c;
+    if (k > 32 || 2 * n > 4 * (32 / k)) continue;
+    int lg = 0;
+    while ((1 << lg) < k) lg++;
+    if (c + lg < best) {
+      best = c + lg;
+      *C = c;
+      *K = k;
+    }
+  }
+  return best < (1 << 30);
+}
+
 __global__ void __launch_bounds__(kResThreads)
     prop_resident_f32_kernel(int n, int d, int nslices, const float* __restrict__ Dr,
                              const float* __restrict__ Di, int steps_per_slice, int B, int chunk,
@@ -318,6 +409,18 @@ cudaError_t launch_propagate_resident_f64(int n, int nslices, const z64* P, int 
 cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P, int steps_per_slice, int B,
                                                z64* states, int adjoint, z64* hist, int sm_count,
                                                cudaStream_t st) {
+  int lc = 0, lk = 0;
+  if (n <= 16 && !adjoint && hist == nullptr && B <= sm_count && lat_split(n, &lc, &lk)) {
+    // few states: one CTA of four warps per state (latency form)
+    count_launch();
+    if (lc <= 2)
+      prop_lat_f64_kernel<2><<<B, 128, 0, st>>>(n, lc, lk, nslices, P, steps_per_slice, states);
+    else if (lc <= 4)
+      prop_lat_f64_kernel<4><<<B, 128, 0, st>>>(n, lc, lk, nslices, P, steps_per_slice, states);
+    else
+      prop_lat_f64_kernel<8><<<B, 128, 0, st>>>(n, lc, lk, nslices, P, steps_per_slice, states);
+    return cudaGetLastError();
+  }
   if (n <= 16 && !adjoint && hist == nullptr) {
     const int grid = (B * 32 + 127) / 128;
     const int K = 32 / n, C = (n + K - 1) / K;

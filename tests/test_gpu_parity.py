@@ -520,10 +520,12 @@ def test_run_instances_matches_oracle(lbm, dev, prec, tol):
         assert err <= tol, (x["model"].d, err)
 
 
-@pytest.mark.parametrize("d,B,S,m", [(1, 3, 2, 5), (2, 1, 3, 50), (3, 7, 2, 10), (4, 33, 2, 4), (5, 2, 1, 6)])
+@pytest.mark.parametrize("d,B,S,m", [(1, 3, 2, 5), (2, 1, 3, 50), (3, 7, 2, 10), (3, 1, 1, 400), (4, 33, 2, 4),
+                                     (3, 300, 2, 3), (4, 200, 1, 5), (5, 2, 1, 6)])
 def test_propagate_fp64_small_n_forms(lbm, dev, d, B, S, m):
-    """n = 1, 4, 9, 16 take the one-warp latency kernel, n = 25 the shared
-    memory kernel."""
+    """n = 1, 4, 9, 16 with at most one state per SM take the four-warp
+    latency kernel (one CTA per state), with more states the one-warp-per-
+    state kernel; n = 25 the shared memory kernel."""
     from workloads.rng import ginibre_states
 
     n = d * d
