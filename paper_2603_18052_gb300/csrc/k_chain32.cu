@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
                         float* __restrict__ Ot, float* __restrict__ part, unsigned* __restrict__ cnt) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float2 cs[CB];
+  __shared__ float2 trp[4][CB];
   __shared__ int is_last;
   const int tid = threadIdx.x;
   const int j0 = blockIdx.x * CB, m0 = blockIdx.y * CB, z = blockIdx.z, splits = gridDim.z;
@@ -108,27 +109,26 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     if (s < nkt) load(s, kt0 + s);
     cp_commit();
   }
-  // per-state factor: 1 / Tr(R_b) (complex), 0 for padding states
-  if (tid < CB) {
-    float2 c = make_float2(0.f, 0.f);
-    const int b = m0 + tid;
+  // per-state factor 1 / Tr(R_b) (complex; 0 for padding states): the d
+  // diagonal entries of the CTA's 64 states are loaded by all 256 threads at
+  // once (four partial sums per state, combined after the K loop), so no
+  // warp waits on a chain of dependent loads before its first K block
+  if (RENORM) {
+    const int b = m0 + (tid & (CB - 1)), q0 = tid >> 6;  // q0 in 0..3
+    float tr = 0.f, ti = 0.f;
     if (b < g.B) {
-      if (RENORM) {
-        float tr = 0.f, ti = 0.f;
-        for (int i = 0; i < g.d; i++) {
+#pragma unroll
+      for (int u = 0; u < 8; u++) {  // d <= 27: at most 7 entries per partial sum
+        const int i = q0 + 4 * u;
+        if (i < g.d) {
           const long long k = (long long)i * (g.d + 1) * g.Bp + b;
-          tr += Rt[k];
-          ti += Rt[pA + k];
+          tr += __ldg(Rt + k);
+          ti += __ldg(Rt + pA + k);
         }
-        const float m2 = tr * tr + ti * ti;
-        c = make_float2(tr / m2, -ti / m2);
-      } else {
-        c = make_float2(1.f, 0.f);
       }
     }
-    cs[tid] = c;
+    trp[q0][tid & (CB - 1)] = make_float2(tr, ti);
   }
-
   const int w = tid >> 5, l = tid & 31;
   const int am = (w >> 2) * 32 + (l & 7) * 4;  // this thread's 4 states
   const int bn = (w & 3) * 16 + (l >> 3) * 4;  // this thread's 4 outputs
@@ -183,6 +183,21 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   }
   cp_wait<0>();
   __syncthreads();
+  if (tid < CB) {
+    float2 c = make_float2(0.f, 0.f);
+    if (m0 + tid < g.B) {
+      if (RENORM) {
+        const float tr = (trp[0][tid].x + trp[1][tid].x) + (trp[2][tid].x + trp[3][tid].x);
+        const float ti = (trp[0][tid].y + trp[1][tid].y) + (trp[2][tid].y + trp[3][tid].y);
+        const float m2 = tr * tr + ti * ti;
+        c = make_float2(tr / m2, -ti / m2);
+      } else {
+        c = make_float2(1.f, 0.f);
+      }
+    }
+    cs[tid] = c;
+  }
+  __syncthreads();
 
   float re[4][4], im[4][4];
 #pragma unroll
@@ -218,10 +233,13 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   for (int q = tid; q < CB * CB / 4; q += CTHREADS) {
     const int jl = q / (CB / 4), b4 = (q % (CB / 4)) * 4;
     float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
-    for (int zz = 0; zz < splits; zz++) {
-      const float* Pz = P0 + (long long)zz * 2 * CB * CB;
-      sr = f4add(sr, __ldcg((const float4*)(Pz + jl * CB + b4)));
-      si = f4add(si, __ldcg((const float4*)(Pz + CB * CB + jl * CB + b4)));
+#pragma unroll
+    for (int zz = 0; zz < 8; zz++) {  // splits <= 8; all loads in flight at once
+      if (zz < splits) {
+        const float* Pz = P0 + (long long)zz * 2 * CB * CB;
+        sr = f4add(sr, __ldcg((const float4*)(Pz + jl * CB + b4)));
+        si = f4add(si, __ldcg((const float4*)(Pz + CB * CB + jl * CB + b4)));
+      }
     }
     chain_finish(g, Rt, Ot, cs + b4, j0 + jl, m0 + b4, sr, si);
   }

@@ -11,8 +11,9 @@
 // K contiguous (K-major).  For C = X Y the A operand is X and the B operand
 // is Y^T (both K-major).  TMA loads 64-wide K blocks with the 128-byte swizzle
 // into a two-stage shared-memory ring: warp 0 issues the copies, one thread of
-// warp 1 issues the MMAs, and after the last K block all four warps read the
-// 128 x BN accumulator tile out of TMEM and apply the FP64 epilogue
+// warp 1 issues the MMAs, and after the last K block all eight warps read the
+// 128 x BN accumulator tile out of TMEM and apply the epilogue (FP32
+// arithmetic, FP64 outputs by exact widening)
 //   C  = alpha acc + sum_t coef_t X_t + gamma I + beta C
 //   C2 = alpha2 acc + sum_t coef2_t X_t + gamma2 I          (optional)
 // and optionally write the split planes of C (row-major and/or transposed)
@@ -34,6 +35,7 @@ namespace {
 constexpr int TBM = 128;           // rows per tile (M of one MMA)
 constexpr int TBK = 64;            // K per stage (128 bytes of BF16)
 constexpr int NSTAGE = 2;
+constexpr int TC_THREADS = 256;   // warps 0-3 and 4-7 share the epilogue
 constexpr int A_PLANE = TBM * 128;  // bytes per A plane per stage
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
@@ -45,7 +47,25 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = 2 * NPA * A_PLANE + 2 * NPB * B_PLANE;
   static constexpr int SMEM = NSTAGE * STAGE_BYTES + 1024;
   static_assert(TBM * (BN + 1) * 8 <= NSTAGE * STAGE_BYTES, "epilogue tile must fit in the ring");
+  // residual tile prefetched behind the ring (light epilogue), if it fits
+  static constexpr int XTILE = TBM * BN * 8;
+  static constexpr bool XPRE_FITS = SMEM + XTILE + 4096 <= 232448;
+  // split-K partials staged in the ring behind the epilogue tile
+  static constexpr int PART_OFF = (TBM * (BN + 1) * 8 + 1023) / 1024 * 1024;
+  static constexpr int PART_SMEM = (NSTAGE * STAGE_BYTES - PART_OFF) / (TBM * BN * 8);
 };
+
+__device__ __forceinline__ void cpa8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cpa16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -136,11 +156,33 @@ __device__ __forceinline__ void put_planes(__nv_bfloat16* base, long long idx, l
   base[idx + 3 * plane] = l;
 }
 
+// Planes of four consecutive elements (idx a multiple of 4, 8-byte aligned):
+// one 8-byte store per plane.
+__device__ __forceinline__ void put_planes4(__nv_bfloat16* base, long long idx, long long plane, const float* re,
+                                            const float* im) {
+  __nv_bfloat16 h[4], l[4], hi_[4], li_[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    split2f(re[j], h[j], l[j]);
+    split2f(im[j], hi_[j], li_[j]);
+  }
+  auto pack = [](const __nv_bfloat16* v) {
+    uint2 w;
+    w.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+    w.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+    return w;
+  };
+  *(uint2*)(base + idx) = pack(h);
+  *(uint2*)(base + idx + plane) = pack(l);
+  *(uint2*)(base + idx + 2 * plane) = pack(hi_);
+  *(uint2*)(base + idx + 3 * plane) = pack(li_);
+}
+
 // Products kept: pieces (i, j) with i + j < max(NPA, NPB): for two pieces
 // each, hi*hi + hi*lo + lo*hi; for a three-piece B also the two products
 // that carry B's third piece.
-template <int NPA, int NPB, int TBN>
-__global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+template <int NPA, int NPB, int TBN, bool LIGHT>
+__global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                                                        const __grid_constant__ CUtensorMap mapB,
                                                        const __grid_constant__ TcProblem P, int ksplit, int kbps) {
   using Cfg = TcCfg<NPA, NPB, TBN>;
@@ -237,10 +279,33 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&acc_bar))
                  : "memory");
   }
+  constexpr bool XPRE = LIGHT && Cfg::XPRE_FITS;
+  float2* xs = (float2*)(sm + NSTAGE * STAGE_BYTES);  // residual tile (XPRE)
+  if (XPRE && warp >= 2 && P.nterms > 0) {
+    // the residual tile X[0] (rows m0.., columns n0..) into shared memory,
+    // copied by the two warps that are idle while the K loop runs
+    const float2* x0 = P.X[0] + (long long)b * P.sX[0];
+    if (P.ldc % 2 == 0 && P.sX[0] % 2 == 0 && ((uintptr_t)P.X[0] & 15) == 0) {
+      for (int e = 2 * (tid - 64); e < TBM * TBN; e += 2 * (TC_THREADS - 64)) {  // pairs: 16-byte copies
+        const int row = m0 + e / TBN, col = n0 + e % TBN;
+        if (row >= P.M || col >= P.N) continue;
+        if (col + 1 < P.N)
+          cpa16(xs + e, x0 + (long long)row * P.ldc + col);
+        else
+          cpa8(xs + e, x0 + (long long)row * P.ldc + col);
+      }
+    } else {
+      for (int e = tid - 64; e < TBM * TBN; e += TC_THREADS - 64) {
+        const int row = m0 + e / TBN, col = n0 + e % TBN;
+        if (row < P.M && col < P.N) cpa8(xs + e, x0 + (long long)row * P.ldc + col);
+      }
+    }
+    cpa_wait_all();
+  }
   if (warp >= 2 && P.rs_src != nullptr) {
-    // per-row factor 1 / Tr (rows m0 .. m0 + 127), computed by the two warps
+    // per-row factor 1 / Tr (rows m0 .. m0 + 127), computed by the warps
     // that are idle while the K loop runs
-    for (int r = tid - 64; r < TBM; r += 64) {
+    for (int r = tid - 64; r < TBM; r += TC_THREADS - 64) {
       float2 c = make_float2(1.f, 0.f);
       const int row = m0 + r;
       if (row < P.M) {
@@ -285,12 +350,15 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     // global reads and writes of the epilogue are coalesced.
     constexpr int LDS = TBN + 1;  // padded row of float2
     float2* tile = (float2*)sm;
-    for (int c0 = 0; c0 < TBN; c0 += 16) {
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quadrant), half
+    // w / 4 of the columns
+    const int quad = warp & 3, half = warp >> 2;
+    for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 16) {
       float vr[16], vi[16];
-      const uint32_t ta = tacc + ((uint32_t)(warp * 32) << 16) + c0;
+      const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16) + c0;
       tmem_ld16(ta, vr);
       tmem_ld16(ta + TBN, vi);
-      const int r = warp * 32 + lane;
+      const int r = quad * 32 + lane;
 #pragma unroll
       for (int j = 0; j < 16; j++) tile[r * LDS + c0 + j] = make_float2(vr[j], vi[j]);
     }
@@ -306,7 +374,7 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     float2* part = P.part + (long long)tile_id * ksplit * TBM * TBN;
     if (good) {
       float4* mine = (float4*)(part + (long long)zs * TBM * TBN);
-      for (int e = tid; e < TBM * TBN / 2; e += 128) {
+      for (int e = tid; e < TBM * TBN / 2; e += TC_THREADS) {
         const float2 u = tile[(2 * e / TBN) * LDS + (2 * e) % TBN], v = tile[(2 * e / TBN) * LDS + (2 * e) % TBN + 1];
         mine[e] = make_float4(u.x, u.y, v.x, v.y);
       }
@@ -318,18 +386,42 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     emit = good && last_cta;
     if (last_cta) {
       __threadfence();
-      if (good) {
+      constexpr int E4 = TBM * TBN / 2;  // float4 (two complex values) per partial tile
+      if (good && ksplit <= Cfg::PART_SMEM) {
+        // all partials into the idle ring with every copy in flight, then
+        // summed in split order from shared memory
+        float4* ps = (float4*)(sm + Cfg::PART_OFF);
         const float4* p4 = (const float4*)part;
-        constexpr int E4 = TBM * TBN / 2;  // float4 (two complex values) per partial tile
-#pragma unroll 4
-        for (int e = tid; e < E4; e += 128) {
-          float4 a = __ldcg(p4 + e);
+        for (int e = tid; e < ksplit * E4; e += TC_THREADS) cpa16(ps + e, p4 + e);
+        cpa_wait_all();
+        __syncthreads();
+        for (int e = tid; e < E4; e += TC_THREADS) {
+          float4 a = ps[e];
           for (int z = 1; z < ksplit; z++) {
-            const float4 v = __ldcg(p4 + (long long)z * E4 + e);
+            const float4 v = ps[z * E4 + e];
             a.x += v.x;
             a.y += v.y;
             a.z += v.z;
             a.w += v.w;
+          }
+          const int r = 2 * e / TBN, cc = (2 * e) % TBN;
+          tile[r * LDS + cc] = make_float2(a.x, a.y);
+          tile[r * LDS + cc + 1] = make_float2(a.z, a.w);
+        }
+      } else if (good) {
+        const float4* p4 = (const float4*)part;
+#pragma unroll 4
+        for (int e = tid; e < E4; e += TC_THREADS) {
+          float4 a = __ldcg(p4 + e);
+#pragma unroll
+          for (int z = 1; z < 8; z++) {  // ksplit <= 8
+            if (z < ksplit) {
+              const float4 v = __ldcg(p4 + (long long)z * E4 + e);
+              a.x += v.x;
+              a.y += v.y;
+              a.z += v.z;
+              a.w += v.w;
+            }
           }
           const int r = 2 * e / TBN, cc = (2 * e) % TBN;
           tile[r * LDS + cc] = make_float2(a.x, a.y);
@@ -349,60 +441,131 @@ __global__ void __launch_bounds__(128) zgemm_tc_kernel(const __grid_constant__ C
     // diagonal term.  The X terms of EU elements are loaded before any of
     // them is stored (the outputs may alias nothing the compiler can prove),
     // so one L2 round trip covers EU elements.
-    constexpr int EU = 8;
-    static_assert((TBM * TBN) % (128 * EU) == 0, "epilogue batches");
-    for (int e0 = tid; e0 < TBM * TBN; e0 += 128 * EU) {
-      float2 xv[4][EU];
+    // Each thread takes quads of four consecutive columns of one row, so the
+    // FP32 output and the BF16 planes go out as 16- and 8-byte stores (one
+    // store instruction per quad and plane instead of one per element);
+    // ragged or misaligned quads fall back to element stores.  The X terms of
+    // QU quads are read before any of them is stored.
+    constexpr int QR = TBN / 4;          // quads per row
+    constexpr int QU = LIGHT ? 4 : 2;    // quads per thread per batch
+    static_assert((TBM * QR) % (TC_THREADS * QU) == 0, "epilogue batches");
+    const int nterms = LIGHT ? (P.nterms > 0 ? 1 : 0) : P.nterms;
+    const bool cf_vec = P.Cf != nullptr && P.ldc % 2 == 0 && P.sC % 2 == 0 && ((uintptr_t)P.Cf & 15) == 0;
+    const bool sp_vec = P.sp != nullptr && P.sp_ld % 4 == 0 && P.sp_plane % 4 == 0 && ((uintptr_t)P.sp & 7) == 0;
+    for (int e0 = tid; e0 < TBM * QR; e0 += TC_THREADS * QU) {
+      float2 xv[4][QU][4];
 #pragma unroll
-      for (int u = 0; u < EU; u++) {
-        const int e = e0 + 128 * u;
-        const int r = e / TBN, cc = e - (e / TBN) * TBN;
-        const int row = m0 + r, col = n0 + cc;
-        const bool in = row < P.M && col < P.N;
+      for (int q = 0; q < 4; q++) {
+        if (q < nterms) {  // uniform: X[q] is set
+          const float2* xq = P.X[q] + bs * P.sX[q];
 #pragma unroll
-        for (int q = 0; q < 4; q++)
-          xv[q][u] = (q < P.nterms && in) ? __ldg(P.X[q] + bs * P.sX[q] + (long long)row * P.ldc + col)
-                                          : make_float2(0.f, 0.f);
+          for (int u = 0; u < QU; u++) {
+            const int e4 = e0 + TC_THREADS * u;
+            const int r = e4 / QR, cq = (e4 % QR) * 4;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+              if (XPRE) {
+                xv[q][u][j] = xs[r * TBN + cq + j];
+              } else {
+                const int row = min(m0 + r, P.M - 1), col = min(n0 + cq + j, P.N - 1);  // in bounds
+                xv[q][u][j] = __ldg(xq + (long long)row * P.ldc + col);
+              }
+            }
+          }
+        }
       }
 #pragma unroll
-      for (int u = 0; u < EU; u++) {
-        const int e = e0 + 128 * u;
-        const int r = e / TBN, cc = e - (e / TBN) * TBN;
-        const int row = m0 + r, col = n0 + cc;
+      for (int u = 0; u < QU; u++) {
+        const int e4 = e0 + TC_THREADS * u;
+        const int r = e4 / QR, cq = (e4 % QR) * 4;
+        const int row = m0 + r, col = n0 + cq;
         if (row >= P.M || col >= P.N) continue;
-        const float2 a2 = tile[r * LDS + cc];
-        const long long off = bs * P.sC + (long long)row * P.ldc + col;
-        float cr = P.alpha * a2.x, ci = P.alpha * a2.y;
-        float dr = P.alpha2 * a2.x, di = P.alpha2 * a2.y;
+        const bool full = col + 3 < P.N;
+        float cr[4], ci[4], dr[4], di[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          if (q >= P.nterms) break;
-          cr = fmaf(P.coef[q], xv[q][u].x, cr);
-          ci = fmaf(P.coef[q], xv[q][u].y, ci);
-          dr = fmaf(P.coef2[q], xv[q][u].x, dr);
-          di = fmaf(P.coef2[q], xv[q][u].y, di);
+        for (int j = 0; j < 4; j++) {
+          const float2 a2 = tile[r * LDS + cq + j];
+          cr[j] = P.alpha * a2.x;
+          ci[j] = P.alpha * a2.y;
+          dr[j] = P.alpha2 * a2.x;
+          di[j] = P.alpha2 * a2.y;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            if (q < nterms) {
+              cr[j] = fmaf(P.coef[q], xv[q][u][j].x, cr[j]);
+              ci[j] = fmaf(P.coef[q], xv[q][u][j].y, ci[j]);
+              if (!LIGHT) {
+                dr[j] = fmaf(P.coef2[q], xv[q][u][j].x, dr[j]);
+                di[j] = fmaf(P.coef2[q], xv[q][u][j].y, di[j]);
+              }
+            }
+          }
+          if (P.rs_src != nullptr) {
+            const float2 c = rscale[r];
+            const float t = cr[j] * c.x - ci[j] * c.y;
+            ci[j] = cr[j] * c.y + ci[j] * c.x;
+            cr[j] = t;
+          }
         }
-        if (P.rs_src != nullptr) {
-          const float2 c = rscale[r];
-          const float t = cr * c.x - ci * c.y;
-          ci = cr * c.y + ci * c.x;
-          cr = t;
+        const long long off = bs * P.sC + (long long)row * P.ldc + col;
+        if (P.Cf != nullptr) {
+          if (cf_vec && full) {
+            float4* d4 = (float4*)(P.Cf + off);
+            d4[0] = make_float4(cr[0], ci[0], cr[1], ci[1]);
+            d4[1] = make_float4(cr[2], ci[2], cr[3], ci[3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if (col + j < P.N) P.Cf[off + j] = make_float2(cr[j], ci[j]);
+          }
         }
-        if (P.Cf != nullptr) P.Cf[off] = make_float2(cr, ci);
-        if (P.Cd != nullptr) P.Cd[off] = make_double2(row == col ? widen(cr) + P.gamma : widen(cr), widen(ci));
-        if (P.C2d != nullptr)
-          P.C2d[off] = make_double2(row == col ? widen(dr) + P.gamma2 : widen(dr), widen(di));
-        if (P.sp != nullptr)
-          put_planes(P.sp, bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col, P.sp_plane,
-                     row == col ? cr - P.sp_shift : cr, ci);
-        if (P.spT != nullptr) tile[r * LDS + cc] = make_float2(row == col ? cr - P.spT_shift : cr, ci);
+        if (!LIGHT) {
+          // FP64 outputs: exact widening only; the diagonal terms are added
+          // in a separate pass (FP64 arithmetic costs 64 cycles per warp
+          // instruction, taken or not)
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            if (col + j >= P.N) continue;
+            if (P.Cd != nullptr) P.Cd[off + j] = make_double2(widen(cr[j]), widen(ci[j]));
+            if (P.C2d != nullptr) P.C2d[off + j] = make_double2(widen(dr[j]), widen(di[j]));
+          }
+        }
+        if (P.sp != nullptr) {
+          float pr[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) pr[j] = (row == col + j) ? cr[j] - P.sp_shift : cr[j];
+          const long long idx = bs * 4 * P.sp_plane + (long long)row * P.sp_ld + col;
+          if (sp_vec && full) {
+            put_planes4(P.sp, idx, P.sp_plane, pr, ci);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if (col + j < P.N) put_planes(P.sp, idx + j, P.sp_plane, pr[j], ci[j]);
+          }
+        }
+        if (!LIGHT && P.spT != nullptr) {
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            tile[r * LDS + cq + j] = make_float2(row == col + j ? cr[j] - P.spT_shift : cr[j], ci[j]);
+        }
       }
     }
-    if (P.spT != nullptr) {
+    if (!LIGHT && (P.Cd != nullptr || P.C2d != nullptr)) {
+      // diagonal of the tile: + gamma, + gamma2 (this thread's own stores
+      // above are visible to the CTA after the barrier)
+      __syncthreads();
+      const int dg = m0 + tid;
+      if (tid < TBM && dg >= n0 && dg < n0 + TBN && dg < P.M && dg < P.N) {
+        const long long off = bs * P.sC + (long long)dg * P.ldc + dg;
+        if (P.Cd != nullptr) P.Cd[off].x += P.gamma;
+        if (P.C2d != nullptr) P.C2d[off].x += P.gamma2;
+      }
+    }
+    if (!LIGHT && P.spT != nullptr) {
       // transposed planes (B-operand layout): consecutive threads take
       // consecutive rows, which are contiguous in the transpose
       __syncthreads();
-      for (int e = tid; e < TBM * TBN; e += 128) {
+      for (int e = tid; e < TBM * TBN; e += TC_THREADS) {
         const int cc = e / TBM, r = e - (e / TBM) * TBM;
         const int row = m0 + r, col = n0 + cc;
         if (row >= P.M || col >= P.N) continue;
@@ -472,12 +635,12 @@ __global__ void lincomb_splitT_kernel(int n, long long total, const float2* __re
 
 // One warp per state (FP32): optional division by the trace, then the
 // state's two-piece planes (row b of the [4][B][ld] plane tensor).
-__global__ void renorm_split_kernel(int n, int d, int B, int renorm, float2* __restrict__ X,
+__global__ void renorm_split_kernel(int n, int d, int B, int renorm, float2* __restrict__ X, long long xld,
                                     __nv_bfloat16* __restrict__ planes, long long ld, long long plane) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= B) return;
-  float2* x = X + (long long)w * n;
+  float2* x = X + (long long)w * xld;
   float cr = 1.f, ci = 0.f;
   if (renorm) {
     float sr = 0.f, si = 0.f;
@@ -503,16 +666,24 @@ __global__ void renorm_split_kernel(int n, int d, int B, int renorm, float2* __r
   }
 }
 
-__global__ void states_c64_to_f32_kernel(long long total, const z64* __restrict__ a, float2* __restrict__ b) {
+// states: complex128 rows of n (stride n) <-> FP32 rows of n (stride ld >= n)
+__global__ void states_c64_to_f32_kernel(int n, long long total, const z64* __restrict__ a, float2* __restrict__ b,
+                                         long long ld) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    b[e] = make_float2((float)a[e].x, (float)a[e].y);
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n, c = e - (e / n) * n;
+    b[r * ld + c] = make_float2((float)a[e].x, (float)a[e].y);
+  }
 }
 
-__global__ void states_f32_to_c64_kernel(long long total, const float2* __restrict__ a, z64* __restrict__ b) {
+__global__ void states_f32_to_c64_kernel(int n, long long total, const float2* __restrict__ a, long long ld,
+                                         z64* __restrict__ b) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    b[e] = make_double2(widen(a[e].x), widen(a[e].y));
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n, c = e - (e / n) * n;
+    const float2 v = a[r * ld + c];
+    b[e] = make_double2(widen(v.x), widen(v.y));
+  }
 }
 
 unsigned grid_for(long long total) {
@@ -567,28 +738,30 @@ cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, __nv_bfloat16* planes, long long ld,
-                                long long plane, cudaStream_t st) {
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, long long xld, __nv_bfloat16* planes,
+                                long long ld, long long plane, cudaStream_t st) {
   const int grid = (B * 32 + 255) / 256;
   count_launch();
-  renorm_split_kernel<<<grid, 256, 0, st>>>(n, d, B, renorm, X, planes, ld, plane);
+  renorm_split_kernel<<<grid, 256, 0, st>>>(n, d, B, renorm, X, xld, planes, ld, plane);
   return cudaGetLastError();
 }
 
-cudaError_t launch_states_c64_f32(long long count, const z64* a, float2* b, cudaStream_t st) {
+cudaError_t launch_states_c64_f32(int n, int B, const z64* a, float2* b, long long ld, cudaStream_t st) {
+  const long long count = (long long)n * B;
   count_launch();
-  states_c64_to_f32_kernel<<<grid_for(count), 256, 0, st>>>(count, a, b);
+  states_c64_to_f32_kernel<<<grid_for(count), 256, 0, st>>>(n, count, a, b, ld);
   return cudaGetLastError();
 }
 
-cudaError_t launch_states_f32_c64(long long count, const float2* a, z64* b, cudaStream_t st) {
+cudaError_t launch_states_f32_c64(int n, int B, const float2* a, long long ld, z64* b, cudaStream_t st) {
+  const long long count = (long long)n * B;
   count_launch();
-  states_f32_to_c64_kernel<<<grid_for(count), 256, 0, st>>>(count, a, b);
+  states_f32_to_c64_kernel<<<grid_for(count), 256, 0, st>>>(n, count, a, ld, b);
   return cudaGetLastError();
 }
 
 namespace {
-template <int NPA, int NPB, int BN>
+template <int NPA, int NPB, int BN, bool LIGHT>
 cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
   using Cfg = TcCfg<NPA, NPB, BN>;
   static_assert(Cfg::SMEM <= 232448, "shared memory");
@@ -596,7 +769,8 @@ cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
   if (!encode_planes(&ma, p.Aop, p.M, p.K, p.a_ld, p.a_plane, 2 * NPA * p.batch, TBM) ||
       !encode_planes(&mb, p.Bop, p.N, p.K, p.b_ld, p.b_plane, 2 * NPB * p.batch, BN))
     return cudaErrorInvalidValue;
-  cudaError_t e = set_smem_once((const void*)zgemm_tc_kernel<NPA, NPB, BN>, Cfg::SMEM);
+  constexpr int SMEM = Cfg::SMEM + ((LIGHT && Cfg::XPRE_FITS) ? Cfg::XTILE : 0);
+  cudaError_t e = set_smem_once((const void*)zgemm_tc_kernel<NPA, NPB, BN, LIGHT>, SMEM);
   if (e != cudaSuccess) return e;
   const int gx = (p.N + BN - 1) / BN, gy = (p.M + TBM - 1) / TBM;
   const int tiles = gx * gy * p.batch, nk = (p.K + TBK - 1) / TBK;
@@ -607,15 +781,18 @@ cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
   ksplit = (nk + kbps - 1) / kbps;
   dim3 grid(gx, gy, p.batch * ksplit);
   count_launch();
-  zgemm_tc_kernel<NPA, NPB, BN><<<grid, 128, Cfg::SMEM, st>>>(ma, mb, p, ksplit, kbps);
+  zgemm_tc_kernel<NPA, NPB, BN, LIGHT><<<grid, TC_THREADS, SMEM, st>>>(ma, mb, p, ksplit, kbps);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st) {
   if (p.M <= 0 || p.N <= 0 || p.batch <= 0) return cudaSuccess;
-  if (p.npa == 2 && p.npb == 2) return launch_tc<2, 2, 64>(p, st);
-  if (p.npa == 2 && p.npb == 3) return launch_tc<2, 3, 32>(p, st);
+  // the light epilogue (one X term, FP32 output, row-major planes, row
+  // factor) serves the propagation steps
+  const bool light = p.nterms <= 1 && p.Cd == nullptr && p.C2d == nullptr && p.spT == nullptr;
+  if (p.npa == 2 && p.npb == 2) return light ? launch_tc<2, 2, 64, true>(p, st) : launch_tc<2, 2, 64, false>(p, st);
+  if (p.npa == 2 && p.npb == 3) return light ? launch_tc<2, 3, 32, true>(p, st) : launch_tc<2, 3, 32, false>(p, st);
   return cudaErrorInvalidValue;
 }
 

@@ -681,12 +681,14 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
     // real product, FP32 accumulation, K split over CTAs when the tiles do
     // not fill the GPU.
     const long long ld = plane_ld(n), dpl = (long long)n * ld, rpl = (long long)B * ld;
-    float2* cur = (float2*)c->Rtmp;  // the FP64 scratch holds two FP32 state buffers
-    float2* nxt = cur + (long long)B * n;
+    // FP32 states with rows padded to ld (16-byte aligned rows: vector
+    // stores in the epilogue), in the FP32 chain's state buffers
+    float2* cur = (float2*)c->C32a;
+    float2* nxt = (float2*)c->C32b;
     __nv_bfloat16* pc = c->spR[0];
     __nv_bfloat16* pn = c->spR[1];
-    LB_CUDA(launch_states_c64_f32((long long)B * n, X, cur, st));
-    LB_CUDA(launch_renorm_split(n, d, B, 0, cur, pc, ld, rpl, st));
+    LB_CUDA(launch_states_c64_f32(n, B, X, cur, ld, st));
+    LB_CUDA(launch_renorm_split(n, d, B, 0, cur, ld, pc, ld, rpl, st));
     for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
       const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
       LB_CUDA(launch_split(n, n, S, Pz + s0 * nn, n, nn, 1.0, 0, c->sp[0], ld, dpl, st, 3));
@@ -697,7 +699,7 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
           q.npa = 2; q.npb = 3;
           q.Aop = pc; q.a_ld = ld; q.a_plane = rpl;
           q.Bop = c->sp[0] + (long long)s * 6 * dpl; q.b_ld = ld; q.b_plane = dpl;
-          q.ldc = n;
+          q.ldc = ld;
           q.nterms = 1; q.X[0] = cur; q.coef[0] = 1.f;
           q.Cf = nxt;
           q.sp = pn; q.sp_ld = ld; q.sp_plane = rpl;
@@ -713,8 +715,8 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
         }
     }
     // the last step's trace factor (the others were applied one step late)
-    if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, cur, pn, ld, rpl, st));
-    LB_CUDA(launch_states_f32_c64((long long)B * n, cur, X, st));
+    if (renorm_trace) LB_CUDA(launch_renorm_split(n, d, B, 1, cur, ld, pn, ld, rpl, st));
+    LB_CUDA(launch_states_f32_c64(n, B, cur, ld, X, st));
     return LB_OK;
   }
   // FP32: D = P - I in FP32, states in FP32

@@ -257,10 +257,10 @@ cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* 
                                   float c1, float c2, __nv_bfloat16* dst, long long ldd, long long plane,
                                   cudaStream_t st);
 // per FP32 state: optional division by the trace, then the row's two-piece planes
-cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, __nv_bfloat16* planes, long long ld,
-                                long long plane, cudaStream_t st);
-cudaError_t launch_states_c64_f32(long long count, const z64* a, float2* b, cudaStream_t st);
-cudaError_t launch_states_f32_c64(long long count, const float2* a, z64* b, cudaStream_t st);
+cudaError_t launch_renorm_split(int n, int d, int B, int renorm, float2* X, long long xld, __nv_bfloat16* planes,
+                                long long ld, long long plane, cudaStream_t st);
+cudaError_t launch_states_c64_f32(int n, int B, const z64* a, float2* b, long long ld, cudaStream_t st);
+cudaError_t launch_states_f32_c64(int n, int B, const float2* a, long long ld, z64* b, cudaStream_t st);
 long long plane_ld(int K);
 // planes of src (R x Kc per slice) or of its transpose, diagonal shifted
 // np BF16 pieces per value: planes [S][2 np][..] (re pieces, then im pieces)
