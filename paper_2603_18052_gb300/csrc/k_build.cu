@@ -187,6 +187,15 @@ __global__ void lincomb3_kernel(long long total, const z64* __restrict__ X0, con
   }
 }
 
+// Z[e] += 2 X[e] (FP64; one add per component, 2 X is exact)
+__global__ void add_twice_kernel(long long total, const z64* __restrict__ X, z64* __restrict__ Z) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const z64 a = X[e], z = Z[e];
+    Z[e] = make_double2(z.x + 2.0 * a.x, z.y + 2.0 * a.y);
+  }
+}
+
 __global__ void copy_block_kernel(int S, long long ld, long long stride, int r0, int nr, int c0, int nc,
                                   const z64* __restrict__ src, z64* __restrict__ dst) {
   const long long per = (long long)nr * nc;
@@ -385,6 +394,15 @@ cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z
   const long long total = (long long)nn * S;
   count_launch();
   lincomb3_kernel<<<grid_for(total, 256, 152), 256, 0, st>>>(total, X0, X1, X2, c0, c1, c2, Z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_twice(long long nn, int S, const z64* X, z64* Z, cudaStream_t st) {
+  const long long total = nn * S;
+  long long g = (total + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  count_launch();
+  add_twice_kernel<<<(unsigned)g, 256, 0, st>>>(total, X, Z);
   return cudaGetLastError();
 }
 

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   constexpr int B_PLANE = Cfg::B_PLANE;
   constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr int NPMAX = NPA > NPB ? NPA : NPB;
+  if (P.active != nullptr && P.active[blockIdx.z / ksplit] <= P.active_iter) return;  // whole CTA, before any setup
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE], acc_bar;

@@ -572,7 +572,26 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
     ZGemmProblem q = sq(n, S, P, P, c->Z1);
     q.active = c->sc;
     q.active_iter = it;
-    if (prec != LB_FP64) {
+    if (prec == LB_BF16X3) {
+      // D D on the tensor cores (D = P - I: rows in two BF16 pieces, D^T in
+      // three), Z1 = D D - I widened to FP64, then Z1 = 2P + Z1 in FP64
+      const long long ld = plane_ld(n), pl = (long long)n * ld;
+      LB_CUDA(launch_split(n, n, S, P, n, nn, 1.0, 0, c->sp[1], ld, pl, st, 2));
+      LB_CUDA(launch_split(n, n, S, P, n, nn, 1.0, 1, c->sp[0], ld, pl, st, 3));
+      TcProblem t;
+      t.M = t.N = t.K = n;
+      t.batch = S;
+      t.npa = 2; t.npb = 3;
+      t.Aop = c->sp[1]; t.a_ld = ld; t.a_plane = pl;
+      t.Bop = c->sp[0]; t.b_ld = ld; t.b_plane = pl;
+      t.ldc = n; t.sC = nn;
+      t.Cd = c->Z1; t.gamma = -1.0;
+      t.active = c->kmix; t.active_iter = it;
+      t.err = c->err_dev;
+      LB_CUDA(zgemm_tc(t, st));
+      LB_CUDA(launch_add_twice(nn, S, P, c->Z1, st));
+      q.active_lo = c->kmix;
+    } else if (prec != LB_FP64) {
       ZGemmProblem qm = sq(n, S, P, P, c->Z1);
       qm.shiftA = qm.shiftB = 1.0;
       qm.nterms = 1;

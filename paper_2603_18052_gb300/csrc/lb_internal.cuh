@@ -147,6 +147,8 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
 // Z[b] = c0*X0[b] + c1*X1[b] + c2*X2[b]  (n x n each, batch strides = n*n)
 cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z64* X2, double c0,
                             double c1, double c2, z64* Z, cudaStream_t st);
+// Z[b] += 2 X[b] (nn elements per batch element)
+cudaError_t launch_add_twice(long long nn, int S, const z64* X, z64* Z, cudaStream_t st);
 
 // --------------------------------------------------------------- LU -------
 // Factor the kb x kb diagonal block at (k0, k0) of M[b] (no pivot search),
@@ -249,6 +251,8 @@ struct TcProblem {
   // in part (max_ctas x 128 x 64 float2), one ticket per tile in cnt
   // (zero between launches); the last CTA of a tile sums them in split order
   float2* part = nullptr; unsigned* cnt = nullptr; int max_ctas = 0;
+  // optional batch mask: batch element b is skipped when active[b] <= active_iter
+  const int* active = nullptr; int active_iter = 0;
   unsigned int* err = nullptr;
 };
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
