@@ -335,8 +335,21 @@ ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C) {
 
 // Blocked LU of Mx[s] (no pivot search) applied to the right-hand sides held in
 // N[s] (n x nrhs, leading dimension ldN, slice stride sN), then back
-// substitution into N[s]:  N <- Mx^{-1} N.  Y (same shape as N) and Uf (n x n
-// per slice) are scratch, Lp scratch (n x nb per slice, stride n*n).
+// substitution into N[s]:  N <- Mx^{-1} N.  Uf (U), Lp (L) and Y (same shape
+// as N) are n x n-per-slice scratch.
+//
+// Left-looking (Crout) order: at block step k the block row and the block
+// column of Mx are first brought up to date with everything factored so far,
+// each in one GEMM whose K is all previous blocks (K = k0), together with
+// the block row of the right-hand sides; then the 32 x 32 diagonal block is
+// factored and inverted in shared memory (lu_diag) and the new U row panel,
+// L column panel and forward-substituted rows follow from the block
+// inverses (K = 32).  The back substitution is left-looking too.  The
+// FLOPs are those of the right-looking form; almost all of them now sit in
+// GEMMs with long K loops instead of K = 32 updates, whose fixed costs
+// (operand loads before the first multiply, the complex epilogue in FP64,
+// one round trip per tile) are paid once per output tile instead of once
+// per block step.
 lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, int nrhs, long long ldN, long long sN,
                            z64* Uf, z64* Y, z64* Lp, cudaStream_t st) {
   const long long nn = (long long)n * n;
@@ -345,58 +358,78 @@ lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, int nrhs, l
   for (int k = 0; k < nbk; k++) {
     const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, rest = n - k0 - kb;
     z64* Uinv_k = c->Uinv + (long long)k * nb * nb;
+    if (k0 > 0) {
+      ZGemmProblem pr[3];
+      int np = 0;
+      {  // block row k, columns k0..n-1:  Mx[k0:k0+kb, k0:] -= L[k0:k0+kb, :k0] U[:k0, k0:]
+        ZGemmProblem& a = pr[np++];
+        a.M = kb; a.N = n - k0; a.K = k0;
+        a.A = Lp + (long long)k0 * n; a.lda = n; a.sA = nn;
+        a.B = Uf + k0; a.ldb = n; a.sB = nn;
+        a.C = Mx + (long long)k0 * n + k0; a.ldc = n; a.sC = nn;
+        a.alpha = -1.0; a.beta = 1.0; a.batch = S;
+      }
+      if (rest > 0) {  // block column k below the diagonal:  Mx[k0+kb:, k0:k0+kb] -= L[k0+kb:, :k0] U[:k0, k0:k0+kb]
+        ZGemmProblem& b = pr[np++];
+        b.M = rest; b.N = kb; b.K = k0;
+        b.A = Lp + (long long)(k0 + kb) * n; b.lda = n; b.sA = nn;
+        b.B = Uf + k0; b.ldb = n; b.sB = nn;
+        b.C = Mx + (long long)(k0 + kb) * n + k0; b.ldc = n; b.sC = nn;
+        b.alpha = -1.0; b.beta = 1.0; b.batch = S;
+      }
+      {  // right-hand sides, block row k:  N[k0:k0+kb, :] -= L[k0:k0+kb, :k0] Y[:k0, :]
+        ZGemmProblem& q = pr[np++];
+        q.M = kb; q.N = nrhs; q.K = k0;
+        q.A = Lp + (long long)k0 * n; q.lda = n; q.sA = nn;
+        q.B = Y; q.ldb = ldN; q.sB = sN;
+        q.C = N + (long long)k0 * ldN; q.ldc = ldN; q.sC = sN;
+        q.alpha = -1.0; q.beta = 1.0; q.batch = S;
+      }
+      LB_CUDA(zgemm_f64(pr, np, c->sm_count, st));
+    }
     LB_CUDA(launch_lu_diag(n, S, k0, kb, Mx, Uf, c->Linv, sLinv, Uinv_k, sUinv, c->err_dev, st));
-    ZGemmProblem pr[3];
-    int np = 0;
-    if (rest > 0) {
-      // (a) Lp = Mx[k0+kb:, k0:k0+kb] Uinv_k
-      ZGemmProblem& a = pr[np++];
-      a.M = rest; a.N = kb; a.K = kb;
-      a.A = Mx + (long long)(k0 + kb) * n + k0; a.lda = n; a.sA = nn;
-      a.B = Uinv_k; a.ldb = nb; a.sB = sUinv;
-      a.C = Lp; a.ldc = nb; a.sC = nn;
-      a.batch = S;
-      // (b) Uf[k0:k0+kb, k0+kb:] = Linv_k Mx[k0:k0+kb, k0+kb:]
-      ZGemmProblem& b = pr[np++];
-      b.M = kb; b.N = rest; b.K = kb;
-      b.A = c->Linv; b.lda = nb; b.sA = sLinv;
-      b.B = Mx + (long long)k0 * n + k0 + kb; b.ldb = n; b.sB = nn;
-      b.C = Uf + (long long)k0 * n + k0 + kb; b.ldc = n; b.sC = nn;
-      b.batch = S;
-    }
     {
-      // (c) Y[k0:k0+kb, :] = Linv_k N[k0:k0+kb, :]
-      ZGemmProblem& q = pr[np++];
-      q.M = kb; q.N = nrhs; q.K = kb;
-      q.A = c->Linv; q.lda = nb; q.sA = sLinv;
-      q.B = N + (long long)k0 * ldN; q.ldb = ldN; q.sB = sN;
-      q.C = Y + (long long)k0 * ldN; q.ldc = ldN; q.sC = sN;
-      q.batch = S;
-    }
-    LB_CUDA(zgemm_f64(pr, np, c->sm_count, st));
-    if (rest > 0) {
-      ZGemmProblem tr[2];
-      // (d) Mx[k0+kb:, k0+kb:] -= Lp Uf[k0:k0+kb, k0+kb:]
-      ZGemmProblem& d = tr[0];
-      d.M = rest; d.N = rest; d.K = kb;
-      d.A = Lp; d.lda = nb; d.sA = nn;
-      d.B = Uf + (long long)k0 * n + k0 + kb; d.ldb = n; d.sB = nn;
-      d.C = Mx + (long long)(k0 + kb) * n + k0 + kb; d.ldc = n; d.sC = nn;
-      d.alpha = -1.0; d.beta = 1.0; d.batch = S;
-      // (e) N[k0+kb:, :] -= Lp Y[k0:k0+kb, :]
-      ZGemmProblem& e = tr[1];
-      e.M = rest; e.N = nrhs; e.K = kb;
-      e.A = Lp; e.lda = nb; e.sA = nn;
-      e.B = Y + (long long)k0 * ldN; e.ldb = ldN; e.sB = sN;
-      e.C = N + (long long)(k0 + kb) * ldN; e.ldc = ldN; e.sC = sN;
-      e.alpha = -1.0; e.beta = 1.0; e.batch = S;
-      LB_CUDA(zgemm_f64(tr, 2, c->sm_count, st));
+      ZGemmProblem pr[3];
+      int np = 0;
+      if (rest > 0) {
+        // U[k0:k0+kb, k0+kb:] = Linv_k Mx[k0:k0+kb, k0+kb:]
+        ZGemmProblem& u = pr[np++];
+        u.M = kb; u.N = rest; u.K = kb;
+        u.A = c->Linv; u.lda = nb; u.sA = sLinv;
+        u.B = Mx + (long long)k0 * n + k0 + kb; u.ldb = n; u.sB = nn;
+        u.C = Uf + (long long)k0 * n + k0 + kb; u.ldc = n; u.sC = nn;
+        u.batch = S;
+        // L[k0+kb:, k0:k0+kb] = Mx[k0+kb:, k0:k0+kb] Uinv_k
+        ZGemmProblem& l = pr[np++];
+        l.M = rest; l.N = kb; l.K = kb;
+        l.A = Mx + (long long)(k0 + kb) * n + k0; l.lda = n; l.sA = nn;
+        l.B = Uinv_k; l.ldb = nb; l.sB = sUinv;
+        l.C = Lp + (long long)(k0 + kb) * n + k0; l.ldc = n; l.sC = nn;
+        l.batch = S;
+      }
+      // Y[k0:k0+kb, :] = Linv_k N[k0:k0+kb, :]
+      ZGemmProblem& y = pr[np++];
+      y.M = kb; y.N = nrhs; y.K = kb;
+      y.A = c->Linv; y.lda = nb; y.sA = sLinv;
+      y.B = N + (long long)k0 * ldN; y.ldb = ldN; y.sB = sN;
+      y.C = Y + (long long)k0 * ldN; y.ldc = ldN; y.sC = sN;
+      y.batch = S;
+      LB_CUDA(zgemm_f64(pr, np, c->sm_count, st));
     }
   }
-  // back substitution: X_k = Uinv_k Y_k; Y[:k0] -= Uf[:k0, k0:k0+kb] X_k
+  // back substitution: X_k = Uinv_k (Y_k - U[k0:k0+kb, k0+kb:] X[k0+kb:]), X into N
   for (int k = nbk - 1; k >= 0; k--) {
-    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb;
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, rest = n - k0 - kb;
     z64* Uinv_k = c->Uinv + (long long)k * nb * nb;
+    if (rest > 0) {
+      ZGemmProblem g;
+      g.M = kb; g.N = nrhs; g.K = rest;
+      g.A = Uf + (long long)k0 * n + k0 + kb; g.lda = n; g.sA = nn;
+      g.B = N + (long long)(k0 + kb) * ldN; g.ldb = ldN; g.sB = sN;
+      g.C = Y + (long long)k0 * ldN; g.ldc = ldN; g.sC = sN;
+      g.alpha = -1.0; g.beta = 1.0; g.batch = S;
+      LB_CUDA(zgemm_f64(&g, 1, c->sm_count, st));
+    }
     ZGemmProblem f;
     f.M = kb; f.N = nrhs; f.K = kb;
     f.A = Uinv_k; f.lda = nb; f.sA = sUinv;
@@ -404,15 +437,6 @@ lb_status lu_solve_blocked(lb_ctx* c, int n, int S, z64* Mx, z64* N, int nrhs, l
     f.C = N + (long long)k0 * ldN; f.ldc = ldN; f.sC = sN;
     f.batch = S;
     LB_CUDA(zgemm_f64(&f, 1, c->sm_count, st));
-    if (k0 > 0) {
-      ZGemmProblem gq;
-      gq.M = k0; gq.N = nrhs; gq.K = kb;
-      gq.A = Uf + k0; gq.lda = n; gq.sA = nn;
-      gq.B = N + (long long)k0 * ldN; gq.ldb = ldN; gq.sB = sN;
-      gq.C = Y; gq.ldc = ldN; gq.sC = sN;
-      gq.alpha = -1.0; gq.beta = 1.0; gq.batch = S;
-      LB_CUDA(zgemm_f64(&gq, 1, c->sm_count, st));
-    }
   }
   return LB_OK;
 }
