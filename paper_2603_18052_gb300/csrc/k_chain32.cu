@@ -53,6 +53,12 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Programmatic dependent launch: a step launched with programmatic stream
+// serialisation may start while the previous step drains; it reads nothing
+// the previous step writes before griddep_wait() (a no-op otherwise).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
@@ -94,19 +100,30 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   const int nkt = kt1 - kt0;
   const long long pA = (long long)g.Kp * g.Bp, pB = (long long)g.Kp * g.Np;
 
-  auto load = [&](int stage, int kt) {
+  auto loadA = [&](int stage, int kt) {  // states: written by the previous step
     float* sA = sm + stage * STAGE_FLOATS;
-    float* sB = sA + OPER_FLOATS;
     const int k0 = kt * CK;
     for (int c = tid; c < NPL * CK * (CB / 4); c += CTHREADS) {
       const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
       cp16(sA + (p * CK + r) * CB + 4 * q, Rt + p * pA + (long long)(k0 + r) * g.Bp + m0 + 4 * q);
+    }
+  };
+  auto loadB = [&](int stage, int kt) {  // D^T: written before the chain started
+    float* sB = sm + stage * STAGE_FLOATS + OPER_FLOATS;
+    const int k0 = kt * CK;
+    for (int c = tid; c < NPL * CK * (CB / 4); c += CTHREADS) {
+      const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
       cp16(sB + (p * CK + r) * CB + 4 * q, Dt + p * pB + (long long)(k0 + r) * g.Np + j0 + 4 * q);
     }
   };
+  // the first stages of D^T before the wait for the previous step, then the states
+#pragma unroll
+  for (int s = 0; s < CSTAGE - 1; s++)
+    if (s < nkt) loadB(s, kt0 + s);
+  griddep_wait();
 #pragma unroll
   for (int s = 0; s < CSTAGE - 1; s++) {
-    if (s < nkt) load(s, kt0 + s);
+    if (s < nkt) loadA(s, kt0 + s);
     cp_commit();
   }
   // per-state factor 1 / Tr(R_b) (complex; 0 for padding states): the d
@@ -143,7 +160,10 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     __syncthreads();
     {
       const int nx = it + CSTAGE - 1;
-      if (nx < nkt) load(nx % CSTAGE, kt0 + nx);
+      if (nx < nkt) {
+        loadA(nx % CSTAGE, kt0 + nx);
+        loadB(nx % CSTAGE, kt0 + nx);
+      }
       cp_commit();
     }
     const float* sA = sm + (it % CSTAGE) * STAGE_FLOATS;
@@ -182,6 +202,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     }
   }
   cp_wait<0>();
+  griddep_launch();  // the next step may start its prologue
   __syncthreads();
   if (tid < CB) {
     float2 c = make_float2(0.f, 0.f);
@@ -382,7 +403,7 @@ cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt,
 }
 
 cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
-                                unsigned* cnt, int sm_count, cudaStream_t st) {
+                                unsigned* cnt, int sm_count, bool pdl, cudaStream_t st) {
   ChainDims g;
   g.n = n;
   g.d = chain_isqrt(n);
@@ -400,20 +421,22 @@ cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const
   splits = (ktiles + kps - 1) / kps;
   if (splits > 1 && (tiles * splits > 2 * sm_count || tiles > sm_count))
     return cudaErrorInvalidValue;  // scratch is sized for 2 x sm_count partial tiles, sm_count tickets
-  dim3 grid(tilesN, tilesM, splits);
-  cudaError_t e;
-  if (renorm) {
-    e = set_smem_once((const void*)chain32_step_kernel<true>, STEP_SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    chain32_step_kernel<true><<<grid, CTHREADS, STEP_SMEM, st>>>(g, kps, Dt, Rt, Ot, part, cnt);
-  } else {
-    e = set_smem_once((const void*)chain32_step_kernel<false>, STEP_SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    chain32_step_kernel<false><<<grid, CTHREADS, STEP_SMEM, st>>>(g, kps, Dt, Rt, Ot, part, cnt);
-  }
-  return cudaGetLastError();
+  void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*) =
+      renorm ? chain32_step_kernel<true> : chain32_step_kernel<false>;
+  cudaError_t e = set_smem_once((const void*)kern, STEP_SMEM);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tilesN, tilesM, splits);
+  cfg.blockDim = dim3(CTHREADS);
+  cfg.dynamicSmemBytes = STEP_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;  // only after another step (the D^T planes must be complete)
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, g, kps, Dt, Rt, Ot, part, cnt);
 }
 
 }  // namespace lb

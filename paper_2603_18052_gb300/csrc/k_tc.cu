@@ -69,6 +69,13 @@ __device__ __forceinline__ void cpa_wait_all() {
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch (propagation steps): the B operand (D
+// planes, written before the chain) is fetched before griddep_wait(); the
+// states, the X term and every global write come after it.  Both are no-ops
+// for an ordinary launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t ph) {
   uint32_t ok;
   asm volatile(
@@ -222,11 +229,26 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   const uint32_t tacc = tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // producer: TMA copies of the K blocks into the ring
-    for (int kb = 0; kb < nk; kb++) {
+    // producer: TMA copies of the K blocks into the ring; the B planes of
+    // the first stages go out before the wait for the previous grid
+    const int pre = nk < NSTAGE ? nk : NSTAGE;
+    for (int kb = 0; kb < pre; kb++) {
+      const uint32_t base = su32(sm + kb * STAGE_BYTES);
+      const uint32_t fb = su32(&full_bar[kb]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
+      for (int p = 0; p < 2 * NPB; p++)
+        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, (kb0 + kb) * TBK, n0, b * 2 * NPB + p, fb);
+    }
+    griddep_wait();
+    for (int kb = 0; kb < pre; kb++) {
+      const uint32_t base = su32(sm + kb * STAGE_BYTES);
+      const uint32_t fb = su32(&full_bar[kb]);
+      for (int p = 0; p < 2 * NPA; p++) tma3(base + p * A_PLANE, &mapA, (kb0 + kb) * TBK, m0, b * 2 * NPA + p, fb);
+    }
+    for (int kb = pre; kb < nk; kb++) {
       const int s = kb % NSTAGE;
       const int kx = (kb0 + kb) * TBK;
-      if (kb >= NSTAGE && !mbar_wait(su32(&empty_bar[s]), ((kb - NSTAGE) / NSTAGE) & 1)) {
+      if (!mbar_wait(su32(&empty_bar[s]), ((kb - NSTAGE) / NSTAGE) & 1)) {
         atomicOr(P.err, ERR_TIMEOUT);
         give_up = 1;
         break;
@@ -282,6 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   }
   constexpr bool XPRE = LIGHT && Cfg::XPRE_FITS;
   float2* xs = (float2*)(sm + NSTAGE * STAGE_BYTES);  // residual tile (XPRE)
+  if (warp >= 2) griddep_wait();  // the X tile and the trace read the previous grid's output
   if (XPRE && warp >= 2 && P.nterms > 0) {
     // the residual tile X[0] (rows m0.., columns n0..) into shared memory,
     // copied by the two warps that are idle while the K loop runs
@@ -337,6 +360,8 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   if (!have && tid == 0) atomicOr(P.err, ERR_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool good = __syncthreads_and(have ? 1 : 0) && !give_up;  // uniform across the CTA
+  griddep_wait();    // every thread: global writes below go to the previous grid's inputs
+  griddep_launch();  // the next grid may start its prologue
   // the producer may still have copies in flight after a give-up: wait for
   // them (bounded) before the shared memory is released
   if (!good && tid == 0) {
@@ -782,7 +807,18 @@ cudaError_t launch_tc(const TcProblem& p, cudaStream_t st) {
   ksplit = (nk + kbps - 1) / kbps;
   dim3 grid(gx, gy, p.batch * ksplit);
   count_launch();
-  zgemm_tc_kernel<NPA, NPB, BN, LIGHT><<<grid, TC_THREADS, SMEM, st>>>(ma, mb, p, ksplit, kbps);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = p.pdl ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, zgemm_tc_kernel<NPA, NPB, BN, LIGHT>, ma, mb, p, ksplit, kbps);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 }  // namespace

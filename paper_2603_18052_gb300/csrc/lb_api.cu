@@ -751,6 +751,7 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
             q.rs_d = d;
           }
           q.part = (float2*)c->part32; q.cnt = c->cnt32; q.max_ctas = c->sm_count;
+          q.pdl = (s > 0 || t > 0) ? 1 : 0;  // the first step of a chunk follows the plane split
           q.err = c->err_dev;
           LB_CUDA(zgemm_tc(q, st));
           float2* t1 = cur; cur = nxt; nxt = t1;
@@ -783,8 +784,9 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
     LB_CUDA(launch_chain32_dplanes(n, S, Pz + s0 * nn, c->Dpl, st));
     for (int s = 0; s < S; s++)
       for (int t = 0; t < steps_per_slice; t++) {
+        const bool pdl = s > 0 || t > 0;  // the first step of a chunk follows the D^T conversion
         LB_CUDA(launch_chain32_step(n, B, renorm_trace, c->Dpl + s * dpl, cur, nxt, c->part32, c->cnt32,
-                                    c->sm_count, st));
+                                    c->sm_count, pdl, st));
         float* t1 = cur;
         cur = nxt;
         nxt = t1;

@@ -187,8 +187,10 @@ size_t chain32_part_floats(int sm_count);
 cudaError_t launch_chain32_dplanes(int n, int S, const z64* P, float* Dt, cudaStream_t st);
 cudaError_t launch_chain32_states_in(int n, int B, const z64* X, float* Rt, cudaStream_t st);
 cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt, z64* X, cudaStream_t st);
+// pdl: launch with programmatic stream serialisation (only when the
+// previous launch on the stream is another step of the same chain)
 cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
-                                unsigned* cnt, int sm_count, cudaStream_t st);
+                                unsigned* cnt, int sm_count, bool pdl, cudaStream_t st);
 
 // n x n square problem, batch S, slice stride n*n (helper for the build).
 ZGemmProblem sq(int n, int S, const z64* A, const z64* B, z64* C);
@@ -253,6 +255,10 @@ struct TcProblem {
   float2* part = nullptr; unsigned* cnt = nullptr; int max_ctas = 0;
   // optional batch mask: batch element b is skipped when active[b] <= active_iter
   const int* active = nullptr; int active_iter = 0;
+  // launch with programmatic stream serialisation: only when the previous
+  // launch on the stream is a step of the same chain (it writes the A
+  // operand and the X terms, never the B operand)
+  int pdl = 0;
   unsigned int* err = nullptr;
 };
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);

@@ -38,7 +38,7 @@ def _setup(lbm, prec):
     return ctx, w, Lb, Ld, u, P, s0
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 def test_captured_build_and_propagation_replay(lbm, prec):
     ctx, w, Lb, Ld, u, P, s0 = _setup(lbm, prec)
     lbm.lb_set_max_squarings(ctx, 4)
@@ -113,3 +113,36 @@ def test_captured_mixed_instances_replay(lbm):
     lbm.lb_sync_status(ctx)
     for a, r in zip(arg, ref):
         assert torch.equal(a["states"], r)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_captured_chain_replay_d27(lbm, prec):
+    """n = 729 chain steps (launched back to back with programmatic
+    dependent launch) captured in a graph: replays equal the uncaptured run
+    bit for bit and stay within the form's tolerance of the oracle."""
+    dev = torch.device("cuda:0")
+    w = make_workload("d27_chain", B=16, nslices=3)
+    Ps = O.slice_propagators(O.lindbladian(w["H0"], w["jumps"]), O.drive_generator(w["X"]), w["u"], w["dt"])
+    ctx = lbm.Context(0, max_n=729, max_batch=16, max_slices=3)
+    P = torch.from_numpy(Ps).to(dev)
+    s0 = torch.from_numpy(w["states"]).to(dev)
+
+    def run(R):
+        lbm.lb_propagate_batch(ctx, P, R, steps_per_slice=2, prec=prec, renorm_trace=True)
+
+    ref = s0.clone()
+    run(ref)
+    lbm.lb_sync_status(ctx)
+    R = s0.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run(R)
+    for _ in range(2):
+        R.copy_(s0)
+        g.replay()
+        torch.cuda.synchronize()
+        lbm.lb_sync_status(ctx)
+        assert torch.equal(R, ref)
+    exact = O.propagate_chain(Ps, w["states"], 2)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - exact, axis=1))
+    assert err <= 1e-5, err
