@@ -2,9 +2,11 @@
 // split-BF16 x3 form:  every FP64 operand x is stored as two BF16 numbers,
 // x ~ hi + lo (hi = bf16(x), lo = bf16(x - hi)), and a real product is
 // A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in TMEM.  A
-// complex product takes the four real products of (Ar + i Ai)(Br + i Bi),
-// 12 BF16 MMAs per K step, two TMEM accumulators (re, im); the minus sign of
-// Ai Bi is the instruction's negate-A bit.
+// complex product needs the four real products of (Ar + i Ai)(Br + i Bi):
+// with the real and imaginary planes of a B piece stacked along N, one MMA
+// of width 2 BN gives Ar [Br | Bi] and one gives Ai [Br | Bi] (two TMEM
+// accumulators), and the epilogue forms Re = Ar Br - Ai Bi and
+// Im = Ar Bi + Ai Br; 2 MMAs per piece pair and K step.
 //
 // Operands are pre-split "plane" tensors: for a batch of S complex R x K
 // matrices, bf16 [S][4][R][ld] with planes (re_hi, re_lo, im_hi, im_lo) and
@@ -206,6 +208,9 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * TBN, m0 = blockIdx.y * TBM, b = blockIdx.z / ksplit, zs = blockIdx.z % ksplit;
   const int nkt = (P.K + TBK - 1) / TBK;
+  // B planes sit in the ring as [Br_0, Bi_0, Br_1, Bi_1, ...]: each piece's
+  // [Br; Bi] is one 2 TBN-row operand (tensor plane p: Re pieces first)
+  auto bslot = [](int p) { return p < NPB ? 2 * p : 2 * (p - NPB) + 1; };
   const int kb0 = zs * kbps;                           // this CTA's K blocks [kb0, kb0 + nk)
   const int nk = min(nkt, kb0 + kbps) - kb0;
 
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                 "r"(2 * TBN));
+                 "r"(4 * TBN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
       const uint32_t fb = su32(&full_bar[kb]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
       for (int p = 0; p < 2 * NPB; p++)
-        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, (kb0 + kb) * TBK, n0, b * 2 * NPB + p, fb);
+        tma3(base + 2 * NPA * A_PLANE + bslot(p) * B_PLANE, &mapB, (kb0 + kb) * TBK, n0, b * 2 * NPB + p, fb);
     }
     griddep_wait();
     for (int kb = 0; kb < pre; kb++) {
@@ -258,11 +263,12 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
       for (int p = 0; p < 2 * NPA; p++) tma3(base + p * A_PLANE, &mapA, kx, m0, b * 2 * NPA + p, fb);
       for (int p = 0; p < 2 * NPB; p++)
-        tma3(base + 2 * NPA * A_PLANE + p * B_PLANE, &mapB, kx, n0, b * 2 * NPB + p, fb);
+        tma3(base + 2 * NPA * A_PLANE + bslot(p) * B_PLANE, &mapB, kx, n0, b * 2 * NPB + p, fb);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t tre = tacc, tim = tacc + TBN;
+    // accumulators: Ar [Br | Bi] in columns [0, 2 TBN), Ai [Br | Bi] in [2 TBN, 4 TBN)
+    const uint32_t tA = tacc, tB = tacc + 2 * TBN;
     bool ok = true;
     for (int kb = 0; kb < nk && ok; kb++) {
       const int s = kb % NSTAGE;
@@ -285,12 +291,10 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
           for (int j = 0; j < NPB; j++) {
             if (i + j >= NPMAX) continue;
             const uint64_t Ar = desc_sw128(base + i * A_PLANE + o), Ai = desc_sw128(base + (NPA + i) * A_PLANE + o);
-            const uint64_t Br = desc_sw128(bb + j * B_PLANE + o), Bi = desc_sw128(bb + (NPB + j) * B_PLANE + o);
+            const uint64_t Bj = desc_sw128(bb + 2 * j * B_PLANE + o);  // [Br_j ; Bi_j], 2 TBN rows
             const uint32_t acc = started ? 1u : first;
-            mma(tre, Ar, Br, idesc(0, TBN), acc);
-            mma(tre, Ai, Bi, idesc(1, TBN), 1);
-            mma(tim, Ar, Bi, idesc(0, TBN), acc);
-            mma(tim, Ai, Br, idesc(0, TBN), 1);
+            mma(tA, Ar, Bj, idesc(0, 2 * TBN), acc);
+            mma(tB, Ai, Bj, idesc(0, 2 * TBN), acc);
             started = true;
           }
       }
@@ -380,13 +384,15 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
     // w / 4 of the columns
     const int quad = warp & 3, half = warp >> 2;
     for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 16) {
-      float vr[16], vi[16];
+      float rr[16], ri[16], ir[16], ii[16];  // Ar Br, Ar Bi, Ai Br, Ai Bi
       const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16) + c0;
-      tmem_ld16(ta, vr);
-      tmem_ld16(ta + TBN, vi);
+      tmem_ld16(ta, rr);
+      tmem_ld16(ta + TBN, ri);
+      tmem_ld16(ta + 2 * TBN, ir);
+      tmem_ld16(ta + 3 * TBN, ii);
       const int r = quad * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < 16; j++) tile[r * LDS + c0 + j] = make_float2(vr[j], vi[j]);
+      for (int j = 0; j < 16; j++) tile[r * LDS + c0 + j] = make_float2(rr[j] - ii[j], ri[j] + ir[j]);
     }
     __syncthreads();
   }
@@ -602,7 +608,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(const __grid_const
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(2 * TBN));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(4 * TBN));
 }
 
 // Split planes of a batch of complex FP64 matrices: dst[s][p][r][c] for the
