@@ -18,13 +18,21 @@
 // which keeps shared-memory traffic at two planes): 64 x 64 output tiles, 256 threads with
 // 4 x 4 complex outputs each (fragments double-buffered in registers), a
 // four-stage cp.async ring of 16-deep K blocks, two CTAs per SM.  When there
-// are fewer tiles than two per SM the K range is split over
-// CTAs; each writes its partial tile to global scratch and the CTA that
-// arrives last (atomic ticket, no waiting) sums the partials in split order,
-// so the result does not depend on arrival order.
+// are fewer tiles than two per SM the K range is split over CTAs.  If the
+// split CTAs of a tile fit on the GPU as one thread-block cluster, each keeps
+// its partial tile in shared memory and, after a cluster barrier, sums one
+// share of the tile's rows over all partials through distributed shared
+// memory; otherwise each writes its partial to global scratch and the CTA
+// that takes the last ticket (atomic, no waiting) sums them.  Either way the
+// partials are added in split order, so the result does not depend on
+// arrival order.
 #include "lb_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 namespace lb {
 
@@ -88,7 +96,8 @@ __device__ __forceinline__ void chain_finish(const ChainDims& g, const float* __
 template <bool RENORM>
 __global__ void __launch_bounds__(CTHREADS, 2)
     chain32_step_kernel(ChainDims g, int kps, const float* __restrict__ Dt, const float* __restrict__ Rt,
-                        float* __restrict__ Ot, float* __restrict__ part, unsigned* __restrict__ cnt) {
+                        float* __restrict__ Ot, float* __restrict__ part, unsigned* __restrict__ cnt,
+                        int use_cluster) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float2 cs[CB];
   __shared__ float2 trp[4][CB];
@@ -236,6 +245,39 @@ __global__ void __launch_bounds__(CTHREADS, 2)
                    make_float4(im[0][j], im[1][j], im[2][j], im[3][j]));
     return;
   }
+  if (use_cluster) {
+    // partial tile [2][CB (j)][CB (b)] in this CTA's (idle) ring; CTA r of
+    // the cluster (r = the K split) finishes rows [r * rows, (r + 1) * rows)
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    float* Ps = sm;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      *(float4*)(Ps + (bn + j) * CB + am) = make_float4(re[0][j], re[1][j], re[2][j], re[3][j]);
+      *(float4*)(Ps + CB * CB + (bn + j) * CB + am) = make_float4(im[0][j], im[1][j], im[2][j], im[3][j]);
+    }
+    cl.sync();
+    const int rank = (int)cl.block_rank();
+    const int rows = (CB + splits - 1) / splits;
+    const int jl0 = rank * rows, jl1 = min(CB, jl0 + rows);
+    const float* src[8];
+#pragma unroll
+    for (int zz = 0; zz < 8; zz++) src[zz] = zz < splits ? cl.map_shared_rank(Ps, zz) : Ps;
+    for (int q = tid; q < (jl1 - jl0) * (CB / 4); q += CTHREADS) {
+      const int jl = jl0 + q / (CB / 4), b4 = (q % (CB / 4)) * 4;
+      float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
+#pragma unroll
+      for (int zz = 0; zz < 8; zz++) {
+        if (zz < splits) {
+          sr = f4add(sr, *(const float4*)(src[zz] + jl * CB + b4));
+          si = f4add(si, *(const float4*)(src[zz] + CB * CB + jl * CB + b4));
+        }
+      }
+      chain_finish(g, Rt, Ot, cs + b4, j0 + jl, m0 + b4, sr, si);
+    }
+    cl.sync();  // the partials stay readable until every CTA of the cluster is done
+    return;
+  }
   // split K: partial tile [2][CB (j)][CB (b)] to scratch, last CTA reduces
   const int tile = blockIdx.y * gridDim.x + blockIdx.x;
   float* P = part + ((long long)tile * splits + z) * 2 * CB * CB;
@@ -365,6 +407,39 @@ __global__ void chain32_states_out_kernel(int n, int d, int B, int Kp, int Bp, i
 
 int rup(int x, int m) { return (x + m - 1) / m * m; }
 
+// Whether `tiles` clusters of `splits` CTAs of this kernel can be resident at
+// once (queried once per kernel and cluster size).
+bool cluster_fits(void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*, int),
+                  bool renorm, int splits, int tiles) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(dev * 16 + (renorm ? 8 : 0), splits);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, 1, splits);
+    cfg.blockDim = dim3(CTHREADS);
+    cfg.dynamicSmemBytes = STEP_SMEM;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 1;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = splits;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, (const void*)kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      num = 0;
+    }
+    it = cache.emplace(key, num).first;
+  }
+  return it->second >= tiles;
+}
+
 int chain_isqrt(int n) {
   int d = 1;
   while ((d + 1) * (d + 1) <= n) d++;
@@ -421,7 +496,7 @@ cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const
   splits = (ktiles + kps - 1) / kps;
   if (splits > 1 && (tiles * splits > 2 * sm_count || tiles > sm_count))
     return cudaErrorInvalidValue;  // scratch is sized for 2 x sm_count partial tiles, sm_count tickets
-  void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*) =
+  void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*, int) =
       renorm ? chain32_step_kernel<true> : chain32_step_kernel<false>;
   cudaError_t e = set_smem_once((const void*)kern, STEP_SMEM);
   if (e != cudaSuccess) return e;
@@ -430,13 +505,26 @@ cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const
   cfg.blockDim = dim3(CTHREADS);
   cfg.dynamicSmemBytes = STEP_SMEM;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  // the split CTAs of a tile as one cluster, if that many clusters fit at once
+  const bool cluster = splits > 1 && cluster_fits(kern, renorm, splits, tiles);
+  if (cluster) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = 1;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = splits;
+    na++;
+  }
+  if (pdl) {  // only after another step (the D^T planes must be complete)
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    na++;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;  // only after another step (the D^T planes must be complete)
+  cfg.numAttrs = na;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, kern, g, kps, Dt, Rt, Ot, part, cnt);
+  return cudaLaunchKernelEx(&cfg, kern, g, kps, Dt, Rt, Ot, part, cnt, cluster ? 1 : 0);
 }
 
 }  // namespace lb
