@@ -73,10 +73,9 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2603_18052_gb300 import ranks
+
+    return ranks.dist_env()
 
 
 def host_cores():
@@ -205,7 +204,13 @@ def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
 
     from workloads.configs import make_instances
 
+    from paper_2603_18052_gb300 import ranks
+
     inst, models = make_instances(count)
+    rank, world, _ = ranks.dist_env()
+    if world > 1:  # this rank's share of the independent problems
+        costs = [ranks.instance_cost(x["d"], len(x["u"]), x["states"].shape[0]) for x in inst]
+        inst = [inst[i] for i in ranks.partition(costs, world)[rank]]
 
     def dput(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -257,7 +262,8 @@ def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
 
     counts = collections.Counter(x["d"] for x in inst)
     res = {"workload": "%d instances (d=3/9/27: %d/%d/%d), 50 slices each, B~U{1..64}; %d builds, %d state-steps"
-                       % (count, counts[3], counts[9], counts[27], builds, ssteps)}
+                       % (len(inst), counts[3], counts[9], counts[27], builds, ssteps)
+                       + ("" if world == 1 else " (this rank's share of %d, split by cost)" % count)}
     for k, ms in (("run_instances_bf16x3", ms_mixed), ("run_instances_fp64", ms_fp64),
                   ("per_instance_fp64_launches", ms_loop)):
         res[k] = {"ms": ms, "builds_per_s": builds / (ms / 1e3), "state_steps_per_s": ssteps / (ms / 1e3)}
@@ -398,11 +404,9 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2603_18052_gb300 import ranks
+
+        return ranks.max_over_ranks(x, dev)
 
     def timed(form, sampler=None):
         for _ in range(args.warmup):

@@ -309,6 +309,19 @@ lb_status lb_adam_step_f64(long long count, double* p, const double* g, double* 
 lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64* P, int steps_per_slice, int B,
                                     lb_c64* states, void* stream);
 
+/*
+ * lb_selftest_wait_timeout -- failure-detection self test (the paper has no
+ * counterpart).  Queues one CTA on `stream` whose thread waits on a
+ * shared-memory mbarrier that nothing ever completes, the same bounded wait
+ * the tensor-core kernels use, for at most `cycles` SM clock cycles
+ * (clamped to [1e3, 4e9]; 2e6 is about 1 ms).  The wait gives up, sets the
+ * timeout bit of the context's device error word and the kernel returns;
+ * nothing faults or hangs.  The next lb_sync_status returns LB_ETIMEOUT and
+ * clears the word, after which the context is usable as before.
+ *   Errors: LB_EINVAL for a null ctx; LB_ECUDA if the launch fails.
+ */
+lb_status lb_selftest_wait_timeout(lb_ctx* ctx, long long cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

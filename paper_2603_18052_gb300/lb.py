@@ -52,6 +52,7 @@ EXPORTED = (
     "lb_mse_loss_grad",
     "lb_adam_step",
     "lb_adam_step_f64",
+    "lb_selftest_wait_timeout",
 )
 
 
@@ -117,6 +118,8 @@ def lib():
     L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
     L.lb_propagate_batch_static.restype = i32
     L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
+    L.lb_selftest_wait_timeout.restype = i32
+    L.lb_selftest_wait_timeout.argtypes = [vp, ctypes.c_longlong, vp]
     L.lb_run_instances.restype = i32
     L.lb_run_instances.argtypes = [vp, ctypes.POINTER(Instance), i32, f64, i32, i32, vp]
     f32 = ctypes.c_float
@@ -290,6 +293,12 @@ def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelit
                                _ptr(fidelity_out, torch.float64, "fidelity_out", (1,)),
                                _ptr(grad_out, torch.float64, "grad_out", (S,)), _stream(stream)),
            "lb_grape_grad")
+
+
+def lb_selftest_wait_timeout(ctx, cycles=2_000_000, stream=None):
+    """Queue a bounded wait that runs out; the next lb_sync_status raises
+    LBError with name LB_ETIMEOUT."""
+    _check(lib().lb_selftest_wait_timeout(ctx.handle, int(cycles), _stream(stream)), "lb_selftest_wait_timeout")
 
 
 def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
