@@ -348,7 +348,59 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     out["d9_grape"] = {"workload": "d=9 GRAPE landscape point: 100 slices, 100 Pade builds + Frechet "
                                    "derivatives, forward/adjoint chains of 4 basis operators", "ms": ms}
     ctx.close()
+    out["paper_model_build_breakdown"] = paper_model_breakdown(lb, dev)
     return out
+
+
+def paper_model_breakdown(lb, dev):
+    """Build-time split of the paper's GRAPE landscape-point model (H0 =
+    diag(0..d-1), drive a + a^+, T1 = 50, T2 = 30, dt = 0.5; 3 / 5 / 6
+    squarings per segment at d = 3 / 9 / 27) in the terms of its build
+    breakdown table: solve, Pade products, squarings, other (norm, scaling,
+    checks), per build, for the FP64 and split-BF16 forms."""
+    import numpy as np
+    import torch
+
+    from workloads.transmon import paper_grape_model
+
+    def dput(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    res = {}
+    for d, S in ((3, 100), (9, 100), (27, 20)):
+        m = paper_grape_model(d)
+        n = d * d
+        ctx = lb.Context(dev.index or 0, max_n=n, max_batch=1, max_slices=S)
+        Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+        Ld = torch.empty_like(Lb)
+        lb.lb_assemble(ctx, dput(m.H0), dput(m.jumps), Lb)
+        lb.lb_assemble(ctx, dput(m.X), None, Ld)
+        u = dput(0.1 * np.sin(0.3 * np.arange(S)))
+        P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+        s_out = torch.empty(S, dtype=torch.int32, device=dev)
+        entry = {}
+        for prec in ("fp64", "bf16x3"):
+            lb.lb_expm_pade(ctx, Lb, Ld, u, m.dt, P, prec=prec, s_out=s_out)  # warm-up
+            lb.lb_sync_status(ctx)
+            reps = 3
+            lb.lb_set_stage_timing(ctx, True)
+            for _ in range(reps):
+                lb.lb_expm_pade(ctx, Lb, Ld, u, m.dt, P, prec=prec, s_out=s_out)
+            lb.lb_sync_status(ctx)
+            st, _ = lb.lb_stage_times(ctx)
+            lb.lb_set_stage_timing(ctx, False)
+            per = {k: v / (reps * S) for k, v in st.items()}  # ms per build
+            tot = sum(per.values())
+            entry[prec] = {"build_ms": tot,
+                           "solve_pct": 100 * per["lu_solve"] / tot,
+                           "pade_products_pct": 100 * per["pade_products"] / tot,
+                           "squarings_pct": 100 * per["squarings"] / tot,
+                           "other_pct": 100 * (per["prepare"] + per["check"]) / tot}
+        entry["s_per_segment"] = sorted(set(int(x) for x in s_out.cpu().numpy()))
+        entry["builds"] = S
+        res["d%d" % d] = entry
+        ctx.close()
+    return res
 
 def run_ours(args):
     import numpy as np
