@@ -554,7 +554,7 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 is absent from "
                                "MEASURED_PEAKS.json); DFMA probe measured 1.20 TFLOP/s",
                 "algorithmic_flops_per_launch": lu_flops, "launch_ms": lu_ms}
-    # propagation phase (spec roofline target), each form against its own peak
+    # propagation phase, each form against its own peak
     prop_flops = S * B * accounting.state_step_flops(n)
 
     def prop_roof(form, peak, note):
