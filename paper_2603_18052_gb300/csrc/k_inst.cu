@@ -10,6 +10,7 @@
 // states) item and runs that instance's whole chain with its propagators in
 // shared memory; larger n use the batched GEMM path per instance.
 #include "lb_internal.cuh"
+#include "res32.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -47,10 +48,11 @@ __global__ void gather_gen_kernel(int n, long long total, const GenEntry* __rest
 }
 
 // One CTA per work item.  FP64: Gauss three-product form with P planes
-// (re, im, re + im).  F32: D = P - I in FP32 planes, rho <- rho + D rho,
-// optional trace renormalisation.
+// (re, im, re + im).  F32: D = P - I in FP32 (interleaved complex),
+// rho <- rho + D rho by the register-blocked step of res32.cuh, optional
+// trace renormalisation.
 template <bool F32>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     worklist_kernel(int n, int d, int chunk, const WorkItem* __restrict__ items, int renorm) {
   extern __shared__ __align__(16) double wsm[];
   const WorkItem it = items[blockIdx.x];
@@ -103,69 +105,42 @@ __global__ void __launch_bounds__(256)
     }
     for (int e = tid; e < work; e += blockDim.x) it.X[e] = make_double2(xr[e], xi[e]);
   } else {
-    float* dr = (float*)wsm;
-    float* di = dr + nn;
-    float* xr = di + nn;
-    float* xi = xr + chunk * n;
-    float* yr = xi + chunk * n;
-    float* yi = yr + chunk * n;
-    float* tr = yi + chunk * n;
-    for (int e = tid; e < work; e += blockDim.x) {
+    float2* D = (float2*)wsm;
+    float2* X = D + nn;
+    float2* Y = X + chunk * n;
+    float2* C = Y + chunk * n;
+    const int nt = blockDim.x;
+    for (int e = tid; e < work; e += nt) {
       const z64 v = it.X[e];
-      xr[e] = (float)v.x;
-      xi[e] = (float)v.y;
+      X[e] = make_float2((float)v.x, (float)v.y);
     }
+    __syncthreads();
+    if (renorm) res32_traces(n, d, nb, X, C, tid, nt);
     for (int s = 0; s < it.nslices; s++) {
       __syncthreads();
-      for (int e = tid; e < nn; e += blockDim.x) {
+      for (int e = tid; e < nn; e += nt) {
         z64 v = it.P[s * nn + e];
         if (e / n == e % n) v.x -= 1.0;
-        dr[e] = (float)v.x;
-        di[e] = (float)v.y;
+        D[e] = make_float2((float)v.x, (float)v.y);
       }
       __syncthreads();
       for (int t = 0; t < it.steps; t++) {
-        for (int e = tid; e < work; e += blockDim.x) {
-          const int q = e / n, i = e - (e / n) * n;
-          float re = 0.f, im = 0.f;
-          for (int j = 0; j < n; j++) {
-            const float pr = dr[i * n + j], pi = di[i * n + j], ar = xr[q * n + j], ai = xi[q * n + j];
-            re = fmaf(pr, ar, fmaf(-pi, ai, re));
-            im = fmaf(pr, ai, fmaf(pi, ar, im));
-          }
-          yr[e] = xr[e] + re;
-          yi[e] = xi[e] + im;
-        }
+        res32_step<2>(n, nb, D, X, Y, tid, nt, renorm ? C : nullptr);  // trace factor of X applied to Y
         __syncthreads();
         if (renorm) {
-          for (int q = tid; q < nb; q += blockDim.x) {
-            float sr = 0.f, si = 0.f;
-            for (int k = 0; k < d; k++) {
-              sr += yr[q * n + k * (d + 1)];
-              si += yi[q * n + k * (d + 1)];
-            }
-            const float m2 = sr * sr + si * si;
-            tr[2 * q] = sr / m2;
-            tr[2 * q + 1] = -si / m2;
-          }
+          res32_traces(n, d, nb, Y, C, tid, nt);
           __syncthreads();
         }
-        for (int e = tid; e < work; e += blockDim.x) {
-          float r = yr[e], im = yi[e];
-          if (renorm) {
-            const int q = e / n;
-            const float cr = tr[2 * q], ci = tr[2 * q + 1];
-            const float r2 = r * cr - im * ci;
-            im = r * ci + im * cr;
-            r = r2;
-          }
-          xr[e] = r;
-          xi[e] = im;
-        }
-        __syncthreads();
+        float2* tmp = X;
+        X = Y;
+        Y = tmp;
       }
     }
-    for (int e = tid; e < work; e += blockDim.x) it.X[e] = make_double2((double)xr[e], (double)xi[e]);
+    if (renorm && (long long)it.nslices * it.steps > 0) {  // the last step's trace factor
+      res32_renorm(n, d, nb, X, C, tid, nt);
+      __syncthreads();
+    }
+    for (int e = tid; e < work; e += nt) it.X[e] = make_double2((double)X[e].x, (double)X[e].y);
   }
 }
 
@@ -287,8 +262,9 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
         const size_t smem = worklist_smem(n, 8, f32);
         if (f32) {
           LB_CUDA(set_smem_once((const void*)worklist_kernel<true>, smem));
+          const int threads = std::max(64, (n * 4 + 31) / 32 * 32);  // (row, pair of states) units, 8 states
           count_launch();
-          worklist_kernel<true><<<ch.items, 256, smem, st>>>(n, d, 8, ditem + ch.item0, renorm_trace);
+          worklist_kernel<true><<<ch.items, threads, smem, st>>>(n, d, 8, ditem + ch.item0, renorm_trace);
         } else {
           LB_CUDA(set_smem_once((const void*)worklist_kernel<false>, smem));
           count_launch();

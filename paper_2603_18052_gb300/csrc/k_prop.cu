@@ -13,6 +13,7 @@
 // exactly, so the rounding of the stored propagator scales with |D| rather
 // than with |P| ~ 1), optional per-step division by the trace.
 #include "lb_internal.cuh"
+#include "res32.cuh"
 
 #include <algorithm>
 
@@ -278,85 +279,50 @@ bool lat_split(int n, int* C, int* K) {
   return best < (1 << 30);
 }
 
-__global__ void __launch_bounds__(kResThreads)
+// FP32 resident chain (n <= 81): D = P - I and the CTA's states in shared
+// memory for the whole chain, one register-blocked step per barrier
+// (res32.cuh), optional trace renormalisation after every step.
+__global__ void __launch_bounds__(1024)
     prop_resident_f32_kernel(int n, int d, int nslices, const float* __restrict__ Dr,
                              const float* __restrict__ Di, int steps_per_slice, int B, int chunk,
                              int renorm, z64* __restrict__ states) {
-  extern __shared__ __align__(16) float smf[];
-  float* dr = smf;
-  float* di = dr + n * n;
-  float* xr = di + n * n;
-  float* xi = xr + chunk * n;
-  float* yr = xi + chunk * n;
-  float* yi = yr + chunk * n;
-  float* tr = yi + chunk * n;  // 2 * chunk: reciprocal trace (re, im)
+  extern __shared__ __align__(16) float2 sm2[];
+  float2* D = sm2;
+  float2* X = D + n * n;
+  float2* Y = X + chunk * n;
+  float2* C = Y + chunk * n;
   const int b0 = blockIdx.x * chunk;
   if (b0 >= B) return;
   const int nb = min(chunk, B - b0);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const long long nn = (long long)n * n;
-  for (int e = tid; e < nb * n; e += blockDim.x) {
+  for (int e = tid; e < nb * n; e += nt) {
     const z64 v = states[(long long)b0 * n + e];
-    xr[e] = (float)v.x;
-    xi[e] = (float)v.y;
+    X[e] = make_float2((float)v.x, (float)v.y);
   }
-  const int work = nb * n;
+  __syncthreads();
+  if (renorm) res32_traces(n, d, nb, X, C, tid, nt);
   for (int s = 0; s < nslices; s++) {
     __syncthreads();
-    for (int e = tid; e < n * n; e += blockDim.x) {
-      dr[e] = Dr[s * nn + e];
-      di[e] = Di[s * nn + e];
-    }
+    for (int e = tid; e < n * n; e += nt) D[e] = make_float2(Dr[s * nn + e], Di[s * nn + e]);
     __syncthreads();
     for (int t = 0; t < steps_per_slice; t++) {
-      for (int e = tid; e < work; e += blockDim.x) {
-        const int q = e / n, i = e - (e / n) * n;
-        const float* pr = dr + i * n;
-        const float* pi = di + i * n;
-        const float* ar = xr + q * n;
-        const float* ai = xi + q * n;
-        float re = 0.f, im = 0.f;
-#pragma unroll 3
-        for (int j = 0; j < n; j++) {
-          re = fmaf(pr[j], ar[j], re);
-          re = fmaf(-pi[j], ai[j], re);
-          im = fmaf(pr[j], ai[j], im);
-          im = fmaf(pi[j], ar[j], im);
-        }
-        yr[e] = xr[e] + re;
-        yi[e] = xi[e] + im;
-      }
+      res32_step<2>(n, nb, D, X, Y, tid, nt, renorm ? C : nullptr);  // trace factor of X applied to Y
       __syncthreads();
       if (renorm) {
-        for (int q = tid; q < nb; q += blockDim.x) {
-          float sr = 0.f, si = 0.f;
-          for (int k = 0; k < d; k++) {
-            sr += yr[q * n + k * (d + 1)];
-            si += yi[q * n + k * (d + 1)];
-          }
-          const float m2 = sr * sr + si * si;
-          tr[2 * q] = sr / m2;
-          tr[2 * q + 1] = -si / m2;
-        }
+        res32_traces(n, d, nb, Y, C, tid, nt);
         __syncthreads();
-        for (int e = tid; e < work; e += blockDim.x) {
-          const int q = e / n;
-          const float cr = tr[2 * q], ci = tr[2 * q + 1];
-          const float r = yr[e], im = yi[e];
-          xr[e] = r * cr - im * ci;
-          xi[e] = r * ci + im * cr;
-        }
-      } else {
-        for (int e = tid; e < work; e += blockDim.x) {
-          xr[e] = yr[e];
-          xi[e] = yi[e];
-        }
       }
-      __syncthreads();
+      float2* tmp = X;
+      X = Y;
+      Y = tmp;
     }
   }
-  for (int e = tid; e < nb * n; e += blockDim.x)
-    states[(long long)b0 * n + e] = make_double2((double)xr[e], (double)xi[e]);
+  if (renorm && (long long)nslices * steps_per_slice > 0) {  // the last step's trace factor
+    res32_renorm(n, d, nb, X, C, tid, nt);
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * n; e += nt) states[(long long)b0 * n + e] = make_double2((double)X[e].x, (double)X[e].y);
 }
 
 __global__ void make_delta_f32_kernel(int n, long long total, const z64* __restrict__ P,
@@ -469,9 +435,12 @@ cudaError_t launch_propagate_resident_f32(int n, int nslices, const float* Dr, c
   cudaError_t e = set_smem_once((const void*)prop_resident_f32_kernel, smem);
   if (e != cudaSuccess) return e;
   const int grid = (B + chunk - 1) / chunk;
+  // one thread per (row, pair of states) of the register-blocked step
+  int threads = (n * ((chunk + 1) / 2) + 31) / 32 * 32;
+  threads = std::max(64, std::min(1024, threads));
   count_launch();
-  prop_resident_f32_kernel<<<grid, kResThreads, smem, st>>>(n, isqrt_exact(n), nslices, Dr, Di,
-                                                            steps_per_slice, B, chunk, renorm, states);
+  prop_resident_f32_kernel<<<grid, threads, smem, st>>>(n, isqrt_exact(n), nslices, Dr, Di, steps_per_slice, B,
+                                                        chunk, renorm, states);
   return cudaGetLastError();
 }
 
