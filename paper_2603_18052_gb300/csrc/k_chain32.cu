@@ -41,7 +41,7 @@ namespace {
 constexpr int CB = 64;        // tile rows (states) and columns (outputs)
 constexpr int CK = 16;        // K per stage
 constexpr int CSTAGE = 4;     // cp.async ring depth
-constexpr int CTHREADS = 256;
+constexpr int kChainTM = 4;  // complex outputs per thread along the states (TM = 8 measured 27% slower)
 constexpr int NPL = 2;                         // planes per operand (Re, Im)
 constexpr int OPER_FLOATS = NPL * CK * CB;     // one operand
 constexpr int STAGE_FLOATS = 2 * OPER_FLOATS;  // A (states) and B (D^T)
@@ -93,14 +93,18 @@ __device__ __forceinline__ void chain_finish(const ChainDims& g, const float* __
   *(float4*)(Ot + pl + idx) = make_float4(oii[0], oii[1], oii[2], oii[3]);
 }
 
-template <bool RENORM>
-__global__ void __launch_bounds__(CTHREADS, 2)
+// TM states x 4 outputs per thread: TM = 4 with 256 threads (2 x 4 warps
+// of 8 x 4 threads) or TM = 8 with 128 threads (2 x 2 warps of 4 x 8).
+template <bool RENORM, int TM>
+__global__ void __launch_bounds__(1024 / TM, 2)
     chain32_step_kernel(ChainDims g, int kps, const float* __restrict__ Dt, const float* __restrict__ Rt,
                         float* __restrict__ Ot, float* __restrict__ part, unsigned* __restrict__ cnt,
                         int use_cluster) {
+  constexpr int NT = 1024 / TM;  // threads
+  constexpr int NQ = NT / CB;    // partial trace sums per state
   extern __shared__ __align__(16) float sm[];
   __shared__ float2 cs[CB];
-  __shared__ float2 trp[4][CB];
+  __shared__ float2 trp[NQ][CB];
   __shared__ int is_last;
   const int tid = threadIdx.x;
   const int j0 = blockIdx.x * CB, m0 = blockIdx.y * CB, z = blockIdx.z, splits = gridDim.z;
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   auto loadA = [&](int stage, int kt) {  // states: written by the previous step
     float* sA = sm + stage * STAGE_FLOATS;
     const int k0 = kt * CK;
-    for (int c = tid; c < NPL * CK * (CB / 4); c += CTHREADS) {
+    for (int c = tid; c < NPL * CK * (CB / 4); c += NT) {
       const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
       cp16(sA + (p * CK + r) * CB + 4 * q, Rt + p * pA + (long long)(k0 + r) * g.Bp + m0 + 4 * q);
     }
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   auto loadB = [&](int stage, int kt) {  // D^T: written before the chain started
     float* sB = sm + stage * STAGE_FLOATS + OPER_FLOATS;
     const int k0 = kt * CK;
-    for (int c = tid; c < NPL * CK * (CB / 4); c += CTHREADS) {
+    for (int c = tid; c < NPL * CK * (CB / 4); c += NT) {
       const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
       cp16(sB + (p * CK + r) * CB + 4 * q, Dt + p * pB + (long long)(k0 + r) * g.Np + j0 + 4 * q);
     }
@@ -136,16 +140,16 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     cp_commit();
   }
   // per-state factor 1 / Tr(R_b) (complex; 0 for padding states): the d
-  // diagonal entries of the CTA's 64 states are loaded by all 256 threads at
-  // once (four partial sums per state, combined after the K loop), so no
+  // diagonal entries of the CTA's 64 states are loaded by all threads at
+  // once (NQ partial sums per state, combined after the K loop), so no
   // warp waits on a chain of dependent loads before its first K block
   if (RENORM) {
-    const int b = m0 + (tid & (CB - 1)), q0 = tid >> 6;  // q0 in 0..3
+    const int b = m0 + (tid & (CB - 1)), q0 = tid / CB;  // q0 in 0..NQ-1
     float tr = 0.f, ti = 0.f;
     if (b < g.B) {
 #pragma unroll
-      for (int u = 0; u < 8; u++) {  // d <= 27: at most 7 entries per partial sum
-        const int i = q0 + 4 * u;
+      for (int u = 0; u < 32 / NQ; u++) {  // d <= 27 < 32
+        const int i = q0 + NQ * u;
         if (i < g.d) {
           const long long k = (long long)i * (g.d + 1) * g.Bp + b;
           tr += __ldg(Rt + k);
@@ -156,11 +160,12 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     trp[q0][tid & (CB - 1)] = make_float2(tr, ti);
   }
   const int w = tid >> 5, l = tid & 31;
-  const int am = (w >> 2) * 32 + (l & 7) * 4;  // this thread's 4 states
-  const int bn = (w & 3) * 16 + (l >> 3) * 4;  // this thread's 4 outputs
-  float t1[4][4], t2[4][4], t3[4][4];
+  // this thread's TM states (am..) and 4 outputs (bn..)
+  const int am = TM == 4 ? (w >> 2) * 32 + (l & 7) * 4 : (w >> 1) * 32 + (l & 3) * 8;
+  const int bn = TM == 4 ? (w & 3) * 16 + (l >> 3) * 4 : (w & 1) * 32 + (l >> 2) * 4;
+  float t1[TM][4], t2[TM][4], t3[TM][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < TM; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) t1[i][j] = t2[i][j] = t3[i][j] = 0.f;
 
@@ -178,10 +183,12 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     const float* sA = sm + (it % CSTAGE) * STAGE_FLOATS;
     const float* sB = sA + OPER_FLOATS;
     // fragments of step k + 1 are read while step k multiplies
-    float4 fa[2][NPL], fb[2][NPL];
+    constexpr int QA = TM / 4;  // float4 per A plane
+    float4 fa[2][NPL][QA], fb[2][NPL];
 #pragma unroll
     for (int p = 0; p < NPL; p++) {
-      fa[0][p] = *(const float4*)(sA + (p * CK) * CB + am);
+#pragma unroll
+      for (int h = 0; h < QA; h++) fa[0][p][h] = *(const float4*)(sA + (p * CK) * CB + am + 4 * h);
       fb[0][p] = *(const float4*)(sB + (p * CK) * CB + bn);
     }
 #pragma unroll
@@ -190,18 +197,26 @@ __global__ void __launch_bounds__(CTHREADS, 2)
       if (k + 1 < CK) {
 #pragma unroll
         for (int p = 0; p < NPL; p++) {
-          fa[cur ^ 1][p] = *(const float4*)(sA + (p * CK + k + 1) * CB + am);
+#pragma unroll
+          for (int h = 0; h < QA; h++) fa[cur ^ 1][p][h] = *(const float4*)(sA + (p * CK + k + 1) * CB + am + 4 * h);
           fb[cur ^ 1][p] = *(const float4*)(sB + (p * CK + k + 1) * CB + bn);
         }
       }
-      const float ar[4] = {fa[cur][0].x, fa[cur][0].y, fa[cur][0].z, fa[cur][0].w};
-      const float ai[4] = {fa[cur][1].x, fa[cur][1].y, fa[cur][1].z, fa[cur][1].w};
-      const float as[4] = {ar[0] + ai[0], ar[1] + ai[1], ar[2] + ai[2], ar[3] + ai[3]};
+      float ar[TM], ai[TM], as[TM];
+#pragma unroll
+      for (int h = 0; h < QA; h++) {
+        ar[4 * h] = fa[cur][0][h].x; ar[4 * h + 1] = fa[cur][0][h].y;
+        ar[4 * h + 2] = fa[cur][0][h].z; ar[4 * h + 3] = fa[cur][0][h].w;
+        ai[4 * h] = fa[cur][1][h].x; ai[4 * h + 1] = fa[cur][1][h].y;
+        ai[4 * h + 2] = fa[cur][1][h].z; ai[4 * h + 3] = fa[cur][1][h].w;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; i++) as[i] = ar[i] + ai[i];
       const float br[4] = {fb[cur][0].x, fb[cur][0].y, fb[cur][0].z, fb[cur][0].w};
       const float bi[4] = {fb[cur][1].x, fb[cur][1].y, fb[cur][1].z, fb[cur][1].w};
       const float bs[4] = {br[0] + bi[0], br[1] + bi[1], br[2] + bi[2], br[3] + bi[3]};
 #pragma unroll
-      for (int i = 0; i < 4; i++)
+      for (int i = 0; i < TM; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           t1[i][j] = fmaf(ar[i], br[j], t1[i][j]);
@@ -217,8 +232,12 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     float2 c = make_float2(0.f, 0.f);
     if (m0 + tid < g.B) {
       if (RENORM) {
-        const float tr = (trp[0][tid].x + trp[1][tid].x) + (trp[2][tid].x + trp[3][tid].x);
-        const float ti = (trp[0][tid].y + trp[1][tid].y) + (trp[2][tid].y + trp[3][tid].y);
+        float tr = 0.f, ti = 0.f;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+          tr += trp[q][tid].x;
+          ti += trp[q][tid].y;
+        }
         const float m2 = tr * tr + ti * ti;
         c = make_float2(tr / m2, -ti / m2);
       } else {
@@ -229,20 +248,24 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   }
   __syncthreads();
 
-  float re[4][4], im[4][4];
+  float re[TM][4], im[TM][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < TM; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       re[i][j] = t1[i][j] - t2[i][j];
       im[i][j] = t3[i][j] - t1[i][j] - t2[i][j];
     }
+  // four consecutive states h*4.. of column j as float4
+  auto quad_re = [&](int h, int j) { return make_float4(re[4 * h][j], re[4 * h + 1][j], re[4 * h + 2][j], re[4 * h + 3][j]); };
+  auto quad_im = [&](int h, int j) { return make_float4(im[4 * h][j], im[4 * h + 1][j], im[4 * h + 2][j], im[4 * h + 3][j]); };
 
   if (splits == 1) {
 #pragma unroll
     for (int j = 0; j < 4; j++)
-      chain_finish(g, Rt, Ot, cs + am, j0 + bn + j, m0 + am, make_float4(re[0][j], re[1][j], re[2][j], re[3][j]),
-                   make_float4(im[0][j], im[1][j], im[2][j], im[3][j]));
+#pragma unroll
+      for (int h = 0; h < TM / 4; h++)
+        chain_finish(g, Rt, Ot, cs + am + 4 * h, j0 + bn + j, m0 + am + 4 * h, quad_re(h, j), quad_im(h, j));
     return;
   }
   if (use_cluster) {
@@ -252,10 +275,12 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     cg::cluster_group cl = cg::this_cluster();
     float* Ps = sm;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      *(float4*)(Ps + (bn + j) * CB + am) = make_float4(re[0][j], re[1][j], re[2][j], re[3][j]);
-      *(float4*)(Ps + CB * CB + (bn + j) * CB + am) = make_float4(im[0][j], im[1][j], im[2][j], im[3][j]);
-    }
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+      for (int h = 0; h < TM / 4; h++) {
+        *(float4*)(Ps + (bn + j) * CB + am + 4 * h) = quad_re(h, j);
+        *(float4*)(Ps + CB * CB + (bn + j) * CB + am + 4 * h) = quad_im(h, j);
+      }
     cl.sync();
     const int rank = (int)cl.block_rank();
     const int rows = (CB + splits - 1) / splits;
@@ -263,7 +288,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
     const float* src[8];
 #pragma unroll
     for (int zz = 0; zz < 8; zz++) src[zz] = zz < splits ? cl.map_shared_rank(Ps, zz) : Ps;
-    for (int q = tid; q < (jl1 - jl0) * (CB / 4); q += CTHREADS) {
+    for (int q = tid; q < (jl1 - jl0) * (CB / 4); q += NT) {
       const int jl = jl0 + q / (CB / 4), b4 = (q % (CB / 4)) * 4;
       float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
 #pragma unroll
@@ -282,10 +307,12 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   const int tile = blockIdx.y * gridDim.x + blockIdx.x;
   float* P = part + ((long long)tile * splits + z) * 2 * CB * CB;
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    *(float4*)(P + (bn + j) * CB + am) = make_float4(re[0][j], re[1][j], re[2][j], re[3][j]);
-    *(float4*)(P + CB * CB + (bn + j) * CB + am) = make_float4(im[0][j], im[1][j], im[2][j], im[3][j]);
-  }
+  for (int j = 0; j < 4; j++)
+#pragma unroll
+    for (int h = 0; h < TM / 4; h++) {
+      *(float4*)(P + (bn + j) * CB + am + 4 * h) = quad_re(h, j);
+      *(float4*)(P + CB * CB + (bn + j) * CB + am + 4 * h) = quad_im(h, j);
+    }
   __threadfence();
   __syncthreads();
   if (tid == 0) is_last = atomicAdd(&cnt[tile], 1u) == (unsigned)(splits - 1);
@@ -293,7 +320,7 @@ __global__ void __launch_bounds__(CTHREADS, 2)
   if (!is_last) return;
   __threadfence();
   const float* P0 = part + (long long)tile * splits * 2 * CB * CB;
-  for (int q = tid; q < CB * CB / 4; q += CTHREADS) {
+  for (int q = tid; q < CB * CB / 4; q += NT) {
     const int jl = q / (CB / 4), b4 = (q % (CB / 4)) * 4;
     float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
 #pragma unroll
@@ -411,6 +438,7 @@ int rup(int x, int m) { return (x + m - 1) / m * m; }
 // once (queried once per kernel and cluster size).
 bool cluster_fits(void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*, int),
                   bool renorm, int splits, int tiles) {
+  constexpr int NT = 1024 / kChainTM;
   static std::mutex mu;
   static std::map<std::pair<int, int>, int> cache;
   int dev = 0;
@@ -421,7 +449,7 @@ bool cluster_fits(void (*kern)(ChainDims, int, const float*, const float*, float
   if (it == cache.end()) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, 1, splits);
-    cfg.blockDim = dim3(CTHREADS);
+    cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = STEP_SMEM;
     cudaLaunchAttribute a;
     a.id = cudaLaunchAttributeClusterDimension;
@@ -497,12 +525,12 @@ cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const
   if (splits > 1 && (tiles * splits > 2 * sm_count || tiles > sm_count))
     return cudaErrorInvalidValue;  // scratch is sized for 2 x sm_count partial tiles, sm_count tickets
   void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*, int) =
-      renorm ? chain32_step_kernel<true> : chain32_step_kernel<false>;
+      renorm ? chain32_step_kernel<true, kChainTM> : chain32_step_kernel<false, kChainTM>;
   cudaError_t e = set_smem_once((const void*)kern, STEP_SMEM);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(tilesN, tilesM, splits);
-  cfg.blockDim = dim3(CTHREADS);
+  cfg.blockDim = dim3(1024 / kChainTM);
   cfg.dynamicSmemBytes = STEP_SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
