@@ -349,7 +349,47 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
                                    "derivatives, forward/adjoint chains of 4 basis operators", "ms": ms}
     ctx.close()
     out["paper_model_build_breakdown"] = paper_model_breakdown(lb, dev)
+    out["control_reuse_d9"] = control_reuse(lb, dev, time_ms)
     return out
+
+
+def control_reuse(lb, dev, time_ms):
+    """Reuse of slice propagators for nearby controls (the paper's discussion
+    recommends it for GRAPE line searches): P and dP/du for 100 slices at
+    d = 9 once (lb_expm_frechet), then P(u + delta) ~ P + delta dP
+    (lb_control_update) against a full FP64 rebuild at u + delta."""
+    import numpy as np
+    import torch
+
+    from workloads import transmon_chain
+
+    m = transmon_chain(2)
+    n, S = 81, 100
+    ctx = lb.Context(dev.index or 0, max_n=n, max_batch=4, max_slices=S)
+
+    def dput(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    Ld = torch.empty_like(Lb)
+    lb.lb_assemble(ctx, dput(m.H0), dput(m.jumps), Lb)
+    lb.lb_assemble(ctx, dput(m.X), None, Ld)
+    u0 = 0.05 * np.sin(0.3 * np.arange(S))
+    delta = 1e-3
+    u, du = dput(u0), dput(np.full(S, delta))
+    u1 = dput(u0 + delta)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    dP, Pn, Pr = torch.empty_like(P), torch.empty_like(P), torch.empty_like(P)
+    t_fre = time_ms(lambda: lb.lb_expm_frechet(ctx, Lb, Ld, u, m.dt, P, dP))
+    t_upd = time_ms(lambda: lb.lb_control_update(P, dP, du, Pn))
+    t_reb = time_ms(lambda: lb.lb_expm_pade(ctx, Lb, Ld, u1, m.dt, Pr))
+    lb.lb_sync_status(ctx)
+    err = float(torch.max(torch.linalg.matrix_norm(Pn - Pr) / torch.linalg.matrix_norm(Pr)))
+    ctx.close()
+    return {"workload": "d=9, 100 slices: P and dP/du once, then propagators for u + 1e-3 by the first-order "
+                        "update vs an FP64 rebuild",
+            "frechet_build_ms": t_fre, "update_ms": t_upd, "rebuild_ms": t_reb,
+            "update_speedup": t_reb / t_upd, "update_rel_error": err}
 
 
 def paper_model_breakdown(lb, dev):

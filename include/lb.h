@@ -286,6 +286,35 @@ lb_status lb_adam_step_f64(long long count, double* p, const double* g, double* 
                            double beta1, double beta2, double eps, int step, int ascend, void* stream);
 
 /*
+ * lb_expm_frechet -- slice propagators and their control derivatives (the
+ * reuse of P for nearby controls recommended in the paper's discussion, Sec.
+ * 5, built on the differentiated Pade build of lb_grape_grad, Sec. 2.5):
+ *   P_out[s]  = exp(A_s),  A_s = (Lbase + u[s] Ldrv) dt             (Alg. 1)
+ *   dP_out[s] = d/du exp((Lbase + u Ldrv) dt) at u = u[s], the Frechet
+ *               derivative of exp at A_s in the direction Ldrv dt.
+ *   FP64.  Lbase, Ldrv: n x n; u: nslices doubles; P_out, dP_out:
+ *   nslices x n x n complex128, row-major, caller-owned device memory.
+ *   Contexts with max_n <= 81 (the GRAPE workspace); nslices <= max_slices.
+ *   Reads the largest squaring count back to the host, so it cannot be
+ *   captured in a CUDA graph (LB_EUNSUPPORTED while capturing).
+ *   Errors: LB_EINVAL (null pointer, bad size, non-finite dt),
+ *   LB_EUNSUPPORTED (context too large, too many slices, capture).
+ */
+lb_status lb_expm_frechet(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                          const double* u, double dt, lb_c64* P_out, lb_c64* dP_out, void* stream);
+
+/*
+ * lb_control_update -- first-order update of slice propagators for changed
+ * controls, P_out[s] = P[s] + delta[s] dP[s] (FP64), with dP from
+ * lb_expm_frechet; its error against a rebuild at u + delta is second order
+ * in delta.  n x n x nslices complex128 arrays, delta: nslices doubles, all
+ * device memory on the current device; P_out may alias P.  No context.
+ *   Errors: LB_EINVAL (null pointer, n < 1); LB_ECUDA (launch failure).
+ */
+lb_status lb_control_update(int n, int nslices, const lb_c64* P, const lb_c64* dP, const double* delta,
+                            lb_c64* P_out, void* stream);
+
+/*
  * lb_propagate_batch_static -- the FP64 form of lb_propagate_batch for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this exists for applications whose device memory is already owned by their

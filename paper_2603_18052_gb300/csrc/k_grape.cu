@@ -17,6 +17,7 @@
 #include "lb_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 
 namespace lb {
 
@@ -150,32 +151,12 @@ using namespace lb;
     if (e_ != cudaSuccess) return LB_ECUDA; \
   } while (0)
 
-extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
-                                   const double* u, double dt, int steps_per_slice, int B, const lb_c64* X0,
-                                   const lb_c64* Xtarget, double* fidelity_out, double* grad_out,
-                                   void* stream) {
-  if (c == nullptr || Lbase == nullptr || Ldrv == nullptr || u == nullptr || X0 == nullptr ||
-      Xtarget == nullptr || fidelity_out == nullptr || grad_out == nullptr)
-    return LB_EINVAL;
-  if (n < 1 || n > c->max_n || nslices < 1 || steps_per_slice < 1 || B < 1 || B > c->max_batch) return LB_EINVAL;
-  int d = 1;
-  while (d * d < n) d++;
-  if (d * d != n) return LB_EINVAL;
-  if (c->max_n > kGrapeMaxN || n > kGrapeMaxN || B > kGrapeMaxB || nslices > c->max_slices ||
-      steps_per_slice > kGrapeMaxStepsPerSlice)
-    return LB_EUNSUPPORTED;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != c->device) cudaSetDevice(c->device);
-  cudaStream_t st = (cudaStream_t)stream;
-  const int S = nslices, m = steps_per_slice;
+// P_s = exp(A_s) and dP_s = d/du_s exp((Lbase + u_s Ldrv) dt) into w.R and
+// w.dR for the S slices (the differentiated Pade build described above).
+static lb_status frechet_build(lb_ctx* c, int n, int S, const z64* Lb, const z64* Ld, const double* u, double dt,
+                        GrapeWs& w, cudaStream_t st) {
   const long long nn = (long long)n * n;
   const double* b = c->pade_b;
-  GrapeWs w = carve(c);
-  const z64* Lb = (const z64*)Lbase;
-  const z64* Ld = (const z64*)Ldrv;
-
-  lb_status rs = [&]() -> lb_status {
     // scaled A and E, s per slice
     LB_CUDA(launch_slice_prepare(n, S, Lb, Ld, u, dt, c->A, c->norm_bits, c->sc, nullptr, nullptr, c->err_dev,
                                  c->sm_count, st));
@@ -275,6 +256,36 @@ extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* 
       LB_CUDA(launch_copy_active(nn, S, w.T1, w.dR, c->sc, it, st));
       LB_CUDA(launch_copy_active(nn, S, w.T2, w.R, c->sc, it, st));
     }
+  return LB_OK;
+}
+
+extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                                   const double* u, double dt, int steps_per_slice, int B, const lb_c64* X0,
+                                   const lb_c64* Xtarget, double* fidelity_out, double* grad_out,
+                                   void* stream) {
+  if (c == nullptr || Lbase == nullptr || Ldrv == nullptr || u == nullptr || X0 == nullptr ||
+      Xtarget == nullptr || fidelity_out == nullptr || grad_out == nullptr)
+    return LB_EINVAL;
+  if (n < 1 || n > c->max_n || nslices < 1 || steps_per_slice < 1 || B < 1 || B > c->max_batch) return LB_EINVAL;
+  int d = 1;
+  while (d * d < n) d++;
+  if (d * d != n) return LB_EINVAL;
+  if (c->max_n > kGrapeMaxN || n > kGrapeMaxN || B > kGrapeMaxB || nslices > c->max_slices ||
+      steps_per_slice > kGrapeMaxStepsPerSlice)
+    return LB_EUNSUPPORTED;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = nslices, m = steps_per_slice;
+  const long long nn = (long long)n * n;
+  GrapeWs w = carve(c);
+  const z64* Lb = (const z64*)Lbase;
+  const z64* Ld = (const z64*)Ldrv;
+
+  lb_status rs = [&]() -> lb_status {
+    lb_status fb = frechet_build(c, n, S, Lb, Ld, u, dt, w, st);
+    if (fb != LB_OK) return fb;
     // forward and adjoint chains with history
     const long long T = (long long)S * m;
     const long long bn = (long long)B * n;
@@ -297,4 +308,59 @@ extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* 
   }();
   if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
   return rs;
+}
+
+namespace lb {
+namespace {
+__global__ void control_update_kernel(long long nn, long long total, const z64* __restrict__ P,
+                                      const z64* __restrict__ dP, const double* __restrict__ delta,
+                                      z64* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double dl = delta[e / nn];
+    const z64 p = P[e], q = dP[e];
+    out[e] = make_double2(fma(dl, q.x, p.x), fma(dl, q.y, p.y));
+  }
+}
+}  // namespace
+}  // namespace lb
+
+extern "C" lb_status lb_expm_frechet(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                                     const double* u, double dt, lb_c64* P_out, lb_c64* dP_out, void* stream) {
+  if (c == nullptr || Lbase == nullptr || Ldrv == nullptr || u == nullptr || P_out == nullptr || dP_out == nullptr)
+    return LB_EINVAL;
+  if (n < 1 || n > c->max_n || nslices < 0 || !std::isfinite(dt)) return LB_EINVAL;
+  if (nslices == 0) return LB_OK;
+  if (c->max_n > lb::kGrapeMaxN || nslices > c->max_slices) return LB_EUNSUPPORTED;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return LB_EUNSUPPORTED;  // reads the squaring count back to the host
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  GrapeWs w = carve(c);
+  lb_status rs = frechet_build(c, n, nslices, (const lb::z64*)Lbase, (const lb::z64*)Ldrv, u, dt, w, st);
+  if (rs == LB_OK) {
+    const size_t bytes = sizeof(lb::z64) * (size_t)n * n * nslices;
+    if (cudaMemcpyAsync(P_out, w.R, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dP_out, w.dR, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      rs = LB_ECUDA;
+  }
+  if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+  return rs;
+}
+
+extern "C" lb_status lb_control_update(int n, int nslices, const lb_c64* P, const lb_c64* dP, const double* delta,
+                                       lb_c64* P_out, void* stream) {
+  if (P == nullptr || dP == nullptr || delta == nullptr || P_out == nullptr) return LB_EINVAL;
+  if (n < 1 || nslices < 0) return LB_EINVAL;
+  if (nslices == 0) return LB_OK;
+  const long long nn = (long long)n * n, total = nn * nslices;
+  long long g = (total + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  lb::count_launch();
+  lb::control_update_kernel<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(
+      nn, total, (const lb::z64*)P, (const lb::z64*)dP, delta, (lb::z64*)P_out);
+  return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
 }

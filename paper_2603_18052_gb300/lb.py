@@ -53,6 +53,8 @@ EXPORTED = (
     "lb_adam_step",
     "lb_adam_step_f64",
     "lb_selftest_wait_timeout",
+    "lb_expm_frechet",
+    "lb_control_update",
 )
 
 
@@ -118,6 +120,10 @@ def lib():
     L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
     L.lb_propagate_batch_static.restype = i32
     L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
+    L.lb_expm_frechet.restype = i32
+    L.lb_expm_frechet.argtypes = [vp, i32, i32, vp, vp, vp, f64, vp, vp, vp]
+    L.lb_control_update.restype = i32
+    L.lb_control_update.argtypes = [i32, i32, vp, vp, vp, vp, vp]
     L.lb_selftest_wait_timeout.restype = i32
     L.lb_selftest_wait_timeout.argtypes = [vp, ctypes.c_longlong, vp]
     L.lb_run_instances.restype = i32
@@ -293,6 +299,26 @@ def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelit
                                _ptr(fidelity_out, torch.float64, "fidelity_out", (1,)),
                                _ptr(grad_out, torch.float64, "grad_out", (S,)), _stream(stream)),
            "lb_grape_grad")
+
+
+def lb_expm_frechet(ctx, Lbase, Ldrv, u, dt, P_out, dP_out, stream=None):
+    """P_out[s] = exp((Lbase + u[s] Ldrv) dt) and dP_out[s] = its derivative
+    with respect to u[s] (FP64; contexts with max_n <= 81)."""
+    c128 = torch.complex128
+    n = Lbase.shape[0]
+    S = u.shape[0]
+    _check(lib().lb_expm_frechet(ctx.handle, n, S, _ptr(Lbase, c128, "Lbase", (n, n)), _ptr(Ldrv, c128, "Ldrv", (n, n)),
+                                 _ptr(u, torch.float64, "u", (S,)), float(dt), _ptr(P_out, c128, "P_out", (S, n, n)),
+                                 _ptr(dP_out, c128, "dP_out", (S, n, n)), _stream(stream)), "lb_expm_frechet")
+
+
+def lb_control_update(P, dP, delta, P_out, stream=None):
+    """P_out[s] = P[s] + delta[s] dP[s]: propagators for nearby controls."""
+    c128 = torch.complex128
+    S, n = P.shape[0], P.shape[1]
+    _check(lib().lb_control_update(n, S, _ptr(P, c128, "P", (S, n, n)), _ptr(dP, c128, "dP", (S, n, n)),
+                                   _ptr(delta, torch.float64, "delta", (S,)), _ptr(P_out, c128, "P_out", (S, n, n)),
+                                   _stream(stream)), "lb_control_update")
 
 
 def lb_selftest_wait_timeout(ctx, cycles=2_000_000, stream=None):

@@ -49,6 +49,8 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_grape_grad(None, 9, 1, vp(8), vp(8), vp(8), 0.1, 1, 1, vp(8), vp(8), vp(8), vp(8), None) == 1
     assert L.lb_sync_status(None, None) == 1
     assert L.lb_selftest_wait_timeout(None, 1000, None) == 1
+    assert L.lb_expm_frechet(None, 9, 1, vp(8), vp(8), vp(8), 0.1, vp(8), vp(8), None) == 1
+    assert L.lb_control_update(9, 1, None, vp(8), vp(8), vp(8), None) == 1
     assert L.lb_destroy(None) == 0
 
 
