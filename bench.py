@@ -38,6 +38,7 @@ WORKLOAD_DESC = ("d=27 three-transmon chain: 200 control slices u~U(-0.1,0.1), 2
 SM_COUNT = 152
 FP64_PEAK = SM_COUNT * 2 * 2 * 2.07e9   # 2 DFMA/clk/SM x 2 FLOP x 2.07 GHz max clock = 1.259 TFLOP/s
 FP32_PEAK = SM_COUNT * 128 * 2 * 2.07e9  # 128 FFMA/clk/SM = 80.5 TFLOP/s
+INT_MAC_PEAK = SM_COUNT * 64 * 2.07e9    # 32-bit integer multiply-add: 64 lanes/clk/SM = 20.1 T/s
 
 
 def _measured_bf16_peak():
@@ -350,6 +351,175 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     ctx.close()
     out["paper_model_build_breakdown"] = paper_model_breakdown(lb, dev)
     out["control_reuse_d9"] = control_reuse(lb, dev, time_ms)
+    out["fixed_point"] = fixed_point(lb, dev, stream)
+    out["gpu_timing_models"] = gpu_timing_models(lb, dev, stream)
+    return out
+
+
+def fixed_point(lb, dev, stream):
+    """The Q1.15 fixed-point step of Algorithm alg:fpga on the GPU: the d = 3
+    single-state chain (per-step latency and its spread, beside the board's
+    94 cycles at 108 MHz) and batched throughput at d = 3 and d = 9, counted
+    in exact integer products (4 n^2 per state-step) against the 32-bit
+    integer multiply-add rate."""
+    import numpy as np
+    import torch
+
+    from paper_2603_18052_gb300 import timing
+    from workloads import transmon_chain
+
+    def ev_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    out = {}
+    ctx = lb.Context(dev.index or 0, max_n=81, max_batch=8, max_slices=1)
+    for nq, B, N in ((1, 1, 10000), (1, 1 << 17, 1000), (2, 1 << 14, 200)):
+        m = transmon_chain(nq)
+        n = m.d * m.d
+        Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+        Ld = torch.empty_like(Lb)
+        lb.lb_assemble(ctx, torch.from_numpy(m.H0).to(dev), torch.from_numpy(m.jumps).to(dev), Lb)
+        lb.lb_assemble(ctx, torch.from_numpy(m.X).to(dev), None, Ld)
+        P = torch.empty((1, n, n), dtype=torch.complex128, device=dev)
+        lb.lb_expm_pade(ctx, Lb, Ld, torch.tensor([0.05], dtype=torch.float64, device=dev), m.dt, P)
+        Pq = torch.empty((n, n, 2), dtype=torch.int16, device=dev)
+        lb.lb_fixed_quantize(P[0], Pq, 15)
+        x0 = np.zeros((B, n), dtype=np.complex128)
+        x0[:, 0] = 1.0
+        X = torch.empty((B, n, 2), dtype=torch.int16, device=dev)
+        lb.lb_fixed_quantize(torch.from_numpy(x0).to(dev), X, 15)
+        ts = ev_ms(lambda: lb.lb_propagate_fixed(Pq, X, N, 15))
+        ms = statistics.median(ts)
+        key = "d%d_q115_%s" % (m.d, "single" if B == 1 else "batch")
+        r = {"workload": "d=%d, %d state%s, %d chained Q1.15 steps" % (m.d, B, "" if B == 1 else "s", N),
+             "ms": ms, "state_steps_per_s": B * N / (ms / 1e3)}
+        if B == 1:
+            r["ns_per_step"] = 1e6 * ms / N
+            r["ns_per_step_min_max"] = [1e6 * min(ts) / N, 1e6 * max(ts) / N]
+            r["fpga_ns_per_step"] = 1e9 * (timing.fpga_cycles(n, 1, N) - 1) / N / 108e6
+        else:
+            macs = 4.0 * n * n * B * N / (ms / 1e3)
+            r["roofline"] = {"bound": "alu", "achieved": macs / 1e12, "peak": INT_MAC_PEAK / 1e12,
+                             "unit": "T int-MAC/s", "frac": macs / INT_MAC_PEAK}
+        out[key] = r
+    lb.lb_sync_status(ctx)
+    ctx.close()
+    return out
+
+
+def gpu_timing_models(lb, dev, stream):
+    """The three GPU timing models of Sec. 3.4 (Eq. 7-9) on this GPU, as in
+    Table tab:cost_model_gpu: the device probes of Table tab:probes_gpu
+    (launch, launch + sync, copy latency and pageable H2D / D2H rates, stream
+    and stride-n gather reads of 8.3 MB and 64 MiB), then for d = 3, 9, 27
+    and b = 1, 8, 32, 128 the idealized cost from those probes beside the
+    measured median of five trials of 50 one-step calls: kernel-only with
+    CUDA events (lb_propagate_batch), resident-P and host-visible with the
+    host clock around the whole call (lb_propagate_resident,
+    lb_propagate_host; the ctypes call is inside the timed region)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_18052_gb300 import timing
+    from workloads import transmon_chain
+
+    med = statistics.median
+    launch = med(lb.lb_probe_launch(1000, False) for _ in range(5))
+    launch_sync = med(lb.lb_probe_launch(200, True) for _ in range(5))
+
+    def copy_us(nbytes, to_dev, reps):
+        h = torch.zeros(nbytes // 8, dtype=torch.float64)  # pageable host memory
+        d = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+        return med(lb.lb_probe_copy(h, d, to_dev, reps) for _ in range(5))
+
+    big = 64 << 20
+    lat_h2d, lat_d2h = copy_us(16, True, 200), copy_us(16, False, 200)
+    h2d = big / (1e3 * (copy_us(big, True, 5) - lat_h2d))
+    d2h = big / (1e3 * (copy_us(big, False, 5) - lat_d2h))
+
+    def read_gbs(nbytes, n):
+        count = nbytes // 16
+        buf = torch.ones(count, dtype=torch.complex128, device=dev)
+        sink = torch.zeros(1, dtype=torch.int64, device=dev)
+        read = 16 * (count if n == 0 else (count // n) * n)
+        ts = []
+        lb.lb_probe_read(buf, n, sink)
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(20):
+                lb.lb_probe_read(buf, n, sink)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 20)
+        return read / (med(ts) * 1e6)
+
+    ws27 = 16 * (729 * 729 + 2 * 729)  # the d = 27 working set, "8.3 MB"
+    reads = {"stream_8p3MB": read_gbs(ws27, 0), "gather_8p3MB": read_gbs(ws27, 729),
+             "stream_64MiB": read_gbs(big, 0), "gather_64MiB": read_gbs(big, 729)}
+    probes = timing.Probes(launch_us=launch, launch_sync_us=launch_sync, lat_h2d_us=lat_h2d, lat_d2h_us=lat_d2h,
+                           h2d_gbs=h2d, d2h_gbs=d2h, stream_gbs=max(reads["stream_8p3MB"], reads["stream_64MiB"]),
+                           alloc_calls=4, alloc_us_each=3.0)
+    out = {"probes": {"launch_us": launch, "launch_sync_us": launch_sync, "copy_latency_h2d_us": lat_h2d,
+                      "copy_latency_d2h_us": lat_d2h, "h2d_gbs": h2d, "d2h_gbs": d2h, **{k + "_gbs": v for k, v in reads.items()},
+                      "alloc": "4 calls (2 cudaMalloc + 2 cudaFree) at the paper's stated 3 us each"},
+           "rows": []}
+    ctx = lb.Context(dev.index or 0, max_n=729, max_batch=128, max_slices=1)
+    for nq in (1, 2, 3):
+        m = transmon_chain(nq)
+        n = m.d * m.d
+        Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+        Ld = torch.empty_like(Lb)
+        lb.lb_assemble(ctx, torch.from_numpy(m.H0).to(dev), torch.from_numpy(m.jumps).to(dev), Lb)
+        lb.lb_assemble(ctx, torch.from_numpy(m.X).to(dev), None, Ld)
+        P = torch.empty((1, n, n), dtype=torch.complex128, device=dev)
+        lb.lb_expm_pade(ctx, Lb, Ld, torch.tensor([0.05], dtype=torch.float64, device=dev), m.dt, P)
+        P_host = P[0].cpu().contiguous()
+        for b in (1, 8, 32, 128):
+            x0 = np.zeros((b, n), dtype=np.complex128)
+            x0[:, 0] = 1.0
+            Xd = torch.from_numpy(x0).to(dev)
+            Xh = torch.from_numpy(x0.copy())
+            reps = 50
+
+            def kernel_trial():
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    lb.lb_propagate_batch(ctx, P, Xd, 1, "fp64")
+                e.record(stream)
+                e.synchronize()
+                return a.elapsed_time(e) * 1e6 / reps / b
+
+            def host_trial(fn):
+                t0 = time.perf_counter_ns()
+                for _ in range(reps):
+                    fn()
+                return (time.perf_counter_ns() - t0) / reps / b
+
+            meas = {}
+            for name, trial in (("kernel", kernel_trial),
+                                ("resident", lambda: host_trial(lambda: lb.lb_propagate_resident(ctx, P[0], Xh))),
+                                ("host", lambda: host_trial(lambda: lb.lb_propagate_host(ctx, P_host, Xh)))):
+                trial()  # warm-up: one untimed trial of 50 calls
+                meas[name] = med(trial() for _ in range(5))
+            row = {"d": m.d, "batch": b}
+            for name, f in timing.MODELS:
+                ideal = f(n, b, probes)
+                row[name] = {"idealized_ns": ideal, "measured_ns": meas[name], "ratio": meas[name] / ideal}
+            out["rows"].append(row)
+    lb.lb_sync_status(ctx)
+    ctx.close()
     return out
 
 

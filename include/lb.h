@@ -351,6 +351,111 @@ lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64* P, int ste
  */
 lb_status lb_selftest_wait_timeout(lb_ctx* ctx, long long cycles, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Fixed-point propagation: the element-serial Q1.15 step of the FPGA design
+ * (Algorithm alg:fpga, Sec. 3.5; formats Sec. 2.2) and its Q1.31 variant
+ * (Figure fig:fixed_point_drift), bit-exact.  No lb_ctx: these run on the
+ * CURRENT CUDA device (sm_103 only, else LB_ENODEV), which must hold every
+ * pointer passed.  Asynchronous on `stream`; they allocate nothing.
+ *
+ * Codes: frac_bits = 15 or 31 (else LB_EINVAL).  A Q1.f complex value is a
+ * pair (re, im) of two's-complement codes standing for code / 2^f: two
+ * int16 (4 bytes per complex value) for f = 15, two int32 (8 bytes) for
+ * f = 31, re first.  A state is the row-major vectorisation of rho
+ * (n = d^2 values); B states are stored one after another.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * lb_fixed_quantize -- q[e] = nearest code of x[e] (x * 2^f rounded to the
+ * nearest integer, ties to even), saturated to [-2^f, 2^f - 1], real and
+ * imaginary parts separately; so 1.0 becomes 2^f - 1.  NaN becomes 0.
+ *   count complex128 values in x (device), count code pairs out in q
+ *   (device).  count = 0 does nothing.  LB_EINVAL for count < 0 or a null
+ *   pointer with count > 0.
+ */
+lb_status lb_fixed_quantize(int frac_bits, long long count, const lb_c64* x, void* q, void* stream);
+
+/*
+ * lb_fixed_dequantize -- x[e] = q[e] / 2^f (exact in double).  Same
+ * argument rules as lb_fixed_quantize.
+ */
+lb_status lb_fixed_dequantize(int frac_bits, long long count, const void* q, lb_c64* x, void* stream);
+
+/*
+ * lb_propagate_fixed -- nsteps chained steps of Algorithm alg:fpga on each
+ * of B states with one propagator:
+ *     acc_i = sum_j P[i][j] rho_j            (exact: four integer products
+ *                                             per term, 64-bit sums for
+ *                                             Q1.15, 128-bit for Q1.31)
+ *     rho_i <- sat(floor(acc_i / 2^f))       (floor = towards -infinity,
+ *                                             sat = clamp to the code range)
+ *   n:        d^2 with 1 <= n <= 81 (P is held in shared memory).
+ *   P_q:      n x n code pairs, row-major, row i produces output i (device).
+ *   nsteps:   >= 0; 0 does nothing.
+ *   B:        >= 1 states in states_q (B x n code pairs, device), overwritten
+ *             with the states after nsteps steps.
+ *   Errors: LB_EINVAL for an unsupported frac_bits, n, nsteps < 0, B < 1 or
+ *   a null pointer; LB_ECUDA if the launch fails.
+ */
+lb_status lb_propagate_fixed(int frac_bits, int n, const void* P_q, int nsteps, int B, void* states_q,
+                             void* stream);
+
+/* ------------------------------------------------------------------------
+ * The three GPU timing models of Sec. 3.4 (Eq. 7-9) and the device probes
+ * behind their constants (Table tab:probes_gpu).  Kernel-only timing is
+ * lb_propagate_batch with one step; the two calls below add what Eq. 8 and
+ * Eq. 9 add to it.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * lb_propagate_resident -- resident-P timing model (Eq. 8): one FP64
+ * propagation step (P = one n x n propagator, device) of B states that live
+ * in HOST memory (B x n complex128, pageable or pinned): copies them to the
+ * context's device buffer, runs the same step as lb_propagate_batch with
+ * prec = LB_FP64, copies the result back into states_host and synchronises
+ * `stream` before returning.
+ *   Errors: LB_EINVAL for a null argument, n not a square in [1, max_n] or
+ *   B outside [1, max_batch]; LB_ECUDA for a failed copy or launch.
+ */
+lb_status lb_propagate_resident(lb_ctx* ctx, int n, const lb_c64* P, int B, lb_c64* states_host, void* stream);
+
+/*
+ * lb_propagate_host -- host-visible timing model (Eq. 9): as
+ * lb_propagate_resident, but P is in HOST memory too and the device buffers
+ * for P and the states are allocated (cudaMalloc) and freed (cudaFree)
+ * inside every call, as by a caller that keeps nothing on the device.
+ *   Errors: as lb_propagate_resident; LB_ENOMEM if an allocation fails.
+ *   Buffers are freed on every path.
+ */
+lb_status lb_propagate_host(lb_ctx* ctx, int n, const lb_c64* P_host, int B, lb_c64* states_host, void* stream);
+
+/*
+ * lb_probe_launch -- host time per launch of an empty kernel on `stream`,
+ * in microseconds (*us_out), over `reps` >= 1 launches: back to back
+ * (sync_each = 0: the launch cost t_launch) or each followed by a stream
+ * synchronise (sync_each = 1: launch + sync).  Waits for the stream first.
+ */
+lb_status lb_probe_launch(int reps, int sync_each, double* us_out, void* stream);
+
+/*
+ * lb_probe_copy -- host time per synchronous copy of `bytes` bytes between
+ * `host` (pageable or pinned) and `device` (to_device = 1: host to device,
+ * 0: device to host), in microseconds, over `reps` >= 1 copies, each
+ * followed by a synchronise of `stream`.
+ */
+lb_status lb_probe_copy(void* host, void* device, long long bytes, int to_device, int reps, double* us_out,
+                        void* stream);
+
+/*
+ * lb_probe_read -- one read pass over `count` complex128 values of `buf`
+ * (device): n = 0 is a coalesced stream (consecutive threads read
+ * consecutive values); n >= 1 is the stride-n gather of Algorithm alg:gpu
+ * (one thread per row of n values, consecutive threads consecutive rows;
+ * the count % n trailing values are not read).  `sink` (device, 8 bytes)
+ * is written only on an impossible match.  Time it with events on `stream`.
+ */
+lb_status lb_probe_read(const lb_c64* buf, long long count, int n, unsigned long long* sink, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,21 @@ namespace lb {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+lb_status current_device_sm103(int* dev, int* sms) {
+  int d = -1, major = 0, minor = 0, s = 0;
+  if (cudaGetDevice(&d) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, d) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, d) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ENODEV;
+  }
+  if (major != 10 || minor != 3 || s <= 0) return LB_ENODEV;
+  *dev = d;
+  *sms = s;
+  return LB_OK;
+}
+
 cudaError_t set_smem_once(const void* kernel, size_t bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> done;
@@ -33,18 +48,6 @@ cudaError_t set_smem_once(const void* kernel, size_t bytes) {
 }  // namespace lb
 
 namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 #define LB_CUDA(call)                       \
   do {                                      \
@@ -143,6 +146,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add(S * sizeof(int));                                     // kmix
   add(sizeof(z64) * 64 * 64);                               // G
   add((size_t)max_batch * max_n * zb);                      // Rtmp
+  add((size_t)max_batch * max_n * zb);                      // Xh
   const size_t plane_elems = (size_t)max_n * (size_t)plane_ld(max_n);
   for (int i = 0; i < 9; i++) add((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));  // split planes
   for (int i = 0; i < 2; i++) add(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
@@ -185,6 +189,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->kmix = (int*)ar.take(S * sizeof(int));
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
+  c->Xh = Z((size_t)max_batch * max_n);
   for (int i = 0; i < 9; i++)
     c->sp[i] = (__nv_bfloat16*)ar.take((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));
   for (int i = 0; i < 2; i++)

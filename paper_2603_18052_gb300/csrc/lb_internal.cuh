@@ -39,6 +39,24 @@ struct Arena {
 // Process-wide count of kernel launches issued by the library.
 void count_launch();
 
+// For the entry points that take no lb_ctx: the current CUDA device, which
+// must be an sm_103 part, and its SM count.  LB_ENODEV otherwise.
+lb_status current_device_sm103(int* dev, int* sms);
+
+// Makes `dev` current for the guard's lifetime, then restores the previous
+// device.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace lb
 
 struct lb_ctx {
@@ -75,6 +93,7 @@ struct lb_ctx {
   __nv_bfloat16* spR[2] = {};  // state planes, 4 x max_batch x ld each
   // --- propagation ---
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
+  lb::z64* Xh = nullptr;    // max_batch x max_n: device copy of host states (lb_propagate_resident)
   float *Dr = nullptr, *Di = nullptr;  // per slice max_n^2 (n <= 81), inside Dpl
   float* Dpl = nullptr;                // FP32 D^T planes of the chain, per slice chain32_dplane_floats
   float *C32a = nullptr, *C32b = nullptr;  // FP32 state planes, chain32_state_floats(max_n, max_batch)

@@ -55,6 +55,14 @@ EXPORTED = (
     "lb_selftest_wait_timeout",
     "lb_expm_frechet",
     "lb_control_update",
+    "lb_fixed_quantize",
+    "lb_fixed_dequantize",
+    "lb_propagate_fixed",
+    "lb_propagate_resident",
+    "lb_propagate_host",
+    "lb_probe_launch",
+    "lb_probe_copy",
+    "lb_probe_read",
 )
 
 
@@ -142,6 +150,22 @@ def lib():
     L.lb_adam_step_f64.argtypes = [ll, vp, vp, vp, vp, f64, f64, f64, f64, i32, i32, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
+    L.lb_fixed_quantize.restype = i32
+    L.lb_fixed_quantize.argtypes = [i32, ll, vp, vp, vp]
+    L.lb_fixed_dequantize.restype = i32
+    L.lb_fixed_dequantize.argtypes = [i32, ll, vp, vp, vp]
+    L.lb_propagate_fixed.restype = i32
+    L.lb_propagate_fixed.argtypes = [i32, i32, vp, i32, i32, vp, vp]
+    L.lb_propagate_resident.restype = i32
+    L.lb_propagate_resident.argtypes = [vp, i32, vp, i32, vp, vp]
+    L.lb_propagate_host.restype = i32
+    L.lb_propagate_host.argtypes = [vp, i32, vp, i32, vp, vp]
+    L.lb_probe_launch.restype = i32
+    L.lb_probe_launch.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), vp]
+    L.lb_probe_copy.restype = i32
+    L.lb_probe_copy.argtypes = [vp, vp, ll, i32, i32, ctypes.POINTER(ctypes.c_double), vp]
+    L.lb_probe_read.restype = i32
+    L.lb_probe_read.argtypes = [vp, ll, i32, vp, vp]
     del ip, dp
     _lib = L
     return L
@@ -337,6 +361,106 @@ def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
     _check(lib().lb_propagate_batch_static(n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
                                            _ptr(states, c128, "states", (B, n)), _stream(stream)),
            "lb_propagate_batch_static")
+
+
+_CODE_DTYPES = {15: torch.int16, 31: torch.int32}
+
+
+def _code_ptr(t, frac_bits, what, count=None):
+    """A contiguous CUDA tensor of code pairs: int16 (Q1.15) or int32 (Q1.31),
+    last dimension 2 (re, im).  Returns (pointer, number of complex values)."""
+    dt = _CODE_DTYPES.get(frac_bits)
+    if dt is None:
+        raise ValueError("frac_bits must be 15 or 31")
+    if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous() \
+            or t.dim() < 1 or t.shape[-1] != 2:
+        raise ValueError("%s must be a contiguous CUDA %s tensor of shape (..., 2)" % (what, dt))
+    m = t.numel() // 2
+    if count is not None and m != count:
+        raise ValueError("%s holds %d complex values, expected %d" % (what, m, count))
+    return ctypes.c_void_p(t.data_ptr()), m
+
+
+def lb_fixed_quantize(x, q, frac_bits=15, stream=None):
+    """q = Q1.f codes of the complex128 tensor x (nearest, ties to even,
+    saturated); q has x's shape plus a last dimension 2."""
+    qp, m = _code_ptr(q, frac_bits, "q", x.numel())
+    _check(lib().lb_fixed_quantize(int(frac_bits), m, _ptr(x, torch.complex128, "x"), qp, _stream(stream)),
+           "lb_fixed_quantize")
+
+
+def lb_fixed_dequantize(q, x, frac_bits=15, stream=None):
+    """x = q / 2^f as complex128."""
+    qp, m = _code_ptr(q, frac_bits, "q", x.numel())
+    _check(lib().lb_fixed_dequantize(int(frac_bits), m, qp, _ptr(x, torch.complex128, "x"), _stream(stream)),
+           "lb_fixed_dequantize")
+
+
+def lb_propagate_fixed(P_q, states_q, nsteps, frac_bits=15, stream=None):
+    """nsteps fixed-point steps (Algorithm alg:fpga) of the B states in
+    states_q (B x n x 2 codes, overwritten) with the propagator P_q
+    (n x n x 2 codes)."""
+    n = P_q.shape[0]
+    pp, _ = _code_ptr(P_q, frac_bits, "P_q", n * n)
+    B = states_q.shape[0]
+    sp, _ = _code_ptr(states_q, frac_bits, "states_q", B * n)
+    _check(lib().lb_propagate_fixed(int(frac_bits), n, pp, int(nsteps), B, sp, _stream(stream)),
+           "lb_propagate_fixed")
+
+
+def _host_ptr(t, what, shape):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CPU complex128 tensor" % what)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (what, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lb_propagate_resident(ctx, P, states_host, stream=None):
+    """One FP64 step of the host-memory states (B x n CPU tensor, overwritten)
+    with the device propagator P (n x n): the resident-P model (Eq. 8)."""
+    n = P.shape[0]
+    B = states_host.shape[0]
+    _check(lib().lb_propagate_resident(ctx.handle, n, _ptr(P, torch.complex128, "P", (n, n)), B,
+                                       _host_ptr(states_host, "states_host", (B, n)), _stream(stream)),
+           "lb_propagate_resident")
+
+
+def lb_propagate_host(ctx, P_host, states_host, stream=None):
+    """As lb_propagate_resident with P in host memory too, device buffers
+    allocated and freed inside the call: the host-visible model (Eq. 9)."""
+    n = P_host.shape[0]
+    B = states_host.shape[0]
+    _check(lib().lb_propagate_host(ctx.handle, n, _host_ptr(P_host, "P_host", (n, n)), B,
+                                   _host_ptr(states_host, "states_host", (B, n)), _stream(stream)),
+           "lb_propagate_host")
+
+
+def lb_probe_launch(reps=1000, sync_each=False, stream=None):
+    """Host microseconds per empty-kernel launch (sync_each: launch + sync)."""
+    us = ctypes.c_double(0.0)
+    _check(lib().lb_probe_launch(int(reps), int(bool(sync_each)), ctypes.byref(us), _stream(stream)),
+           "lb_probe_launch")
+    return us.value
+
+
+def lb_probe_copy(host, device, to_device, reps=20, stream=None):
+    """Host microseconds per synchronous copy between the CPU tensor `host`
+    and the CUDA tensor `device` (same byte size)."""
+    nb = host.numel() * host.element_size()
+    if host.is_cuda or not device.is_cuda or device.numel() * device.element_size() != nb:
+        raise ValueError("host must be a CPU tensor and device a CUDA tensor of the same byte size")
+    us = ctypes.c_double(0.0)
+    _check(lib().lb_probe_copy(ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(device.data_ptr()), nb,
+                               int(bool(to_device)), int(reps), ctypes.byref(us), _stream(stream)), "lb_probe_copy")
+    return us.value
+
+
+def lb_probe_read(buf, n, sink, stream=None):
+    """One read pass over the complex128 CUDA tensor buf: n = 0 coalesced
+    stream, n >= 1 stride-n gather (Algorithm alg:gpu's access pattern)."""
+    _check(lib().lb_probe_read(_ptr(buf, torch.complex128, "buf"), buf.numel(), int(n),
+                               _ptr(sink, torch.int64, "sink"), _stream(stream)), "lb_probe_read")
 
 
 def lb_run_instances(ctx, instances, dt, prec="fp64", renorm_trace=False, stream=None):

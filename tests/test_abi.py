@@ -51,6 +51,17 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_selftest_wait_timeout(None, 1000, None) == 1
     assert L.lb_expm_frechet(None, 9, 1, vp(8), vp(8), vp(8), 0.1, vp(8), vp(8), None) == 1
     assert L.lb_control_update(9, 1, None, vp(8), vp(8), vp(8), None) == 1
+    assert L.lb_propagate_resident(None, 9, vp(8), 1, vp(8), None) == 1
+    assert L.lb_propagate_host(None, 9, vp(8), 1, vp(8), None) == 1
+    assert L.lb_propagate_fixed(15, 9, None, 1, 1, vp(8), None) == 1
+    assert L.lb_propagate_fixed(16, 9, vp(8), 1, 1, vp(8), None) == 1  # only Q1.15 and Q1.31
+    assert L.lb_propagate_fixed(15, 100, vp(8), 1, 1, vp(8), None) == 1  # n above 81
+    assert L.lb_propagate_fixed(15, 8, vp(8), 1, 1, vp(8), None) == 1  # n not a square
+    assert L.lb_fixed_quantize(15, 4, None, vp(8), None) == 1
+    assert L.lb_fixed_dequantize(7, 4, vp(8), vp(8), None) == 1
+    assert L.lb_probe_read(None, 16, 0, vp(8), None) == 1
+    assert L.lb_probe_launch(0, 0, None, None) == 1
+    assert L.lb_probe_copy(None, vp(8), 16, 1, 1, None, None) == 1
     assert L.lb_destroy(None) == 0
 
 
