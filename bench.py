@@ -352,7 +352,75 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     out["paper_model_build_breakdown"] = paper_model_breakdown(lb, dev)
     out["control_reuse_d9"] = control_reuse(lb, dev, time_ms)
     out["fixed_point"] = fixed_point(lb, dev, stream)
+    out["action_of_exponential_d27"] = action_of_exponential(lb, dev, stream)
     out["gpu_timing_models"] = gpu_timing_models(lb, dev, stream)
+    return out
+
+
+def action_of_exponential(lb, dev, stream, S=10):
+    """The d = 27 chain's first S slices without dense propagators
+    (lb_expmv: truncated Taylor series, FP64, no LU) against the dense route
+    (Pade build of the S propagators, then the chain) in FP64 and in the
+    split-BF16 form, for B = 1, 8, 64 states.  The Taylor products count
+    8 n^2 B FLOPs each."""
+    import numpy as np
+    import torch
+
+    from workloads import make_workload
+
+    out = {}
+    w = make_workload("d27_chain", B=64, nslices=S)
+    n = w["n"]
+    ctx = lb.Context(dev.index or 0, max_n=n, max_batch=64, max_slices=S)
+    Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    Ld = torch.empty_like(Lb)
+    lb.lb_assemble(ctx, torch.from_numpy(w["H0"]).to(dev), torch.from_numpy(w["jumps"]).to(dev), Lb)
+    lb.lb_assemble(ctx, torch.from_numpy(w["X"]).to(dev), None, Ld)
+    u = torch.from_numpy(np.ascontiguousarray(w["u"][:S])).to(dev)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    for B in (1, 8, 64):
+        X = torch.from_numpy(np.ascontiguousarray(w["states"][:B])).to(dev)
+        ms_pair = [None]
+
+        def taylor():
+            ms_pair[0] = lb.lb_expmv(ctx, Lb, Ld, u, w["dt"], X)
+
+        def dense():
+            lb.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P)
+            lb.lb_propagate_batch(ctx, P, X, 1, "fp64")
+
+        def dense_mixed():
+            lb.lb_expm_pade(ctx, Lb, Ld, u, w["dt"], P, prec="bf16x3")
+            lb.lb_propagate_batch(ctx, P, X, 1, "bf16x3")
+
+        t_taylor = timed(taylor)
+        t_dense = timed(dense)
+        t_mixed = timed(dense_mixed)
+        m, s = ms_pair[0]
+        fl = S * s * m * 8.0 * n * n * B
+        out["B%d" % B] = {"taylor_ms_per_slice": t_taylor / S, "dense_fp64_ms_per_slice": t_dense / S,
+                          "dense_bf16x3_ms_per_slice": t_mixed / S,
+                          "speedup_vs_dense_fp64": t_dense / t_taylor, "speedup_vs_dense_bf16x3": t_mixed / t_taylor,
+                          "m": m, "s": s,
+                          "taylor_roofline": {"bound": "alu", "achieved": fl / (t_taylor / 1e3) / 1e12,
+                                              "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                                              "frac": fl / (t_taylor / 1e3) / FP64_PEAK}}
+    lb.lb_sync_status(ctx)
+    ctx.close()
     return out
 
 

@@ -351,6 +351,35 @@ lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64* P, int ste
  */
 lb_status lb_selftest_wait_timeout(lb_ctx* ctx, long long cycles, void* stream);
 
+/*
+ * lb_expmv -- the states through the control slices WITHOUT forming the
+ * propagators (the action-of-the-exponential route that the paper's
+ * discussion, Sec. 5, names for removing the LU solve; Al-Mohy and Higham's
+ * truncated Taylor series with scaling):
+ *     for s = 0 .. nslices-1:  X <- exp(A_s) X,  A_s = (Lbase + u[s] Ldrv) dt
+ * with each state a row of X (as in lb_propagate_batch).  exp(A_s) x is the
+ * sum of s_sub sub-steps of the degree-m Taylor series; one pair (m, s_sub)
+ * serves the whole call, the one with the fewest products m * s_sub such
+ * that a / s_sub <= theta_m, where a is the largest ||A_s||_1 (maximum
+ * absolute column sum) of the call and theta_m the largest theta with
+ * theta^(m+1)/(m+1)! e^theta <= 2^-53 (1 <= m <= 55).  FP64 throughout.
+ *   n:       <= ctx max_n (any n; not only squares).
+ *   Lbase, Ldrv, u: as lb_expm_pade (device): Ldrv = NULL means Lbase holds
+ *            nslices generators and u is ignored.
+ *   dt:      finite slice length.
+ *   B:       1 .. ctx max_batch states in `states` (B x n complex128,
+ *            device), overwritten.
+ *   ms_out:  NULL or host int[2] receiving (m, s_sub).
+ *   Reads the largest norm back to the host (the stream is synchronised
+ *   once), so it cannot be captured in a CUDA graph (LB_EUNSUPPORTED when
+ *   the stream is capturing).  Uses the context's build and state scratch.
+ *   Errors: LB_EINVAL for bad arguments; LB_ENONFINITE for a NaN or Inf in
+ *   a generator; LB_EUNSUPPORTED if more than 65536 sub-steps would be
+ *   needed; LB_ECUDA for a failed launch.
+ */
+lb_status lb_expmv(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv, const double* u,
+                   double dt, int B, lb_c64* states, int* ms_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Fixed-point propagation: the element-serial Q1.15 step of the FPGA design
  * (Algorithm alg:fpga, Sec. 3.5; formats Sec. 2.2) and its Q1.31 variant

@@ -145,12 +145,6 @@ cudaError_t launch_redot(int S, long long len, const z64* L, long long sL, const
 
 using namespace lb;
 
-#define LB_CUDA(call)                       \
-  do {                                      \
-    cudaError_t e_ = (call);                \
-    if (e_ != cudaSuccess) return LB_ECUDA; \
-  } while (0)
-
 // P_s = exp(A_s) and dP_s = d/du_s exp((Lbase + u_s Ldrv) dt) into w.R and
 // w.dR for the S slices (the differentiated Pade build described above).
 static lb_status frechet_build(lb_ctx* c, int n, int S, const z64* Lb, const z64* Ld, const double* u, double dt,

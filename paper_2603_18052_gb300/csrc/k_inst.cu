@@ -158,12 +158,6 @@ size_t inst_table_bytes() { return (size_t)kMaxEntries * sizeof(GenEntry) + (siz
 
 using namespace lb;
 
-#define LB_CUDA(call)                       \
-  do {                                      \
-    cudaError_t e_ = (call);                \
-    if (e_ != cudaSuccess) return LB_ECUDA; \
-  } while (0)
-
 extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int count, double dt, lb_precision prec,
                                       int renorm_trace, void* stream) {
   if (c == nullptr || (inst == nullptr && count > 0) || count < 0) return LB_EINVAL;

@@ -150,12 +150,6 @@ bool check_dims(int nlayers, const int* dims, int batch) {
 
 using namespace lb;
 
-#define LB_CUDA(call)                       \
-  do {                                      \
-    cudaError_t e_ = (call);                \
-    if (e_ != cudaSuccess) return LB_ECUDA; \
-  } while (0)
-
 extern "C" {
 
 lb_status lb_mlp_forward(int nlayers, const int* dims, int batch, const void* W, const float* b, const float* x,

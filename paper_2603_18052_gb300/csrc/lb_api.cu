@@ -49,12 +49,6 @@ cudaError_t set_smem_once(const void* kernel, size_t bytes) {
 
 namespace {
 
-#define LB_CUDA(call)                       \
-  do {                                      \
-    cudaError_t e_ = (call);                \
-    if (e_ != cudaSuccess) return LB_ECUDA; \
-  } while (0)
-
 // [13/13] Pade coefficients of exp from the recurrence of the closed form
 // b_j = (2m-j)! m! / ((2m)! j! (m-j)!):  b_j = b_{j-1} (m - j + 1) / (j (2m - j + 1)).
 void pade13(double* b) {
@@ -695,7 +689,8 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   is_square(n, &d);
   const long long nn = (long long)n * n;
   if (prec == LB_FP64) {
-    if (resident_f64_fits(n)) {
+    const bool gemv = gemv_f64_preferred(n, B);
+    if (!gemv && resident_f64_fits(n)) {
       LB_CUDA(launch_propagate_resident_f64(n, nslices, Pz, steps_per_slice, B, X, c->sm_count, st));
       return LB_OK;
     }
@@ -704,6 +699,13 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
     for (int s = 0; s < nslices; s++)
       for (int t = 0; t < steps_per_slice; t++) {
         // next[b][i] = sum_j P[i][j] cur[b][j]  ->  C = cur * P^T
+        if (gemv) {
+          LB_CUDA(launch_zgemv_f64(n, B, Pz + s * nn, n, cur, n, nxt, n, 1.0, nullptr, 0, st));
+          z64* tmp = cur;
+          cur = nxt;
+          nxt = tmp;
+          continue;
+        }
         ZGemmProblem q;
         q.M = B; q.N = n; q.K = n;
         q.A = cur; q.lda = n;

@@ -39,6 +39,13 @@ struct Arena {
 // Process-wide count of kernel launches issued by the library.
 void count_launch();
 
+// Return LB_ECUDA from the enclosing lb_status function on a CUDA error.
+#define LB_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return LB_ECUDA; \
+  } while (0)
+
 // For the entry points that take no lb_ctx: the current CUDA device, which
 // must be an sm_103 part, and its SM count.  LB_ENODEV otherwise.
 lb_status current_device_sm103(int* dev, int* sms);
@@ -139,6 +146,18 @@ struct ZGemmProblem {
 
 // Launch up to 4 problems in one grouped launch.  Returns a CUDA error code.
 cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
+
+// Few-state FP64 products (k_gemv.cu), B <= kGemvMaxB:
+//   V[b][i] = alpha sum_j A[i][j] X[b][j];  Yacc[b][i] += the same (Yacc may be null)
+constexpr int kGemvMaxB = 8;
+cudaError_t launch_zgemv_f64(int n, int B, const z64* A, long long lda, const z64* X, long long ldx, z64* V,
+                             long long ldv, double alpha, z64* Yacc, long long ldacc, cudaStream_t st);
+// Whether a B-state FP64 propagation step at size n goes to launch_zgemv_f64.
+bool gemv_f64_preferred(int n, int B);
+
+// (m, s) of the truncated Taylor series for ||A||_1 = a (k_expmv.cu); false
+// for a non-finite a or more than 65536 sub-steps.
+bool taylor_parameters(double a, int* m_out, int* s_out);
 
 // Autotuner: in tuning mode every GEMM launch times its candidate tile
 // configurations and records the fastest for its shape (see k_gemm.cu).

@@ -55,6 +55,7 @@ EXPORTED = (
     "lb_selftest_wait_timeout",
     "lb_expm_frechet",
     "lb_control_update",
+    "lb_expmv",
     "lb_fixed_quantize",
     "lb_fixed_dequantize",
     "lb_propagate_fixed",
@@ -150,6 +151,8 @@ def lib():
     L.lb_adam_step_f64.argtypes = [ll, vp, vp, vp, vp, f64, f64, f64, f64, i32, i32, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
+    L.lb_expmv.restype = i32
+    L.lb_expmv.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.lb_fixed_quantize.restype = i32
     L.lb_fixed_quantize.argtypes = [i32, ll, vp, vp, vp]
     L.lb_fixed_dequantize.restype = i32
@@ -176,12 +179,19 @@ def _check(status, what):
         raise LBError(status, what)
 
 
+# The raw handle of the current stream without building a Stream object
+# (a few microseconds per call otherwise, which shows in one-step calls).
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream):
     if stream is None:
-        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if _raw_stream is not None:
+            return _raw_stream(torch.cuda.current_device())
+        return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, torch.cuda.Stream):
-        return ctypes.c_void_p(stream.cuda_stream)
-    return ctypes.c_void_p(int(stream))
+        return stream.cuda_stream
+    return int(stream)
 
 
 def _ptr(t, dtype, what, shape=None, allow_none=False):
@@ -193,7 +203,7 @@ def _ptr(t, dtype, what, shape=None, allow_none=False):
         raise ValueError("%s must be a contiguous CUDA %s tensor" % (what, dtype))
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError("%s has shape %s, expected %s" % (what, tuple(t.shape), tuple(shape)))
-    return ctypes.c_void_p(t.data_ptr())
+    return t.data_ptr()
 
 
 class Context:
@@ -361,6 +371,28 @@ def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
     _check(lib().lb_propagate_batch_static(n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
                                            _ptr(states, c128, "states", (B, n)), _stream(stream)),
            "lb_propagate_batch_static")
+
+
+def lb_expmv(ctx, Lbase, Ldrv, u, dt, states, stream=None):
+    """states (B x n, overwritten) <- exp((Lbase + u[s] Ldrv) dt) states for
+    every slice s, without forming the propagators (truncated Taylor series
+    with scaling, FP64).  Ldrv None: Lbase is (S, n, n) and u is ignored.
+    Returns the Taylor degree m and the number of sub-steps per slice."""
+    c128 = torch.complex128
+    B, n = states.shape
+    if Ldrv is None:
+        S = Lbase.shape[0]
+        lbp = _ptr(Lbase, c128, "Lbase", (S, n, n))
+        ldp = up = None
+    else:
+        S = u.shape[0]
+        lbp = _ptr(Lbase, c128, "Lbase", (n, n))
+        ldp = _ptr(Ldrv, c128, "Ldrv", (n, n))
+        up = _ptr(u, torch.float64, "u", (S,))
+    ms = (ctypes.c_int * 2)()
+    _check(lib().lb_expmv(ctx.handle, n, S, lbp, ldp, up, float(dt), B, _ptr(states, c128, "states", (B, n)), ms,
+                          _stream(stream)), "lb_expmv")
+    return int(ms[0]), int(ms[1])
 
 
 _CODE_DTYPES = {15: torch.int16, 31: torch.int32}

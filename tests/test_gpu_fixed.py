@@ -86,7 +86,8 @@ def test_board_drift_bit_exact(lbm, f, driven):
 
 @pytest.mark.parametrize("f,n,B,steps", [
     (15, 9, 1, 3), (15, 9, 300, 25), (15, 81, 1000, 12), (15, 4, 7, 5), (15, 1, 33, 40),
-    (31, 9, 300, 10), (31, 81, 3, 4), (31, 4, 5, 6), (31, 1, 2, 30),
+    (15, 16, 40, 9), (15, 25, 7, 5), (15, 9, 5000, 3),
+    (31, 9, 300, 10), (31, 81, 3, 4), (31, 4, 5, 6), (31, 1, 2, 30), (31, 16, 3, 4),
 ])
 def test_random_codes_bit_exact(lbm, f, n, B, steps):
     # codes over the whole range (P scaled so sums wander but also saturate),

@@ -175,7 +175,8 @@ def _slice_props(w, u):
 
 
 @pytest.mark.parametrize("name,B,S,m", [("d3_single", 1, 1, 200), ("d3_single", 5, 3, 4),
-                                        ("d9_batch", 37, 2, 3), ("d9_batch", 300, 1, 5)])
+                                        ("d9_batch", 37, 2, 3), ("d9_batch", 300, 1, 5),
+                                        ("d9_batch", 1, 2, 50), ("d9_batch", 4, 1, 7), ("d9_batch", 5, 1, 3)])
 def test_propagate_fp64_resident(lbm, dev, name, B, S, m):
     w = make_workload(name, B=B)
     u = np.linspace(-0.1, 0.1, S)
@@ -190,8 +191,10 @@ def test_propagate_fp64_resident(lbm, dev, name, B, S, m):
         assert _relf(Rg[b], ref[b]) <= 1e-12
 
 
-@pytest.mark.parametrize("B,S,m", [(256, 2, 1), (37, 1, 2)])
+@pytest.mark.parametrize("B,S,m", [(256, 2, 1), (37, 1, 2), (1, 2, 3), (3, 1, 2), (8, 2, 1), (9, 1, 1)])
 def test_propagate_fp64_d27(lbm, dev, B, S, m):
+    """B <= 8 states take the warp-per-row product (k_gemv.cu), more the
+    tiled GEMM."""
     w = make_workload("d27_chain", B=B, nslices=S)
     Ps = _slice_props(w, w["u"])
     ctx = lbm.Context(0, max_n=w["n"], max_batch=B, max_slices=S)
@@ -521,11 +524,12 @@ def test_run_instances_matches_oracle(lbm, dev, prec, tol):
 
 
 @pytest.mark.parametrize("d,B,S,m", [(1, 3, 2, 5), (2, 1, 3, 50), (3, 7, 2, 10), (3, 1, 1, 400), (4, 33, 2, 4),
-                                     (3, 300, 2, 3), (4, 200, 1, 5), (5, 2, 1, 6)])
+                                     (3, 300, 2, 3), (4, 200, 1, 5), (5, 2, 1, 6), (7, 4, 2, 3), (6, 5, 1, 2)])
 def test_propagate_fp64_small_n_forms(lbm, dev, d, B, S, m):
     """n = 1, 4, 9, 16 with at most one state per SM take the four-warp
     latency kernel (one CTA per state), with more states the one-warp-per-
-    state kernel; n = 25 the shared memory kernel."""
+    state kernel; 16 < n <= 81 the warp-per-row product for at most four
+    states, else the shared memory kernel."""
     from workloads.rng import ginibre_states
 
     n = d * d
