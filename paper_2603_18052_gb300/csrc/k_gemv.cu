@@ -7,14 +7,15 @@
 //
 // With few states a tiled GEMM leaves most of the GPU idle (a 64-row tile
 // holds one state; n = 729 gives 12 CTAs), and FP64 runs at 1/64 of the FP32
-// rate, so the work has to reach every SM sub-partition.  One warp owns one
-// output row i for all B states: its lanes stride over j, so each load of
-// A's row is coalesced (the transpose of the paper's gather, Algorithm
-// alg:gpu), A[i][j] is read once for all B states, and the states (B x n,
-// at most 94 KB) stay in L1 and L2.  The lane sums meet in a butterfly of
-// shuffles that leaves the same bits in every lane; lane b writes state b.
-// n = 729 gives 729 warps, about five per SM.  The result does not depend
-// on the launch configuration.
+// rate, so the work has to reach every SM sub-partition.  A warp owns one
+// output row i (or, for n > 256, half of it) for all B states: its lanes
+// stride over j, so each load of A's row is coalesced (the transpose of the
+// paper's gather, Algorithm alg:gpu), A[i][j] is read once for all B states,
+// and the states (B x n, at most 94 KB) stay in L1 and L2.  The lane sums
+// meet in a butterfly of shuffles that leaves the same bits in every lane;
+// lane b writes state b.  n = 729 gives 1458 half-row warps over the 608
+// sub-partitions.  The summation order is fixed, so the result is the same
+// on every run.
 #include "lb_internal.cuh"
 
 namespace lb {
@@ -23,31 +24,38 @@ namespace {
 constexpr int kGemvWarps = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
-// U row loads of A per lane are issued before their products: with about
-// five warps per SM nothing else hides the latency of a load from L2 or HBM.
-template <int BB, int U>
+// Row i is split into H contiguous parts, one warp each (H = 2 for long
+// rows: 2n parts over the 608 sub-partitions balance better than n rows);
+// the parts of a row sit in one CTA and meet in shared memory, part 0 adding
+// the others in order.  U row loads of A per lane are issued before their
+// products: with a few warps per SM nothing else hides the latency of a load
+// from L2 or HBM.
+template <int BB, int U, int H>
 __global__ void __launch_bounds__(kGemvWarps * 32)
     zgemv_f64_kernel(int n, int B, const z64* __restrict__ A, long long lda, const z64* __restrict__ X,
                      long long ldx, z64* __restrict__ V, long long ldv, double alpha, z64* __restrict__ Yacc,
                      long long ldacc) {
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * kGemvWarps + (threadIdx.x >> 5);
-  if (row >= n) return;
+  __shared__ double red[kGemvWarps][2 * BB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = blockIdx.x * (kGemvWarps / H) + w / H, part = w % H;
+  const bool rowok = row < n;  // no early return: the parts meet at a barrier
+  const int seg = (n + H - 1) / H;
+  const int jb = part * seg, je = min(n, jb + seg);
   double ar[BB], ai[BB];
 #pragma unroll
   for (int b = 0; b < BB; b++) ar[b] = ai[b] = 0.0;
-  const z64* a = A + (long long)row * lda;
-  for (int j0 = lane; j0 < n; j0 += 32 * U) {
+  const z64* a = A + (long long)(rowok ? row : 0) * lda;
+  for (int j0 = jb + lane; rowok && j0 < je; j0 += 32 * U) {
     z64 p[U];
 #pragma unroll
     for (int k = 0; k < U; k++) {
       const int j = j0 + 32 * k;
-      p[k] = j < n ? a[j] : make_double2(0.0, 0.0);
+      p[k] = j < je ? a[j] : make_double2(0.0, 0.0);
     }
 #pragma unroll
     for (int k = 0; k < U; k++) {
       const int j = j0 + 32 * k;
-      if (j < n) {
+      if (j < je) {
 #pragma unroll
         for (int b = 0; b < BB; b++) {
           if (b < B) {
@@ -71,9 +79,28 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
       }
     }
   }
+  if (H > 1) {
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < BB; b++) {
+        red[w][2 * b] = ar[b];
+        red[w][2 * b + 1] = ai[b];
+      }
+    }
+    __syncthreads();
+    if (part == 0) {
+#pragma unroll
+      for (int b = 0; b < BB; b++) {
+        for (int h = 1; h < H; h++) {
+          ar[b] += red[w + h][2 * b];
+          ai[b] += red[w + h][2 * b + 1];
+        }
+      }
+    }
+  }
 #pragma unroll
   for (int b = 0; b < BB; b++) {
-    if (b < B && lane == b) {
+    if (rowok && part == 0 && b < B && lane == b) {
       V[b * ldv + row] = make_double2(alpha * ar[b], alpha * ai[b]);
       if (Yacc != nullptr) {
         z64* y = Yacc + b * ldacc + row;
@@ -89,17 +116,29 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
 cudaError_t launch_zgemv_f64(int n, int B, const z64* A, long long lda, const z64* X, long long ldx, z64* V,
                              long long ldv, double alpha, z64* Yacc, long long ldacc, cudaStream_t st) {
   if (B < 1 || B > kGemvMaxB || n < 1) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((n + kGemvWarps - 1) / kGemvWarps);
   const int threads = kGemvWarps * 32;
   count_launch();
-  if (B == 1)
-    zgemv_f64_kernel<1, 8><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
-  else if (B == 2)
-    zgemv_f64_kernel<2, 8><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
-  else if (B <= 4)
-    zgemv_f64_kernel<4, 4><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
-  else
-    zgemv_f64_kernel<8, 4><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+  if (n > 256) {  // two warps per row
+    const unsigned grid = (unsigned)((n + kGemvWarps / 2 - 1) / (kGemvWarps / 2));
+    if (B == 1)
+      zgemv_f64_kernel<1, 12, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else if (B == 2)
+      zgemv_f64_kernel<2, 12, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else if (B <= 4)
+      zgemv_f64_kernel<4, 4, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else
+      zgemv_f64_kernel<8, 4, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+  } else {
+    const unsigned grid = (unsigned)((n + kGemvWarps - 1) / kGemvWarps);
+    if (B == 1)
+      zgemv_f64_kernel<1, 8, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else if (B == 2)
+      zgemv_f64_kernel<2, 8, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else if (B <= 4)
+      zgemv_f64_kernel<4, 4, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else
+      zgemv_f64_kernel<8, 4, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+  }
   return cudaGetLastError();
 }
 
