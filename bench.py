@@ -323,14 +323,15 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     w = make_workload("d9_batch")
     _, _, P = props(w)
     N, B, n = w["steps_per_slice"], w["B"], w["n"]
-    for prec, renorm in (("fp64", False), ("fp32", True)):
+    for prec, renorm in (("fp64", False), ("fp32", True), ("bf16x3", True)):
         R = dput(w["states"])
         ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N, prec=prec, renorm_trace=renorm))
         fl = B * N * accounting.state_step_flops(n) / (ms / 1e3)
-        peak = FP64_PEAK if prec == "fp64" else FP32_PEAK
+        peak = {"fp64": FP64_PEAK, "fp32": FP32_PEAK, "bf16x3": BF16_PEAK / 5}[prec]
         out["d9_batch_" + prec] = {"workload": "d=9, 1024 states, 1000 steps, %s" % prec, "ms": ms,
                                    "state_steps_per_s": B * N / (ms / 1e3),
-                                   "roofline": {"bound": "alu", "achieved": fl / 1e12, "peak": peak / 1e12,
+                                   "roofline": {"bound": "tensor" if prec == "bf16x3" else "alu",
+                                                "achieved": fl / 1e12, "peak": peak / 1e12,
                                                 "unit": "TFLOP/s", "frac": fl / peak}}
     # one GRAPE landscape point at d = 9
     m = transmon_chain(2)
