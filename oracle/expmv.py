@@ -85,10 +85,17 @@ def expmv_chain(L_base, L_drv, u, dt, X):
     """The states through the control slices: X <- exp((L_base + u_s L_drv)
     dt) X for s = 0, 1, ..., with one (m, s) for the whole call, chosen from
     the largest ||(L_base + u_s L_drv) dt||_1.  Returns (X, (m, s))."""
-    As = [(np.asarray(L_base) + us * np.asarray(L_drv)) * dt for us in u]
-    a = max(onenorm(A) for A in As) if As else 0.0
+    L_base = np.asarray(L_base)
+    L_drv = np.asarray(L_drv)
+
+    def gen(us):
+        return (L_base + us * L_drv) * dt
+
+    # two passes (norms, then the products) so that only one generator is
+    # held at a time
+    a = max((onenorm(gen(us)) for us in u), default=0.0)
     ms = parameters(a)
     Y = np.array(X, dtype=np.complex128, copy=True)
-    for A in As:
-        Y = expmv(A, Y, ms)
+    for us in u:
+        Y = expmv(gen(us), Y, ms)
     return Y, ms

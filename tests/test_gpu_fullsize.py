@@ -1,0 +1,74 @@
+"""The d = 27 chain at full size, in the launch configuration the bench
+times (200 slices of 729 x 729 propagators, 256 states, one step per slice):
+sampled propagators against the oracle's Pade route, sampled final states
+against the oracle's Taylor route carried through all 200 slices (it needs
+no dense propagator, so it finishes in seconds), and properties of every
+state (trace and Hermiticity) in each of the three forms."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import expmv as E
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SAMPLED_SLICES = (0, 117, 199)
+SAMPLED_STATES = (0, 255)
+# per form: propagator relative Frobenius error, final-state absolute
+# Frobenius error per state (200 steps; the stated 1000-step bounds are
+# 1e-5 for FP32 and 1e-4 for split-BF16), trace and Hermiticity error
+TOL = {"fp64": (1e-12, 1e-12, 1e-12, 1e-12), "fp32": (1e-6, 1e-5, 1e-6, 1e-5),
+       "bf16x3": (1e-6, 1e-4, 1e-6, 1e-4)}
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_2603_18052_gb300 import _build, lb
+
+    _build.build()
+    assert torch.cuda.is_available()
+    w = make_workload("d27_chain")
+    assert (w["n"], w["nslices"], w["B"], w["steps_per_slice"]) == (729, 200, 256, 1)
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    P_ref = {s: O.expm_pade13(O.slice_generator(Lb, Ld, w["u"][s]) * w["dt"]) for s in SAMPLED_SLICES}
+    X_ref, _ = E.expmv_chain(Lb, Ld, w["u"], w["dt"], w["states"][list(SAMPLED_STATES)])
+    ctx = lb.Context(0, max_n=729, max_batch=256, max_slices=200)
+    yield lb, w, P_ref, X_ref, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "fp64"])
+def test_full_chain(full, prec):
+    lb, w, P_ref, X_ref, ctx = full
+    dev = torch.device("cuda:0")
+    n, S, d = w["n"], w["nslices"], w["d"]
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    # the bench's step: assemble both generators, build 200 propagators,
+    # propagate 256 states through them (trace renormalised in the
+    # reduced forms)
+    Lbd = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    Ldd = torch.empty_like(Lbd)
+    lb.lb_assemble(ctx, put(w["H0"]), put(w["jumps"]), Lbd)
+    lb.lb_assemble(ctx, put(w["X"]), None, Ldd)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lb.lb_expm_pade(ctx, Lbd, Ldd, put(w["u"]), w["dt"], P, prec=prec)
+    R = put(w["states"])
+    lb.lb_propagate_batch(ctx, P, R, steps_per_slice=1, prec=prec, renorm_trace=prec != "fp64")
+    lb.lb_sync_status(ctx)
+    tp, tx, tt, th = TOL[prec]
+    for s, ref in P_ref.items():
+        got = P[s].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tp, (prec, s)
+    Rg = R.cpu().numpy()
+    for k, q in enumerate(SAMPLED_STATES):
+        assert np.linalg.norm(Rg[q] - X_ref[k]) <= tx, (prec, q, np.linalg.norm(Rg[q] - X_ref[k]))
+    rho = Rg.reshape(-1, d, d)
+    tr = np.trace(rho, axis1=1, axis2=2)
+    assert np.max(np.abs(tr - 1.0)) <= tt, prec
+    herm = np.linalg.norm(rho - np.conj(np.transpose(rho, (0, 2, 1))), axis=(1, 2))
+    assert np.max(herm) <= th, prec
