@@ -539,9 +539,14 @@ def gpu_timing_models(lb, dev, stream):
     probes = timing.Probes(launch_us=launch, launch_sync_us=launch_sync, lat_h2d_us=lat_h2d, lat_d2h_us=lat_d2h,
                            h2d_gbs=h2d, d2h_gbs=d2h, stream_gbs=max(reads["stream_8p3MB"], reads["stream_64MiB"]),
                            alloc_calls=4, alloc_us_each=3.0)
+    # the allocation term measured (a cudaMalloc + cudaFree pair of the d = 27
+    # propagator's size), beside the paper's stated 3 us per call
+    alloc_pair_us = med(lb.lb_probe_alloc(16 * 729 * 729, 10) for _ in range(5))
+    probes_measured_alloc = timing.Probes(**{**probes.__dict__, "alloc_calls": 2, "alloc_us_each": alloc_pair_us})
     out = {"probes": {"launch_us": launch, "launch_sync_us": launch_sync, "copy_latency_h2d_us": lat_h2d,
                       "copy_latency_d2h_us": lat_d2h, "h2d_gbs": h2d, "d2h_gbs": d2h, **{k + "_gbs": v for k, v in reads.items()},
-                      "alloc": "4 calls (2 cudaMalloc + 2 cudaFree) at the paper's stated 3 us each"},
+                      "alloc": "4 calls (2 cudaMalloc + 2 cudaFree) at the paper's stated 3 us each",
+                      "alloc_pair_measured_us": alloc_pair_us},
            "rows": []}
     ctx = lb.Context(dev.index or 0, max_n=729, max_batch=128, max_slices=1)
     for nq in (1, 2, 3):
@@ -586,6 +591,9 @@ def gpu_timing_models(lb, dev, stream):
             for name, f in timing.MODELS:
                 ideal = f(n, b, probes)
                 row[name] = {"idealized_ns": ideal, "measured_ns": meas[name], "ratio": meas[name] / ideal}
+            ideal = timing.cost_host(n, b, probes_measured_alloc)
+            row["host"]["idealized_measured_alloc_ns"] = ideal
+            row["host"]["ratio_measured_alloc"] = meas["host"] / ideal
             out["rows"].append(row)
     lb.lb_sync_status(ctx)
     ctx.close()

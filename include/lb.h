@@ -476,6 +476,14 @@ lb_status lb_probe_copy(void* host, void* device, long long bytes, int to_device
                         void* stream);
 
 /*
+ * lb_probe_alloc -- host time of one cudaMalloc of `bytes` bytes followed
+ * by its cudaFree on the CURRENT device, in microseconds, averaged over
+ * `reps` >= 1 pairs (the allocation term of Eq. 9).  Synchronises the
+ * device first.  LB_ENOMEM if an allocation fails.
+ */
+lb_status lb_probe_alloc(long long bytes, int reps, double* us_out);
+
+/*
  * lb_probe_read -- one read pass over `count` complex128 values of `buf`
  * (device): n = 0 is a coalesced stream (consecutive threads read
  * consecutive values); n >= 1 is the stride-n gather of Algorithm alg:gpu

@@ -40,9 +40,21 @@ template <> struct Fx<31> {
 __device__ __forceinline__ short2 make_pair_code(short r, short i) { return make_short2(r, i); }
 __device__ __forceinline__ int2 make_pair_code(int r, int i) { return make_int2(r, i); }
 
-// Exact product of two codes, widened to the accumulator type.
-__device__ __forceinline__ long long prod(short a, short b) { return (long long)((int)a * (int)b); }
-__device__ __forceinline__ __int128 prod(int a, int b) { return (__int128)((long long)a * (long long)b); }
+// acc + a * b exactly, a and b codes: for Q1.15 a 32 x 32 -> 64-bit
+// multiply-add (the negated code -a of a subtracted term still fits 32 bits);
+// for Q1.31 a 64-bit product added into 128 bits.
+__device__ __forceinline__ long long mac(long long acc, short a, short b) {
+  return acc + (long long)(int)a * (long long)(int)b;
+}
+__device__ __forceinline__ long long mac_neg(long long acc, short a, short b) {
+  return acc + (long long)(-(int)a) * (long long)(int)b;
+}
+__device__ __forceinline__ __int128 mac(__int128 acc, int a, int b) {
+  return acc + (__int128)((long long)a * (long long)b);
+}
+__device__ __forceinline__ __int128 mac_neg(__int128 acc, int a, int b) {
+  return acc - (__int128)((long long)a * (long long)b);
+}
 
 // sat(floor(acc / 2^F)): the arithmetic right shift of a signed integer
 // rounds towards minus infinity.
@@ -82,8 +94,8 @@ __global__ void __launch_bounds__(1024) fixed_chain_kernel(int n, int nsteps, in
       acc ar = 0, ai = 0;
       for (int j = 0; j < n; j++) {
         const pair a = prow[j], v = x[j];
-        ar += prod(a.x, v.x) - prod(a.y, v.y);
-        ai += prod(a.x, v.y) + prod(a.y, v.x);
+        ar = mac_neg(mac(ar, a.x, v.x), a.y, v.y);
+        ai = mac(mac(ai, a.x, v.y), a.y, v.x);
       }
       nxt[u] = make_pair_code(floor_sat<F>(ar), floor_sat<F>(ai));
     }

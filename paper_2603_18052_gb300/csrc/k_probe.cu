@@ -14,6 +14,8 @@
 // The probes: an empty kernel launched back to back (launch cost) or with a
 // synchronise after each (launch + sync), synchronous copies of a given size
 // in either direction (latency and asymptotic bandwidth of the host link),
+// one cudaMalloc + cudaFree pair of a given size (the allocation term of
+// Eq. 9, which the paper states rather than measures),
 // and two read kernels over a device buffer, a coalesced stream and the
 // stride-n gather of Algorithm alg:gpu (consecutive threads read consecutive
 // rows of n complex values, so at each inner index the warp's addresses are
@@ -110,6 +112,25 @@ extern "C" lb_status lb_probe_copy(void* host, void* device, long long bytes, in
     if (cudaMemcpyAsync(to_device ? device : host, to_device ? host : device, (size_t)bytes, k, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return LB_ECUDA;
+  }
+  *us_out = (now_us() - t0) / reps;
+  return LB_OK;
+}
+
+extern "C" lb_status lb_probe_alloc(long long bytes, int reps, double* us_out) {
+  if (bytes < 1 || reps < 1 || us_out == nullptr) return LB_EINVAL;
+  int dev = 0, sms = 0;
+  lb_status s = current_device_sm103(&dev, &sms);
+  if (s != LB_OK) return s;
+  if (cudaDeviceSynchronize() != cudaSuccess) return LB_ECUDA;
+  const double t0 = now_us();
+  for (int r = 0; r < reps; r++) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return LB_ENOMEM;
+    }
+    if (cudaFree(p) != cudaSuccess) return LB_ECUDA;
   }
   *us_out = (now_us() - t0) / reps;
   return LB_OK;

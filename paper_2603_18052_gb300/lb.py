@@ -64,6 +64,7 @@ EXPORTED = (
     "lb_probe_launch",
     "lb_probe_copy",
     "lb_probe_read",
+    "lb_probe_alloc",
 )
 
 
@@ -167,6 +168,8 @@ def lib():
     L.lb_probe_launch.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), vp]
     L.lb_probe_copy.restype = i32
     L.lb_probe_copy.argtypes = [vp, vp, ll, i32, i32, ctypes.POINTER(ctypes.c_double), vp]
+    L.lb_probe_alloc.restype = i32
+    L.lb_probe_alloc.argtypes = [ll, i32, ctypes.POINTER(ctypes.c_double)]
     L.lb_probe_read.restype = i32
     L.lb_probe_read.argtypes = [vp, ll, i32, vp, vp]
     del ip, dp
@@ -485,6 +488,13 @@ def lb_probe_copy(host, device, to_device, reps=20, stream=None):
     us = ctypes.c_double(0.0)
     _check(lib().lb_probe_copy(ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(device.data_ptr()), nb,
                                int(bool(to_device)), int(reps), ctypes.byref(us), _stream(stream)), "lb_probe_copy")
+    return us.value
+
+
+def lb_probe_alloc(nbytes, reps=20):
+    """Host microseconds per cudaMalloc + cudaFree pair of nbytes bytes."""
+    us = ctypes.c_double(0.0)
+    _check(lib().lb_probe_alloc(int(nbytes), int(reps), ctypes.byref(us)), "lb_probe_alloc")
     return us.value
 
 

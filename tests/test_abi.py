@@ -62,6 +62,7 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_fixed_dequantize(7, 4, vp(8), vp(8), None) == 1
     assert L.lb_probe_read(None, 16, 0, vp(8), None) == 1
     assert L.lb_probe_launch(0, 0, None, None) == 1
+    assert L.lb_probe_alloc(0, 1, None) == 1
     assert L.lb_probe_copy(None, vp(8), 16, 1, 1, None, None) == 1
     assert L.lb_destroy(None) == 0
 

@@ -72,3 +72,48 @@ def test_full_chain(full, prec):
     assert np.max(np.abs(tr - 1.0)) <= tt, prec
     herm = np.linalg.norm(rho - np.conj(np.transpose(rho, (0, 2, 1))), axis=(1, 2))
     assert np.max(herm) <= th, prec
+
+
+def _props(w, u):
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    return np.array([O.expm_pade13(O.slice_generator(Lb, Ld, us) * w["dt"]) for us in u])
+
+
+def test_d3_single_state_full(full):
+    """d = 3, one state, 10^4 FP64 steps, as timed by the bench."""
+    lb, _, _, _, ctx = full
+    w = make_workload("d3_single")
+    assert (w["n"], w["B"], w["steps_per_slice"]) == (9, 1, 10000)
+    Ps = _props(w, w["u"])
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    R = put(w["states"])
+    lb.lb_propagate_batch(ctx, put(Ps), R, steps_per_slice=w["steps_per_slice"])
+    lb.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, w["states"], w["steps_per_slice"])
+    got = R.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16x3", 1e-4)])
+def test_d9_batch_full(full, prec, tol):
+    """d = 9, 1024 states, 1000 steps, as timed by the bench: every state
+    against the oracle (FP64: relative; reduced forms: the stated absolute
+    Frobenius bound after 1000 steps, trace renormalised)."""
+    lb, _, _, _, _ = full
+    w = make_workload("d9_batch")
+    assert (w["n"], w["B"], w["steps_per_slice"]) == (81, 1024, 1000)
+    Ps = _props(w, w["u"])
+    ctx = lb.Context(0, max_n=81, max_batch=1024, max_slices=1)
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    R = put(w["states"])
+    lb.lb_propagate_batch(ctx, put(Ps), R, steps_per_slice=1000, prec=prec, renorm_trace=prec != "fp64")
+    lb.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, w["states"], 1000)
+    got = R.cpu().numpy()
+    if prec == "fp64":
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+    else:
+        err = np.max(np.linalg.norm(got - ref, axis=1))
+        assert err <= tol, (prec, err)
+    ctx.close()

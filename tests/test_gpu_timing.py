@@ -90,6 +90,7 @@ def test_probes_run(lbm):
     d = torch.empty(1 << 16, dtype=torch.float64, device="cuda")
     assert lbm.lb_probe_copy(h, d, True, 5) > 0.0
     assert lbm.lb_probe_copy(h, d, False, 5) > 0.0
+    assert lbm.lb_probe_alloc(1 << 20, 3) > 0.0
     buf = torch.zeros(1 << 20, dtype=torch.complex128, device="cuda")
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     for n in (0, 729):
