@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(1024) fixed_chain_kernel(int n, int nsteps, in
       const pair* prow = Ps + i * n;
       const pair* x = cur + q * n;
       acc ar = 0, ai = 0;
+#pragma unroll 9  // measured: 20 % faster than no hint for one state at n = 9, 15 % for batches
       for (int j = 0; j < n; j++) {
         const pair a = prow[j], v = x[j];
         ar = mac_neg(mac(ar, a.x, v.x), a.y, v.y);

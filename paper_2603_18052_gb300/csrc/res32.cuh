@@ -34,7 +34,7 @@ __device__ __forceinline__ void res32_step(int n, int nb, const float2* __restri
     for (int r = 0; r < RS; r++) ar[r] = ai[r] = 0.f;
     const float2* drow = D + i * n;
     const float2* xq = X + q0 * n;
-#pragma unroll 3
+#pragma unroll 9  // measured at n = 81: 10 % faster than 3; 27 is slower
     for (int j = 0; j < n; j++) {
       const float2 a = drow[j];
 #pragma unroll
