@@ -319,6 +319,13 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N))
     out["d3_single"] = {"workload": "d=3, 1 state, 10^4 chained FP64 steps", "ns_per_step": 1e6 * ms / N,
                         "state_steps_per_s": N / (ms / 1e3), "paper_context_ns_per_step": 309.5}
+    # the same chain on the density matrix's 9 real coordinates (FP64)
+    R = dput(w["states"])
+    ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N, prec="fp64_hermitian"))
+    out["d3_single_hermitian"] = {"workload": "d=3, 1 state, 10^4 chained FP64 steps on the real coordinates "
+                                              "of the density matrix (lb_propagate_batch, fp64_hermitian)",
+                                  "ns_per_step": 1e6 * ms / N, "state_steps_per_s": N / (ms / 1e3),
+                                  "paper_context_ns_per_step": 309.5}
     # d = 9, 1024 states, 1000 steps
     w = make_workload("d9_batch")
     _, _, P = props(w)

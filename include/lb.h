@@ -50,7 +50,10 @@ typedef enum {
 typedef enum {
   LB_FP64 = 0,    /* every product in FP64 */
   LB_FP32 = 1,    /* products in FP32 with FP32 accumulation */
-  LB_BF16X3 = 2   /* products as split-BF16 x3 on the tensor cores, FP32 accumulation */
+  LB_BF16X3 = 2,  /* products as split-BF16 x3 on the tensor cores, FP32 accumulation */
+  LB_FP64_HERMITIAN = 3  /* lb_propagate_batch only: FP64 on the n real coordinates of
+                            Hermitian states (density matrices) with a Hermiticity-
+                            preserving P, as exp(L dt) of any Lindbladian is; see there */
 } lb_precision;
 
 typedef struct lb_ctx lb_ctx;
@@ -193,6 +196,14 @@ lb_status lb_expm_pade(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, con
  *   renorm_trace : if nonzero and prec != LB_FP64, divide every state by
  *            its trace (sum of entries i*d + i) after each step.
  * Limits: n a perfect square, n <= max_n; 1 <= B <= max_batch.
+  *   prec = LB_FP64_HERMITIAN: the states must be Hermitian (each read from
+ *   its diagonal real parts and upper triangle) and P must map Hermitian
+ *   matrices to Hermitian matrices; the step then runs on the n real
+ *   coordinates of each state (n^2 real multiply-adds instead of 4 n^2) and
+ *   the states come back exactly Hermitian.  Same result as LB_FP64 up to
+ *   rounding for such inputs.  Used for n <= 9 (one warp per state, state
+ *   exchanged by shuffles); larger n run the LB_FP64 path.  renorm_trace is
+ *   ignored, as for LB_FP64.
  */
 lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, int steps_per_slice,
                              int B, lb_c64* states, lb_precision prec, int renorm_trace,

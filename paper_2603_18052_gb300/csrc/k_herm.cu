@@ -1,0 +1,198 @@
+// FP64 propagation of density matrices on their real coordinates (the
+// LB_FP64_HERMITIAN form of Algorithm 2, Sec. 3.2).
+//
+// A density matrix is Hermitian, and every propagator exp(L dt) of a
+// Lindbladian maps Hermitian matrices to Hermitian matrices.  A Hermitian
+// d x d matrix is fixed by n = d^2 real numbers, its coordinates
+//   c = ( rho_00, ..., rho_{d-1,d-1},  Re rho_kl, Im rho_kl for k < l ),
+// the pairs (k, l) in row-major order of the upper triangle; on them the
+// step rho <- P rho is the real n x n map
+//   R[a][b] = d(out_a) / d(c_b),
+// with, for an output entry (k, l) and an input coordinate b,
+//   b = rho_ii   :  P[kl][ii]
+//   b = Re rho_ij:  P[kl][ij] + P[kl][ji]
+//   b = Im rho_ij:  i (P[kl][ij] - P[kl][ji])
+// and out_a the real part (diagonal and Re coordinates) or the imaginary
+// part (Im coordinates) of that derivative.  A step then costs n^2 real
+// multiply-adds instead of the 4 n^2 of the complex product: on a part whose
+// FP64 instructions take 64 cycles per warp, that is what matters.  The
+// result equals the complex product for Hermitian inputs up to rounding; the
+// state is read from its diagonal and upper triangle, and written back
+// exactly Hermitian.
+//
+// Latency form (n <= 9, d <= 3): one warp per state.  Output coordinate o is
+// summed by K lanes with C products each (C + ceil(log2 K) dependent FP64
+// instructions, five at n = 9 against six for the complex step), and the new
+// coordinates reach the lanes that need them by warp shuffles, so a step has
+// no shared-memory exchange and no barrier.
+#include "lb_internal.cuh"
+
+namespace lb {
+namespace {
+
+// coordinate a of a d x d Hermitian matrix -> (k, l, part): part 0 = the
+// diagonal entry rho_kk (k = l), 1 = Re rho_kl, 2 = Im rho_kl (k < l)
+__host__ __device__ inline void herm_coord(int a, int d, int* k, int* l, int* part) {
+  if (a < d) {
+    *k = a;
+    *l = a;
+    *part = 0;
+    return;
+  }
+  int q = (a - d) >> 1;
+  *part = 1 + ((a - d) & 1);
+  int r = 0;
+  while (q >= d - 1 - r) {
+    q -= d - 1 - r;
+    r++;
+  }
+  *k = r;
+  *l = r + 1 + q;
+}
+
+__global__ void herm_matrix_kernel(int n, int d, int S, const z64* __restrict__ P, double* __restrict__ R) {
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)S * nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / nn);
+    const int a = (int)((t / n) % n), b = (int)(t % n);
+    int k, l, pa, i, j, pb;
+    herm_coord(a, d, &k, &l, &pa);
+    herm_coord(b, d, &i, &j, &pb);
+    const z64* row = P + s * nn + (long long)(k * d + l) * n;
+    z64 v;
+    if (pb == 0) {
+      v = row[i * d + i];
+    } else {
+      const z64 pij = row[i * d + j], pji = row[j * d + i];
+      v = pb == 1 ? make_double2(pij.x + pji.x, pij.y + pji.y)      // Re rho_ij
+                  : make_double2(-(pij.y - pji.y), pij.x - pji.x);  // Im rho_ij: i (P_ij - P_ji)
+    }
+    R[t] = pa == 2 ? v.y : v.x;
+  }
+}
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+template <int CMAX>
+__global__ void __launch_bounds__(32)
+    prop_herm_lat_kernel(int n, int d, int C, int K, int nslices, const double* __restrict__ R, int steps_per_slice,
+                         z64* __restrict__ states) {
+  __shared__ double cst[32];
+  const int lane = threadIdx.x;
+  const int o = lane / K, p = lane - (lane / K) * K;
+  const bool active = o < n;
+  z64* x = states + (long long)blockIdx.x * n;
+  if (lane < n) {  // the state's real coordinates
+    int k, l, part;
+    herm_coord(lane, d, &k, &l, &part);
+    const z64 v = x[k * d + l];
+    cst[lane] = part == 2 ? v.y : v.x;
+  }
+  __syncwarp();
+  // this lane's C inputs (coordinate indices), their values, the lane holding
+  // each of them after a step
+  int xin[CMAX];
+  double xv[CMAX];
+#pragma unroll
+  for (int c = 0; c < CMAX; c++) {
+    const int j = p * C + c;
+    xin[c] = (active && c < C && j < n) ? j : -1;
+    xv[c] = xin[c] >= 0 ? cst[xin[c]] : 0.0;
+  }
+  const long long nn = (long long)n * n;
+  double out = 0.0;
+  for (int s = 0; s < nslices; s++) {
+    double cf[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; c++) cf[c] = xin[c] >= 0 ? R[s * nn + (long long)o * n + xin[c]] : 0.0;
+    for (int t = 0; t < steps_per_slice; t++) {
+      double acc = cf[0] * xv[0];
+#pragma unroll
+      for (int c = 1; c < CMAX; c++)
+        if (c < C) acc = fma(cf[c], xv[c], acc);
+      // sum over the K lanes of output o; lane o*K ends with it.  For K = 3
+      // both neighbours' sums are fetched at once and added in order
+      // ((a0 + a1) + a2, as the two-level tree does), which takes one shuffle
+      // off the dependent chain
+      if (K == 3) {
+        const double v1 = __shfl_down_sync(kFullMask, acc, 1);
+        const double v2 = __shfl_down_sync(kFullMask, acc, 2);
+        if (p == 0) acc = (acc + v1) + v2;
+      } else {
+        for (int off = 1; off < K; off <<= 1) {
+          const double v = __shfl_down_sync(kFullMask, acc, off);
+          if (p + off < K) acc += v;
+        }
+      }
+      out = acc;
+#pragma unroll
+      for (int c = 0; c < CMAX; c++) {
+        const double v = __shfl_sync(kFullMask, acc, xin[c] >= 0 ? xin[c] * K : 0);
+        if (xin[c] >= 0) xv[c] = v;
+      }
+    }
+  }
+  if ((long long)nslices * steps_per_slice == 0) return;
+  if (active && p == 0) cst[o] = out;
+  __syncwarp();
+  if (lane < n) {  // back to the complex matrix, exactly Hermitian
+    const int r = lane / d, c = lane - (lane / d) * d;
+    z64 v;
+    if (r == c) {
+      v = make_double2(cst[r], 0.0);
+    } else {
+      const int k = r < c ? r : c, l = r < c ? c : r;
+      int q = 0;
+      for (int rr = 0; rr < k; rr++) q += d - 1 - rr;
+      q += l - k - 1;
+      const double re = cst[d + 2 * q], im = cst[d + 2 * q + 1];
+      v = make_double2(re, r < c ? im : -im);
+    }
+    x[lane] = v;
+  }
+}
+
+}  // namespace
+
+// Split of the n real products of an output over K lanes with C each: at
+// most 32 lanes for the n outputs, fewest dependent FP64 instructions
+// (C + ceil(log2 K)), then the fewest lanes.
+bool herm_lat_split(int n, int* C, int* K) {
+  if (n < 1 || n > 9) return false;
+  int best = 1 << 30;
+  for (int k = 1; k * n <= 32; k++) {
+    const int c = (n + k - 1) / k;
+    int lg = 0;
+    while ((1 << lg) < k) lg++;
+    if (c + lg < best) {
+      best = c + lg;
+      *C = c;
+      *K = k;
+    }
+  }
+  return best < (1 << 30);
+}
+
+cudaError_t launch_herm_matrix(int n, int d, int S, const z64* P, double* R, int sm_count, cudaStream_t st) {
+  const long long total = (long long)S * n * n;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)sm_count * 8) blocks = (long long)sm_count * 8;
+  count_launch();
+  herm_matrix_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, S, P, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prop_herm_lat(int n, int d, int nslices, const double* R, int steps_per_slice, int B, z64* X,
+                                 cudaStream_t st) {
+  int C = 0, K = 0;
+  if (!herm_lat_split(n, &C, &K)) return cudaErrorInvalidValue;
+  count_launch();
+  if (C <= 3)
+    prop_herm_lat_kernel<3><<<B, 32, 0, st>>>(n, d, C, K, nslices, R, steps_per_slice, X);
+  else
+    prop_herm_lat_kernel<9><<<B, 32, 0, st>>>(n, d, C, K, nslices, R, steps_per_slice, X);
+  return cudaGetLastError();
+}
+
+}  // namespace lb

@@ -672,7 +672,7 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   int d = 0;
   if (n < 1 || n > c->max_n || !is_square(n, &d)) return LB_EINVAL;
   if (nslices < 0 || steps_per_slice < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
-  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN) return LB_EINVAL;
   if (nslices == 0 || steps_per_slice == 0) return LB_OK;
   DeviceGuard g(c->device);
   return lb::propagate_impl(c, n, nslices, (const z64*)P, steps_per_slice, B, (z64*)states, prec, renorm_trace,
@@ -688,6 +688,20 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   int d = 0;
   is_square(n, &d);
   const long long nn = (long long)n * n;
+  if (prec == LB_FP64_HERMITIAN) {
+    int C = 0, K = 0;
+    if (herm_lat_split(n, &C, &K)) {
+      // real transfer matrices of a chunk of slices in the build scratch
+      double* R = (double*)c->Z1;
+      for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+        const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+        LB_CUDA(launch_herm_matrix(n, d, S, Pz + s0 * nn, R, c->sm_count, st));
+        LB_CUDA(launch_prop_herm_lat(n, d, S, R, steps_per_slice, B, X, st));
+      }
+      return LB_OK;
+    }
+    prec = LB_FP64;  // the complex product is exact for every state
+  }
   if (prec == LB_FP64) {
     const bool gemv = gemv_f64_preferred(n, B);
     if (!gemv && resident_f64_fits(n)) {

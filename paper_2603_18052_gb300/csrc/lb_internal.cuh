@@ -155,6 +155,14 @@ cudaError_t launch_zgemv_f64(int n, int B, const z64* A, long long lda, const z6
 // Whether a B-state FP64 propagation step at size n goes to launch_zgemv_f64.
 bool gemv_f64_preferred(int n, int B);
 
+// Hermitian (real-coordinate) FP64 propagation, k_herm.cu: the lane split of
+// the one-warp latency form (false: n above 9), the real transfer matrices of
+// S propagators (S x n x n doubles), and the propagation of B states.
+bool herm_lat_split(int n, int* C, int* K);
+cudaError_t launch_herm_matrix(int n, int d, int S, const z64* P, double* R, int sm_count, cudaStream_t st);
+cudaError_t launch_prop_herm_lat(int n, int d, int nslices, const double* R, int steps_per_slice, int B, z64* X,
+                                 cudaStream_t st);
+
 // (m, s) of the truncated Taylor series for ||A||_1 = a (k_expmv.cu); false
 // for a non-finite a or more than 65536 sub-steps.
 bool taylor_parameters(double a, int* m_out, int* s_out);

@@ -14,8 +14,8 @@ import torch
 
 from . import _build
 
-LB_FP64, LB_FP32, LB_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3}
+LB_FP64, LB_FP32, LB_BF16X3, LB_FP64_HERMITIAN = 0, 1, 2, 3
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3, "fp64_hermitian": LB_FP64_HERMITIAN}
 
 _STATUS = {
     0: "LB_OK",
