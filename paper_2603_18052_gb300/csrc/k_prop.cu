@@ -248,9 +248,20 @@ __global__ void __launch_bounds__(128)
       for (int k = 0; k < CMAX; k++)
         if (k < C) acc = fma(cf[k], X[cur][xidx[k]], acc);
       // segmented tree over the K lanes of the group; the first lane ends with the sum
-      for (int off = 1; off < K; off <<= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, acc, off);
-        if (part + off < K) acc += v;
+      if (K == 6) {
+        // after the pairwise level the first lane needs the pair sums of
+        // lanes 2 and 4: both are fetched at once, and the additions are the
+        // tree's, ((a0 + a1) + (a2 + a3)) + (a4 + a5)
+        const double v = __shfl_down_sync(0xffffffffu, acc, 1);
+        if (part + 1 < K) acc += v;
+        const double v2 = __shfl_down_sync(0xffffffffu, acc, 2);
+        const double v4 = __shfl_down_sync(0xffffffffu, acc, 4);
+        if (part == 0) acc = (acc + v2) + v4;
+      } else {
+        for (int off = 1; off < K; off <<= 1) {
+          const double v = __shfl_down_sync(0xffffffffu, acc, off);
+          if (part + off < K) acc += v;
+        }
       }
       if (active && part == 0) X[cur ^ 1][o] = acc;
       __syncthreads();
