@@ -330,11 +330,13 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     w = make_workload("d9_batch")
     _, _, P = props(w)
     N, B, n = w["steps_per_slice"], w["B"], w["n"]
-    for prec, renorm in (("fp64", False), ("fp32", True), ("bf16x3", True)):
+    for prec, renorm in (("fp64", False), ("fp32", True), ("bf16x3", True), ("fp64_hermitian", False)):
         R = dput(w["states"])
         ms = time_ms(lambda: lb.lb_propagate_batch(ctx, P, R, steps_per_slice=N, prec=prec, renorm_trace=renorm))
-        fl = B * N * accounting.state_step_flops(n) / (ms / 1e3)
-        peak = {"fp64": FP64_PEAK, "fp32": FP32_PEAK, "bf16x3": BF16_PEAK / 5}[prec]
+        # the Hermitian form does n^2 real multiply-adds per state-step
+        per = 2.0 * n * n if prec == "fp64_hermitian" else accounting.state_step_flops(n)
+        fl = B * N * per / (ms / 1e3)
+        peak = {"fp64": FP64_PEAK, "fp32": FP32_PEAK, "bf16x3": BF16_PEAK / 5, "fp64_hermitian": FP64_PEAK}[prec]
         out["d9_batch_" + prec] = {"workload": "d=9, 1024 states, 1000 steps, %s" % prec, "ms": ms,
                                    "state_steps_per_s": B * N / (ms / 1e3),
                                    "roofline": {"bound": "tensor" if prec == "bf16x3" else "alu",

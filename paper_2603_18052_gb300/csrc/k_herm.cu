@@ -20,12 +20,18 @@
 // state is read from its diagonal and upper triangle, and written back
 // exactly Hermitian.
 //
+// Shared-memory form (9 < n <= 81): R and the CTA's states in shared
+// memory, one thread per output coordinate, like the complex resident form
+// with a third of its FP64 instructions.
+//
 // Latency form (n <= 9, d <= 3): one warp per state.  Output coordinate o is
 // summed by K lanes with C products each (C + ceil(log2 K) dependent FP64
 // instructions, five at n = 9 against six for the complex step), and the new
 // coordinates reach the lanes that need them by warp shuffles, so a step has
 // no shared-memory exchange and no barrier.
 #include "lb_internal.cuh"
+
+#include <algorithm>
 
 namespace lb {
 namespace {
@@ -153,7 +159,90 @@ __global__ void __launch_bounds__(32)
   }
 }
 
+// Shared-memory form (9 < n <= 81): R of the current slice and the CTA's
+// states (real coordinates, ping-pong) in shared memory for the whole
+// chain, one thread per (state, coordinate) output, one barrier per step.
+__global__ void __launch_bounds__(1024)
+    prop_herm_resident_kernel(int n, int d, int nslices, const double* __restrict__ R, int steps_per_slice, int B,
+                              int chunk, z64* __restrict__ states) {
+  extern __shared__ __align__(16) double hsm[];
+  double* Rs = hsm;
+  double* x = Rs + n * n;  // chunk x n
+  double* y = x + chunk * n;
+  const int b0 = blockIdx.x * chunk;
+  if (b0 >= B) return;
+  const int nb = min(chunk, B - b0);
+  const int tid = threadIdx.x, nt = blockDim.x, work = nb * n;
+  const long long nn = (long long)n * n;
+  z64* X = states + (long long)b0 * n;
+  for (int e = tid; e < work; e += nt) {
+    const int q = e / n, a = e - (e / n) * n;
+    int k, l, part;
+    herm_coord(a, d, &k, &l, &part);
+    const z64 v = X[(long long)q * n + k * d + l];
+    x[e] = part == 2 ? v.y : v.x;
+  }
+  for (int s = 0; s < nslices; s++) {
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) Rs[e] = R[s * nn + e];
+    __syncthreads();
+    for (int t = 0; t < steps_per_slice; t++) {
+      for (int e = tid; e < work; e += nt) {
+        const int q = e / n, a = e - (e / n) * n;
+        const double* r = Rs + a * n;
+        const double* xq = x + q * n;
+        double acc = 0.0;
+#pragma unroll 9
+        for (int b = 0; b < n; b++) acc = fma(r[b], xq[b], acc);
+        y[e] = acc;
+      }
+      __syncthreads();
+      double* tmp = x;
+      x = y;
+      y = tmp;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < work; e += nt) {  // back to complex matrices, exactly Hermitian
+    const int q = e / n, m = e - (e / n) * n;
+    const int r = m / d, c = m - (m / d) * d;
+    const double* xq = x + q * n;
+    z64 v;
+    if (r == c) {
+      v = make_double2(xq[r], 0.0);
+    } else {
+      const int k = r < c ? r : c, l = r < c ? c : r;
+      int qq = 0;
+      for (int rr = 0; rr < k; rr++) qq += d - 1 - rr;
+      qq += l - k - 1;
+      const double re = xq[d + 2 * qq], im = xq[d + 2 * qq + 1];
+      v = make_double2(re, r < c ? im : -im);
+    }
+    X[e] = v;
+  }
+}
+
 }  // namespace
+
+size_t herm_resident_smem(int n, int chunk) { return sizeof(double) * ((size_t)n * n + 2ull * chunk * n); }
+
+bool herm_resident_fits(int n) { return n <= 81 && herm_resident_smem(n, 1) <= 227 * 1024; }
+
+cudaError_t launch_prop_herm_resident(int n, int d, int nslices, const double* R, int steps_per_slice, int B,
+                                      z64* X, int sm_count, cudaStream_t st) {
+  int chunk = std::max(1, (B + sm_count - 1) / sm_count);
+  chunk = std::min(chunk, std::max(1, 1024 / n));  // one thread per output
+  while (chunk > 1 && herm_resident_smem(n, chunk) > 227 * 1024) chunk = (chunk + 1) / 2;
+  const size_t smem = herm_resident_smem(n, chunk);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = set_smem_once((const void*)prop_herm_resident_kernel, smem);
+  if (e != cudaSuccess) return e;
+  const int threads = std::min(1024, (chunk * n + 31) / 32 * 32);
+  const int grid = (B + chunk - 1) / chunk;
+  count_launch();
+  prop_herm_resident_kernel<<<grid, threads, smem, st>>>(n, d, nslices, R, steps_per_slice, B, chunk, X);
+  return cudaGetLastError();
+}
 
 // Split of the n real products of an output over K lanes with C each: at
 // most 32 lanes for the n outputs, fewest dependent FP64 instructions

@@ -690,13 +690,17 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   const long long nn = (long long)n * n;
   if (prec == LB_FP64_HERMITIAN) {
     int C = 0, K = 0;
-    if (herm_lat_split(n, &C, &K)) {
+    const bool lat = herm_lat_split(n, &C, &K);
+    if (lat || herm_resident_fits(n)) {
       // real transfer matrices of a chunk of slices in the build scratch
       double* R = (double*)c->Z1;
       for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
         const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
         LB_CUDA(launch_herm_matrix(n, d, S, Pz + s0 * nn, R, c->sm_count, st));
-        LB_CUDA(launch_prop_herm_lat(n, d, S, R, steps_per_slice, B, X, st));
+        if (lat)
+          LB_CUDA(launch_prop_herm_lat(n, d, S, R, steps_per_slice, B, X, st));
+        else
+          LB_CUDA(launch_prop_herm_resident(n, d, S, R, steps_per_slice, B, X, c->sm_count, st));
       }
       return LB_OK;
     }

@@ -162,6 +162,9 @@ bool herm_lat_split(int n, int* C, int* K);
 cudaError_t launch_herm_matrix(int n, int d, int S, const z64* P, double* R, int sm_count, cudaStream_t st);
 cudaError_t launch_prop_herm_lat(int n, int d, int nslices, const double* R, int steps_per_slice, int B, z64* X,
                                  cudaStream_t st);
+bool herm_resident_fits(int n);
+cudaError_t launch_prop_herm_resident(int n, int d, int nslices, const double* R, int steps_per_slice, int B,
+                                      z64* X, int sm_count, cudaStream_t st);
 
 // (m, s) of the truncated Taylor series for ||A||_1 = a (k_expmv.cu); false
 // for a non-finite a or more than 65536 sub-steps.

@@ -1,9 +1,10 @@
 """FP64 propagation of density matrices on their real coordinates
 (lb_propagate_batch with prec LB_FP64_HERMITIAN) against the oracle's
 complex product: within 1e-12 for Hermitian states at n = 1, 4 and 9 (the
-one-warp form), the d = 3 single-state workload over 10^4 steps, outputs
-exactly Hermitian, the upper-triangle reading of the input, and the complex
-FP64 path above n = 9."""
+one-warp form) and 16 <= n <= 81 (the shared-memory form), the d = 3
+single-state workload over 10^4 steps, outputs exactly Hermitian, the
+upper-triangle reading of the input, and the complex FP64 path above
+n = 81."""
 
 import numpy as np
 import pytest
@@ -97,8 +98,28 @@ def test_reads_the_upper_triangle(lbm):
     ctx.close()
 
 
-@pytest.mark.parametrize("d,B", [(4, 3), (5, 2), (9, 6)])
-def test_above_n9_runs_the_complex_path(lbm, d, B):
+@pytest.mark.parametrize("d,B,S,m", [(4, 3, 2, 5), (5, 2, 1, 20), (9, 1, 2, 3), (9, 200, 1, 50), (9, 1030, 1, 4)])
+def test_shared_memory_form_matches_oracle(lbm, d, B, S, m):
+    """9 < n <= 81: R and the states in shared memory, one thread per
+    output coordinate; B = 1030 leaves a ragged last CTA."""
+    n = d * d
+    Ps = _props(d, S, scale=0.05)
+    X0 = ginibre_states(700 + d + B, d, B)
+    ctx = lbm.Context(0, max_n=n, max_batch=B, max_slices=S)
+    R = torch.from_numpy(X0).cuda()
+    lbm.lb_propagate_batch(ctx, torch.from_numpy(Ps).cuda(), R, steps_per_slice=m, prec="fp64_hermitian")
+    lbm.lb_sync_status(ctx)
+    ref = O.propagate_chain(Ps, X0, m)
+    got = R.cpu().numpy()
+    for b in range(B):
+        assert _rel(got[b], ref[b]) <= 1e-12, b
+    rho = got.reshape(B, d, d)
+    assert np.array_equal(rho, np.conj(np.transpose(rho, (0, 2, 1))))
+    ctx.close()
+
+
+@pytest.mark.parametrize("d,B", [(11, 3)])
+def test_above_n81_runs_the_complex_path(lbm, d, B):
     n = d * d
     Ps = _props(d, 2, scale=0.05)
     X0 = ginibre_states(600 + d, d, B)
