@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the split-BF16 form and print its launch count per step (for a "
                          "profiler's launch list); no other forms, end-to-end run or side workloads")
+    ap.add_argument("--trials", default=None, metavar="PATH",
+                    help="also write the raw timings (every timed step of each form, every trial of the "
+                         "GPU timing models) to PATH as JSON lines")
     return ap.parse_args()
 
 
@@ -590,16 +593,18 @@ def gpu_timing_models(lb, dev, stream):
                     fn()
                 return (time.perf_counter_ns() - t0) / reps / b
 
-            meas = {}
+            meas, trials = {}, {}
             for name, trial in (("kernel", kernel_trial),
                                 ("resident", lambda: host_trial(lambda: lb.lb_propagate_resident(ctx, P[0], Xh))),
                                 ("host", lambda: host_trial(lambda: lb.lb_propagate_host(ctx, P_host, Xh)))):
                 trial()  # warm-up: one untimed trial of 50 calls
-                meas[name] = med(trial() for _ in range(5))
+                trials[name] = [trial() for _ in range(5)]
+                meas[name] = med(trials[name])
             row = {"d": m.d, "batch": b}
             for name, f in timing.MODELS:
                 ideal = f(n, b, probes)
-                row[name] = {"idealized_ns": ideal, "measured_ns": meas[name], "ratio": meas[name] / ideal}
+                row[name] = {"idealized_ns": ideal, "measured_ns": meas[name], "ratio": meas[name] / ideal,
+                             "trials_ns": trials[name]}
             ideal = timing.cost_host(n, b, probes_measured_alloc)
             row["host"]["idealized_measured_alloc_ns"] = ideal
             row["host"]["ratio_measured_alloc"] = meas["host"] / ideal
@@ -785,7 +790,7 @@ def run_ours(args):
             ph["propagate_ms"] += ev[2].elapsed_time(ev[3]) / args.steps
         stages = {k: v / max(chunks, 1) for k, v in stages.items()}
         return dict(ms_per_step=total_ms / args.steps, phases=ph, build_stages_ms=stages,
-                    launches=n1 - n0, clocks=clocks)
+                    launches=n1 - n0, clocks=clocks, step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs])
 
     t_tune = time.perf_counter()
     tuned = lb.lb_autotune(ctx, n, S, B)
@@ -892,6 +897,16 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(w, 6)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if rank == 0 and args.trials:  # raw timings, one JSON object per line
+        with open(args.trials, "a") as fh:
+            for f, r in res.items():
+                for k, v in enumerate(r["step_ms"]):
+                    fh.write(json.dumps({"kind": "d27_chain_step", "form": f, "step": k, "ms": v}) + "\n")
+            for row in line["other_workloads"]["gpu_timing_models"]["rows"]:
+                for name in ("kernel", "resident", "host"):
+                    for i, v in enumerate(row[name]["trials_ns"]):
+                        fh.write(json.dumps({"kind": "gpu_timing_model", "model": name, "d": row["d"],
+                                             "batch": row["batch"], "trial": i, "ns_per_state_step": v}) + "\n")
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
