@@ -163,13 +163,35 @@ def oracle_sample(w, nslices):
     return t1 - t0
 
 
+def oracle_single_thread(nslices=1):
+    """The same oracle sample in a child process whose BLAS and OpenMP pools
+    have one thread (their size is fixed when numpy loads).  Seconds, or None
+    if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import json, bench; from workloads import make_workload; "
+            "print(json.dumps(bench.oracle_sample(make_workload(bench.WORKLOAD), %d)))" % nslices)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=900)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def cpu_baseline(w, nslices):
     t = oracle_sample(w, nslices)
     B = w["B"]
-    return {"value": B * nslices / t, "unit": "state-steps/s", "builds_per_s": nslices / t, "cores": host_cores(),
-            "kind": "oracle",
-            "sample": "%d of the 200 slices: %d Pade-13 builds (729x729, numpy FP64 with its BLAS threads) and "
-                      "%d states x %d steps, %.1f s" % (nslices, nslices, B, nslices, t)}
+    out = {"value": B * nslices / t, "unit": "state-steps/s", "builds_per_s": nslices / t, "cores": host_cores(),
+           "kind": "oracle",
+           "sample": "%d of the 200 slices: %d Pade-13 builds (729x729, numpy FP64 with its BLAS threads) and "
+                     "%d states x %d steps, %.1f s" % (nslices, nslices, B, nslices, t)}
+    t1 = oracle_single_thread(1)
+    if t1 is not None:
+        out["single_thread"] = {"value": B / t1, "unit": "state-steps/s", "builds_per_s": 1.0 / t1, "cores": 1,
+                                "sample": "1 slice (one build and 256 state-steps), one BLAS / OpenMP thread, "
+                                          "%.1f s" % t1}
+    return out
 
 
 def run_reference(args):
