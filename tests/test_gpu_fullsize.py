@@ -72,6 +72,10 @@ def test_full_chain(full, prec):
     assert np.max(np.abs(tr - 1.0)) <= tt, prec
     herm = np.linalg.norm(rho - np.conj(np.transpose(rho, (0, 2, 1))), axis=(1, 2))
     assert np.max(herm) <= th, prec
+    # positivity: the Hermitian part of every state has no eigenvalue below
+    # the form's bound (the FP64 bound is the stated -1e-12)
+    lam = np.linalg.eigvalsh(0.5 * (rho + np.conj(np.transpose(rho, (0, 2, 1)))))
+    assert np.min(lam) >= -tx, (prec, np.min(lam))
 
 
 def _props(w, u):
