@@ -445,11 +445,13 @@ def action_of_exponential(lb, dev, stream, S=10):
         t_taylor = timed(taylor)
         t_dense = timed(dense)
         t_mixed = timed(dense_mixed)
+        t_herm = timed(lambda: lb.lb_expmv(ctx, Lb, Ld, u, w["dt"], X, hermitian=True)) if B <= 8 else None
         m, s = ms_pair[0]
         fl = S * s * m * 8.0 * n * n * B
         out["B%d" % B] = {"taylor_ms_per_slice": t_taylor / S, "dense_fp64_ms_per_slice": t_dense / S,
                           "dense_bf16x3_ms_per_slice": t_mixed / S,
                           "speedup_vs_dense_fp64": t_dense / t_taylor, "speedup_vs_dense_bf16x3": t_mixed / t_taylor,
+                          "taylor_hermitian_ms_per_slice": t_herm / S if t_herm else None,
                           "m": m, "s": s,
                           "taylor_roofline": {"bound": "alu", "achieved": fl / (t_taylor / 1e3) / 1e12,
                                               "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",

@@ -391,6 +391,20 @@ lb_status lb_selftest_wait_timeout(lb_ctx* ctx, long long cycles, void* stream);
 lb_status lb_expmv(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv, const double* u,
                    double dt, int B, lb_c64* states, int* ms_out, void* stream);
 
+/*
+ * lb_expmv_hermitian -- lb_expmv for density matrices: the same route on the
+ * n = d^2 real coordinates of Hermitian states (diagonal, Re and Im of the
+ * upper triangle), where each generator A_s is a real n x n matrix G_s and
+ * every Taylor term a real product (a quarter of the FP64 multiply-adds).
+ * (m, s_sub) follows lb_expmv's rule with a = the largest ||G_s||_1.
+ *   Same arguments as lb_expmv; n must be a square.  The states must be
+ *   Hermitian (each is read from its diagonal real parts and upper
+ *   triangle) and come back exactly Hermitian.  B <= 8 (the few-state
+ *   product); larger B run lb_expmv.  Same errors as lb_expmv.
+ */
+lb_status lb_expmv_hermitian(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                             const double* u, double dt, int B, lb_c64* states, int* ms_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Fixed-point propagation: the element-serial Q1.15 step of the FPGA design
  * (Algorithm alg:fpga, Sec. 3.5; formats Sec. 2.2) and its Q1.31 variant

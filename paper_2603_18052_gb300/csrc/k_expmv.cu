@@ -217,3 +217,100 @@ extern "C" lb_status lb_expmv(lb_ctx* c, int n, int nslices, const lb_c64* Lbase
   }
   return LB_OK;
 }
+
+// The same route on the real coordinates of Hermitian states (density
+// matrices): the generators A_s map Hermitian matrices to Hermitian
+// matrices, so on the n real coordinates of a state (diagonal, Re and Im of
+// the upper triangle) each A_s is a real n x n matrix G_s (herm_matrix_kernel
+// forms it from A_s as it does for a propagator), and every Taylor term is a
+// real matrix-vector product: a quarter of the FP64 multiply-adds.  (m, s)
+// follows the same rule with a = the largest ||G_s||_1.  Few states only
+// (B <= 8, the few-state product); larger batches take lb_expmv.
+extern "C" lb_status lb_expmv_hermitian(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const lb_c64* Ldrv,
+                                        const double* u, double dt, int B, lb_c64* states, int* ms_out,
+                                        void* stream) {
+  if (c == nullptr || Lbase == nullptr || states == nullptr) return LB_EINVAL;
+  if (n < 1 || n > c->max_n || nslices < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
+  int d = 1;
+  while (d * d < n) d++;
+  if (d * d != n) return LB_EINVAL;
+  if (Ldrv != nullptr && u == nullptr) return LB_EINVAL;
+  if (!std::isfinite(dt)) return LB_EINVAL;
+  if (nslices == 0) return LB_OK;
+  if (B > kGemvMaxB) return lb_expmv(c, n, nslices, Lbase, Ldrv, u, dt, B, states, ms_out, stream);
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return LB_EUNSUPPORTED;  // the parameter choice reads the norm back to the host
+  const long long nn = (long long)n * n;
+  const z64* Lb = (const z64*)Lbase;
+  const z64* Ld = (const z64*)Ldrv;
+  auto grid_for = [&](int S) {
+    const long long gr = (long long)S * ((n + kGenCols - 1) / kGenCols);
+    const long long cap = (long long)c->sm_count * 8;
+    return (unsigned)(gr < 1 ? 1 : (gr > cap ? cap : gr));
+  };
+  double* G = (double*)c->Z1;  // S real n x n generators
+  auto form = [&](int s0, int S, unsigned long long* nb) -> lb_status {
+    count_launch();
+    expmv_generators_kernel<<<grid_for(S), kGenCols * kGenRowGroups, 0, st>>>(
+        n, S, Ld != nullptr ? Lb : Lb + s0 * nn, Ld, u != nullptr ? u + s0 : nullptr, dt, c->A, nullptr);
+    LB_CUDA(cudaGetLastError());
+    LB_CUDA(launch_herm_matrix(n, d, S, c->A, G, c->sm_count, st));
+    if (nb != nullptr) LB_CUDA(launch_real_colnorm(n, S, G, nb, c->sm_count, st));
+    return LB_OK;
+  };
+
+  // 1. the largest ||G_s||_1 over the call, then (m, s)
+  unsigned long long* nb = c->norm_bits;
+  LB_CUDA(cudaMemsetAsync(nb, 0, sizeof(unsigned long long), st));
+  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+    lb_status r = form(s0, S, nb);
+    if (r != LB_OK) return r;
+  }
+  unsigned long long bits = 0;
+  LB_CUDA(cudaMemcpyAsync(&bits, nb, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  LB_CUDA(cudaStreamSynchronize(st));
+  double a = 0.0;
+  std::memcpy(&a, &bits, sizeof(a));
+  if (!std::isfinite(a)) return LB_ENONFINITE;
+  int m = 0, s = 0;
+  if (!taylor_parameters(a, &m, &s)) return LB_EUNSUPPORTED;
+  if (ms_out != nullptr) {
+    ms_out[0] = m;
+    ms_out[1] = s;
+  }
+
+  // 2. the states' coordinates through the slices
+  z64* X = (z64*)states;
+  double* Y = (double*)c->Xh;
+  double* Va = (double*)c->Rtmp;  // two B x n term buffers
+  double* Vb = Va + (size_t)B * n;
+  LB_CUDA(launch_herm_coords_in(n, d, B, X, Y, c->sm_count, st));
+  const bool one_chunk = nslices <= c->max_slices;
+  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+    if (!one_chunk) {
+      lb_status r = form(s0, S, nullptr);
+      if (r != LB_OK) return r;
+    }
+    for (int sl = 0; sl < S; sl++) {
+      const double* Gs = G + sl * nn;
+      for (int sub = 0; sub < s; sub++) {
+        LB_CUDA(cudaMemcpyAsync(Va, Y, sizeof(double) * (size_t)B * n, cudaMemcpyDeviceToDevice, st));
+        double* prev = Va;
+        double* next = Vb;
+        for (int k = 1; k <= m; k++) {
+          LB_CUDA(launch_dgemv_f64(n, B, Gs, n, prev, n, next, n, 1.0 / ((double)s * (double)k), Y, n, st));
+          double* tmp = prev;
+          prev = next;
+          next = tmp;
+        }
+      }
+    }
+  }
+  LB_CUDA(launch_herm_coords_out(n, d, B, Y, X, c->sm_count, st));
+  return LB_OK;
+}

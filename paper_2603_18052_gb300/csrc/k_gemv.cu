@@ -111,7 +111,89 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
   }
 }
 
+// The same product for real matrices and states (the Hermitian coordinates
+// of density matrices): V[b][i] = alpha sum_j A[i][j] X[b][j], Yacc += it.
+template <int BB, int U, int H>
+__global__ void __launch_bounds__(kGemvWarps * 32)
+    dgemv_f64_kernel(int n, int B, const double* __restrict__ A, long long lda, const double* __restrict__ X,
+                     long long ldx, double* __restrict__ V, long long ldv, double alpha, double* __restrict__ Yacc,
+                     long long ldacc) {
+  __shared__ double red[kGemvWarps][BB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = blockIdx.x * (kGemvWarps / H) + w / H, part = w % H;
+  const bool rowok = row < n;  // no early return: the parts meet at a barrier
+  const int seg = (n + H - 1) / H;
+  const int jb = part * seg, je = min(n, jb + seg);
+  double acc[BB];
+#pragma unroll
+  for (int b = 0; b < BB; b++) acc[b] = 0.0;
+  const double* a = A + (long long)(rowok ? row : 0) * lda;
+  for (int j0 = jb + lane; rowok && j0 < je; j0 += 32 * U) {
+    double p[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const int j = j0 + 32 * k;
+      p[k] = j < je ? a[j] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const int j = j0 + 32 * k;
+      if (j < je) {
+#pragma unroll
+        for (int b = 0; b < BB; b++)
+          if (b < B) acc[b] = fma(p[k], X[b * ldx + j], acc[b]);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int b = 0; b < BB; b++)
+      if (b < B) acc[b] += __shfl_xor_sync(kFull, acc[b], off);
+  }
+  if (H > 1) {
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < BB; b++) red[w][b] = acc[b];
+    }
+    __syncthreads();
+    if (part == 0) {
+#pragma unroll
+      for (int b = 0; b < BB; b++)
+        for (int h = 1; h < H; h++) acc[b] += red[w + h][b];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BB; b++) {
+    if (rowok && part == 0 && b < B && lane == b) {
+      V[b * ldv + row] = alpha * acc[b];
+      if (Yacc != nullptr) Yacc[b * ldacc + row] = fma(alpha, acc[b], Yacc[b * ldacc + row]);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_dgemv_f64(int n, int B, const double* A, long long lda, const double* X, long long ldx, double* V,
+                             long long ldv, double alpha, double* Yacc, long long ldacc, cudaStream_t st) {
+  if (B < 1 || B > kGemvMaxB || n < 1) return cudaErrorInvalidValue;
+  const int threads = kGemvWarps * 32;
+  count_launch();
+  if (n > 256) {  // two warps per row
+    const unsigned grid = (unsigned)((n + kGemvWarps / 2 - 1) / (kGemvWarps / 2));
+    if (B <= 2)
+      dgemv_f64_kernel<2, 12, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else
+      dgemv_f64_kernel<8, 4, 2><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+  } else {
+    const unsigned grid = (unsigned)((n + kGemvWarps - 1) / kGemvWarps);
+    if (B <= 2)
+      dgemv_f64_kernel<2, 8, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+    else
+      dgemv_f64_kernel<8, 4, 1><<<grid, threads, 0, st>>>(n, B, A, lda, X, ldx, V, ldv, alpha, Yacc, ldacc);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_zgemv_f64(int n, int B, const z64* A, long long lda, const z64* X, long long ldx, z64* V,
                              long long ldv, double alpha, z64* Yacc, long long ldacc, cudaStream_t st) {

@@ -36,26 +36,6 @@
 namespace lb {
 namespace {
 
-// coordinate a of a d x d Hermitian matrix -> (k, l, part): part 0 = the
-// diagonal entry rho_kk (k = l), 1 = Re rho_kl, 2 = Im rho_kl (k < l)
-__host__ __device__ inline void herm_coord(int a, int d, int* k, int* l, int* part) {
-  if (a < d) {
-    *k = a;
-    *l = a;
-    *part = 0;
-    return;
-  }
-  int q = (a - d) >> 1;
-  *part = 1 + ((a - d) & 1);
-  int r = 0;
-  while (q >= d - 1 - r) {
-    q -= d - 1 - r;
-    r++;
-  }
-  *k = r;
-  *l = r + 1 + q;
-}
-
 __global__ void herm_matrix_kernel(int n, int d, int S, const z64* __restrict__ P, double* __restrict__ R) {
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)S * nn;
@@ -222,7 +202,87 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// states (complex B x n) <-> real coordinates (B x n)
+__global__ void herm_coords_in_kernel(int n, int d, long long total, const z64* __restrict__ X, double* __restrict__ Y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n;
+    const int a = (int)(t - b * n);
+    int k, l, part;
+    herm_coord(a, d, &k, &l, &part);
+    const z64 v = X[b * n + k * d + l];
+    Y[t] = part == 2 ? v.y : v.x;
+  }
+}
+
+__global__ void herm_coords_out_kernel(int n, int d, long long total, const double* __restrict__ Y, z64* __restrict__ X) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n;
+    const int m = (int)(t - b * n), r = m / d, c = m - (m / d) * d;
+    const double* y = Y + b * n;
+    if (r == c) {
+      X[t] = make_double2(y[r], 0.0);
+    } else {
+      const int idx = herm_pair_coord(r < c ? r : c, r < c ? c : r, d);
+      X[t] = make_double2(y[idx], r < c ? y[idx + 1] : -y[idx + 1]);
+    }
+  }
+}
+
+// Largest column abs-sum of S real n x n matrices into *norm_bits (bits of a
+// non-negative double, integer max); 8 columns x 32 row groups per CTA, the
+// partial sums of a column added in a fixed order.
+__global__ void __launch_bounds__(256) real_colnorm_kernel(int n, int S, const double* __restrict__ G,
+                                                          unsigned long long* __restrict__ norm_bits) {
+  __shared__ double part[32][8];
+  const long long nn = (long long)n * n;
+  const int c = threadIdx.x % 8, rg = threadIdx.x / 8;
+  const int cblocks = (n + 7) / 8;
+  for (long long t = blockIdx.x; t < (long long)S * cblocks; t += gridDim.x) {
+    const int s = (int)(t / cblocks), j = (int)(t - (t / cblocks) * cblocks) * 8 + c;
+    double sum = 0.0;
+    if (j < n)
+      for (int i = rg; i < n; i += 32) sum += fabs(G[s * nn + (long long)i * n + j]);
+    part[rg][c] = sum;
+    __syncthreads();
+    if (rg == 0 && j < n) {
+      double col = 0.0;
+      for (int r = 0; r < 32; r++) col += part[r][c];
+      if (!(col == col)) col = INFINITY;
+      atomicMax(norm_bits, (unsigned long long)__double_as_longlong(col));
+    }
+    __syncthreads();
+  }
+}
+
+unsigned grid_cap(long long work, int per_block, int sm_count) {
+  long long g = (work + per_block - 1) / per_block;
+  const long long cap = (long long)sm_count * 8;
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
 }  // namespace
+
+cudaError_t launch_herm_coords_in(int n, int d, int B, const z64* X, double* Y, int sm_count, cudaStream_t st) {
+  const long long total = (long long)B * n;
+  count_launch();
+  herm_coords_in_kernel<<<grid_cap(total, 256, sm_count), 256, 0, st>>>(n, d, total, X, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_herm_coords_out(int n, int d, int B, const double* Y, z64* X, int sm_count, cudaStream_t st) {
+  const long long total = (long long)B * n;
+  count_launch();
+  herm_coords_out_kernel<<<grid_cap(total, 256, sm_count), 256, 0, st>>>(n, d, total, Y, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_colnorm(int n, int S, const double* G, unsigned long long* norm_bits, int sm_count,
+                                cudaStream_t st) {
+  const long long tiles = (long long)S * ((n + 7) / 8);
+  count_launch();
+  real_colnorm_kernel<<<grid_cap(tiles, 1, sm_count), 256, 0, st>>>(n, S, G, norm_bits);
+  return cudaGetLastError();
+}
 
 size_t herm_resident_smem(int n, int chunk) { return sizeof(double) * ((size_t)n * n + 2ull * chunk * n); }
 

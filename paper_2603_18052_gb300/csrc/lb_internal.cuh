@@ -152,8 +152,39 @@ cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaSt
 constexpr int kGemvMaxB = 8;
 cudaError_t launch_zgemv_f64(int n, int B, const z64* A, long long lda, const z64* X, long long ldx, z64* V,
                              long long ldv, double alpha, z64* Yacc, long long ldacc, cudaStream_t st);
+// The real counterpart (real A and states), B <= kGemvMaxB.
+cudaError_t launch_dgemv_f64(int n, int B, const double* A, long long lda, const double* X, long long ldx, double* V,
+                             long long ldv, double alpha, double* Yacc, long long ldacc, cudaStream_t st);
 // Whether a B-state FP64 propagation step at size n goes to launch_zgemv_f64.
 bool gemv_f64_preferred(int n, int B);
+
+// Real coordinates of a d x d Hermitian matrix (n = d^2 of them): the
+// diagonal entries, then Re and Im of the upper-triangle entries (k < l) in
+// row-major order.  Coordinate a -> (k, l, part): part 0 = rho_kk (k = l),
+// 1 = Re rho_kl, 2 = Im rho_kl.
+__host__ __device__ inline void herm_coord(int a, int d, int* k, int* l, int* part) {
+  if (a < d) {
+    *k = a;
+    *l = a;
+    *part = 0;
+    return;
+  }
+  int q = (a - d) >> 1;
+  *part = 1 + ((a - d) & 1);
+  int r = 0;
+  while (q >= d - 1 - r) {
+    q -= d - 1 - r;
+    r++;
+  }
+  *k = r;
+  *l = r + 1 + q;
+}
+// Index of the Re coordinate of the upper-triangle entry (k, l), k < l.
+__host__ __device__ inline int herm_pair_coord(int k, int l, int d) {
+  int q = 0;
+  for (int r = 0; r < k; r++) q += d - 1 - r;
+  return d + 2 * (q + l - k - 1);
+}
 
 // Hermitian (real-coordinate) FP64 propagation, k_herm.cu: the lane split of
 // the one-warp latency form (false: n above 9), the real transfer matrices of
@@ -163,6 +194,10 @@ cudaError_t launch_herm_matrix(int n, int d, int S, const z64* P, double* R, int
 cudaError_t launch_prop_herm_lat(int n, int d, int nslices, const double* R, int steps_per_slice, int B, z64* X,
                                  cudaStream_t st);
 bool herm_resident_fits(int n);
+cudaError_t launch_herm_coords_in(int n, int d, int B, const z64* X, double* Y, int sm_count, cudaStream_t st);
+cudaError_t launch_herm_coords_out(int n, int d, int B, const double* Y, z64* X, int sm_count, cudaStream_t st);
+cudaError_t launch_real_colnorm(int n, int S, const double* G, unsigned long long* norm_bits, int sm_count,
+                                cudaStream_t st);
 cudaError_t launch_prop_herm_resident(int n, int d, int nslices, const double* R, int steps_per_slice, int B,
                                       z64* X, int sm_count, cudaStream_t st);
 

@@ -56,6 +56,7 @@ EXPORTED = (
     "lb_expm_frechet",
     "lb_control_update",
     "lb_expmv",
+    "lb_expmv_hermitian",
     "lb_fixed_quantize",
     "lb_fixed_dequantize",
     "lb_propagate_fixed",
@@ -154,6 +155,8 @@ def lib():
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
     L.lb_expmv.restype = i32
     L.lb_expmv.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, ctypes.POINTER(ctypes.c_int), vp]
+    L.lb_expmv_hermitian.restype = i32
+    L.lb_expmv_hermitian.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.lb_fixed_quantize.restype = i32
     L.lb_fixed_quantize.argtypes = [i32, ll, vp, vp, vp]
     L.lb_fixed_dequantize.restype = i32
@@ -376,11 +379,13 @@ def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
            "lb_propagate_batch_static")
 
 
-def lb_expmv(ctx, Lbase, Ldrv, u, dt, states, stream=None):
+def lb_expmv(ctx, Lbase, Ldrv, u, dt, states, stream=None, hermitian=False):
     """states (B x n, overwritten) <- exp((Lbase + u[s] Ldrv) dt) states for
     every slice s, without forming the propagators (truncated Taylor series
     with scaling, FP64).  Ldrv None: Lbase is (S, n, n) and u is ignored.
-    Returns the Taylor degree m and the number of sub-steps per slice."""
+    hermitian: the states are density matrices, propagated on their real
+    coordinates (lb_expmv_hermitian).  Returns the Taylor degree m and the
+    number of sub-steps per slice."""
     c128 = torch.complex128
     B, n = states.shape
     if Ldrv is None:
@@ -393,8 +398,9 @@ def lb_expmv(ctx, Lbase, Ldrv, u, dt, states, stream=None):
         ldp = _ptr(Ldrv, c128, "Ldrv", (n, n))
         up = _ptr(u, torch.float64, "u", (S,))
     ms = (ctypes.c_int * 2)()
-    _check(lib().lb_expmv(ctx.handle, n, S, lbp, ldp, up, float(dt), B, _ptr(states, c128, "states", (B, n)), ms,
-                          _stream(stream)), "lb_expmv")
+    fn = lib().lb_expmv_hermitian if hermitian else lib().lb_expmv
+    _check(fn(ctx.handle, n, S, lbp, ldp, up, float(dt), B, _ptr(states, c128, "states", (B, n)), ms, _stream(stream)),
+           "lb_expmv_hermitian" if hermitian else "lb_expmv")
     return int(ms[0]), int(ms[1])
 
 

@@ -53,6 +53,7 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_control_update(9, 1, None, vp(8), vp(8), vp(8), None) == 1
     assert L.lb_propagate_resident(None, 9, vp(8), 1, vp(8), None) == 1
     assert L.lb_expmv(None, 9, 1, vp(8), None, None, 0.1, 1, vp(8), None, None) == 1
+    assert L.lb_expmv_hermitian(None, 9, 1, vp(8), None, None, 0.1, 1, vp(8), None, None) == 1
     assert L.lb_propagate_host(None, 9, vp(8), 1, vp(8), None) == 1
     assert L.lb_propagate_fixed(15, 9, None, 1, 1, vp(8), None) == 1
     assert L.lb_propagate_fixed(16, 9, vp(8), 1, 1, vp(8), None) == 1  # only Q1.15 and Q1.31

@@ -97,3 +97,44 @@ def test_expmv_errors(lbm):
     assert lbm.lb_expmv(ctx, torch.zeros((1, 9, 9), dtype=torch.complex128, device="cuda"), None, None, 0.1, X) == (1, 1)
     assert torch.equal(X.cpu(), torch.ones((2, 9), dtype=torch.complex128))
     ctx.close()
+
+
+@pytest.mark.parametrize("model,B,S", [("chain1", 1, 3), ("chain1", 8, 2), ("chain2", 3, 2), ("paper3", 2, 4),
+                                       ("chain3", 1, 2), ("chain3", 5, 1)])
+def test_expmv_hermitian_matches_oracle(lbm, model, B, S):
+    """Density matrices on their real coordinates: within 1e-12 of the
+    oracle's complex Taylor route, exactly Hermitian."""
+    if model.startswith("chain"):
+        m = transmon_chain(int(model[-1]))
+    else:
+        m = paper_grape_model(int(model[-1]))
+    Lb, Ld = O.lindbladian(m.H0, m.jumps), O.drive_generator(m.X)
+    n = Lb.shape[0]
+    u = np.linspace(-0.08, 0.1, S)
+    X = ginibre_states(90 + B, m.d, B)
+    ctx = lbm.Context(0, max_n=n, max_batch=max(B, 8), max_slices=S)
+    Xd = _t(X)
+    lbm.lb_expmv(ctx, _t(Lb), _t(Ld), _t(u), m.dt, Xd, hermitian=True)
+    lbm.lb_sync_status(ctx)
+    ref, _ = E.expmv_chain(Lb, Ld, u, m.dt, X)
+    got = Xd.cpu().numpy()
+    assert _rel(got, ref) <= 1e-12
+    rho = got.reshape(B, m.d, m.d)
+    assert np.array_equal(rho, np.conj(np.transpose(rho, (0, 2, 1))))
+    ctx.close()
+
+
+def test_expmv_hermitian_large_batch_is_the_complex_route(lbm):
+    m = transmon_chain(1)
+    Lb, Ld = O.lindbladian(m.H0, m.jumps), O.drive_generator(m.X)
+    u = np.array([0.03, -0.05])
+    X = ginibre_states(123, m.d, 12)
+    ctx = lbm.Context(0, max_n=9, max_batch=12, max_slices=2)
+    outs = []
+    for herm in (False, True):
+        Xd = _t(X)
+        lbm.lb_expmv(ctx, _t(Lb), _t(Ld), _t(u), m.dt, Xd, hermitian=herm)
+        lbm.lb_sync_status(ctx)
+        outs.append(Xd.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    ctx.close()
