@@ -15,6 +15,15 @@ state-steps per step, builds included); `builds_per_s` is propagator builds/s
 (200 per step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--headline-only] [--trials PATH]
+
+Besides the headline, the line carries the roofline of the dominant stage
+(the FP64 LU + solve), each form's propagation roofline, the end-to-end run
+with host buffers, the clocks seen during the timed region, the CPU oracle
+baseline, and "other_workloads": the d = 3 and d = 9 configurations, a
+GRAPE landscape point, the mixed-size batch, the reuse of P for nearby
+controls, the action of the exponential, the fixed-point step, and the GPU
+timing models of the paper's Sec. 3.4.
 """
 
 import argparse
