@@ -1,0 +1,33 @@
+"""The bench's command-line contract (no GPU needed): with no flags it runs
+one GPU with at least three warm-up steps, the reference arm is selectable,
+and the reported metric is the one the workload is quoted on."""
+
+import sys
+
+import pytest
+
+
+@pytest.fixture()
+def bench(monkeypatch):
+    import bench as b
+
+    return b
+
+
+def test_defaults(bench, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "ours"
+    assert a.trials is None and not a.headline_only
+
+
+def test_reference_arm_and_flags(bench, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "4",
+                                      "--warmup", "3", "--trials", "t.jsonl"])
+    a = bench.parse()
+    assert (a.impl, a.gpus, a.steps, a.warmup, a.trials) == ("reference", 2, 4, 3, "t.jsonl")
+
+
+def test_metric_names_the_workload(bench):
+    assert "state-steps/s" in bench.METRIC and "d=27" in bench.METRIC
+    assert bench.WORKLOAD == "d27_chain"
