@@ -201,9 +201,10 @@ lb_status lb_expm_pade(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, con
  *   matrices to Hermitian matrices; the step then runs on the n real
  *   coordinates of each state (n^2 real multiply-adds instead of 4 n^2) and
  *   the states come back exactly Hermitian.  Same result as LB_FP64 up to
- *   rounding for such inputs.  Used for n <= 9 (one warp per state, state
- *   exchanged by shuffles); larger n run the LB_FP64 path.  renorm_trace is
- *   ignored, as for LB_FP64.
+ *   rounding for such inputs.  n <= 9: one warp per state, the state
+ *   exchanged by shuffles; 9 < n <= 81: the real transfer matrix and each
+ *   CTA's states in shared memory; larger n run the LB_FP64 path.
+ *   renorm_trace is ignored, as for LB_FP64.
  */
 lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, int steps_per_slice,
                              int B, lb_c64* states, lb_precision prec, int renorm_trace,
