@@ -5,25 +5,34 @@ One step = one pass of the whole hot path over the d = 27 three-transmon
 chain workload: assemble the base and drive Lindbladians (729 x 729), build
 the 200 slice propagators by Pade-13 scaling and squaring with the FP64 LU
 solve, and propagate 256 density matrices through the 200-slice chain (one
-step per slice).  Three forms are timed: split-BF16 on the tcgen05 tensor
-cores, FP32, and all-FP64 (the LU factorisation and solve are FP64 in every
-form).  The faster of the two mixed forms is the headline; all three are
-reported under "forms".
+step per slice).  Five forms are timed:
 
-Prints ONE JSON line.  `value` is state-steps/s of the whole step (256 x 200
-state-steps per step, builds included); `builds_per_s` is propagator builds/s
-(200 per step).
+  fp64_hermitian  (headline) all FP64, every product, the LU and the solve on
+                  the real coordinates of Hermitian matrices (real n x n
+                  matrices: one FMA per multiply-add instead of four)
+  fp64            all FP64 on the complex superoperators, as the paper states
+                  the method
+  fp32_hermitian  real-coordinate build with FP32 Pade products and near-I
+                  squarings, FP64 LU and solve; FP32 propagation
+  bf16x3          split-BF16 on the tcgen05 tensor cores, FP64 LU and solve
+  fp32            FP32 products and propagation, FP64 LU and solve
+
+Prints ONE JSON line.  `value` is state-steps/s of the whole step in the
+FP64 form (256 x 200 state-steps per step, builds included); `builds_per_s`
+is propagator builds/s (200 per step); `mixed` holds the fastest
+reduced-precision form with every mixed form's numbers and errors.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--headline-only] [--trials PATH]
 
-Besides the headline, the line carries the roofline of the dominant stage
-(the FP64 LU + solve), each form's propagation roofline, the end-to-end run
-with host buffers, the clocks seen during the timed region, the CPU oracle
-baseline, and "other_workloads": the d = 3 and d = 9 configurations, a
-GRAPE landscape point, the mixed-size batch, the reuse of P for nearby
-controls, the action of the exponential, the fixed-point step, and the GPU
-timing models of the paper's Sec. 3.4.
+Besides the headline, the line carries the arithmetic peaks measured by the
+library's probes in this run, the roofline of the dominant kernel, each
+form's propagation roofline and its accuracy against the oracle, the
+end-to-end run with host buffers, the clocks seen during the timed region,
+the CPU oracle baseline, and "other_workloads": the d = 3 and d = 9
+configurations, a GRAPE landscape point, the mixed-size batch, the reuse of
+P for nearby controls, the action of the exponential, the fixed-point step,
+and the GPU timing models of the paper's Sec. 3.4.
 """
 
 import argparse
@@ -45,6 +54,7 @@ WORKLOAD_DESC = ("d=27 three-transmon chain: 200 control slices u~U(-0.1,0.1), 2
                  "729x729 complex propagators (FP64 LU), B=256 Ginibre states propagated through the "
                  "200-slice chain, 1 step per slice")
 SM_COUNT = 152
+# fallbacks from unit counts, used only where a probe of this run failed
 FP64_PEAK = SM_COUNT * 2 * 2 * 2.07e9   # 2 DFMA/clk/SM x 2 FLOP x 2.07 GHz max clock = 1.259 TFLOP/s
 FP32_PEAK = SM_COUNT * 128 * 2 * 2.07e9  # 128 FFMA/clk/SM = 80.5 TFLOP/s
 INT_MAC_PEAK = SM_COUNT * 64 * 2.07e9    # 32-bit integer multiply-add: 64 lanes/clk/SM = 20.1 T/s
@@ -58,15 +68,29 @@ def _measured_bf16_peak():
 
 
 BF16_PEAK = _measured_bf16_peak()
-DTYPES = {"bf16x3": "bf16 split (x3 build, x5 propagation) + f64", "fp32": "f32+f64", "fp64": "f64"}
+# form: (build precision, propagation precision, per-step trace renormalisation)
+FORMS = {"fp64_hermitian": ("fp64_hermitian", "fp64_hermitian", False), "fp64": ("fp64", "fp64", False),
+         "fp32_hermitian": ("fp32_hermitian", "fp32", True), "bf16x3": ("bf16x3", "bf16x3", True),
+         "fp32": ("fp32", "fp32", True)}
+HEADLINE = "fp64_hermitian"
+MIXED_FORMS = ("fp32_hermitian", "bf16x3", "fp32")
+DTYPES = {"fp64_hermitian": "f64", "fp64": "f64", "fp32_hermitian": "f32+f64",
+          "bf16x3": "bf16 split (x3 build, x5 propagation) + f64", "fp32": "f32+f64"}
 PRECISION_DESC = {
+    "fp64_hermitian": "all FP64 on the real coordinates of Hermitian matrices (diagonal, Re and Im of the upper "
+                      "triangle): the real form of each slice generator, Pade products, LU, solve and squarings "
+                      "as real 729x729 FP64 matrices, P rebuilt from its real form; propagation on the states' "
+                      "real coordinates; same result as the complex FP64 form to 1e-12",
+    "fp64": "all FP64 on the complex superoperators",
+    "fp32_hermitian": "real-coordinate build with FP32 Pade products (FP32 accumulation) and FP32 D-form "
+                      "squarings, FP64 generator, norm, LU and solve; FP32 propagation (D = P - I, per-step trace "
+                      "renormalisation)",
     "bf16x3": "split-BF16 on tcgen05 tensor cores with FP32 accumulation: Pade products as hi+lo pieces "
               "(3 products per real product), propagation with D = P - I in three pieces and states in two "
               "(5 products), FP32 states and per-step trace renormalisation; FP32 D-form squarings; FP64 norm, "
               "LU and solve",
     "fp32": "FP32 Pade products, FP32 D-form squarings and FP32 propagation (D = P - I, per-step trace "
             "renormalisation); FP64 norm, LU and solve",
-    "fp64": "all FP64",
 }
 
 
@@ -220,7 +244,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "builds_per_s": per_step / t,
-            "config": {"workload": WORKLOAD_DESC, "sample_per_step": "%d slices (builds + 256-state steps)" % per_step},
+            "config": {"workload": WORKLOAD_DESC,
+                       "sample_per_step": "%d of the 200 slices per step (%d Pade builds + 256 states x %d steps); the "
+                                          "rate is per state-step and per build, so a full 200-slice step would take "
+                                          "%d times as long (linear extrapolation, not run)" % (per_step, per_step,
+                                                                                                per_step,
+                                                                                                200 // per_step)},
             "cpu_baseline": {"value": v, "unit": "state-steps/s", "cores": host_cores(), "kind": "oracle",
                              "sample": "%d slices per step of the d=27 chain, FP64 numpy oracle" % per_step},
             "e2e": {"value": v, "unit": "state-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -307,7 +336,7 @@ def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
     return res
 
 
-def other_workloads(lb, accounting, dev, stream, reps=5):
+def other_workloads(lb, accounting, dev, stream, reps=5, fp64_peak=None, fp32_peak=None, bf16_peak=None):
     """Secondary measurements on the smaller workloads: the d = 3 single-state
     chain (latency per step), the d = 9 batch (FP64 and FP32 throughput), and
     one d = 9 GRAPE landscape point (100 slices, 4 basis operators)."""
@@ -370,7 +399,8 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
         # the Hermitian form does n^2 real multiply-adds per state-step
         per = 2.0 * n * n if prec == "fp64_hermitian" else accounting.state_step_flops(n)
         fl = B * N * per / (ms / 1e3)
-        peak = {"fp64": FP64_PEAK, "fp32": FP32_PEAK, "bf16x3": BF16_PEAK / 5, "fp64_hermitian": FP64_PEAK}[prec]
+        p64, p32, p16 = fp64_peak or FP64_PEAK, fp32_peak or FP32_PEAK, bf16_peak or BF16_PEAK
+        peak = {"fp64": p64, "fp32": p32, "bf16x3": p16 / 5, "fp64_hermitian": p64}[prec]
         out["d9_batch_" + prec] = {"workload": "d=9, 1024 states, 1000 steps, %s" % prec, "ms": ms,
                                    "state_steps_per_s": B * N / (ms / 1e3),
                                    "roofline": {"bound": "tensor" if prec == "bf16x3" else "alu",
@@ -396,12 +426,12 @@ def other_workloads(lb, accounting, dev, stream, reps=5):
     out["paper_model_build_breakdown"] = paper_model_breakdown(lb, dev)
     out["control_reuse_d9"] = control_reuse(lb, dev, time_ms)
     out["fixed_point"] = fixed_point(lb, dev, stream)
-    out["action_of_exponential_d27"] = action_of_exponential(lb, dev, stream)
+    out["action_of_exponential_d27"] = action_of_exponential(lb, dev, stream, fp64_peak=fp64_peak)
     out["gpu_timing_models"] = gpu_timing_models(lb, dev, stream)
     return out
 
 
-def action_of_exponential(lb, dev, stream, S=10):
+def action_of_exponential(lb, dev, stream, S=10, fp64_peak=None):
     """The d = 27 chain's first S slices without dense propagators
     (lb_expmv: truncated Taylor series, FP64, no LU) against the dense route
     (Pade build of the S propagators, then the chain) in FP64 and in the
@@ -463,8 +493,8 @@ def action_of_exponential(lb, dev, stream, S=10):
                           "taylor_hermitian_ms_per_slice": t_herm / S if t_herm else None,
                           "m": m, "s": s,
                           "taylor_roofline": {"bound": "alu", "achieved": fl / (t_taylor / 1e3) / 1e12,
-                                              "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
-                                              "frac": fl / (t_taylor / 1e3) / FP64_PEAK}}
+                                              "peak": (fp64_peak or FP64_PEAK) / 1e12, "unit": "TFLOP/s",
+                                              "frac": fl / (t_taylor / 1e3) / (fp64_peak or FP64_PEAK)}}
     lb.lb_sync_status(ctx)
     ctx.close()
     return out
@@ -736,6 +766,47 @@ def paper_model_breakdown(lb, dev):
         ctx.close()
     return res
 
+def measure_peaks(lb):
+    """The arithmetic ceilings of this GPU, measured by the library's probes
+    in this run (TFLOP/s; None where a probe failed)."""
+    out = {}
+    for key, fn in (("dfma", lb.lb_probe_dfma), ("ffma", lb.lb_probe_ffma), ("dmma", lb.lb_probe_dmma),
+                    ("bf16_tc", lb.lb_probe_bf16_tc)):
+        try:
+            out[key] = fn()
+        except lb.LBError as e:
+            out[key] = None
+            out[key + "_error"] = e.name
+    return out
+
+
+def form_errors(lb, ctx, w, dev, forms, run_form):
+    """Accuracy of each form in this run: two sampled propagators against the
+    oracle's Pade build and two sampled final states against the oracle's
+    Taylor route through all 200 slices (no dense propagator needed)."""
+    import numpy as np
+
+    import oracle as O
+    from oracle import expmv as E
+
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    sl, st = (0, w["nslices"] - 1), (0, w["B"] - 1)
+    P_ref = {s: O.expm_pade13(O.slice_generator(Lb, Ld, w["u"][s]) * w["dt"]) for s in sl}
+    X_ref, _ = E.expmv_chain(Lb, Ld, w["u"], w["dt"], w["states"][list(st)])
+    out = {}
+    for f in forms:
+        P, R, s_out = run_form(f)
+        eP = max(float(np.linalg.norm(P[s].cpu().numpy() - P_ref[s]) / np.linalg.norm(P_ref[s])) for s in sl)
+        Rg = R.cpu().numpy()
+        eX = max(float(np.linalg.norm(Rg[q] - X_ref[k])) for k, q in enumerate(st))
+        out[f] = {"propagator_rel_frobenius": eP, "state_abs_frobenius_after_200_steps": eX,
+                  "sampled": "propagators of slices %d and %d vs the oracle's Pade build; final states %d and %d vs "
+                             "the oracle's Taylor route through the 200 slices" % (sl + st),
+                  "squarings": sorted(set(int(x) for x in s_out))}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -756,6 +827,14 @@ def run_ours(args):
     w = make_workload(WORKLOAD)
     n, S, B, dt = w["n"], w["nslices"], w["B"], w["dt"]
     ctx = lb.Context(local, max_n=n, max_batch=B, max_slices=S)
+    stream = torch.cuda.current_stream()
+    peaks = measure_peaks(lb)
+    fp64_peak = 1e12 * peaks["dfma"] if peaks.get("dfma") else FP64_PEAK
+    fp32_peak = 1e12 * peaks["ffma"] if peaks.get("ffma") else FP32_PEAK
+    bf16_peak = 1e12 * peaks["bf16_tc"] if peaks.get("bf16_tc") else BF16_PEAK
+    peak_src = {"fp64": "lb_probe_dfma, this run" if peaks.get("dfma") else "derived from unit counts",
+                "fp32": "lb_probe_ffma, this run" if peaks.get("ffma") else "derived from unit counts",
+                "bf16": "lb_probe_bf16_tc, this run" if peaks.get("bf16_tc") else "MEASURED_PEAKS.json bf16_tflops"}
 
     def dput(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -765,11 +844,8 @@ def run_ours(args):
     Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
     Ld = torch.empty_like(Lb)
     P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
-    stream = torch.cuda.current_stream()
 
-    FORMS = {"bf16x3": ("bf16x3", "bf16x3", True), "fp32": ("fp32", "fp32", True), "fp64": ("fp64", "fp64", False)}
-
-    def step(form, ev=None, H0=H0, Ls=Ls, X=X, u=u, R=R):
+    def step(form, ev=None, H0=H0, Ls=Ls, X=X, u=u, R=R, s_out=None):
         pb, pp, renorm = FORMS[form]
         if ev is not None:
             ev[0].record(stream)
@@ -777,7 +853,7 @@ def run_ours(args):
         lb.lb_assemble(ctx, X, None, Ld)
         if ev is not None:
             ev[1].record(stream)
-        lb.lb_expm_pade(ctx, Lb, Ld, u, dt, P, prec=pb)
+        lb.lb_expm_pade(ctx, Lb, Ld, u, dt, P, prec=pb, s_out=s_out)
         if ev is not None:
             ev[2].record(stream)
         lb.lb_propagate_batch(ctx, P, R, steps_per_slice=1, prec=pp, renorm_trace=renorm)
@@ -794,52 +870,71 @@ def run_ours(args):
 
         return ranks.max_over_ranks(x, dev)
 
-    def timed(form, sampler=None):
-        for _ in range(args.warmup):
+    def timed(form, steps, warmup, sampler=None, ntrials=5):
+        """warmup untimed steps, then `steps` timed steps in up to five
+        trials of consecutive steps; ms_per_step is the median over the
+        trials of the trial's time per step (max over ranks)."""
+        for _ in range(warmup):
             step(form)
         lb.lb_sync_status(ctx)
         lb.lb_set_stage_timing(ctx, True)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        ntr = max(1, min(ntrials, steps))
+        sizes = [steps // ntr + (1 if t < steps % ntr else 0) for t in range(ntr)]
+        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ntr)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         if sampler:
             sampler.start()
         n0 = lb.lb_launch_count()
         e0.record(stream)
-        for k in range(args.steps):
-            step(form, evs[k])
+        k = 0
+        for t in range(ntr):
+            tev[t][0].record(stream)
+            for _ in range(sizes[t]):
+                step(form, evs[k])
+                k += 1
+            tev[t][1].record(stream)
         e1.record(stream)
         n1 = lb.lb_launch_count()
         barrier()
         clocks = sampler.stop() if sampler else None
         lb.lb_sync_status(ctx)
+        trial = [tev[t][0].elapsed_time(tev[t][1]) / sizes[t] for t in range(ntr)]
+        med = max_over_ranks(statistics.median(trial))
         total_ms = max_over_ranks(e0.elapsed_time(e1))
         stages, chunks = lb.lb_stage_times(ctx)
         lb.lb_set_stage_timing(ctx, False)
         ph = {"assemble_ms": 0.0, "build_ms": 0.0, "propagate_ms": 0.0}
         for ev in evs:
-            ph["assemble_ms"] += ev[0].elapsed_time(ev[1]) / args.steps
-            ph["build_ms"] += ev[1].elapsed_time(ev[2]) / args.steps
-            ph["propagate_ms"] += ev[2].elapsed_time(ev[3]) / args.steps
-        stages = {k: v / max(chunks, 1) for k, v in stages.items()}
-        return dict(ms_per_step=total_ms / args.steps, phases=ph, build_stages_ms=stages,
-                    launches=n1 - n0, clocks=clocks, step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs])
+            ph["assemble_ms"] += ev[0].elapsed_time(ev[1]) / steps
+            ph["build_ms"] += ev[1].elapsed_time(ev[2]) / steps
+            ph["propagate_ms"] += ev[2].elapsed_time(ev[3]) / steps
+        stages = {k: v / steps for k, v in stages.items()}
+        return dict(ms_per_step=med, mean_ms_per_step=total_ms / steps, trial_ms_per_step=trial, steps=steps,
+                    warmup=warmup, phases=ph, build_stages_ms=stages, launches=(n1 - n0) // steps, clocks=clocks,
+                    step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs])
 
     t_tune = time.perf_counter()
     tuned = lb.lb_autotune(ctx, n, S, B)
     t_tune = time.perf_counter() - t_tune
     sampler = ClockSampler(local)
     if args.headline_only:
-        r = timed("bf16x3")
+        r = timed(HEADLINE, args.steps, args.warmup)
         if rank == 0:
-            print(json.dumps({"headline_only": True, "form": "bf16x3", "ms_per_step": r["ms_per_step"],
+            print(json.dumps({"headline_only": True, "form": HEADLINE, "ms_per_step": r["ms_per_step"],
                               "steps": args.steps, "warmup": args.warmup,
-                              "launches_per_step": r["launches"] // max(args.steps, 1)}), flush=True)
+                              "launches_per_step": r["launches"]}), flush=True)
         ctx.close()
         return
-    res = {"bf16x3": timed("bf16x3", sampler), "fp32": timed("fp32"), "fp64": timed("fp64")}
-    head = min(("bf16x3", "fp32"), key=lambda f: res[f]["ms_per_step"])
-    mixed, fp64 = res[head], res["fp64"]
+    res = {HEADLINE: timed(HEADLINE, args.steps, args.warmup, sampler)}
+    # the other forms: a bounded number of steps (the complex FP64 form takes
+    # seconds per step), five trials of one step each
+    for f in FORMS:
+        if f != HEADLINE:
+            res[f] = timed(f, min(args.steps, 5), 1 if f == "fp64" else min(args.warmup, 3))
+    head = res[HEADLINE]
+    mixed_form = min(MIXED_FORMS, key=lambda f: res[f]["ms_per_step"])
 
     # end to end through the public API with host buffers: H2D of every input
     # from pinned memory, the three calls, D2H of the final states
@@ -853,7 +948,7 @@ def run_ours(args):
     def e2e_step():
         for k, v in host.items():
             dbuf[k].copy_(v, non_blocking=True)
-        step(head, None, dbuf["H0"], dbuf["jumps"], dbuf["X"], dbuf["u"], dbuf["states"])
+        step(HEADLINE, None, dbuf["H0"], dbuf["jumps"], dbuf["X"], dbuf["u"], dbuf["states"])
         out_host.copy_(dbuf["states"], non_blocking=True)
 
     for _ in range(args.warmup):
@@ -868,63 +963,115 @@ def run_ours(args):
     lb.lb_sync_status(ctx)
     e2e_ms = max_over_ranks(f0.elapsed_time(f1)) / args.steps
 
-    units = B * S  # state-steps per step per rank
-    value = world * units / (mixed["ms_per_step"] / 1e3)
-    builds = world * S / (mixed["ms_per_step"] / 1e3)
+    # accuracy of every form in this run (one step from the initial states)
+    s_dev = torch.empty(S, dtype=torch.int32, device=dev)
 
-    # roofline of the dominant kernel: the FP64 blocked LU + n-RHS solve
-    lu_ms = mixed["build_stages_ms"]["lu_solve"]
-    lu_flops = S * accounting.build_flops_fp64_solve(n)
-    lu_achieved = lu_flops / (lu_ms / 1e3)
+    def run_form(f):
+        Rf = dput(w["states"])
+        step(f, R=Rf, s_out=s_dev)
+        lb.lb_sync_status(ctx)
+        return P, Rf, s_dev.cpu().numpy()
+
+    errors = form_errors(lb, ctx, w, dev, list(FORMS), run_form) if rank == 0 else {}
+    squarings = [int(x) for x in run_form(HEADLINE)[2]]
+
+    units = B * S  # state-steps per step per rank
+
+    def form_line(f):
+        r = res[f]
+        return {"value": world * units / (r["ms_per_step"] / 1e3), "unit": "state-steps/s",
+                "builds_per_s": world * S / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
+                "mean_ms_per_step": r["mean_ms_per_step"], "trial_ms_per_step": r["trial_ms_per_step"],
+                "steps": r["steps"], "warmup": r["warmup"], "phases_ms": r["phases"],
+                "build_stages_ms": r["build_stages_ms"], "launches_per_step": r["launches"], "dtype": DTYPES[f],
+                "precision": PRECISION_DESC[f], "error": errors.get(f)}
+
+    value = world * units / (head["ms_per_step"] / 1e3)
+    builds = world * S / (head["ms_per_step"] / 1e3)
+
+    # roofline of the dominant kernel: the real FP64 GEMM (rgemm_kernel<double>)
+    # that carries every product, LU update and substitution of the build;
+    # its stages' time from the library's stage events on this stream
+    st = head["build_stages_ms"]
+    gemm_ms = st["pade_products"] + st["lu_solve"] + st["squarings"]
+    n3 = float(n) ** 3
+    fl_products = S * 6 * 2 * n3
+    fl_solve = S * accounting.build_flops_real_solve(n)
+    fl_sq = sum(squarings) * 2 * n3
+    gemm_flops = fl_products + fl_solve + fl_sq
+    ach = gemm_flops / (gemm_ms / 1e3)
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "lu_solve_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "rgemm_f64_d27_traffic.json")
     if os.path.exists(tfile):
         t = json.load(open(tfile))
         if t.get("per_slice_bytes"):
             traffic = t["per_slice_bytes"] * S
-    roofline = {"bound": "alu", "kernel": "FP64 blocked LU + n-RHS solve (zgemm_kernel<double> + lu_diag_kernel)",
-                "achieved": lu_achieved / 1e12, "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
-                "frac": lu_achieved / FP64_PEAK, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (FP64 is absent from "
-                               "MEASURED_PEAKS.json); DFMA probe measured 1.20 TFLOP/s",
-                "algorithmic_flops_per_launch": lu_flops, "launch_ms": lu_ms}
-    # propagation phase, each form against its own peak
-    prop_flops = S * B * accounting.state_step_flops(n)
+    roofline = {
+        "bound": "alu", "kernel": "rgemm_kernel<double> (every FP64 product, LU update and substitution of the "
+                                  "real-coordinate build) + lu_diag_real_kernel",
+        "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+        "traffic": traffic, "peak_source": peak_src["fp64"] + " (DFMA, burst); FP64 is absent from "
+                                                               "MEASURED_PEAKS.json",
+        "algorithmic_flops_per_step": gemm_flops,
+        "flops_note": "real FLOPs: 2 per real multiply-add (6 Pade products and s squarings at 2 n^3, LU 2 n^3/3, "
+                      "solve 2 n^3, n = 729, per slice); the GEMMs execute exactly these FMAs",
+        "stage_ms": {"pade_products": st["pade_products"], "lu_solve": st["lu_solve"], "squarings": st["squarings"]},
+        "lu_solve_frac": (fl_solve / (st["lu_solve"] / 1e3)) / fp64_peak,
+        "complex_equivalent_frac": 4.0 * ach / fp64_peak,
+        "complex_equivalent_note": "the same build counted in the complex FLOPs of the paper's Eq. 4 convention "
+                                   "(8 per complex multiply-add, 4x the real count)"}
 
-    def prop_roof(form, peak, note):
-        ach = prop_flops / (res[form]["phases"]["propagate_ms"] / 1e3)
-        return {"bound": "tensor" if form == "bf16x3" else "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": ach / peak, "ms": res[form]["phases"]["propagate_ms"], "note": note}
+    def prop_roof(f):
+        ms = res[f]["phases"]["propagate_ms"]
+        if f == "fp64_hermitian":
+            fl, peak, note = S * B * accounting.state_step_flops_real(n), fp64_peak, \
+                "2 n^2 real FLOP per state-step on the real coordinates against the DFMA probe"
+        elif f in ("fp64",):
+            fl, peak, note = S * B * accounting.state_step_flops(n), fp64_peak, \
+                "8 n^2 FLOP per state-step against the DFMA probe (Gauss form: 6 executed per 8 counted)"
+        elif f == "bf16x3":
+            fl, peak, note = S * B * accounting.state_step_flops(n), bf16_peak / 5.0, \
+                "useful 8 n^2 FLOP per state-step (Eq. 4); peak = BF16 tcgen05 probe / 5 (five BF16 products per " \
+                "real product)"
+        else:
+            fl, peak, note = S * B * accounting.state_step_flops(n), fp32_peak, \
+                "8 n^2 FLOP per state-step against the FFMA probe"
+        a = fl / (ms / 1e3)
+        return {"bound": "tensor" if f == "bf16x3" else "alu", "achieved": a / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": a / peak, "ms": ms, "note": note}
 
+    mixed_line = {"form": mixed_form, **form_line(mixed_form),
+                  "forms": {f: form_line(f) for f in MIXED_FORMS},
+                  "speedup_vs_fp64_headline": head["ms_per_step"] / res[mixed_form]["ms_per_step"],
+                  "roofline_propagation": prop_roof(mixed_form)}
     line = {
         "metric": METRIC, "value": value, "unit": "state-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
-        "builds_per_s": builds, "form": head,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "builds_per_s": builds, "form": HEADLINE,
         "config": {"workload": WORKLOAD_DESC,
-                   "precision": PRECISION_DESC[head],
-                   "l2": "no flush: every step streams 1.7 GB of propagators plus 15 GB of build scratch, "
-                         "far larger than the 129 MB L2",
+                   "precision": PRECISION_DESC[HEADLINE],
+                   "timing": "median over 5 trials of consecutive steps of the time per step (CUDA events on the "
+                             "launching stream); mean_ms_per_step beside it",
+                   "l2": "no flush: every step streams 0.85 GB of real propagators (1.7 GB complex) plus ~8 GB "
+                         "of build scratch, far larger than the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "phases_ms": mixed["phases"], "build_stages_ms": mixed["build_stages_ms"],
-        "forms": {f: {"value": world * units / (res[f]["ms_per_step"] / 1e3), "unit": "state-steps/s",
-                      "builds_per_s": world * S / (res[f]["ms_per_step"] / 1e3), "ms_per_step": res[f]["ms_per_step"],
-                      "phases_ms": res[f]["phases"], "build_stages_ms": res[f]["build_stages_ms"],
-                      "dtype": DTYPES[f], "precision": PRECISION_DESC[f]} for f in res},
+        "mean_ms_per_step": head["mean_ms_per_step"], "trial_ms_per_step": head["trial_ms_per_step"],
+        "phases_ms": head["phases"], "build_stages_ms": head["build_stages_ms"], "error": errors.get(HEADLINE),
+        "mixed": mixed_line,
+        "forms": {f: form_line(f) for f in FORMS},
+        "peaks_measured_tflops": peaks,
         "roofline": roofline,
-        "roofline_propagation": {
-            "bf16x3": prop_roof("bf16x3", BF16_PEAK / 5.0,
-                                "useful 8 n^2 FLOP per state-step (Eq. 4); peak = measured BF16 dense / 5 "
-                                "(five BF16 products per real product)"),
-            "fp32": prop_roof("fp32", FP32_PEAK, "8 n^2 FLOP per state-step against the FFMA peak"),
-            "fp64": prop_roof("fp64", FP64_PEAK, "8 n^2 FLOP per state-step against the DFMA peak")},
+        "roofline_propagation": {f: prop_roof(f) for f in FORMS},
         "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": "state-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "autotune": {"shapes": tuned, "seconds": t_tune},
-        "gpu_launches": mixed["launches"],
-        "clocks": mixed["clocks"],
+        "gpu_launches": head["launches"] * args.steps,
+        "gpu_launches_per_step": head["launches"],
+        "clocks": head["clocks"],
     }
-    line["other_workloads"] = other_workloads(lb, accounting, dev, stream)
+    line["other_workloads"] = other_workloads(lb, accounting, dev, stream, fp64_peak=fp64_peak, fp32_peak=fp32_peak,
+                                              bf16_peak=bf16_peak)
     line["other_workloads"]["mixed_instances"] = mixed_instances(lb, ctx, P, dev, stream, 128)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, 6)
@@ -935,6 +1082,8 @@ def run_ours(args):
             for f, r in res.items():
                 for k, v in enumerate(r["step_ms"]):
                     fh.write(json.dumps({"kind": "d27_chain_step", "form": f, "step": k, "ms": v}) + "\n")
+                for k, v in enumerate(r["trial_ms_per_step"]):
+                    fh.write(json.dumps({"kind": "d27_chain_trial", "form": f, "trial": k, "ms_per_step": v}) + "\n")
             for row in line["other_workloads"]["gpu_timing_models"]["rows"]:
                 for name in ("kernel", "resident", "host"):
                     for i, v in enumerate(row[name]["trials_ns"]):

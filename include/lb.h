@@ -51,9 +51,12 @@ typedef enum {
   LB_FP64 = 0,    /* every product in FP64 */
   LB_FP32 = 1,    /* products in FP32 with FP32 accumulation */
   LB_BF16X3 = 2,  /* products as split-BF16 x3 on the tensor cores, FP32 accumulation */
-  LB_FP64_HERMITIAN = 3  /* lb_propagate_batch only: FP64 on the n real coordinates of
-                            Hermitian states (density matrices) with a Hermiticity-
-                            preserving P, as exp(L dt) of any Lindbladian is; see there */
+  LB_FP64_HERMITIAN = 3, /* FP64 on the n real coordinates of Hermitian matrices: for
+                            Hermiticity-preserving generators and propagators (every
+                            Lindbladian and its exponential are); see lb_expm_pade and
+                            lb_propagate_batch */
+  LB_FP32_HERMITIAN = 4  /* lb_expm_pade: the real-coordinate build with FP32 Pade
+                            products; lb_propagate_batch: the same as LB_FP32 */
 } lb_precision;
 
 typedef struct lb_ctx lb_ctx;
@@ -170,7 +173,21 @@ lb_status lb_assemble(lb_ctx* ctx, int d, const lb_c64* H, int K, const lb_c64* 
  *   Ldrv  : n x n or NULL
  *   u     : nslices doubles (device)
  *   prec  : precision of the six Pade products; LU, solve and squarings are
- *           always FP64
+ *           always FP64 (in the reduced forms a leading squaring whose operand
+ *           is still near I runs as P^2 = 2P - I + D D, D = P - I, with only
+ *           D D in the reduced precision)
+ *           LB_FP64_HERMITIAN / LB_FP32_HERMITIAN: the whole of Algorithm 1
+ *           on the n = d^2 real coordinates of Hermitian matrices (diagonal,
+ *           then Re and Im of the upper triangle, row-major), where L dt and
+ *           exp(L dt) are real n x n matrices G and R: the generators must
+ *           map Hermitian matrices to Hermitian matrices (every Lindbladian
+ *           and every drive term -i[X, .] with X Hermitian does; for others
+ *           the result is not exp(A)); sc is taken from ||G||_1; every
+ *           product, the LU and the solve are real (one FMA per multiply-
+ *           add instead of four); P is rebuilt from R at the end.  The FP32
+ *           variant runs the six Pade products and the near-I squarings in
+ *           FP32; LU, solve and the other squarings stay FP64.  n must be a
+ *           square (else LB_EINVAL).
  *   P_out : nslices x n x n
  *   s_out : nslices ints (device) receiving sc, or NULL
  * The LU takes no pivots: at theta = 0.25 the matrix V - U is strictly
@@ -203,8 +220,11 @@ lb_status lb_expm_pade(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, con
  *   the states come back exactly Hermitian.  Same result as LB_FP64 up to
  *   rounding for such inputs.  n <= 9: one warp per state, the state
  *   exchanged by shuffles; 9 < n <= 81: the real transfer matrix and each
- *   CTA's states in shared memory; larger n run the LB_FP64 path.
+ *   CTA's states in shared memory; n > 81: one real product per step over
+ *   all states (a few-state product for B <= 8) with the real transfer
+ *   matrices of up to max_slices slices in the context's scratch.
  *   renorm_trace is ignored, as for LB_FP64.
+ *   prec = LB_FP32_HERMITIAN runs the LB_FP32 form.
  */
 lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, int steps_per_slice,
                              int B, lb_c64* states, lb_precision prec, int renorm_trace,
@@ -345,7 +365,10 @@ lb_status lb_control_update(int n, int nslices, const lb_c64* P, const lb_c64* d
  *   serialised by the caller.  Nothing in it needs clearing between calls.
  *   The first call on each device looks up the array's device address (which
  *   can load the library's device code on that device); make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept for the life of the
+ *   process: do not use this entry point after a cudaDeviceReset of that
+ *   device.  P and states must be device (or managed) memory of the current
+ *   device, else LB_EINVAL.
  */
 lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64* P, int steps_per_slice, int B,
                                     lb_c64* states, void* stream);
@@ -518,6 +541,27 @@ lb_status lb_probe_alloc(long long bytes, int reps, double* us_out);
  * is written only on an impossible match.  Time it with events on `stream`.
  */
 lb_status lb_probe_read(const lb_c64* buf, long long count, int n, unsigned long long* sink, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Arithmetic peak probes (the measured ceilings of Sec. 3.6, Table
+ * tab:probes_gpu, for the FP64 / FP32 / tensor-core rooflines): each runs
+ * one untimed and five timed launches of a kernel that keeps one unit busy
+ * with independent work and no memory traffic, timed with CUDA events on
+ * `stream` (synchronised), and writes the best rate in TFLOP/s (2 FLOPs per
+ * multiply-add) to *tflops_out (host).  On the CURRENT device (sm_103 only,
+ * else LB_ENODEV); no device memory is allocated.
+ *   lb_probe_dfma     FP64 FMA on the CUDA cores
+ *   lb_probe_ffma     FP32 FMA on the CUDA cores
+ *   lb_probe_dmma     FP64 tensor-core MMA (mma.sync m8n8k4 f64)
+ *   lb_probe_bf16_tc  BF16 tcgen05 MMA, M = 128, N = 256, K = 16, FP32
+ *                     accumulation in TMEM; its wait for the MMAs is
+ *                     bounded (about 2 s), LB_ETIMEOUT if it gives up
+ *   Errors: LB_EINVAL (null pointer), LB_ENODEV, LB_ECUDA, LB_ETIMEOUT.
+ * ------------------------------------------------------------------------ */
+lb_status lb_probe_dfma(double* tflops_out, void* stream);
+lb_status lb_probe_ffma(double* tflops_out, void* stream);
+lb_status lb_probe_dmma(double* tflops_out, void* stream);
+lb_status lb_probe_bf16_tc(double* tflops_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -46,3 +46,22 @@ def gauss_fp64_instr_fraction():
     complex multiply-add: the FP64 pipe executes 3/4 of the FMAs counted
     above."""
     return 0.75
+
+
+# Real-coordinate ("Hermitian") forms: every matrix is a real n x n matrix
+# (the action of the superoperator on the n = d^2 real coordinates of a
+# Hermitian matrix), so a multiply-add is 2 real FLOPs.
+
+def state_step_flops_real(n):
+    return 2 * n * n
+
+
+def build_flops_real(n, s):
+    """Dense real FLOPs of one Pade-13 build on the real coordinates with s
+    squarings: six products and s squarings at 2 n^3, the LU at 2 n^3 / 3
+    and the n-right-hand-side solve at 2 n^3."""
+    return (6 + s) * 2 * n ** 3 + 2 * n ** 3 / 3 + 2 * n ** 3
+
+
+def build_flops_real_solve(n):
+    return 2 * n ** 3 / 3 + 2 * n ** 3

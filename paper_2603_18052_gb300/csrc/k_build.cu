@@ -389,6 +389,13 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
   return cudaGetLastError();
 }
 
+cudaError_t launch_squaring_count(int S, const unsigned long long* norm_bits, int* sc, int* kmix, int* s_out,
+                                  unsigned int* err, cudaStream_t st) {
+  count_launch();
+  squaring_count_kernel<<<(S + 127) / 128, 128, 0, st>>>(S, norm_bits, sc, kmix, s_out, sc + S, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lincomb3(int nn, int S, const z64* X0, const z64* X1, const z64* X2, double c0,
                             double c1, double c2, z64* Z, cudaStream_t st) {
   const long long total = (long long)nn * S;

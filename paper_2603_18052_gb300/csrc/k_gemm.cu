@@ -287,82 +287,103 @@ long long count_tiles(const ZGemmProblem* probs, int nprob, int BM, int BN) {
 namespace {
 
 // ------------------------------------------------------------ autotuner --
-// A launch "shape" is the precision, the number of problems and each
-// problem's (M, N, K, batch, opB, beta).  In tuning mode every launch times
-// each candidate tile configuration (CUDA events, host wait) and records the
+// A launch "shape" is the GEMM family, its precision, the number of problems
+// and each problem's (M, N, K, batch, opB, beta).  In tuning mode (set for
+// the calling host thread only, by lb_autotune) every launch times each
+// candidate tile configuration (CUDA events, host wait) and records the
 // fastest for its shape; afterwards launches of a recorded shape use it, and
-// other shapes use the tile-count heuristic.
-typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int, int,
-                   int, int>
-    ShapeKey;
+// other shapes use the caller's tile-count heuristic.
 std::mutex g_tune_mu;
-std::map<ShapeKey, int> g_tune;
-bool g_tuning = false;
+std::map<TuneKey, int> g_tune;
+thread_local bool t_tuning = false;
 
-ShapeKey shape_key(int prec, const ZGemmProblem* p, int np) {
-  int v[20] = {0};
-  for (int i = 0; i < np && i < 4; i++) {
-    v[5 * i] = p[i].M;
-    v[5 * i + 1] = p[i].N;
-    v[5 * i + 2] = p[i].K;
-    v[5 * i + 3] = p[i].batch;
-    v[5 * i + 4] = p[i].opB * 4 + (p[i].beta != 0.0 ? 2 : 0) + (p[i].active != nullptr ? 1 : 0);
+// Both events of a timing pair, destroyed on every exit path.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok() {
+    return cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   }
-  return ShapeKey(prec, np, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11], v[12], v[13],
-                  v[14], v[15], v[16], v[17], v[18], v[19]);
-}
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
 
-typedef cudaError_t (*cfg_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+}  // namespace
 
-cudaError_t run_tuned(int prec, const cfg_fn* cands, int ncand, int heuristic, const ZGemmProblem* probs, int nprob,
-                      int sm_count, cudaStream_t st) {
-  const ShapeKey key = shape_key(prec, probs, nprob);
-  bool tuning;
+cudaError_t tuned_launch(const TuneKey& key, int ncand, int heuristic, TuneCand run, const void* args,
+                         cudaStream_t st) {
   int choice = heuristic;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    tuning = g_tuning;
-    auto it = g_tune.find(key);
-    if (!tuning && it != g_tune.end()) choice = it->second;
+  if (!t_tuning) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) choice = it->second;
+    }
+    return run(choice, args, st);
   }
-  if (!tuning) return cands[choice](probs, nprob, sm_count, st);
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+  EventPair ev;
+  if (!ev.ok()) return cudaErrorUnknown;
   float best = 1e30f;
   int besti = heuristic;
   for (int c = 0; c < ncand; c++) {
-    cudaError_t e = cands[c](probs, nprob, sm_count, st);  // warm-up
+    cudaError_t e = run(c, args, st);  // warm-up
     if (e != cudaSuccess) return e;
-    cudaEventRecord(e0, st);
-    e = cands[c](probs, nprob, sm_count, st);
-    cudaEventRecord(e1, st);
+    if (cudaEventRecord(ev.e0, st) != cudaSuccess) return cudaErrorUnknown;
+    e = run(c, args, st);
     if (e != cudaSuccess) return e;
-    if (cudaEventSynchronize(e1) != cudaSuccess) return cudaErrorUnknown;
+    if (cudaEventRecord(ev.e1, st) != cudaSuccess || cudaEventSynchronize(ev.e1) != cudaSuccess)
+      return cudaErrorUnknown;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
     if (ms < best) {
       best = ms;
       besti = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = besti;
   return cudaSuccess;
 }
 
-}  // namespace
-
-void set_tuning(bool on) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuning = on;
-}
+void set_tuning(bool on) { t_tuning = on; }
 
 int tuned_shapes() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return (int)g_tune.size();
 }
+
+namespace {
+
+TuneKey zshape_key(int prec, const ZGemmProblem* p, int np) {
+  TuneKey k{};
+  k[0] = 1;  // family: complex GEMM
+  k[1] = prec;
+  k[2] = np;
+  for (int i = 0; i < np && i < 4; i++) {
+    k[3 + 5 * i] = p[i].M;
+    k[4 + 5 * i] = p[i].N;
+    k[5 + 5 * i] = p[i].K;
+    k[6 + 5 * i] = p[i].batch;
+    k[7 + 5 * i] = p[i].opB * 4 + (p[i].beta != 0.0 ? 2 : 0) + (p[i].active != nullptr ? 1 : 0);
+  }
+  return k;
+}
+
+typedef cudaError_t (*cfg_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+
+struct ZArgs {
+  const cfg_fn* cands;
+  const ZGemmProblem* probs;
+  int nprob, sm_count;
+};
+
+cudaError_t zrun(int cand, const void* a, cudaStream_t st) {
+  const ZArgs* z = (const ZArgs*)a;
+  return z->cands[cand](z->probs, z->nprob, z->sm_count, st);
+}
+
+}  // namespace
 
 cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
@@ -371,14 +392,16 @@ cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaSt
   // heuristic: 32x32 tiles when there are enough of them to balance the
   // persistent grid, else 16x16 tiles
   const long long t32 = count_tiles(probs, nprob, 32, 32);
-  return run_tuned(64, cands, 3, t32 >= 8LL * sm_count ? 1 : 0, probs, nprob, sm_count, st);
+  const ZArgs a{cands, probs, nprob, sm_count};
+  return tuned_launch(zshape_key(64, probs, nprob), 3, t32 >= 8LL * sm_count ? 1 : 0, zrun, &a, st);
 }
 
 cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
   static const cfg_fn cands[2] = {launch_cfg<float, 32, 32, 2, 2, false>, launch_cfg<float, 64, 64, 4, 4, false>};
   const long long t64 = count_tiles(probs, nprob, 64, 64);
-  return run_tuned(32, cands, 2, t64 >= 4LL * sm_count ? 1 : 0, probs, nprob, sm_count, st);
+  const ZArgs a{cands, probs, nprob, sm_count};
+  return tuned_launch(zshape_key(32, probs, nprob), 2, t64 >= 4LL * sm_count ? 1 : 0, zrun, &a, st);
 }
 
 }  // namespace lb

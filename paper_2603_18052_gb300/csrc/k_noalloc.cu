@@ -81,6 +81,18 @@ extern "C" lb_status lb_propagate_batch_static(int n, int nslices, const lb_c64*
     return LB_ENODEV;
   }
   if (major != 10 || minor != 3) return LB_ENODEV;
+  // P and the states must be device memory of the current device (a
+  // pointer into another GPU's memory would make the kernels read and write
+  // a peer's memory).  cudaPointerGetAttributes allocates nothing.
+  for (const void* ptr : {(const void*)P, (const void*)states}) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return LB_EINVAL;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+      return LB_EINVAL;
+  }
   double2* scratch = nullptr;
   int sms = 0;
   lb_status s = static_setup(dev, &scratch, &sms);

@@ -1,0 +1,293 @@
+// Element-wise and small-block kernels of the real-coordinate ("Hermitian")
+// propagator build (Algorithm 1 on the real coordinates of Hermitian
+// matrices; the coordinates and the map of a Hermiticity-preserving
+// superoperator onto them are described in k_herm.cu):
+//   * the slice generators G_s = (G_base + u_s G_drv) dt on the real
+//     coordinates, their 1-norms (maximum absolute column sum), the scaling
+//     by 2^-s (Eq. 5 and the scaling line of Algorithm 1),
+//   * the linear combinations of the Pade step and the FP64 -> FP32 copies
+//     of the reduced-precision form,
+//   * the real diagonal-block factorisation of the blocked LU,
+//   * the complex propagator P rebuilt from its real-coordinate matrix R.
+#include "lb_internal.cuh"
+
+namespace lb {
+
+namespace {
+
+inline unsigned grid_of(long long total, int threads, int sm_count) {
+  long long g = (total + threads - 1) / threads;
+  const long long cap = (long long)sm_count * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// v = (Gb[o] + u Gd[o]) dt, rounded as the complex path rounds it (product
+// and sum in one FMA, then the scaling by dt).
+__device__ __forceinline__ double slice_gen(const double* __restrict__ Gb, const double* __restrict__ Gd,
+                                            const double* __restrict__ u, int s, long long nn, long long o,
+                                            double dt) {
+  const double v = Gd == nullptr ? Gb[s * nn + o] : fma(u[s], Gd[o], Gb[o]);
+  return v * dt;
+}
+
+// Per-slice maximum absolute column sum of G_s (8 columns x 32 row groups
+// per CTA, fixed-order sums), max-reduced into norm_bits[s] as the bits of a
+// non-negative double (NaN -> +Inf).
+__global__ void __launch_bounds__(256) real_gen_norm_kernel(int n, int S, const double* __restrict__ Gb,
+                                                           const double* __restrict__ Gd,
+                                                           const double* __restrict__ u, double dt,
+                                                           unsigned long long* __restrict__ norm_bits) {
+  __shared__ double part[32][8];
+  const long long nn = (long long)n * n;
+  const int c = threadIdx.x % 8, rg = threadIdx.x / 8;
+  const int cblocks = (n + 7) / 8;
+  for (long long t = blockIdx.x; t < (long long)S * cblocks; t += gridDim.x) {
+    const int s = (int)(t / cblocks), j = (int)(t - (t / cblocks) * cblocks) * 8 + c;
+    double sum = 0.0;
+    if (j < n)
+      for (int i = rg; i < n; i += 32) sum += fabs(slice_gen(Gb, Gd, u, s, nn, (long long)i * n + j, dt));
+    part[rg][c] = sum;
+    __syncthreads();
+    if (rg == 0 && j < n) {
+      double col = 0.0;
+      for (int r = 0; r < 32; r++) col += part[r][c];
+      if (!(col == col)) col = INFINITY;
+      atomicMax(norm_bits + s, (unsigned long long)__double_as_longlong(col));
+    }
+    __syncthreads();
+  }
+}
+
+// A_s = G_s / 2^sc[s] (exact power-of-two scaling)
+__global__ void real_scale_kernel(int n, int S, const double* __restrict__ Gb, const double* __restrict__ Gd,
+                                  const double* __restrict__ u, double dt, const int* __restrict__ sc,
+                                  double* __restrict__ A) {
+  const long long nn = (long long)n * n, total = nn * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / nn);
+    A[e] = ldexp(slice_gen(Gb, Gd, u, s, nn, e - s * nn, dt), -sc[s]);
+  }
+}
+
+template <typename T>
+__global__ void real_lincomb3_kernel(long long total, const T* __restrict__ X0, const T* __restrict__ X1,
+                                     const T* __restrict__ X2, T c0, T c1, T c2, T* __restrict__ Z) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    Z[e] = c0 * X0[e] + (c1 * X1[e] + c2 * X2[e]);
+}
+
+// dst (FP32) = src - shift I  (n x n per slice)
+__global__ void real_to_f32_kernel(int n, long long total, const double* __restrict__ src, double shift,
+                                   float* __restrict__ dst) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long o = e % nn;
+    double v = src[e];
+    if (o / n == o % n) v -= shift;
+    dst[e] = (float)v;
+  }
+}
+
+__global__ void real_copy_active_kernel(long long nn, int S, const double* __restrict__ src, double* __restrict__ dst,
+                                        const int* __restrict__ active, int iter) {
+  const long long total = nn * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    if (active[e / nn] > iter) dst[e] = src[e];
+}
+
+// P[s] from R[s]: the complex superoperator that acts on Hermitian matrices
+// as R acts on their real coordinates.  Column (k, l) of P is P(E_kl); with
+// Y(r) the Hermitian matrix of coordinate vector r and R_a column a of R,
+//   k = l:  P(E_kk) = Y(R_k)
+//   k < l:  E_kl = H1 + i H2 with H1 = (E_kl + E_lk)/2 (Re coordinate 1/2)
+//           and H2 = -i (E_kl - E_lk)/2 (Im coordinate -1/2), so
+//           P(E_kl) = Y(R_re)/2 - i Y(R_im)/2
+//   k > l:  E_kl = H1 - i H2 for the pair (l, k): P(E_kl) = Y(R_re)/2 + i Y(R_im)/2
+__device__ __forceinline__ z64 herm_entry(const double* __restrict__ R, int n, int d, int i, int j, int col) {
+  if (i == j) return make_double2(R[(long long)i * n + col], 0.0);
+  const int a = herm_pair_coord(i < j ? i : j, i < j ? j : i, d);
+  const double re = R[(long long)a * n + col], im = R[(long long)(a + 1) * n + col];
+  return make_double2(re, i < j ? im : -im);
+}
+
+__global__ void herm_to_complex_kernel(int n, int d, int S, const double* __restrict__ R, z64* __restrict__ P) {
+  const long long nn = (long long)n * n, total = nn * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / nn;
+    const int r = (int)((e - s * nn) / n), c = (int)(e - s * nn - (long long)r * n);
+    const int i = r / d, j = r - (r / d) * d, k = c / d, l = c - (c / d) * d;
+    const double* Rs = R + s * nn;
+    z64 v;
+    if (k == l) {
+      v = herm_entry(Rs, n, d, i, j, k);
+    } else {
+      const int a = herm_pair_coord(k < l ? k : l, k < l ? l : k, d);
+      const z64 yre = herm_entry(Rs, n, d, i, j, a), yim = herm_entry(Rs, n, d, i, j, a + 1);
+      v = k < l ? make_double2(0.5 * (yre.x + yim.y), 0.5 * (yre.y - yim.x))
+                : make_double2(0.5 * (yre.x - yim.y), 0.5 * (yre.y + yim.x));
+    }
+    P[e] = v;
+  }
+}
+
+// Real diagonal block of the blocked LU without pivot search, one CTA per
+// slice: factors the kb x kb block at (k0, k0) of M[s] in shared memory,
+// writes its upper factor into Uf[s] and the inverses of the unit-lower and
+// upper factors into Linv and Uinv (nb x nb, zero outside kb x kb).  A pivot
+// of modulus below 1e-300 (or non-finite) sets the error word.
+__global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb, const double* __restrict__ M,
+                                                           double* __restrict__ Uf, double* __restrict__ Linv,
+                                                           long long sLinv, double* __restrict__ Uinv,
+                                                           long long sUinv, unsigned int* err) {
+  constexpr int NB = kLuNb;
+  __shared__ double a[NB][NB + 1];
+  __shared__ double x[NB][NB + 1];
+  __shared__ double part[8][NB];
+  __shared__ double rinv_s;
+  const int s = blockIdx.x;
+  const long long nn = (long long)n * n;
+  const double* Ms = M + s * nn;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e - (e / NB) * NB;
+    a[i][j] = (i < kb && j < kb) ? Ms[(long long)(k0 + i) * n + (k0 + j)] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; j++) {
+    if (tid == 0) {
+      const double p = a[j][j];
+      if (!(fabs(p) >= 1e-300) || !isfinite(p)) {
+        atomicOr(err, isfinite(p) ? ERR_SINGULAR : ERR_NONFINITE);
+        rinv_s = 1.0;
+      } else {
+        rinv_s = 1.0 / p;
+      }
+    }
+    __syncthreads();
+    const double rinv = rinv_s;
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) a[i][j] *= rinv;
+    __syncthreads();
+    const int w = kb - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e / w, c = j + 1 + (e - (e / w) * w);
+      a[i][c] = fma(-a[i][j], a[j][c], a[i][c]);
+    }
+    __syncthreads();
+  }
+  const int c = tid & 31, p = tid >> 5;  // column, partial-sum group (8 groups)
+  // Linv: X = L^{-1}, L unit lower; X[i][c] = d_ic - sum_{j<i} L[i][j] X[j][c]
+  for (int e = tid; e < NB * NB; e += blockDim.x) x[e / NB][e % NB] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < kb; i++) {
+    double acc = 0.0;
+    if (c < kb)
+      for (int j = p; j < i; j += 8) acc = fma(-a[i][j], x[j][c], acc);
+    part[p][c] = acc;
+    __syncthreads();
+    if (p == 0 && c < kb) {
+      double v = i == c ? 1.0 : 0.0;
+      for (int q = 0; q < 8; q++) v += part[q][c];
+      x[i][c] = v;
+    }
+    __syncthreads();
+  }
+  double* Li = Linv + (long long)s * sLinv;
+  for (int e = tid; e < NB * NB; e += blockDim.x) Li[e] = x[e / NB][e % NB];
+  __syncthreads();
+  // Uinv: X = U^{-1}; X[i][c] = (d_ic - sum_{j>i} U[i][j] X[j][c]) / U[i][i]
+  for (int e = tid; e < NB * NB; e += blockDim.x) x[e / NB][e % NB] = 0.0;
+  __syncthreads();
+  for (int i = kb - 1; i >= 0; i--) {
+    double acc = 0.0;
+    if (c < kb)
+      for (int j = i + 1 + p; j < kb; j += 8) acc = fma(-a[i][j], x[j][c], acc);
+    part[p][c] = acc;
+    __syncthreads();
+    if (p == 0 && c < kb) {
+      double v = i == c ? 1.0 : 0.0;
+      for (int q = 0; q < 8; q++) v += part[q][c];
+      const double dd = a[i][i];
+      x[i][c] = (fabs(dd) >= 1e-300 && isfinite(dd)) ? v / dd : v;
+    }
+    __syncthreads();
+  }
+  double* Ui = Uinv + (long long)s * sUinv;
+  for (int e = tid; e < NB * NB; e += blockDim.x) Ui[e] = x[e / NB][e % NB];
+  double* Ufs = Uf + s * nn;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e - (e / kb) * kb;
+    Ufs[(long long)(k0 + i) * n + (k0 + j)] = (j >= i) ? a[i][j] : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const double* Gd, const double* u, double dt,
+                                      double* A, unsigned long long* norm_bits, int* sc, int* kmix, int* s_out,
+                                      unsigned int* err, int sm_count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(norm_bits, 0, sizeof(unsigned long long) * S, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sc + S, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)S * ((n + 7) / 8);
+  count_launch();
+  real_gen_norm_kernel<<<grid_of(tiles, 1, sm_count), 256, 0, st>>>(n, S, Gb, Gd, u, dt, norm_bits);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_squaring_count(S, norm_bits, sc, kmix, s_out, err, st);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)n * n * S;
+  count_launch();
+  real_scale_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, S, Gb, Gd, u, dt, sc, A);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, const T* X2, double c0, double c1,
+                                 double c2, T* Z, int sm_count, cudaStream_t st) {
+  count_launch();
+  real_lincomb3_kernel<T><<<grid_of(total, 256, sm_count), 256, 0, st>>>(total, X0, X1, X2, T(c0), T(c1), T(c2), Z);
+  return cudaGetLastError();
+}
+template cudaError_t launch_real_lincomb3<double>(long long, const double*, const double*, const double*, double,
+                                                  double, double, double*, int, cudaStream_t);
+template cudaError_t launch_real_lincomb3<float>(long long, const float*, const float*, const float*, double, double,
+                                                 double, float*, int, cudaStream_t);
+
+cudaError_t launch_real_to_f32(int n, int S, const double* src, double shift, float* dst, int sm_count,
+                               cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  real_to_f32_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, total, src, shift, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_copy_active(long long nn, int S, const double* src, double* dst, const int* active, int iter,
+                                    int sm_count, cudaStream_t st) {
+  count_launch();
+  real_copy_active_kernel<<<grid_of(nn * S, 256, sm_count), 256, 0, st>>>(nn, S, src, dst, active, iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_herm_to_complex(int n, int d, int S, const double* R, z64* P, int sm_count, cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  herm_to_complex_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, d, S, R, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_diag_real(int n, int S, int k0, int kb, const double* M, double* Uf, double* Linv,
+                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st) {
+  count_launch();
+  lu_diag_real_kernel<<<S, 256, 0, st>>>(n, k0, kb, M, Uf, Linv, sLinv, Uinv, sUinv, err);
+  return cudaGetLastError();
+}
+
+}  // namespace lb

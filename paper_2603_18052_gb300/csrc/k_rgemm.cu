@@ -1,0 +1,325 @@
+// Grouped, batched REAL GEMM on the CUDA cores, FP64 and FP32.
+//
+// The real-coordinate ("Hermitian") forms of the propagator build and of the
+// propagation run every product of Algorithm 1 (the three powers, the three
+// U/V products, the LU updates, the substitutions, the squarings) and of
+// Algorithm 2 on real n x n matrices: a density matrix is Hermitian and
+// exp(L dt) maps Hermitian matrices to Hermitian matrices, so on the n = d^2
+// real coordinates of a Hermitian matrix both L dt and exp(L dt) are real
+// n x n matrices.  A real multiply-add is one FMA, against three (Gauss form)
+// or four for a complex one, which on GB300, where FP64 runs at 1/64 of the
+// FP32 rate, is what bounds the build.
+//
+//   r_w   = alpha[w] acc + beta[w] O_w(old) + sum_t coef[w][t] X_t + gamma[w] I   (arithmetic in T)
+//   O_w   = r_w                                          (T, when O[w] != null)
+//   Od_w  = double(r_w) + dcoef[w] Xd + dgamma[w] I      (FP64, when Od[w] != null)
+// for w = 0, 1, with acc = opA(A) opB(B) accumulated in T.  FP64 (T = double)
+// uses O; FP32 (T = float: operands and accumulation in FP32, as in the
+// reduced-precision forms) writes FP32 results for the next product and
+// widens the ones the FP64 LU consumes, with the terms that must stay exact
+// (the identity, b_1 A, 2P) added in FP64.
+//
+// The kernel is the same flat list of output tiles over problems x batch,
+// walked by a persistent grid, as the complex GEMM.  FP64 tiles are 32 x 32
+// (2 x 2 per thread; at n = 729 the ragged edge wastes 2 % against 11 % for
+// 64 x 64), FP32 tiles 64 x 64 (4 x 4 per thread, vector loads of the shared
+// tiles, so the FMA pipe and not shared memory is the limit).
+#include "lb_internal.cuh"
+
+#include <algorithm>
+
+namespace lb {
+
+namespace {
+
+template <typename T>
+struct RGroup {
+  RGemmProblem<T> p[4];
+  long long tile_start[5];
+  int tiles_m[4];
+  int tiles_n[4];
+  int nprob;
+};
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ double flip(double v, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)m);
+}
+__device__ __forceinline__ float flip(float v, unsigned long long m) {
+  return __int_as_float(__float_as_int(v) ^ (int)(m >> 32));
+}
+
+template <typename T, int TM>
+struct Vec;
+template <>
+struct Vec<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double* r) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    r[0] = v.x;
+    r[1] = v.y;
+  }
+};
+template <>
+struct Vec<double, 1> {
+  static __device__ __forceinline__ void ld(const double* p, double* r) { r[0] = p[0]; }
+};
+template <>
+struct Vec<double, 4> {
+  static __device__ __forceinline__ void ld(const double* p, double* r) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    r[0] = a.x;
+    r[1] = a.y;
+    r[2] = b.x;
+    r[3] = b.y;
+  }
+};
+template <>
+struct Vec<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float* r) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    r[0] = v.x;
+    r[1] = v.y;
+    r[2] = v.z;
+    r[3] = v.w;
+  }
+};
+template <>
+struct Vec<float, 8> {
+  static __device__ __forceinline__ void ld(const float* p, float* r) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    r[0] = a.x;
+    r[1] = a.y;
+    r[2] = a.z;
+    r[3] = a.w;
+    r[4] = b.x;
+    r[5] = b.y;
+    r[6] = b.z;
+    r[7] = b.w;
+  }
+};
+
+template <typename T, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    rgemm_kernel(const __grid_constant__ RGroup<T> g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int BK = 16;
+  __shared__ __align__(16) T As[BK][BM];
+  __shared__ __align__(16) T Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN);
+  const int ty = tid / (BN / TN);
+  const long long total = g.tile_start[g.nprob];
+
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    int pi = 0;
+    while (pi + 1 < g.nprob && t >= g.tile_start[pi + 1]) pi++;
+    const RGemmProblem<T>& P = g.p[pi];
+    const long long lt = t - g.tile_start[pi];
+    const int tpb = g.tiles_m[pi] * g.tiles_n[pi];
+    const long long b = lt / tpb;
+    const int r = (int)(lt - b * tpb);
+    const int tm = r / g.tiles_n[pi];
+    const int tn = r - tm * g.tiles_n[pi];
+    if (P.active != nullptr && P.active[b] <= P.active_iter) continue;
+    if (P.active_lo != nullptr && P.active_lo[b] > P.active_iter) continue;
+    const int m0 = tm * BM, n0 = tn * BN;
+    const T* __restrict__ A = P.A + b * P.sA;
+    const T* __restrict__ B = P.B + b * P.sB;
+    const int M = P.M, N = P.N, K = P.K;
+
+    // O_0 +- A B and nothing else (the LU updates): start the accumulators
+    // from O_0 and fold the sign into A, so the epilogue is a plain store.
+    const bool fastC = P.beta[0] == 1.0 && (P.alpha[0] == 1.0 || P.alpha[0] == -1.0) && P.nterms == 0 &&
+                       P.gamma[0] == 0.0 && P.O[0] != nullptr && P.Od[0] == nullptr && P.O[1] == nullptr &&
+                       P.Od[1] == nullptr;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        acc[i][j] = T(0);
+        if (fastC) {
+          const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
+          if (gm < M && gn < N) acc[i][j] = P.O[0][b * P.sC + (long long)gm * P.ldc + gn];
+        }
+      }
+    const unsigned long long aneg = (fastC && P.alpha[0] < 0.0) ? 0x8000000000000000ull : 0ull;
+    const T shA = T(P.shiftA), shB = T(P.shiftB);
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += NT) {  // A tile, k contiguous in memory
+        const int m = e / BK, k = e - (e / BK) * BK;
+        const int gm = m0 + m, gk = k0 + k;
+        T v = T(0);
+        if (gm < M && gk < K) {
+          v = A[(long long)gm * P.lda + gk];
+          if (gm == gk) v -= shA;
+        }
+        As[k][m] = flip(v, aneg);
+      }
+      if (!P.transB) {
+        for (int e = tid; e < BK * BN; e += NT) {
+          const int k = e / BN, c = e - (e / BN) * BN;
+          const int gk = k0 + k, gn = n0 + c;
+          T v = T(0);
+          if (gk < K && gn < N) {
+            v = B[(long long)gk * P.ldb + gn];
+            if (gk == gn) v -= shB;
+          }
+          Bs[k][c] = v;
+        }
+      } else {
+        for (int e = tid; e < BK * BN; e += NT) {
+          const int c = e / BK, k = e - (e / BK) * BK;
+          const int gk = k0 + k, gn = n0 + c;
+          T v = T(0);
+          if (gk < K && gn < N) {
+            v = B[(long long)gn * P.ldb + gk];
+            if (gk == gn) v -= shB;
+          }
+          Bs[k][c] = v;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; k++) {
+        T a[TM], bb[TN];
+        Vec<T, TM>::ld(&As[k][ty * TM], a);
+        Vec<T, TN>::ld(&Bs[k][tx * TN], bb);
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < TN; j++) acc[i][j] = fma_t(a[i], bb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int gm = m0 + ty * TM + i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        const int gn = n0 + tx * TN + j;
+        if (gn >= N) continue;
+        const long long off = (long long)gm * P.ldc + gn;
+        const long long idx = b * P.sC + off;
+        if (fastC) {
+          P.O[0][idx] = acc[i][j];
+          continue;
+        }
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+          if (P.O[w] == nullptr && P.Od[w] == nullptr) continue;
+          T v = T(P.alpha[w]) * acc[i][j];
+          if (P.beta[w] != 0.0 && P.O[w] != nullptr) v = fma_t(T(P.beta[w]), P.O[w][idx], v);
+          for (int q = 0; q < P.nterms; q++) v = fma_t(T(P.coef[w][q]), P.X[q][b * P.sX[q] + off], v);
+          if (gm == gn) v += T(P.gamma[w]);
+          if (P.O[w] != nullptr) P.O[w][idx] = v;
+          if (P.Od[w] != nullptr) {
+            double vd = double(v);
+            if (P.dcoef[w] != 0.0) vd = fma(P.dcoef[w], P.Xd[b * P.sXd + off], vd);
+            if (gm == gn) vd += P.dgamma[w];
+            P.Od[w][idx] = vd;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int TM, int TN>
+cudaError_t launch_rcfg(const RGemmProblem<T>* probs, int nprob, int sm_count, cudaStream_t st) {
+  RGroup<T> g;
+  g.nprob = nprob;
+  long long acc = 0;
+  for (int i = 0; i < nprob; i++) {
+    g.p[i] = probs[i];
+    g.tiles_m[i] = (probs[i].M + BM - 1) / BM;
+    g.tiles_n[i] = (probs[i].N + BN - 1) / BN;
+    g.tile_start[i] = acc;
+    if (probs[i].M > 0 && probs[i].N > 0 && probs[i].batch > 0)
+      acc += (long long)g.tiles_m[i] * g.tiles_n[i] * probs[i].batch;
+    else
+      g.tiles_m[i] = g.tiles_n[i] = 1;  // empty problem: zero tiles
+  }
+  for (int i = nprob; i <= 4; i++) g.tile_start[i] = acc;
+  if (acc == 0) return cudaSuccess;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  static int occ = -1;  // resident CTAs per SM for this configuration
+  if (occ < 0) {
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, rgemm_kernel<T, BM, BN, TM, TN>, NT, 0);
+    if (e != cudaSuccess) return e;
+    occ = std::max(1, o);
+  }
+  const long long grid = std::min<long long>(acc, (long long)sm_count * occ);
+  count_launch();
+  rgemm_kernel<T, BM, BN, TM, TN><<<(unsigned)grid, NT, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+long long rtiles(const RGemmProblem<T>* probs, int nprob, int BM, int BN) {
+  long long acc = 0;
+  for (int i = 0; i < nprob; i++)
+    if (probs[i].M > 0 && probs[i].N > 0)
+      acc += (long long)((probs[i].M + BM - 1) / BM) * ((probs[i].N + BN - 1) / BN) * probs[i].batch;
+  return acc;
+}
+
+template <typename T>
+TuneKey rshape_key(const RGemmProblem<T>* p, int np) {
+  TuneKey k{};
+  k[0] = 2;  // family: real GEMM
+  k[1] = sizeof(T) * 8;
+  k[2] = np;
+  for (int i = 0; i < np && i < 4; i++) {
+    k[3 + 5 * i] = p[i].M;
+    k[4 + 5 * i] = p[i].N;
+    k[5 + 5 * i] = p[i].K;
+    k[6 + 5 * i] = p[i].batch;
+    k[7 + 5 * i] = p[i].transB * 4 + (p[i].beta[0] != 0.0 ? 2 : 0) + (p[i].active != nullptr ? 1 : 0);
+  }
+  return k;
+}
+
+template <typename T>
+struct RArgs {
+  cudaError_t (*const* cands)(const RGemmProblem<T>*, int, int, cudaStream_t);
+  const RGemmProblem<T>* probs;
+  int nprob, sm_count;
+};
+
+template <typename T>
+cudaError_t rrun(int cand, const void* a, cudaStream_t st) {
+  const RArgs<T>* r = (const RArgs<T>*)a;
+  return r->cands[cand](r->probs, r->nprob, r->sm_count, st);
+}
+
+}  // namespace
+
+cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count, cudaStream_t st) {
+  if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
+  typedef cudaError_t (*fn)(const RGemmProblem<double>*, int, int, cudaStream_t);
+  static const fn cands[3] = {launch_rcfg<double, 16, 16, 1, 1>, launch_rcfg<double, 32, 32, 2, 2>,
+                              launch_rcfg<double, 64, 64, 4, 4>};
+  // 32 x 32 tiles when there are enough of them to balance the persistent
+  // grid, else 16 x 16
+  const long long t32 = rtiles(probs, nprob, 32, 32);
+  const RArgs<double> a{cands, probs, nprob, sm_count};
+  return tuned_launch(rshape_key(probs, nprob), 3, t32 >= 8LL * sm_count ? 1 : 0, rrun<double>, &a, st);
+}
+
+cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st) {
+  if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
+  typedef cudaError_t (*fn)(const RGemmProblem<float>*, int, int, cudaStream_t);
+  static const fn cands[2] = {launch_rcfg<float, 64, 64, 4, 4>, launch_rcfg<float, 128, 128, 8, 8>};
+  const long long t128 = rtiles(probs, nprob, 128, 128);
+  const RArgs<float> a{cands, probs, nprob, sm_count};
+  return tuned_launch(rshape_key(probs, nprob), 2, t128 >= 4LL * sm_count ? 1 : 0, rrun<float>, &a, st);
+}
+
+}  // namespace lb

@@ -48,6 +48,25 @@ cudaError_t set_smem_once(const void* kernel, size_t bytes) {
 }  // namespace lb
 
 namespace {
+cudaError_t accumulate_slot(lb_ctx* c, int r);
+}
+
+namespace lb {
+lb_status stage_events_begin(lb_ctx* c, cudaStream_t st, cudaEvent_t** ev_out) {
+  *ev_out = nullptr;
+  if (!c->timing) return LB_OK;
+  const int r = c->ring_next;
+  c->ring_next = (r + 1) % lb_ctx::kRing;
+  LB_CUDA(accumulate_slot(c, r));  // only waits if the ring has wrapped
+  cudaEvent_t* ev = c->ev_stage[r];
+  c->ring_used[r] = 1;
+  LB_CUDA(cudaEventRecord(ev[0], st));
+  *ev_out = ev;
+  return LB_OK;
+}
+}  // namespace lb
+
+namespace {
 
 // [13/13] Pade coefficients of exp from the recurrence of the closed form
 // b_j = (2m-j)! m! / ((2m)! j! (m-j)!):  b_j = b_{j-1} (m - j + 1) / (j (2m - j + 1)).
@@ -522,13 +541,9 @@ lb_status expm_chunk(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv,
   const double* b = c->pade_b;
   gemm_fn gemm = (prec == LB_FP64) ? zgemm_f64 : zgemm_f32;
   cudaEvent_t* ev = nullptr;
-  if (c->timing) {
-    const int r = c->ring_next;
-    c->ring_next = (r + 1) % lb_ctx::kRing;
-    LB_CUDA(accumulate_slot(c, r));  // only waits if the ring has wrapped
-    ev = c->ev_stage[r];
-    c->ring_used[r] = 1;
-    LB_CUDA(cudaEventRecord(ev[0], st));
+  {
+    lb_status r = stage_events_begin(c, st, &ev);
+    if (r != LB_OK) return r;
   }
   LB_CUDA(launch_slice_prepare(n, S, Lbase, Ldrv, u, dt, c->A, c->norm_bits, c->sc, c->kmix, s_out,
                                c->err_dev, c->sm_count, st));
@@ -645,7 +660,9 @@ lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const
   if (n < 1 || n > c->max_n || nslices < 0) return LB_EINVAL;
   if (Ldrv != nullptr && u == nullptr) return LB_EINVAL;
   if (!std::isfinite(dt)) return LB_EINVAL;
-  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
+  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && !herm) return LB_EINVAL;
+  if (herm && !is_square(n, nullptr)) return LB_EINVAL;
   if (nslices == 0) return LB_OK;
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -658,8 +675,10 @@ lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const
   for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
     const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
     const z64* Lb = (const z64*)Lbase + (Ldrv == nullptr ? s0 * nn : 0);
-    lb_status r = expm_chunk(c, n, S, Lb, (const z64*)Ldrv, u ? u + s0 : nullptr, dt, prec,
-                             (z64*)P_out + s0 * nn, s_out ? s_out + s0 : nullptr, st);
+    lb_status r = herm ? expm_chunk_herm(c, n, S, Lb, (const z64*)Ldrv, u ? u + s0 : nullptr, dt, prec,
+                                         (z64*)P_out + s0 * nn, s_out ? s_out + s0 : nullptr, st)
+                       : expm_chunk(c, n, S, Lb, (const z64*)Ldrv, u ? u + s0 : nullptr, dt, prec,
+                                    (z64*)P_out + s0 * nn, s_out ? s_out + s0 : nullptr, st);
     if (r != LB_OK) return r;
   }
   return LB_OK;
@@ -672,7 +691,10 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   int d = 0;
   if (n < 1 || n > c->max_n || !is_square(n, &d)) return LB_EINVAL;
   if (nslices < 0 || steps_per_slice < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
-  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN) return LB_EINVAL;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN &&
+      prec != LB_FP32_HERMITIAN)
+    return LB_EINVAL;
+  if (prec == LB_FP32_HERMITIAN) prec = LB_FP32;  // the propagation of the FP32 forms is the same
   if (nslices == 0 || steps_per_slice == 0) return LB_OK;
   DeviceGuard g(c->device);
   return lb::propagate_impl(c, n, nslices, (const z64*)P, steps_per_slice, B, (z64*)states, prec, renorm_trace,
@@ -704,7 +726,7 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
       }
       return LB_OK;
     }
-    prec = LB_FP64;  // the complex product is exact for every state
+    return propagate_herm_large(c, n, nslices, Pz, steps_per_slice, B, X, st);
   }
   if (prec == LB_FP64) {
     const bool gemv = gemv_f64_preferred(n, B);

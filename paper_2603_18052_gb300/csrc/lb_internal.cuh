@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <array>
 #include <cstdint>
 #include <cstddef>
 
@@ -147,6 +148,36 @@ struct ZGemmProblem {
 // Launch up to 4 problems in one grouped launch.  Returns a CUDA error code.
 cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st);
 
+// Grouped, batched REAL GEMM (k_rgemm.cu), FP64 (T = double) or FP32
+// (T = float: FP32 operands and accumulation), for the real-coordinate forms:
+//   r_w  = alpha[w] acc + beta[w] O_w(old) + sum_t coef[w][t] X_t + gamma[w] I   (in T)
+//   O_w  = r_w (when O[w] != null);  Od_w = double(r_w) + dcoef[w] Xd + dgamma[w] I (when Od[w] != null)
+// acc = (A - shiftA I)(B - shiftB I) or (A - shiftA I)(B - shiftB I)^T (transB),
+// row-major; every output and term has leading dimension ldc and batch stride
+// sC (sX[t], sXd for the terms).  Batch element b is skipped when
+// active[b] <= active_iter or active_lo[b] > active_iter.
+template <typename T>
+struct RGemmProblem {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const T* A = nullptr; long long lda = 0, sA = 0;
+  const T* B = nullptr; long long ldb = 0, sB = 0; int transB = 0;
+  long long ldc = 0, sC = 0;
+  T* O[2] = {nullptr, nullptr};
+  double* Od[2] = {nullptr, nullptr};
+  double alpha[2] = {1.0, 1.0}, beta[2] = {0.0, 0.0}, gamma[2] = {0.0, 0.0};
+  int nterms = 0;
+  const T* X[3] = {nullptr, nullptr, nullptr};
+  long long sX[3] = {0, 0, 0};
+  double coef[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  const double* Xd = nullptr; long long sXd = 0;
+  double dcoef[2] = {0.0, 0.0}, dgamma[2] = {0.0, 0.0};
+  const int* active = nullptr; int active_iter = 0;
+  const int* active_lo = nullptr;
+  double shiftA = 0.0, shiftB = 0.0;
+};
+cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count, cudaStream_t st);
+cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st);
+
 // Few-state FP64 products (k_gemv.cu), B <= kGemvMaxB:
 //   V[b][i] = alpha sum_j A[i][j] X[b][j];  Yacc[b][i] += the same (Yacc may be null)
 constexpr int kGemvMaxB = 8;
@@ -205,8 +236,16 @@ cudaError_t launch_prop_herm_resident(int n, int d, int nslices, const double* R
 // for a non-finite a or more than 65536 sub-steps.
 bool taylor_parameters(double a, int* m_out, int* s_out);
 
-// Autotuner: in tuning mode every GEMM launch times its candidate tile
-// configurations and records the fastest for its shape (see k_gemm.cu).
+// Autotuner shared by the GEMM families (k_gemm.cu).  A launch shape key
+// (family, precision, every problem's sizes and flags) and a launcher of
+// candidate tile configuration `cand`.  In tuning mode, which set_tuning
+// switches for the CALLING HOST THREAD only, a launch runs and times every
+// candidate and records the fastest for its shape; otherwise a recorded shape
+// uses its record and other shapes the caller's heuristic.
+typedef std::array<long long, 24> TuneKey;
+typedef cudaError_t (*TuneCand)(int cand, const void* args, cudaStream_t st);
+cudaError_t tuned_launch(const TuneKey& key, int ncand, int heuristic, TuneCand run, const void* args,
+                         cudaStream_t st);
 void set_tuning(bool on);
 int tuned_shapes();
 
@@ -226,6 +265,38 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
                                  double dt, z64* A, unsigned long long* norm_bits, int* sc,
                                  int* kmix, int* s_out, unsigned int* err, int sm_count,
                                  cudaStream_t st);
+
+// sc[s] = max(0, ceil(log2(norm_s / theta))) from norm_bits[s] (and kmix, s_out,
+// the maximum into sc[S], as launch_slice_prepare does).
+cudaError_t launch_squaring_count(int S, const unsigned long long* norm_bits, int* sc, int* kmix, int* s_out,
+                                  unsigned int* err, cudaStream_t st);
+
+// ------------------------------------------- real-coordinate build (k_real.cu)
+// A_s = (Gb + u_s Gd) dt / 2^sc[s] on the real coordinates (Gd == null: Gb
+// holds S generators); per-slice 1-norms, squaring counts as above.
+cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const double* Gd, const double* u, double dt,
+                                      double* A, unsigned long long* norm_bits, int* sc, int* kmix, int* s_out,
+                                      unsigned int* err, int sm_count, cudaStream_t st);
+template <typename T>
+cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, const T* X2, double c0, double c1,
+                                 double c2, T* Z, int sm_count, cudaStream_t st);
+// dst = float(src - shift I), S n x n matrices
+cudaError_t launch_real_to_f32(int n, int S, const double* src, double shift, float* dst, int sm_count,
+                               cudaStream_t st);
+cudaError_t launch_real_copy_active(long long nn, int S, const double* src, double* dst, const int* active, int iter,
+                                    int sm_count, cudaStream_t st);
+// P[s] (complex superoperator) from R[s] (its real-coordinate matrix)
+cudaError_t launch_herm_to_complex(int n, int d, int S, const double* R, z64* P, int sm_count, cudaStream_t st);
+cudaError_t launch_lu_diag_real(int n, int S, int k0, int kb, const double* M, double* Uf, double* Linv,
+                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st);
+// The real-coordinate propagator build (lb_expm_pade with a Hermitian
+// precision) and the real-coordinate propagation for n > 81 (lb_real.cu).
+lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
+                          lb_precision prec, z64* P, int* s_out, cudaStream_t st);
+lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
+                               cudaStream_t st);
+// Stage-timer events of one build chunk (null when timing is off).
+lb_status stage_events_begin(lb_ctx* c, cudaStream_t st, cudaEvent_t** ev_out);
 
 // Elementwise linear combinations used by the Pade step.
 // Z[b] = c0*X0[b] + c1*X1[b] + c2*X2[b]  (n x n each, batch strides = n*n)

@@ -1,0 +1,329 @@
+// Host orchestration of the real-coordinate ("Hermitian") forms: the
+// propagator build of Algorithm 1 and, for n > 81, the propagation chain of
+// Algorithm 2 on the n = d^2 real coordinates of Hermitian matrices.
+//
+// Every Lindbladian maps Hermitian matrices to Hermitian matrices, and so do
+// its exponential and every polynomial in it.  On the real coordinates
+// c = (rho_kk; Re rho_kl, Im rho_kl for k < l) a Hermiticity-preserving
+// superoperator is a real n x n matrix (k_herm.cu builds it from the complex
+// one), and because that correspondence is an algebra map (it takes sums to
+// sums, products to products and I to I) Algorithm 1 run on G = the real form
+// of L dt gives the real form of exp(L dt).  The build here therefore forms
+// the real generators, runs the scaling, the six Pade products, the LU
+// factorisation and solve of (V - U) R = (V + U) and the squarings on real
+// matrices, and rebuilds the complex P from R at the end.  A real
+// multiply-add is one FMA instead of four (three in the Gauss form of the
+// complex GEMM), which is what bounds the build on GB300's FP64 pipe.
+// The scaling parameter s is taken from ||G||_1 on these coordinates.
+#include "lb_internal.cuh"
+
+namespace lb {
+
+namespace {
+
+int nblocks_r(int n) { return (n + kLuNb - 1) / kLuNb; }
+
+RGemmProblem<double> rsq(int n, int S, const double* A, const double* B, double* C) {
+  RGemmProblem<double> p;
+  const long long nn = (long long)n * n;
+  p.M = p.N = p.K = n;
+  p.batch = S;
+  p.A = A; p.lda = n; p.sA = nn;
+  p.B = B; p.ldb = n; p.sB = nn;
+  p.ldc = n; p.sC = nn;
+  p.O[0] = C;
+  return p;
+}
+
+RGemmProblem<float> fsq(int n, int S, const float* A, const float* B, float* C) {
+  RGemmProblem<float> p;
+  const long long nn = (long long)n * n;
+  p.M = p.N = p.K = n;
+  p.batch = S;
+  p.A = A; p.lda = n; p.sA = nn;
+  p.B = B; p.ldb = n; p.sB = nn;
+  p.ldc = n; p.sC = nn;
+  p.O[0] = C;
+  return p;
+}
+
+// C -= L_panel U_panel style update: C(M x N, ldc) += alpha A(M x K) B(K x N)
+RGemmProblem<double> rupd(int M, int N, int K, const double* A, long long lda, long long sA, const double* B,
+                          long long ldb, long long sB, double* C, long long ldc, long long sC, double alpha,
+                          double beta, int S) {
+  RGemmProblem<double> p;
+  p.M = M; p.N = N; p.K = K; p.batch = S;
+  p.A = A; p.lda = lda; p.sA = sA;
+  p.B = B; p.ldb = ldb; p.sB = sB;
+  p.ldc = ldc; p.sC = sC;
+  p.O[0] = C;
+  p.alpha[0] = alpha;
+  p.beta[0] = beta;
+  return p;
+}
+
+// Blocked LU (no pivot search, left-looking) of the real Mx[s] and solve for
+// the n columns of N[s]:  N <- Mx^{-1} N.  Uf (U), Lp (L) and Y are n x n
+// per-slice scratch.  The same schedule as the complex form: at block step
+// k one grouped GEMM brings block row k, block column k and the right-hand
+// sides' block row up to date with all previous blocks (K = 32 k), the
+// diagonal block is factored and inverted in shared memory, and the panels
+// follow from the block inverses; the back substitution is left-looking too.
+lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, double* Uf, double* Y, double* Lp,
+                                cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  const int nb = kLuNb, nbk = nblocks_r(n);
+  const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
+  double* Linv = (double*)c->Linv;
+  double* Uinv = (double*)c->Uinv;
+  for (int k = 0; k < nbk; k++) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, rest = n - k0 - kb;
+    double* Uinv_k = Uinv + (long long)k * nb * nb;
+    if (k0 > 0) {
+      RGemmProblem<double> pr[3];
+      int np = 0;
+      // block row k:  Mx[k0:k0+kb, k0:] -= L[k0:k0+kb, :k0] U[:k0, k0:]
+      pr[np++] = rupd(kb, n - k0, k0, Lp + (long long)k0 * n, n, nn, Uf + k0, n, nn, Mx + (long long)k0 * n + k0, n,
+                      nn, -1.0, 1.0, S);
+      // block column k below the diagonal
+      if (rest > 0)
+        pr[np++] = rupd(rest, kb, k0, Lp + (long long)(k0 + kb) * n, n, nn, Uf + k0, n, nn,
+                        Mx + (long long)(k0 + kb) * n + k0, n, nn, -1.0, 1.0, S);
+      // right-hand sides, block row k:  N[k0:k0+kb, :] -= L[k0:k0+kb, :k0] Y[:k0, :]
+      pr[np++] = rupd(kb, n, k0, Lp + (long long)k0 * n, n, nn, Y, n, nn, N + (long long)k0 * n, n, nn, -1.0, 1.0, S);
+      LB_CUDA(rgemm_f64(pr, np, c->sm_count, st));
+    }
+    LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st));
+    RGemmProblem<double> pr[3];
+    int np = 0;
+    if (rest > 0) {
+      // U[k0:k0+kb, k0+kb:] = Linv_k Mx[k0:k0+kb, k0+kb:]
+      pr[np++] = rupd(kb, rest, kb, Linv, nb, sLinv, Mx + (long long)k0 * n + k0 + kb, n, nn,
+                      Uf + (long long)k0 * n + k0 + kb, n, nn, 1.0, 0.0, S);
+      // L[k0+kb:, k0:k0+kb] = Mx[k0+kb:, k0:k0+kb] Uinv_k
+      pr[np++] = rupd(rest, kb, kb, Mx + (long long)(k0 + kb) * n + k0, n, nn, Uinv_k, nb, sUinv,
+                      Lp + (long long)(k0 + kb) * n + k0, n, nn, 1.0, 0.0, S);
+    }
+    // Y[k0:k0+kb, :] = Linv_k N[k0:k0+kb, :]
+    pr[np++] = rupd(kb, n, kb, Linv, nb, sLinv, N + (long long)k0 * n, n, nn, Y + (long long)k0 * n, n, nn, 1.0, 0.0,
+                    S);
+    LB_CUDA(rgemm_f64(pr, np, c->sm_count, st));
+  }
+  // back substitution: X_k = Uinv_k (Y_k - U[k0:k0+kb, k0+kb:] X[k0+kb:]), X into N
+  for (int k = nbk - 1; k >= 0; k--) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, rest = n - k0 - kb;
+    double* Uinv_k = Uinv + (long long)k * nb * nb;
+    if (rest > 0) {
+      RGemmProblem<double> g = rupd(kb, n, rest, Uf + (long long)k0 * n + k0 + kb, n, nn, N + (long long)(k0 + kb) * n,
+                                    n, nn, Y + (long long)k0 * n, n, nn, -1.0, 1.0, S);
+      LB_CUDA(rgemm_f64(&g, 1, c->sm_count, st));
+    }
+    RGemmProblem<double> f =
+        rupd(kb, n, kb, Uinv_k, nb, sUinv, Y + (long long)k0 * n, n, nn, N + (long long)k0 * n, n, nn, 1.0, 0.0, S);
+    LB_CUDA(rgemm_f64(&f, 1, c->sm_count, st));
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
+lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
+                          lb_precision prec, z64* P, int* s_out, cudaStream_t st) {
+  int d = 1;
+  while (d * d < n) d++;
+  const long long nn = (long long)n * n;
+  const double* b = c->pade_b;
+  cudaEvent_t* ev = nullptr;
+  {
+    lb_status r = stage_events_begin(c, st, &ev);
+    if (r != LB_OK) return r;
+  }
+  double* Ar = (double*)c->A;
+  double* Mx = (double*)c->Mx;
+  double* N = (double*)c->Z1;  // right-hand sides, then the solution R, then the squarings
+  double* T2 = (double*)c->Z2; // squaring products (FP64)
+  // the real generators: G_base, G_drv (or the S generators) in V's buffer
+  double* Gb = (double*)c->V;
+  double* Gd = nullptr;
+  if (Ldrv != nullptr) {
+    Gd = Gb + nn;
+    LB_CUDA(launch_herm_matrix(n, d, 1, Lbase, Gb, c->sm_count, st));
+    LB_CUDA(launch_herm_matrix(n, d, 1, Ldrv, Gd, c->sm_count, st));
+  } else {
+    LB_CUDA(launch_herm_matrix(n, d, S, Lbase, Gb, c->sm_count, st));
+  }
+  LB_CUDA(launch_real_slice_prepare(n, S, Gb, Gd, u, dt, Ar, c->norm_bits, c->sc, c->kmix, s_out, c->err_dev,
+                                    c->sm_count, st));
+  if (c->max_squarings < 0) {
+    LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaEventRecord(c->ev_scmax, st));
+  } else {
+    LB_CUDA(launch_check_bound(c->sc + S, c->max_squarings, c->err_dev, st));
+  }
+  if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
+  if (prec == LB_FP64_HERMITIAN) {
+    double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
+           *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
+    RGemmProblem<double> p = rsq(n, S, Ar, Ar, A2);
+    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    p = rsq(n, S, A2, A2, A4);
+    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    // A6 = A4 A2, and Z1 = b12 A6 + b10 A4 + b8 A2 from the same accumulators
+    p = rsq(n, S, A4, A2, A6);
+    p.O[1] = Z1;
+    p.alpha[1] = b[12];
+    p.nterms = 2;
+    p.X[0] = A4; p.X[1] = A2;
+    p.sX[0] = p.sX[1] = nn;
+    p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
+    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
+    // V = A6 Z1 + b6 A6 + b4 A4 + b2 A2 + b0 I;  W = A6 Z2 + b7 A6 + b5 A4 + b3 A2 + b1 I
+    RGemmProblem<double> vw[2];
+    for (int i = 0; i < 2; i++) {
+      vw[i] = rsq(n, S, A6, i == 0 ? Z1 : Z2, i == 0 ? V : W);
+      vw[i].nterms = 3;
+      vw[i].X[0] = A6; vw[i].X[1] = A4; vw[i].X[2] = A2;
+      vw[i].sX[0] = vw[i].sX[1] = vw[i].sX[2] = nn;
+    }
+    vw[0].coef[0][0] = b[6]; vw[0].coef[0][1] = b[4]; vw[0].coef[0][2] = b[2]; vw[0].gamma[0] = b[0];
+    vw[1].coef[0][0] = b[7]; vw[1].coef[0][1] = b[5]; vw[1].coef[0][2] = b[3]; vw[1].gamma[0] = b[1];
+    LB_CUDA(rgemm_f64(vw, 2, c->sm_count, st));
+    // U = A W:  Mx = V - U, N = V + U
+    p = rsq(n, S, Ar, W, Mx);
+    p.alpha[0] = -1.0;
+    p.O[1] = N;
+    p.nterms = 1;
+    p.X[0] = V; p.sX[0] = nn;
+    p.coef[0][0] = 1.0; p.coef[1][0] = 1.0;
+    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+  } else {
+    // FP32 products (operands and accumulation in FP32), every intermediate
+    // kept in FP32; the FP64 LU inputs V - U and V + U are widened with the
+    // identity and b1 A added in FP64, so the FP32 rounding touches only the
+    // O(A^2) parts.
+    const long long fl = nn * S;
+    float* f0 = (float*)c->Z2;
+    float *Af = f0, *A2f = f0 + fl, *A4f = f0 + 2 * fl, *A6f = f0 + 3 * fl;
+    float* f1 = (float*)c->W;
+    float *Z1f = f1, *Z2f = f1 + fl, *Vsf = f1 + 2 * fl, *Wsf = f1 + 3 * fl;
+    LB_CUDA(launch_real_to_f32(n, S, Ar, 0.0, Af, c->sm_count, st));
+    RGemmProblem<float> p = fsq(n, S, Af, Af, A2f);
+    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    p = fsq(n, S, A2f, A2f, A4f);
+    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    p = fsq(n, S, A4f, A2f, A6f);
+    p.O[1] = Z1f;
+    p.alpha[1] = b[12];
+    p.nterms = 2;
+    p.X[0] = A4f; p.X[1] = A2f;
+    p.sX[0] = p.sX[1] = nn;
+    p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
+    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    LB_CUDA(launch_real_lincomb3<float>(fl, A6f, A4f, A2f, b[13], b[11], b[9], Z2f, c->sm_count, st));
+    RGemmProblem<float> vw[2];
+    for (int i = 0; i < 2; i++) {
+      vw[i] = fsq(n, S, A6f, i == 0 ? Z1f : Z2f, i == 0 ? Vsf : Wsf);
+      vw[i].nterms = 3;
+      vw[i].X[0] = A6f; vw[i].X[1] = A4f; vw[i].X[2] = A2f;
+      vw[i].sX[0] = vw[i].sX[1] = vw[i].sX[2] = nn;
+    }
+    vw[0].coef[0][0] = b[6]; vw[0].coef[0][1] = b[4]; vw[0].coef[0][2] = b[2];
+    vw[1].coef[0][0] = b[7]; vw[1].coef[0][1] = b[5]; vw[1].coef[0][2] = b[3];
+    LB_CUDA(rgemm_f32(vw, 2, c->sm_count, st));
+    // acc = A Ws:  V - U = b0 I + Vs - b1 A - acc,  V + U = b0 I + Vs + b1 A + acc
+    p = fsq(n, S, Af, Wsf, nullptr);
+    p.O[0] = nullptr;
+    p.Od[0] = Mx; p.Od[1] = N;
+    p.alpha[0] = -1.0; p.alpha[1] = 1.0;
+    p.nterms = 1;
+    p.X[0] = Vsf; p.sX[0] = nn;
+    p.coef[0][0] = 1.0; p.coef[1][0] = 1.0;
+    p.Xd = Ar; p.sXd = nn;
+    p.dcoef[0] = -b[1]; p.dcoef[1] = b[1];
+    p.dgamma[0] = b[0]; p.dgamma[1] = b[0];
+    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+  }
+  if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
+  // (V - U) R = (V + U), FP64.  U, Y, L reuse A2, A4, A6.
+  {
+    lb_status r = lu_solve_blocked_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6, st);
+    if (r != LB_OK) return r;
+  }
+  if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
+  int smax = c->max_squarings;
+  if (smax < 0) {
+    LB_CUDA(cudaEventSynchronize(c->ev_scmax));
+    smax = *c->scmax_host;
+  }
+  // squarings; in the FP32 form the leading ones, whose operand is still
+  // near I (kmix[s] of them), run as R^2 = 2R - I + D D with D = R - I and
+  // only D D in FP32; the rest are FP64
+  for (int it = 0; it < smax; it++) {
+    RGemmProblem<double> q = rsq(n, S, N, N, T2);
+    q.active = c->sc;
+    q.active_iter = it;
+    if (prec == LB_FP32_HERMITIAN) {
+      float* Df = (float*)c->V;
+      LB_CUDA(launch_real_to_f32(n, S, N, 1.0, Df, c->sm_count, st));
+      RGemmProblem<float> m = fsq(n, S, Df, Df, nullptr);
+      m.O[0] = nullptr;
+      m.Od[0] = T2;
+      m.Xd = N; m.sXd = nn;
+      m.dcoef[0] = 2.0;
+      m.dgamma[0] = -1.0;
+      m.active = c->kmix;
+      m.active_iter = it;
+      LB_CUDA(rgemm_f32(&m, 1, c->sm_count, st));
+      q.active_lo = c->kmix;
+    }
+    LB_CUDA(rgemm_f64(&q, 1, c->sm_count, st));
+    LB_CUDA(launch_real_copy_active(nn, S, T2, N, c->sc, it, c->sm_count, st));
+  }
+  if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
+  LB_CUDA(launch_herm_to_complex(n, d, S, N, P, c->sm_count, st));
+  LB_CUDA(launch_check_finite(nn * S, P, c->err_dev, st));
+  if (ev) LB_CUDA(cudaEventRecord(ev[5], st));
+  return LB_OK;
+}
+
+// FP64 propagation on the real coordinates for n > 81: the real matrices R_s
+// of a chunk of slices (built from P), the states' coordinates in two
+// ping-pong buffers, one real product per step (a few-state product for
+// B <= 8), and the states written back exactly Hermitian.
+lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
+                               cudaStream_t st) {
+  int d = 1;
+  while (d * d < n) d++;
+  const long long nn = (long long)n * n;
+  double* R = (double*)c->Z1;
+  double* cur = (double*)c->Rtmp;
+  double* nxt = cur + (long long)B * n;
+  LB_CUDA(launch_herm_coords_in(n, d, B, X, cur, c->sm_count, st));
+  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
+    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+    LB_CUDA(launch_herm_matrix(n, d, S, P + s0 * nn, R, c->sm_count, st));
+    for (int s = 0; s < S; s++)
+      for (int t = 0; t < steps_per_slice; t++) {
+        if (B <= kGemvMaxB) {
+          LB_CUDA(launch_dgemv_f64(n, B, R + s * nn, n, cur, n, nxt, n, 1.0, nullptr, 0, st));
+        } else {
+          // next[b][a] = sum_k R_s[a][k] cur[b][k]  ->  next = cur R_s^T
+          RGemmProblem<double> q;
+          q.M = B; q.N = n; q.K = n;
+          q.A = cur; q.lda = n;
+          q.B = R + s * nn; q.ldb = n; q.transB = 1;
+          q.ldc = n;
+          q.O[0] = nxt;
+          LB_CUDA(rgemm_f64(&q, 1, c->sm_count, st));
+        }
+        double* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+  }
+  LB_CUDA(launch_herm_coords_out(n, d, B, cur, X, c->sm_count, st));
+  return LB_OK;
+}
+
+}  // namespace lb

@@ -14,8 +14,9 @@ import torch
 
 from . import _build
 
-LB_FP64, LB_FP32, LB_BF16X3, LB_FP64_HERMITIAN = 0, 1, 2, 3
-PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3, "fp64_hermitian": LB_FP64_HERMITIAN}
+LB_FP64, LB_FP32, LB_BF16X3, LB_FP64_HERMITIAN, LB_FP32_HERMITIAN = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3, "fp64_hermitian": LB_FP64_HERMITIAN,
+              "fp32_hermitian": LB_FP32_HERMITIAN}
 
 _STATUS = {
     0: "LB_OK",
@@ -66,6 +67,10 @@ EXPORTED = (
     "lb_probe_copy",
     "lb_probe_read",
     "lb_probe_alloc",
+    "lb_probe_dfma",
+    "lb_probe_ffma",
+    "lb_probe_dmma",
+    "lb_probe_bf16_tc",
 )
 
 
@@ -175,6 +180,9 @@ def lib():
     L.lb_probe_alloc.argtypes = [ll, i32, ctypes.POINTER(ctypes.c_double)]
     L.lb_probe_read.restype = i32
     L.lb_probe_read.argtypes = [vp, ll, i32, vp, vp]
+    for name in ("lb_probe_dfma", "lb_probe_ffma", "lb_probe_dmma", "lb_probe_bf16_tc"):
+        getattr(L, name).restype = i32
+        getattr(L, name).argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     del ip, dp
     _lib = L
     return L
@@ -374,6 +382,10 @@ def lb_propagate_batch_static(P, states, steps_per_slice=1, stream=None):
     c128 = torch.complex128
     S, n = P.shape[0], P.shape[1]
     B = states.shape[0]
+    cur = torch.cuda.current_device()
+    for t, what in ((P, "P"), (states, "states")):
+        if t.is_cuda and t.device.index != cur:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (what, t.device.index, cur))
     _check(lib().lb_propagate_batch_static(n, S, _ptr(P, c128, "P", (S, n, n)), int(steps_per_slice), B,
                                            _ptr(states, c128, "states", (B, n)), _stream(stream)),
            "lb_propagate_batch_static")
@@ -495,6 +507,32 @@ def lb_probe_copy(host, device, to_device, reps=20, stream=None):
     _check(lib().lb_probe_copy(ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(device.data_ptr()), nb,
                                int(bool(to_device)), int(reps), ctypes.byref(us), _stream(stream)), "lb_probe_copy")
     return us.value
+
+
+def _peak(name, stream):
+    tf = ctypes.c_double(0.0)
+    _check(getattr(lib(), name)(ctypes.byref(tf), _stream(stream)), name)
+    return tf.value
+
+
+def lb_probe_dfma(stream=None):
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    return _peak("lb_probe_dfma", stream)
+
+
+def lb_probe_ffma(stream=None):
+    """Measured FP32 FMA rate of the current device, TFLOP/s."""
+    return _peak("lb_probe_ffma", stream)
+
+
+def lb_probe_dmma(stream=None):
+    """Measured FP64 tensor-core (mma.sync m8n8k4) rate, TFLOP/s."""
+    return _peak("lb_probe_dmma", stream)
+
+
+def lb_probe_bf16_tc(stream=None):
+    """Measured BF16 tcgen05 MMA rate (dense, FP32 accumulation), TFLOP/s."""
+    return _peak("lb_probe_bf16_tc", stream)
 
 
 def lb_probe_alloc(nbytes, reps=20):

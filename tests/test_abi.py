@@ -58,6 +58,8 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_propagate_fixed(15, 9, None, 1, 1, vp(8), None) == 1
     assert L.lb_propagate_fixed(16, 9, vp(8), 1, 1, vp(8), None) == 1  # only Q1.15 and Q1.31
     assert L.lb_propagate_fixed(15, 100, vp(8), 1, 1, vp(8), None) == 1  # n above 81
+    for probe in (L.lb_probe_dfma, L.lb_probe_ffma, L.lb_probe_dmma, L.lb_probe_bf16_tc):
+        assert probe(None, None) == 1
     assert L.lb_propagate_fixed(15, 8, vp(8), 1, 1, vp(8), None) == 1  # n not a square
     assert L.lb_fixed_quantize(15, 4, None, vp(8), None) == 1
     assert L.lb_fixed_dequantize(7, 4, vp(8), vp(8), None) == 1

@@ -40,3 +40,18 @@ def test_counts_by_brute_force():
     assert 8 * subst == pytest.approx(8 * n ** 3, rel=0.04)
     assert A.build_flops_fp64_solve(n) == pytest.approx(8 * n ** 3 / 3 + 8 * n ** 3)
     assert A.build_flops(n, 2) == pytest.approx(8 * 8 * n ** 3 + A.build_flops_fp64_solve(n))
+
+
+def test_real_coordinate_counts_by_brute_force():
+    """A real multiply-add is 2 FLOPs: the real-coordinate state-step is n^2
+    of them, and the real build counts the same multiply-adds as the complex
+    one at 2 FLOPs each (a quarter of the complex count)."""
+    for n in (1, 4, 9):
+        assert A.state_step_flops_real(n) == 2 * sum(1 for _ in range(n) for _ in range(n))
+        assert 4 * A.state_step_flops_real(n) == A.state_step_flops(n)
+    n = 30
+    lu = sum((n - k - 1) ** 2 for k in range(n))
+    subst = sum(k for k in range(n)) * n * 2
+    assert 2 * (lu + subst) == pytest.approx(A.build_flops_real_solve(n), rel=0.06)
+    for s in (0, 1, 6):
+        assert 4 * A.build_flops_real(n, s) == pytest.approx(A.build_flops(n, s))

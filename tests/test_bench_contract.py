@@ -31,3 +31,12 @@ def test_reference_arm_and_flags(bench, monkeypatch):
 def test_metric_names_the_workload(bench):
     assert "state-steps/s" in bench.METRIC and "d=27" in bench.METRIC
     assert bench.WORKLOAD == "d27_chain"
+
+
+def test_headline_form_is_fp64(bench):
+    """The recorded value is an all-FP64 form; the reduced-precision forms
+    are reported under "mixed"."""
+    assert bench.HEADLINE in bench.FORMS and bench.DTYPES[bench.HEADLINE] == "f64"
+    assert bench.FORMS[bench.HEADLINE][:2] == ("fp64_hermitian", "fp64_hermitian")
+    for f in bench.MIXED_FORMS:
+        assert f in bench.FORMS and bench.DTYPES[f] != "f64"

@@ -3,7 +3,9 @@ times (200 slices of 729 x 729 propagators, 256 states, one step per slice):
 sampled propagators against the oracle's Pade route, sampled final states
 against the oracle's Taylor route carried through all 200 slices (it needs
 no dense propagator, so it finishes in seconds), and properties of every
-state (trace and Hermiticity) in each of the three forms."""
+state (trace and Hermiticity) in each of the bench's five forms.  The
+reduced forms are also run for the 1000 steps their stated bounds refer to
+(16 states, five steps per slice through the 200 slices)."""
 
 import numpy as np
 import pytest
@@ -23,6 +25,12 @@ SAMPLED_STATES = (0, 255)
 # 1e-5 for FP32 and 1e-4 for split-BF16), trace and Hermiticity error
 TOL = {"fp64": (1e-12, 1e-12, 1e-12, 1e-12), "fp32": (1e-6, 1e-5, 1e-6, 1e-5),
        "bf16x3": (1e-6, 1e-4, 1e-6, 1e-4)}
+TOL["fp64_hermitian"] = TOL["fp64"]
+TOL["fp32_hermitian"] = TOL["fp32"]
+# the bench's forms: (build precision, propagation precision, trace renormalisation)
+FORMS = {"fp64_hermitian": ("fp64_hermitian", "fp64_hermitian", False), "fp64": ("fp64", "fp64", False),
+         "fp32_hermitian": ("fp32_hermitian", "fp32", True), "bf16x3": ("bf16x3", "bf16x3", True),
+         "fp32": ("fp32", "fp32", True)}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +50,7 @@ def full():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "fp64"])
+@pytest.mark.parametrize("prec", sorted(FORMS))
 def test_full_chain(full, prec):
     lb, w, P_ref, X_ref, ctx = full
     dev = torch.device("cuda:0")
@@ -56,9 +64,10 @@ def test_full_chain(full, prec):
     lb.lb_assemble(ctx, put(w["H0"]), put(w["jumps"]), Lbd)
     lb.lb_assemble(ctx, put(w["X"]), None, Ldd)
     P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
-    lb.lb_expm_pade(ctx, Lbd, Ldd, put(w["u"]), w["dt"], P, prec=prec)
+    pb, pp, renorm = FORMS[prec]
+    lb.lb_expm_pade(ctx, Lbd, Ldd, put(w["u"]), w["dt"], P, prec=pb)
     R = put(w["states"])
-    lb.lb_propagate_batch(ctx, P, R, steps_per_slice=1, prec=prec, renorm_trace=prec != "fp64")
+    lb.lb_propagate_batch(ctx, P, R, steps_per_slice=1, prec=pp, renorm_trace=renorm)
     lb.lb_sync_status(ctx)
     tp, tx, tt, th = TOL[prec]
     for s, ref in P_ref.items():
@@ -76,6 +85,31 @@ def test_full_chain(full, prec):
     # the form's bound (the FP64 bound is the stated -1e-12)
     lam = np.linalg.eigvalsh(0.5 * (rho + np.conj(np.transpose(rho, (0, 2, 1)))))
     assert np.min(lam) >= -tx, (prec, np.min(lam))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp32_hermitian", 1e-5), ("bf16x3", 1e-4)])
+def test_reduced_forms_1000_steps_d27(full, prec, tol):
+    """The reduced forms over the 1000 steps their bounds are stated for:
+    16 states, each of the 200 slices applied five times (propagators built
+    in the form, trace renormalised), against the oracle's Taylor route with
+    each slice's generator times five (exp(5 A) = exp(A)^5); max over the
+    states of ||rho - rho_ref||_F <= 1e-5 (FP32) and 1e-4 (split-BF16)."""
+    lb, w, _, _, ctx = full
+    dev = torch.device("cuda:0")
+    n, S = w["n"], w["nslices"]
+    B, m = 16, 5
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Lb = O.lindbladian(w["H0"], w["jumps"])
+    Ld = O.drive_generator(w["X"])
+    X_ref, _ = E.expmv_chain(Lb, Ld, w["u"], m * w["dt"], w["states"][:B])
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    pb, pp, renorm = FORMS[prec]
+    lb.lb_expm_pade(ctx, put(Lb), put(Ld), put(w["u"]), w["dt"], P, prec=pb)
+    R = put(w["states"][:B])
+    lb.lb_propagate_batch(ctx, P, R, steps_per_slice=m, prec=pp, renorm_trace=renorm)
+    lb.lb_sync_status(ctx)
+    err = np.max(np.linalg.norm(R.cpu().numpy() - X_ref, axis=1))
+    assert err <= tol, (prec, err)
 
 
 def _props(w, u):

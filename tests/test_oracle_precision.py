@@ -68,3 +68,40 @@ def test_stated_accuracy_after_1000_steps():
     e16 = np.max(np.linalg.norm(Q.propagate_bf16x3(P, X, 1000) - ref, axis=1))
     assert 1e-9 < e32 <= 1e-5, e32
     assert 1e-9 < e16 <= 1e-4, e16
+
+
+def _one(z):
+    return np.array([[z]], dtype=np.complex128)
+
+
+def test_fp32_steps_by_hand():
+    """d = 1 (a 1 x 1 propagator p, a state x), worked out by hand in binary32.
+    (a) p = 1 + 2^-30, x = 1 + 2^-23: the increment (p - 1) x = 2^-30 + 2^-53
+    is below half an ulp of x (2^-24), so two FP32 steps leave x exactly as
+    it was (accumulating in FP64 would not).  (b) p = 1 + i 2^-10, x = 1:
+    x1 = 1 + i 2^-10, x2 = (1 - 2^-20) + i 2^-9, all exact (the sign of the
+    Im x Im term).  (c) with the trace division a 1 x 1 state becomes 1."""
+    out = Q.propagate_fp32(_one(1 + 2.0 ** -30), _one(1 + 2.0 ** -23), 2, renorm=False)
+    assert out[0, 0] == 1 + 2.0 ** -23
+    out = Q.propagate_fp32(_one(1 + 1j * 2.0 ** -10), _one(1.0), 2, renorm=False)
+    assert out[0, 0] == (1 - 2.0 ** -20) + 1j * 2.0 ** -9
+    out = Q.propagate_fp32(_one(1 + 1j * 2.0 ** -10), _one(1.0), 2, renorm=True)
+    assert abs(out[0, 0] - 1.0) <= 2.0 ** -22
+
+
+def test_bf16x3_step_by_hand():
+    """One split-BF16 step at d = 1, worked out by hand.  x = (1 + 2^-9)(1 + i)
+    splits into x0 = 1, x1 = 2^-9 (both parts); D = p - 1 with
+    Re D = 16 (1 + 2^-9 + 2^-18) -> pieces 16, 2^-5, 2^-14 and
+    Im D = 16 (1 + 2^-9) -> pieces 16, 2^-5, 0.  With the five products
+    x_i d_j, i + j <= 2, Re y = sum (xr_i dr_j - xi_i di_j) = 2^-14 and
+    Im y = 32 + 2^-3 + 3 2^-14, so x + y = (1 + 2^-9 + 2^-14)
+    + i (33 + 2^-3 + 2^-9 + 3 2^-14), exact in binary32.  The sixth product
+    x1 d2 would add 2^-23 to the real part."""
+    D = 16 * (1 + 2.0 ** -9 + 2.0 ** -18) + 16j * (1 + 2.0 ** -9)
+    x = (1 + 2.0 ** -9) * (1 + 1j)
+    out = Q.propagate_bf16x3(_one(1 + D), _one(x), 1, renorm=False)
+    assert out[0, 0].real == 1 + 2.0 ** -9 + 2.0 ** -14
+    assert out[0, 0].imag == 33 + 2.0 ** -3 + 2.0 ** -9 + 3 * 2.0 ** -14
+    out = Q.propagate_bf16x3(_one(1 + 1j * 2.0 ** -10), _one(1.0), 2, renorm=True)
+    assert abs(out[0, 0] - 1.0) <= 2.0 ** -22
