@@ -106,6 +106,13 @@ def parse():
     ap.add_argument("--trials", default=None, metavar="PATH",
                     help="also write the raw timings (every timed step of each form, every trial of the "
                          "GPU timing models) to PATH as JSON lines")
+    ap.add_argument("--form", default=None, choices=sorted(FORMS),
+                    help="with --headline-only: the form to time (default: the headline form)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the tile autotuner (profiler runs: its launches would precede the step)")
+    ap.add_argument("--profile-size", action="store_true",
+                    help="with --headline-only: the d = 27 chain cut to 8 slices and 16 states (a few GB on the "
+                         "device), for profiler captures of single launches")
     return ap.parse_args()
 
 
@@ -824,11 +831,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     _build.build()
 
-    w = make_workload(WORKLOAD)
+    w = make_workload(WORKLOAD, **({"nslices": 8, "B": 16} if args.profile_size else {}))
     n, S, B, dt = w["n"], w["nslices"], w["B"], w["dt"]
     ctx = lb.Context(local, max_n=n, max_batch=B, max_slices=S)
     stream = torch.cuda.current_stream()
-    peaks = measure_peaks(lb)
+    peaks = measure_peaks(lb) if not args.headline_only else {}
     fp64_peak = 1e12 * peaks["dfma"] if peaks.get("dfma") else FP64_PEAK
     fp32_peak = 1e12 * peaks["ffma"] if peaks.get("ffma") else FP32_PEAK
     bf16_peak = 1e12 * peaks["bf16_tc"] if peaks.get("bf16_tc") else BF16_PEAK
@@ -916,14 +923,16 @@ def run_ours(args):
                     step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs])
 
     t_tune = time.perf_counter()
-    tuned = lb.lb_autotune(ctx, n, S, B)
+    tuned = lb.lb_autotune(ctx, n, S, B) if not args.no_autotune else 0
     t_tune = time.perf_counter() - t_tune
     sampler = ClockSampler(local)
     if args.headline_only:
-        r = timed(HEADLINE, args.steps, args.warmup)
+        form = args.form or HEADLINE
+        r = timed(form, args.steps, args.warmup)
         if rank == 0:
-            print(json.dumps({"headline_only": True, "form": HEADLINE, "ms_per_step": r["ms_per_step"],
-                              "steps": args.steps, "warmup": args.warmup,
+            print(json.dumps({"headline_only": True, "form": form, "ms_per_step": r["ms_per_step"],
+                              "steps": args.steps, "warmup": args.warmup, "slices": S, "states": B,
+                              "build_stages_ms": r["build_stages_ms"], "phases_ms": r["phases"],
                               "launches_per_step": r["launches"]}), flush=True)
         ctx.close()
         return

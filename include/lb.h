@@ -269,7 +269,10 @@ lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, co
  *           memory (n x n generators, nslices controls, B x n states)
  *   prec  : precision of the Pade products and of the propagation, as in
  *           lb_expm_pade and lb_propagate_batch (for n <= 81 the reduced
- *           forms propagate in FP32 with D = P - I)
+ *           forms propagate in FP32 with D = P - I; the Hermitian forms build
+ *           on the real coordinates, LB_FP64_HERMITIAN propagates n <= 81 in
+ *           complex FP64 and n > 81 on the real coordinates,
+ *           LB_FP32_HERMITIAN propagates in FP32)
  *   renorm_trace : as in lb_propagate_batch (reduced forms only)
  * Limits: n <= max_n; nslices <= max_slices per instance; for n > 81,
  * B <= max_batch; at most 262144 slices and 262144 state groups per call

@@ -161,7 +161,12 @@ using namespace lb;
 extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int count, double dt, lb_precision prec,
                                       int renorm_trace, void* stream) {
   if (c == nullptr || (inst == nullptr && count > 0) || count < 0) return LB_EINVAL;
-  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3) return LB_EINVAL;
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN &&
+      prec != LB_FP32_HERMITIAN)
+    return LB_EINVAL;
+  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN;
+  // propagation precision: the FP32 real-coordinate build propagates in FP32
+  const lb_precision pprec = prec == LB_FP32_HERMITIAN ? LB_FP32 : prec;
   long long total_slices = 0, total_items = 0;
   for (int i = 0; i < count; i++) {
     const lb_instance& x = inst[i];
@@ -249,10 +254,12 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
       count_launch();
       gather_gen_kernel<<<(unsigned)g, 256, 0, st>>>(n, total, dtab + ch.tab0, c->Ginst);
       LB_CUDA(cudaGetLastError());
-      lb_status r = expm_chunk_public(c, n, ch.S, c->Ginst, nullptr, nullptr, dt, prec, c->Pinst, nullptr, st);
+      lb_status r = herm ? expm_chunk_herm(c, n, ch.S, c->Ginst, nullptr, nullptr, dt, prec, c->Pinst, nullptr, st)
+                         : expm_chunk_public(c, n, ch.S, c->Ginst, nullptr, nullptr, dt, prec, c->Pinst, nullptr, st);
       if (r != LB_OK) return r;
       if (n <= 81) {
-        const bool f32 = prec != LB_FP64;
+        // FP64 and FP64_HERMITIAN: the complex FP64 step (exact for every state)
+        const bool f32 = pprec != LB_FP64 && pprec != LB_FP64_HERMITIAN;
         const size_t smem = worklist_smem(n, 8, f32);
         if (f32) {
           LB_CUDA(set_smem_once((const void*)worklist_kernel<true>, smem));
@@ -269,7 +276,7 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
         long long off = 0;
         for (int k = ch.first; k < ch.last; k++) {
           const lb_instance& x = inst[order[k]];
-          r = propagate_impl(c, n, x.nslices, c->Pinst + off, x.steps_per_slice, x.B, (z64*)x.states, prec,
+          r = propagate_impl(c, n, x.nslices, c->Pinst + off, x.steps_per_slice, x.B, (z64*)x.states, pprec,
                              renorm_trace, st);
           if (r != LB_OK) return r;
           off += (long long)x.nslices * nn;

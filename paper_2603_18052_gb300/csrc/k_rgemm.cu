@@ -23,7 +23,9 @@
 // walked by a persistent grid, as the complex GEMM.  FP64 tiles are 32 x 32
 // (2 x 2 per thread; at n = 729 the ragged edge wastes 2 % against 11 % for
 // 64 x 64), FP32 tiles 64 x 64 (4 x 4 per thread, vector loads of the shared
-// tiles, so the FMA pipe and not shared memory is the limit).
+// tiles, so the FMA pipe and not shared memory is the limit).  The K loop is
+// double-buffered: the next 16-wide K block is fetched into registers while
+// the current one is multiplied out of shared memory.
 #include "lb_internal.cuh"
 
 #include <algorithm>
@@ -86,27 +88,25 @@ struct Vec<float, 4> {
   }
 };
 template <>
-struct Vec<float, 8> {
+struct Vec<float, 2> {
   static __device__ __forceinline__ void ld(const float* p, float* r) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
-    r[0] = a.x;
-    r[1] = a.y;
-    r[2] = a.z;
-    r[3] = a.w;
-    r[4] = b.x;
-    r[5] = b.y;
-    r[6] = b.z;
-    r[7] = b.w;
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    r[0] = v.x;
+    r[1] = v.y;
   }
 };
 
 template <typename T, int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
     rgemm_kernel(const __grid_constant__ RGroup<T> g) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int BK = 16;
-  __shared__ __align__(16) T As[BK][BM];
-  __shared__ __align__(16) T Bs[BK][BN];
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;  // tile elements each thread stages
+  static_assert(LA * NT == BM * BK && LB * NT == BK * BN, "tile must divide over the threads");
+  // two shared-memory stages: the next K block is fetched into registers
+  // while the current one is multiplied, then stored into the other stage
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN);
   const int ty = tid / (BN / TN);
@@ -147,9 +147,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
     const unsigned long long aneg = (fastC && P.alpha[0] < 0.0) ? 0x8000000000000000ull : 0ull;
     const T shA = T(P.shiftA), shB = T(P.shiftB);
+    const bool bT = P.transB != 0;
 
-    for (int k0 = 0; k0 < K; k0 += BK) {
-      for (int e = tid; e < BM * BK; e += NT) {  // A tile, k contiguous in memory
+    T ra[LA], rb[LB];
+    // global -> registers for the K block at k0 (zero outside the matrices)
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int q = 0; q < LA; q++) {
+        const int e = tid + q * NT;
         const int m = e / BK, k = e - (e / BK) * BK;
         const int gm = m0 + m, gk = k0 + k;
         T v = T(0);
@@ -157,43 +162,64 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
           v = A[(long long)gm * P.lda + gk];
           if (gm == gk) v -= shA;
         }
-        As[k][m] = flip(v, aneg);
+        ra[q] = flip(v, aneg);
       }
-      if (!P.transB) {
-        for (int e = tid; e < BK * BN; e += NT) {
-          const int k = e / BN, c = e - (e / BN) * BN;
-          const int gk = k0 + k, gn = n0 + c;
-          T v = T(0);
-          if (gk < K && gn < N) {
-            v = B[(long long)gk * P.ldb + gn];
-            if (gk == gn) v -= shB;
-          }
-          Bs[k][c] = v;
+#pragma unroll
+      for (int q = 0; q < LB; q++) {
+        const int e = tid + q * NT;
+        int k, c;
+        if (bT) {
+          c = e / BK;
+          k = e - c * BK;
+        } else {
+          k = e / BN;
+          c = e - k * BN;
         }
-      } else {
-        for (int e = tid; e < BK * BN; e += NT) {
-          const int c = e / BK, k = e - (e / BK) * BK;
-          const int gk = k0 + k, gn = n0 + c;
-          T v = T(0);
-          if (gk < K && gn < N) {
-            v = B[(long long)gn * P.ldb + gk];
-            if (gk == gn) v -= shB;
-          }
-          Bs[k][c] = v;
+        const int gk = k0 + k, gn = n0 + c;
+        T v = T(0);
+        if (gk < K && gn < N) {
+          v = bT ? B[(long long)gn * P.ldb + gk] : B[(long long)gk * P.ldb + gn];
+          if (gk == gn) v -= shB;
         }
+        rb[q] = v;
       }
-      __syncthreads();
+    };
+    auto stash = [&](int st) {
+#pragma unroll
+      for (int q = 0; q < LA; q++) {
+        const int e = tid + q * NT;
+        As[st][e - (e / BK) * BK][e / BK] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LB; q++) {
+        const int e = tid + q * NT;
+        if (bT)
+          Bs[st][e - (e / BK) * BK][e / BK] = rb[q];
+        else
+          Bs[st][e / BN][e - (e / BN) * BN] = rb[q];
+      }
+    };
+
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    int st = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      const bool more = k0 + BK < K;
+      if (more) fetch(k0 + BK);  // loads in flight during the products below
 #pragma unroll
       for (int k = 0; k < BK; k++) {
         T a[TM], bb[TN];
-        Vec<T, TM>::ld(&As[k][ty * TM], a);
-        Vec<T, TN>::ld(&Bs[k][tx * TN], bb);
+        Vec<T, TM>::ld(&As[st][k][ty * TM], a);
+        Vec<T, TN>::ld(&Bs[st][k][tx * TN], bb);
 #pragma unroll
         for (int i = 0; i < TM; i++)
 #pragma unroll
           for (int j = 0; j < TN; j++) acc[i][j] = fma_t(a[i], bb[j], acc[i][j]);
       }
+      if (more) stash(st ^ 1);
       __syncthreads();
+      st ^= 1;
     }
 
 #pragma unroll
@@ -316,10 +342,10 @@ cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count
 cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
   typedef cudaError_t (*fn)(const RGemmProblem<float>*, int, int, cudaStream_t);
-  static const fn cands[2] = {launch_rcfg<float, 64, 64, 4, 4>, launch_rcfg<float, 128, 128, 8, 8>};
-  const long long t128 = rtiles(probs, nprob, 128, 128);
+  static const fn cands[2] = {launch_rcfg<float, 32, 32, 2, 2>, launch_rcfg<float, 64, 64, 4, 4>};
+  const long long t64 = rtiles(probs, nprob, 64, 64);
   const RArgs<float> a{cands, probs, nprob, sm_count};
-  return tuned_launch(rshape_key(probs, nprob), 2, t128 >= 4LL * sm_count ? 1 : 0, rrun<float>, &a, st);
+  return tuned_launch(rshape_key(probs, nprob), 2, t64 >= 2LL * sm_count ? 1 : 0, rrun<float>, &a, st);
 }
 
 }  // namespace lb

@@ -850,9 +850,17 @@ lb_status autotune_impl(lb_ctx* c, int n, int nslices, int B, cudaStream_t st, i
   LB_CUDA(cudaMemsetAsync(c->Ginst, 0, sizeof(z64) * nn * nslices, st));
   set_tuning(true);
   lb_status r = expm_chunk(c, n, nslices, c->Ginst, nullptr, nullptr, 1.0, LB_FP32, c->Pinst, nullptr, st);
+  // the real-coordinate builds: FP32 products with the FP64 LU, then the
+  // FP64 products
+  const bool square = is_square(n, nullptr);
+  if (r == LB_OK && square)
+    r = expm_chunk_herm(c, n, nslices, c->Ginst, nullptr, nullptr, 1.0, LB_FP32_HERMITIAN, c->Pinst, nullptr, st);
+  if (r == LB_OK && square)
+    r = expm_chunk_herm(c, n, nslices, c->Ginst, nullptr, nullptr, 1.0, LB_FP64_HERMITIAN, c->Pinst, nullptr, st);
   if (r == LB_OK && n > 81 && (long long)B * n <= nn * c->max_slices) {
     LB_CUDA(cudaMemsetAsync(c->W, 0, sizeof(z64) * B * n, st));
     r = propagate_impl(c, n, 1, c->Pinst, 1, B, c->W, LB_FP64, 0, st);
+    if (r == LB_OK && square) r = propagate_impl(c, n, 1, c->Pinst, 1, B, c->W, LB_FP64_HERMITIAN, 0, st);
   }
   set_tuning(false);
   if (cudaStreamSynchronize(st) != cudaSuccess) return LB_ECUDA;

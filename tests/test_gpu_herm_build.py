@@ -64,10 +64,25 @@ def _gen_pair(d, seed, scale):
     return Lb * f, Ld * f
 
 
-@pytest.mark.parametrize("d,S,scale", [(1, 2, 0.1), (2, 5, 0.2), (3, 4, 3.0), (5, 3, 0.9), (6, 2, 1.3),
+def test_expm_herm_d1(lbm, dev):
+    """d = 1: a Hermiticity-preserving generator is a real number (every
+    Lindbladian of one level is 0); exp of the 1 x 1 real forms, within a
+    few ulps (2.5 x 0.7 takes three squarings, each doubling the relative
+    rounding error of the approximant)."""
+    gens = np.array([[[-0.3]], [[2.5]], [[0.0]]], dtype=np.complex128)
+    ctx = lbm.Context(0, max_n=1, max_batch=1, max_slices=3)
+    P = torch.empty((3, 1, 1), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(gens, dev), None, None, 0.7, P, prec="fp64_hermitian")
+    lbm.lb_sync_status(ctx)
+    for s in range(3):
+        ref = np.exp(0.7 * gens[s, 0, 0].real)
+        assert abs(P.cpu().numpy()[s, 0, 0] - ref) <= 1e-14 * ref
+
+
+@pytest.mark.parametrize("d,S,scale", [(2, 5, 0.2), (3, 4, 3.0), (5, 3, 0.9), (6, 2, 1.3),
                                        (7, 2, 13.0), (9, 3, 1.7), (11, 2, 0.6)])
 def test_expm_herm_fp64_matches_oracle(lbm, dev, d, S, scale):
-    """n = 1 .. 121: one to four LU blocks with a ragged last one, 16 x 16
+    """n = 4 .. 121: one to four LU blocks with a ragged last one, 16 x 16
     and 32 x 32 GEMM tiles with ragged edges, squaring counts 0 to 7."""
     n = d * d
     Lb, Ld = _gen_pair(d, 1500 + d, scale)

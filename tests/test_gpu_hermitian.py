@@ -118,8 +118,11 @@ def test_shared_memory_form_matches_oracle(lbm, d, B, S, m):
     ctx.close()
 
 
-@pytest.mark.parametrize("d,B", [(11, 3)])
-def test_above_n81_runs_the_complex_path(lbm, d, B):
+@pytest.mark.parametrize("d,B", [(11, 3), (11, 40)])
+def test_above_n81_runs_the_real_product(lbm, d, B):
+    """n = 121: one real product per step on the real coordinates (the
+    few-state form for B <= 8, the real GEMM above); equal to the complex
+    FP64 path within 1e-12 relative and exactly Hermitian."""
     n = d * d
     Ps = _props(d, 2, scale=0.05)
     X0 = ginibre_states(600 + d, d, B)
@@ -130,14 +133,18 @@ def test_above_n81_runs_the_complex_path(lbm, d, B):
         lbm.lb_propagate_batch(ctx, torch.from_numpy(Ps).cuda(), R, steps_per_slice=4, prec=prec)
         lbm.lb_sync_status(ctx)
         outs[prec] = R.cpu().numpy()
-    assert np.array_equal(outs["fp64"], outs["fp64_hermitian"])
+    for b in range(B):
+        assert _rel(outs["fp64_hermitian"][b], outs["fp64"][b]) <= 1e-12
+    rho = outs["fp64_hermitian"].reshape(B, d, d)
+    assert np.array_equal(rho, np.conj(np.transpose(rho, (0, 2, 1))))
     ctx.close()
 
 
-def test_other_calls_reject_the_hermitian_form(lbm):
+def test_unknown_precision_is_rejected(lbm):
     ctx = lbm.Context(0, max_n=9, max_batch=2, max_slices=1)
-    L = torch.zeros((9, 9), dtype=torch.complex128, device="cuda")
+    L = torch.zeros((1, 9, 9), dtype=torch.complex128, device="cuda")
     P = torch.empty((1, 9, 9), dtype=torch.complex128, device="cuda")
-    with pytest.raises(lbm.LBError):
-        lbm.lb_expm_pade(ctx, L.reshape(1, 9, 9), None, None, 0.1, P, prec="fp64_hermitian")
+    with pytest.raises(lbm.LBError) as ei:
+        lbm.lb_expm_pade(ctx, L, None, None, 0.1, P, prec=7)
+    assert ei.value.name == "LB_EINVAL"
     ctx.close()
