@@ -96,6 +96,29 @@ struct Vec<float, 2> {
   }
 };
 
+// The epilogue of one output element (see the header comment): r_w in T,
+// then the FP64 widened outputs with their exact FP64 terms.
+template <typename T>
+__device__ __forceinline__ void store_out(const RGemmProblem<T>& P, long long b, int gm, int gn, T accv) {
+  const long long off = (long long)gm * P.ldc + gn;
+  const long long idx = b * P.sC + off;
+#pragma unroll
+  for (int w = 0; w < 2; w++) {
+    if (P.O[w] == nullptr && P.Od[w] == nullptr) continue;
+    T v = T(P.alpha[w]) * accv;
+    if (P.beta[w] != 0.0 && P.O[w] != nullptr) v = fma_t(T(P.beta[w]), P.O[w][idx], v);
+    for (int q = 0; q < P.nterms; q++) v = fma_t(T(P.coef[w][q]), P.X[q][b * P.sX[q] + off], v);
+    if (gm == gn) v += T(P.gamma[w]);
+    if (P.O[w] != nullptr) P.O[w][idx] = v;
+    if (P.Od[w] != nullptr) {
+      double vd = double(v);
+      if (P.dcoef[w] != 0.0) vd = fma(P.dcoef[w], P.Xd[b * P.sXd + off], vd);
+      if (gm == gn) vd += P.dgamma[w];
+      P.Od[w][idx] = vd;
+    }
+  }
+}
+
 template <typename T, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
     rgemm_kernel(const __grid_constant__ RGroup<T> g) {
@@ -124,6 +147,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
     const int tn = r - tm * g.tiles_n[pi];
     if (P.active != nullptr && P.active[b] <= P.active_iter) continue;
     if (P.active_lo != nullptr && P.active_lo[b] > P.active_iter) continue;
+    if (P.pick != nullptr && P.pick[b] != P.pick_val) continue;
     const int m0 = tm * BM, n0 = tn * BN;
     const T* __restrict__ A = P.A + b * P.sA;
     const T* __restrict__ B = P.B + b * P.sB;
@@ -230,29 +254,92 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
       for (int j = 0; j < TN; j++) {
         const int gn = n0 + tx * TN + j;
         if (gn >= N) continue;
-        const long long off = (long long)gm * P.ldc + gn;
-        const long long idx = b * P.sC + off;
         if (fastC) {
-          P.O[0][idx] = acc[i][j];
+          P.O[0][b * P.sC + (long long)gm * P.ldc + gn] = acc[i][j];
           continue;
         }
-#pragma unroll
-        for (int w = 0; w < 2; w++) {
-          if (P.O[w] == nullptr && P.Od[w] == nullptr) continue;
-          T v = T(P.alpha[w]) * acc[i][j];
-          if (P.beta[w] != 0.0 && P.O[w] != nullptr) v = fma_t(T(P.beta[w]), P.O[w][idx], v);
-          for (int q = 0; q < P.nterms; q++) v = fma_t(T(P.coef[w][q]), P.X[q][b * P.sX[q] + off], v);
-          if (gm == gn) v += T(P.gamma[w]);
-          if (P.O[w] != nullptr) P.O[w][idx] = v;
-          if (P.Od[w] != nullptr) {
-            double vd = double(v);
-            if (P.dcoef[w] != 0.0) vd = fma(P.dcoef[w], P.Xd[b * P.sXd + off], vd);
-            if (gm == gn) vd += P.dgamma[w];
-            P.Od[w][idx] = vd;
-          }
-        }
+        store_out(P, b, gm, gn, acc[i][j]);
       }
     }
+  }
+}
+
+// Row-sparse left operand (the zero-skip of the paper's Pade products,
+// Sec. 3.1): one warp per output row gm of batch element b, lane l owning
+// the columns l + 32 q (q < NQ, all N of them); A's row is scanned 32
+// entries at a time (coalesced), a ballot marks the nonzeros, and only those
+// rows of B are multiplied in (coalesced row reads).  For a row with z
+// nonzeros that is z N multiply-adds instead of K N; the low powers of a
+// local Lindbladian have a few percent of nonzeros.
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) rgemm_rowskip_kernel(const __grid_constant__ RGemmProblem<T> P) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long rows = (long long)P.batch * P.M;
+  const T shA = T(P.shiftA);
+  for (long long t = wid; t < rows; t += nw) {
+    const long long b = t / P.M;
+    const int gm = (int)(t - b * P.M);
+    // batch-element tests are the same for every lane of the warp
+    if (P.pick != nullptr && P.pick[b] != P.pick_val) continue;
+    if (P.active != nullptr && P.active[b] <= P.active_iter) continue;
+    if (P.active_lo != nullptr && P.active_lo[b] > P.active_iter) continue;
+    const T* __restrict__ arow = P.A + b * P.sA + (long long)gm * P.lda;
+    const T* __restrict__ B = P.B + b * P.sB;
+    T acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] = T(0);
+    for (int k0 = 0; k0 < P.K; k0 += 32) {
+      const int k = k0 + lane;
+      T v = T(0);
+      if (k < P.K) {
+        v = arow[k];
+        if (k == gm) v -= shA;
+      }
+      unsigned mask = __ballot_sync(kFull, v != T(0));
+      while (mask != 0u) {
+        const int bit = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const T a = __shfl_sync(kFull, v, bit);
+        const T* __restrict__ brow = B + (long long)(k0 + bit) * P.ldb;
+        T bv[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+          const int j = lane + 32 * q;
+          bv[q] = j < P.N ? brow[j] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) acc[q] = fma_t(a, bv[q], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+      const int j = lane + 32 * q;
+      if (j < P.N) store_out(P, b, gm, j, acc[q]);
+    }
+  }
+}
+
+// Counts of nonzero entries per matrix, one CTA per matrix, then the flag.
+template <typename T>
+__global__ void __launch_bounds__(256) sparse_flags_kernel(int n, int S, const T* __restrict__ M, long long max_nnz,
+                                                          int* __restrict__ flag) {
+  __shared__ int part[8];
+  const long long nn = (long long)n * n;
+  for (int s = blockIdx.x; s < S; s += gridDim.x) {
+    int c = 0;
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) c += M[s * nn + e] != T(0);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += part[w];
+      flag[s] = tot <= max_nnz ? 1 : 0;
+    }
+    __syncthreads();
   }
 }
 
@@ -347,5 +434,44 @@ cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count,
   const RArgs<float> a{cands, probs, nprob, sm_count};
   return tuned_launch(rshape_key(probs, nprob), 2, t64 >= 2LL * sm_count ? 1 : 0, rrun<float>, &a, st);
 }
+
+template <typename T, int NQ>
+cudaError_t launch_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t st) {
+  static int occ = -1;
+  if (occ < 0) {
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, rgemm_rowskip_kernel<T, NQ>, 256, 0);
+    if (e != cudaSuccess) return e;
+    occ = std::max(1, o);
+  }
+  const long long warps = (long long)p.batch * p.M;
+  const long long grid = std::min<long long>((warps + 7) / 8, (long long)sm_count * occ);
+  count_launch();
+  rgemm_rowskip_kernel<T, NQ><<<(unsigned)grid, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rgemm_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t st) {
+  if (p.transB != 0 || p.shiftB != 0.0 || p.N > 736 || p.N < 1) return cudaErrorInvalidValue;
+  if (p.M < 1 || p.batch < 1) return cudaSuccess;
+  if (p.N <= 128) return launch_rowskip<T, 4>(p, sm_count, st);
+  if (p.N <= 256) return launch_rowskip<T, 8>(p, sm_count, st);
+  return launch_rowskip<T, 23>(p, sm_count, st);
+}
+template cudaError_t rgemm_rowskip<double>(const RGemmProblem<double>&, int, cudaStream_t);
+template cudaError_t rgemm_rowskip<float>(const RGemmProblem<float>&, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_sparse_flags(int n, int S, const T* M, long long max_nnz, int* flag, int sm_count,
+                                cudaStream_t st) {
+  const int grid = std::min(S, sm_count * 8);
+  if (grid < 1) return cudaSuccess;
+  count_launch();
+  sparse_flags_kernel<T><<<grid, 256, 0, st>>>(n, S, M, max_nnz, flag);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sparse_flags<double>(int, int, const double*, long long, int*, int, cudaStream_t);
+template cudaError_t launch_sparse_flags<float>(int, int, const float*, long long, int*, int, cudaStream_t);
 
 }  // namespace lb

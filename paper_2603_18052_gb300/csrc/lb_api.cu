@@ -157,6 +157,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add(S * sizeof(unsigned long long));                      // norm bits
   add((S + 1) * sizeof(int));                               // sc
   add(S * sizeof(int));                                     // kmix
+  add(2 * S * sizeof(int));                                 // spflag
   add(sizeof(z64) * 64 * 64);                               // G
   add((size_t)max_batch * max_n * zb);                      // Rtmp
   add((size_t)max_batch * max_n * zb);                      // Xh
@@ -200,6 +201,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->norm_bits = (unsigned long long*)ar.take(S * sizeof(unsigned long long));
   c->sc = (int*)ar.take((S + 1) * sizeof(int));
   c->kmix = (int*)ar.take(S * sizeof(int));
+  c->spflag = (int*)ar.take(2 * S * sizeof(int));
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
   c->Xh = Z((size_t)max_batch * max_n);

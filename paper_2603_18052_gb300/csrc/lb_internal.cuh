@@ -114,6 +114,7 @@ struct lb_ctx {
   void* inst_tab_host = nullptr;  // pinned staging of the tables
   size_t inst_tab_bytes = 0;
   cudaEvent_t ev_tab = nullptr;   // the last table upload
+  int* spflag = nullptr;  // 2 x max_slices: sparse-operand flags of the real-coordinate build
   // --- GRAPE (contexts with max_n <= 81) ---
   lb::z64* grape = nullptr;
   size_t grape_bytes = 0;
@@ -173,10 +174,22 @@ struct RGemmProblem {
   double dcoef[2] = {0.0, 0.0}, dgamma[2] = {0.0, 0.0};
   const int* active = nullptr; int active_iter = 0;
   const int* active_lo = nullptr;
+  const int* pick = nullptr; int pick_val = 0;  // also skip b when pick[b] != pick_val
   double shiftA = 0.0, shiftB = 0.0;
 };
 cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count, cudaStream_t st);
 cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st);
+// The same product for a left operand whose rows are mostly zeros (the low
+// powers of a local generator): one warp per output row, only the nonzeros
+// of A's row multiplied.  Needs transB == 0, shiftB == 0 and N <= 736
+// (cudaErrorInvalidValue otherwise).
+template <typename T>
+cudaError_t rgemm_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t st);
+// flag[s] = 1 if M[s] (S row-major n x n matrices) has at most max_nnz
+// nonzero entries, else 0.
+template <typename T>
+cudaError_t launch_sparse_flags(int n, int S, const T* M, long long max_nnz, int* flag, int sm_count,
+                                cudaStream_t st);
 
 // Few-state FP64 products (k_gemv.cu), B <= kGemvMaxB:
 //   V[b][i] = alpha sum_j A[i][j] X[b][j];  Yacc[b][i] += the same (Yacc may be null)

@@ -15,6 +15,10 @@
 // multiply-add is one FMA instead of four (three in the Gauss form of the
 // complex GEMM), which is what bounds the build on GB300's FP64 pipe.
 // The scaling parameter s is taken from ||G||_1 on these coordinates.
+// Four of the six Pade products have A or A^2 as their left operand (A^6 is
+// formed as A^2 A^4); where that operand is sparse, as for a local
+// Lindbladian, they skip its zeros as the paper's products do (Sec. 3.1),
+// chosen per slice on the device from the operand's nonzero count.
 #include "lb_internal.cuh"
 
 namespace lb {
@@ -125,6 +129,37 @@ lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, 
   return LB_OK;
 }
 
+// Density below which a power of A is multiplied as a row-sparse left
+// operand (the zero-skip of the paper's Pade products, Sec. 3.1): the low
+// powers of a local Lindbladian's real form have a few percent of nonzeros
+// (A 1.2 %, A^2 5.6 % for the d = 27 transmon chain), where the row-sparse
+// product is several times cheaper than the dense one.
+constexpr double kSparseDensity = 0.15;
+
+cudaError_t dense_gemm(const RGemmProblem<double>& p, int sms, cudaStream_t st) { return rgemm_f64(&p, 1, sms, st); }
+cudaError_t dense_gemm(const RGemmProblem<float>& p, int sms, cudaStream_t st) { return rgemm_f32(&p, 1, sms, st); }
+
+// C = A B for the S slices, A row-sparse where flag[s] = 1: the row-sparse
+// product for those slices and the dense GEMM for the others (each launch
+// skips the slices that are not its own).
+template <typename T>
+lb_status skip_product(lb_ctx* c, RGemmProblem<T> p, const int* flag, cudaStream_t st) {
+  RGemmProblem<T> q = p;
+  q.pick = flag;
+  q.pick_val = 1;
+  LB_CUDA(rgemm_rowskip(q, c->sm_count, st));
+  p.pick = flag;
+  p.pick_val = 0;
+  LB_CUDA(dense_gemm(p, c->sm_count, st));
+  return LB_OK;
+}
+
+#define LB_TRY(x)                     \
+  do {                                \
+    lb_status r_ = (x);               \
+    if (r_ != LB_OK) return r_;       \
+  } while (0)
+
 }  // namespace
 
 lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
@@ -161,22 +196,28 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     LB_CUDA(launch_check_bound(c->sc + S, c->max_squarings, c->err_dev, st));
   }
   if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
+  const long long max_nnz = (long long)(kSparseDensity * (double)nn);
+  int* flagA = c->spflag;                     // A row-sparse
+  int* flagA2 = c->spflag + c->max_slices;    // A^2 row-sparse
   if (prec == LB_FP64_HERMITIAN) {
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
+    LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
     RGemmProblem<double> p = rsq(n, S, Ar, Ar, A2);
-    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA, st));
+    LB_CUDA(launch_sparse_flags<double>(n, S, A2, max_nnz, flagA2, c->sm_count, st));
     p = rsq(n, S, A2, A2, A4);
-    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
-    // A6 = A4 A2, and Z1 = b12 A6 + b10 A4 + b8 A2 from the same accumulators
-    p = rsq(n, S, A4, A2, A6);
+    LB_TRY(skip_product(c, p, flagA2, st));
+    // A6 = A2 A4 (powers of A commute: A2 is the sparser left operand), and
+    // Z1 = b12 A6 + b10 A4 + b8 A2 from the same accumulators
+    p = rsq(n, S, A2, A4, A6);
     p.O[1] = Z1;
     p.alpha[1] = b[12];
     p.nterms = 2;
     p.X[0] = A4; p.X[1] = A2;
     p.sX[0] = p.sX[1] = nn;
     p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
-    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA2, st));
     LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
     // V = A6 Z1 + b6 A6 + b4 A4 + b2 A2 + b0 I;  W = A6 Z2 + b7 A6 + b5 A4 + b3 A2 + b1 I
     RGemmProblem<double> vw[2];
@@ -196,7 +237,7 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     p.nterms = 1;
     p.X[0] = V; p.sX[0] = nn;
     p.coef[0][0] = 1.0; p.coef[1][0] = 1.0;
-    LB_CUDA(rgemm_f64(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA, st));
   } else {
     // FP32 products (operands and accumulation in FP32), every intermediate
     // kept in FP32; the FP64 LU inputs V - U and V + U are widened with the
@@ -208,18 +249,20 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     float* f1 = (float*)c->W;
     float *Z1f = f1, *Z2f = f1 + fl, *Vsf = f1 + 2 * fl, *Wsf = f1 + 3 * fl;
     LB_CUDA(launch_real_to_f32(n, S, Ar, 0.0, Af, c->sm_count, st));
+    LB_CUDA(launch_sparse_flags<float>(n, S, Af, max_nnz, flagA, c->sm_count, st));
     RGemmProblem<float> p = fsq(n, S, Af, Af, A2f);
-    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA, st));
+    LB_CUDA(launch_sparse_flags<float>(n, S, A2f, max_nnz, flagA2, c->sm_count, st));
     p = fsq(n, S, A2f, A2f, A4f);
-    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
-    p = fsq(n, S, A4f, A2f, A6f);
+    LB_TRY(skip_product(c, p, flagA2, st));
+    p = fsq(n, S, A2f, A4f, A6f);
     p.O[1] = Z1f;
     p.alpha[1] = b[12];
     p.nterms = 2;
     p.X[0] = A4f; p.X[1] = A2f;
     p.sX[0] = p.sX[1] = nn;
     p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
-    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA2, st));
     LB_CUDA(launch_real_lincomb3<float>(fl, A6f, A4f, A2f, b[13], b[11], b[9], Z2f, c->sm_count, st));
     RGemmProblem<float> vw[2];
     for (int i = 0; i < 2; i++) {
@@ -242,7 +285,7 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     p.Xd = Ar; p.sXd = nn;
     p.dcoef[0] = -b[1]; p.dcoef[1] = b[1];
     p.dgamma[0] = b[0]; p.dgamma[1] = b[0];
-    LB_CUDA(rgemm_f32(&p, 1, c->sm_count, st));
+    LB_TRY(skip_product(c, p, flagA, st));
   }
   if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
   // (V - U) R = (V + U), FP64.  U, Y, L reuse A2, A4, A6.

@@ -115,6 +115,36 @@ def test_expm_herm_per_slice_generators_and_chunking(lbm, dev):
         assert _relf(Pg[s], O.expm_pade13(gens[s] * 0.5)) <= 1e-12
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64_hermitian", 1e-12), ("fp32_hermitian", 1e-6)])
+def test_expm_herm_sparse_and_dense_slices(lbm, dev, prec, tol):
+    """Slices whose powers of A are sparse (a dephasing generator: the real
+    form is 2 x 2 block diagonal, so A and A^2 take the zero-skipping
+    products) alternate with dense random generators in one call; every
+    slice against the oracle."""
+    d, S = 4, 6
+    n = d * d
+    rng_h = _rand_c(1800, (d, d))
+    Hd = np.diag(np.real(np.diag(rng_h)))  # diagonal Hamiltonian
+    num = np.diag(np.arange(d, dtype=float)).astype(complex)
+    sparse_gen = O.lindbladian(Hd, [0.3 * num])
+    gens = []
+    for s in range(S):
+        if s % 2 == 0:
+            gens.append(sparse_gen * (0.5 + 0.3 * s))
+        else:
+            gens.append(_gen_pair(d, 1900 + s, 0.4 + 0.7 * s)[0])
+    gens = np.array(gens)
+    assert np.count_nonzero(OH.real_form(gens[0], d)) <= 0.15 * n * n
+    assert np.count_nonzero(OH.real_form(gens[1], d)) > 0.15 * n * n
+    ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=S)
+    P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+    lbm.lb_expm_pade(ctx, _t(gens, dev), None, None, 1.0, P, prec=prec)
+    lbm.lb_sync_status(ctx)
+    for s in range(S):
+        ref = O.expm_pade13(gens[s])
+        assert _relf(P.cpu().numpy()[s], ref) <= tol, (s, _relf(P.cpu().numpy()[s], ref))
+
+
 @pytest.mark.parametrize("name,S", [("d9_batch", 3), ("d27_chain", 2)])
 def test_expm_herm_workloads(lbm, dev, name, S):
     w = make_workload(name, nslices=S)
