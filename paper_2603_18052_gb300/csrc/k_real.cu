@@ -93,6 +93,42 @@ __global__ void real_to_f32_kernel(int n, long long total, const double* __restr
   }
 }
 
+// V, W of the [13/13] approximant as sums of the even powers, for the
+// slices with flag[s] != 0:
+//   V = b12 A^12 + b10 A^10 + b8 A^8 + b6 A^6 + b4 A^4 + b2 A^2 (+ b0 I)
+//   W = b13 A^12 + b11 A^10 + b9 A^8 + b7 A^6 + b5 A^4 + b3 A^2 (+ b1 I)
+// (U = A W), the highest powers added first.
+template <typename T>
+__global__ void real_powsum_kernel(int n, int S, const int* __restrict__ flag, const T* __restrict__ A2,
+                                   const T* __restrict__ A4, const T* __restrict__ A6, const T* __restrict__ A8,
+                                   const T* __restrict__ A10, const T* __restrict__ A12, PadeCoef c,
+                                   int with_identity, T* __restrict__ V, T* __restrict__ W) {
+  const long long nn = (long long)n * n, total = nn * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / nn, o = e - s * nn;
+    if (flag[s] == 0) continue;
+    const T p12 = A12[e], p10 = A10[e], p8 = A8[e], p6 = A6[e], p4 = A4[e], p2 = A2[e];
+    T v = T(c.b[12]) * p12, w = T(c.b[13]) * p12;
+    v = v + T(c.b[10]) * p10;
+    w = w + T(c.b[11]) * p10;
+    v = v + T(c.b[8]) * p8;
+    w = w + T(c.b[9]) * p8;
+    v = v + T(c.b[6]) * p6;
+    w = w + T(c.b[7]) * p6;
+    v = v + T(c.b[4]) * p4;
+    w = w + T(c.b[5]) * p4;
+    v = v + T(c.b[2]) * p2;
+    w = w + T(c.b[3]) * p2;
+    if (with_identity && o / n == o % n) {
+      v += T(c.b[0]);
+      w += T(c.b[1]);
+    }
+    V[e] = v;
+    W[e] = w;
+  }
+}
+
 __global__ void real_copy_active_kernel(long long nn, int S, const double* __restrict__ src, double* __restrict__ dst,
                                         const int* __restrict__ active, int iter) {
   const long long total = nn * S;
@@ -260,6 +296,25 @@ template cudaError_t launch_real_lincomb3<double>(long long, const double*, cons
                                                   double, double, double*, int, cudaStream_t);
 template cudaError_t launch_real_lincomb3<float>(long long, const float*, const float*, const float*, double, double,
                                                  double, float*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_real_powsum(int n, int S, const int* flag, const T* A2, const T* A4, const T* A6, const T* A8,
+                               const T* A10, const T* A12, const double* b, int with_identity, T* V, T* W,
+                               int sm_count, cudaStream_t st) {
+  PadeCoef c;
+  for (int j = 0; j < 14; j++) c.b[j] = b[j];
+  const long long total = (long long)n * n * S;
+  count_launch();
+  real_powsum_kernel<T><<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, S, flag, A2, A4, A6, A8, A10, A12, c,
+                                                                       with_identity, V, W);
+  return cudaGetLastError();
+}
+template cudaError_t launch_real_powsum<double>(int, int, const int*, const double*, const double*, const double*,
+                                                const double*, const double*, const double*, const double*, int,
+                                                double*, double*, int, cudaStream_t);
+template cudaError_t launch_real_powsum<float>(int, int, const int*, const float*, const float*, const float*,
+                                               const float*, const float*, const float*, const double*, int, float*,
+                                               float*, int, cudaStream_t);
 
 cudaError_t launch_real_to_f32(int n, int S, const double* src, double shift, float* dst, int sm_count,
                                cudaStream_t st) {

@@ -293,6 +293,16 @@ cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const doub
 template <typename T>
 cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, const T* X2, double c0, double c1,
                                  double c2, T* Z, int sm_count, cudaStream_t st);
+// The Pade coefficients b_0 .. b_13 by value.
+struct PadeCoef {
+  double b[14];
+};
+// V, W of the approximant as sums of the even powers A^2 .. A^12 (slices
+// with flag[s] != 0), the identity terms b0, b1 added when with_identity.
+template <typename T>
+cudaError_t launch_real_powsum(int n, int S, const int* flag, const T* A2, const T* A4, const T* A6, const T* A8,
+                               const T* A10, const T* A12, const double* b, int with_identity, T* V, T* W,
+                               int sm_count, cudaStream_t st);
 // dst = float(src - shift I), S n x n matrices
 cudaError_t launch_real_to_f32(int n, int S, const double* src, double shift, float* dst, int sm_count,
                                cudaStream_t st);

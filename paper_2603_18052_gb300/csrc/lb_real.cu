@@ -18,7 +18,11 @@
 // Four of the six Pade products have A or A^2 as their left operand (A^6 is
 // formed as A^2 A^4); where that operand is sparse, as for a local
 // Lindbladian, they skip its zeros as the paper's products do (Sec. 3.1),
-// chosen per slice on the device from the operand's nonzero count.
+// chosen per slice on the device from the operand's nonzero count.  Where
+// A^2 is sparse, the two dense products A^6 Z1 and A^6 Z2 are replaced too:
+// A^8, A^10 and A^12 come from three more zero-skipping products with A^2 and
+// V, W are summed term by term from the powers (the same [13/13]
+// approximant), so every product of the build skips zeros.
 #include "lb_internal.cuh"
 
 namespace lb {
@@ -219,13 +223,33 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
     LB_TRY(skip_product(c, p, flagA2, st));
     LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
-    // V = A6 Z1 + b6 A6 + b4 A4 + b2 A2 + b0 I;  W = A6 Z2 + b7 A6 + b5 A4 + b3 A2 + b1 I
+    // slices with a sparse A^2: A^8, A^10, A^12 by three more zero-skipping
+    // products with A^2 and V, W summed from the powers (the same
+    // approximant, its polynomials summed term by term instead of through
+    // the two dense products A^6 Z1, A^6 Z2); in the second halves of the
+    // A^2 .. A^6 buffers
+    {
+      const size_t half = (size_t)c->max_slices * c->max_n * c->max_n;
+      double *A8 = (double*)c->A2 + half, *A10 = (double*)c->A4 + half, *A12 = (double*)c->A6 + half;
+      const double* lo[3] = {A6, A8, A10};
+      double* hi[3] = {A8, A10, A12};
+      for (int i = 0; i < 3; i++) {
+        RGemmProblem<double> h = rsq(n, S, A2, lo[i], hi[i]);
+        h.pick = flagA2;
+        h.pick_val = 1;
+        LB_CUDA(rgemm_rowskip(h, c->sm_count, st));
+      }
+      LB_CUDA(launch_real_powsum<double>(n, S, flagA2, A2, A4, A6, A8, A10, A12, b, 1, V, W, c->sm_count, st));
+    }
+    // other slices: V = A6 Z1 + b6 A6 + b4 A4 + b2 A2 + b0 I;  W = A6 Z2 + b7 A6 + b5 A4 + b3 A2 + b1 I
     RGemmProblem<double> vw[2];
     for (int i = 0; i < 2; i++) {
       vw[i] = rsq(n, S, A6, i == 0 ? Z1 : Z2, i == 0 ? V : W);
       vw[i].nterms = 3;
       vw[i].X[0] = A6; vw[i].X[1] = A4; vw[i].X[2] = A2;
       vw[i].sX[0] = vw[i].sX[1] = vw[i].sX[2] = nn;
+      vw[i].pick = flagA2;
+      vw[i].pick_val = 0;
     }
     vw[0].coef[0][0] = b[6]; vw[0].coef[0][1] = b[4]; vw[0].coef[0][2] = b[2]; vw[0].gamma[0] = b[0];
     vw[1].coef[0][0] = b[7]; vw[1].coef[0][1] = b[5]; vw[1].coef[0][2] = b[3]; vw[1].gamma[0] = b[1];
@@ -264,12 +288,28 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     p.coef[1][0] = b[10]; p.coef[1][1] = b[8];
     LB_TRY(skip_product(c, p, flagA2, st));
     LB_CUDA(launch_real_lincomb3<float>(fl, A6f, A4f, A2f, b[13], b[11], b[9], Z2f, c->sm_count, st));
+    {  // sparse A^2: the higher powers and the power sums, as in the FP64 form (in V's buffer)
+      float* f2 = (float*)c->V;
+      float *A8f = f2, *A10f = f2 + fl, *A12f = f2 + 2 * fl;
+      const float* lo[3] = {A6f, A8f, A10f};
+      float* hi[3] = {A8f, A10f, A12f};
+      for (int i = 0; i < 3; i++) {
+        RGemmProblem<float> h = fsq(n, S, A2f, lo[i], hi[i]);
+        h.pick = flagA2;
+        h.pick_val = 1;
+        LB_CUDA(rgemm_rowskip(h, c->sm_count, st));
+      }
+      LB_CUDA(launch_real_powsum<float>(n, S, flagA2, A2f, A4f, A6f, A8f, A10f, A12f, b, 0, Vsf, Wsf, c->sm_count,
+                                        st));
+    }
     RGemmProblem<float> vw[2];
     for (int i = 0; i < 2; i++) {
       vw[i] = fsq(n, S, A6f, i == 0 ? Z1f : Z2f, i == 0 ? Vsf : Wsf);
       vw[i].nterms = 3;
       vw[i].X[0] = A6f; vw[i].X[1] = A4f; vw[i].X[2] = A2f;
       vw[i].sX[0] = vw[i].sX[1] = vw[i].sX[2] = nn;
+      vw[i].pick = flagA2;
+      vw[i].pick_val = 0;
     }
     vw[0].coef[0][0] = b[6]; vw[0].coef[0][1] = b[4]; vw[0].coef[0][2] = b[2];
     vw[1].coef[0][0] = b[7]; vw[1].coef[0][1] = b[5]; vw[1].coef[0][2] = b[3];
