@@ -108,6 +108,8 @@ def parse():
                          "GPU timing models) to PATH as JSON lines")
     ap.add_argument("--form", default=None, choices=sorted(FORMS),
                     help="with --headline-only: the form to time (default: the headline form)")
+    ap.add_argument("--instances", type=int, default=4096,
+                    help="instances of the mixed-size batch (default: the whole 4096 of the workload)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the tile autotuner (profiler runs: its launches would precede the step)")
     ap.add_argument("--profile-size", action="store_true",
@@ -265,17 +267,22 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours ---
 
-def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
+def mixed_instances(lb, ctx_big, dev, stream, count, trials):
     """The mixed-size batch (d = 3 / 9 / 27 in ratio 8:4:1, 50 slices and
-    1..64 states each), scaled to ``count`` instances: one lb_run_instances
-    call (split-BF16 and FP64) against a loop of per-instance FP64
-    lb_expm_pade + lb_propagate_batch calls."""
+    1..64 states each, `count` instances): every instance in one CUDA graph
+    (lb_run_instances for the d <= 9 instances on a context sized for large
+    chunks, then for the d = 27 instances on the chain's context, both with a
+    fixed squaring bound so that nothing waits on the host), replayed
+    `trials` times in the fastest mixed form; then the FP64 forms against
+    per-instance FP64 launches (lb_expm_pade + lb_propagate_batch per
+    instance), each on a stated sample, extrapolated by instance counts."""
+    import collections
+
     import numpy as np
     import torch
 
-    from workloads.configs import make_instances
-
     from paper_2603_18052_gb300 import ranks
+    from workloads.configs import make_instances
 
     inst, models = make_instances(count)
     rank, world, _ = ranks.dist_env()
@@ -286,60 +293,140 @@ def mixed_instances(lb, ctx, Pbuf, dev, stream, count):
     def dput(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
+    ctx_small = lb.Context(dev.index or 0, max_n=81, max_batch=64, max_slices=4096)
+    for c in (ctx_small, ctx_big):
+        lb.lb_set_max_squarings(c, 2)
     gens = {}
     for q, m in models.items():
         n = m.d * m.d
         Lb = torch.empty((n, n), dtype=torch.complex128, device=dev)
         Ld = torch.empty_like(Lb)
-        lb.lb_assemble(ctx, dput(m.H0), dput(m.jumps), Lb)
-        lb.lb_assemble(ctx, dput(m.X), None, Ld)
+        lb.lb_assemble(ctx_big, dput(m.H0), dput(m.jumps), Lb)
+        lb.lb_assemble(ctx_big, dput(m.X), None, Ld)
         gens[q] = (Lb, Ld)
     dt = models[1].dt
     us = [dput(x["u"]) for x in inst]
     s0 = [dput(x["states"]) for x in inst]
     st = [x.clone() for x in s0]
     arg = [dict(Lbase=gens[x["nq"]][0], Ldrv=gens[x["nq"]][1], u=us[i], states=st[i]) for i, x in enumerate(inst)]
+    small = [i for i, x in enumerate(inst) if x["d"] <= 9]
+    big = [i for i, x in enumerate(inst) if x["d"] > 9]
+    counts = collections.Counter(x["d"] for x in inst)
 
-    def reset():
-        for a, b in zip(st, s0):
-            a.copy_(b)
+    def reset(idx):
+        for i in idx:
+            st[i].copy_(s0[i])
 
-    def timed(fn):
-        reset()
-        torch.cuda.synchronize()
+    def ev_ms(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         fn()
         b.record(stream)
         b.synchronize()
-        lb.lb_sync_status(ctx)
         return a.elapsed_time(b)
 
-    def per_instance():
-        for i, x in enumerate(inst):
-            S = len(x["u"])
-            n = x["d"] * x["d"]
-            Pv = Pbuf.view(-1)[: S * n * n].view(S, n, n)
-            lb.lb_expm_pade(ctx, gens[x["nq"]][0], gens[x["nq"]][1], us[i], dt, Pv, prec="fp64")
-            lb.lb_propagate_batch(ctx, Pv, st[i], steps_per_slice=1, prec="fp64")
+    def run_all(prec, idx_small, idx_big):
+        renorm = prec not in ("fp64", "fp64_hermitian")
+        if idx_small:
+            lb.lb_run_instances(ctx_small, [arg[i] for i in idx_small], dt, prec=prec, renorm_trace=renorm)
+        if idx_big:
+            lb.lb_run_instances(ctx_big, [arg[i] for i in idx_big], dt, prec=prec, renorm_trace=renorm)
 
-    lb.lb_run_instances(ctx, arg[:8], dt, prec="bf16x3", renorm_trace=True)  # warm-up
-    ms_mixed = timed(lambda: lb.lb_run_instances(ctx, arg, dt, prec="bf16x3", renorm_trace=True))
-    ms_fp64 = timed(lambda: lb.lb_run_instances(ctx, arg, dt, prec="fp64"))
-    ms_loop = timed(per_instance)
     builds = sum(len(x["u"]) for x in inst)
     ssteps = sum(len(x["u"]) * x["states"].shape[0] for x in inst)
-    import collections
-
-    counts = collections.Counter(x["d"] for x in inst)
     res = {"workload": "%d instances (d=3/9/27: %d/%d/%d), 50 slices each, B~U{1..64}; %d builds, %d state-steps"
                        % (len(inst), counts[3], counts[9], counts[27], builds, ssteps)
                        + ("" if world == 1 else " (this rank's share of %d, split by cost)" % count)}
-    for k, ms in (("run_instances_bf16x3", ms_mixed), ("run_instances_fp64", ms_fp64),
-                  ("per_instance_fp64_launches", ms_loop)):
-        res[k] = {"ms": ms, "builds_per_s": builds / (ms / 1e3), "state_steps_per_s": ssteps / (ms / 1e3)}
-    res["speedup_fp64_batched_vs_per_instance"] = ms_loop / ms_fp64
-    res["speedup_bf16x3_batched_vs_per_instance_fp64"] = ms_loop / ms_mixed
+
+    # the whole batch in one captured graph, fastest mixed form
+    form = "fp32_hermitian"
+    reset(range(len(inst)))
+    run_all(form, small, big)  # warm-up (tables, kernels)
+    torch.cuda.synchronize()
+    lb.lb_sync_status(ctx_small)
+    lb.lb_sync_status(ctx_big)
+    g = torch.cuda.CUDAGraph()
+    n0 = lb.lb_launch_count()
+    with torch.cuda.graph(g):
+        run_all(form, small, big)
+    launches = lb.lb_launch_count() - n0
+    ts = []
+    for _ in range(max(1, trials)):
+        reset(range(len(inst)))
+        ts.append(ev_ms(g.replay))
+    lb.lb_sync_status(ctx_small)
+    lb.lb_sync_status(ctx_big)
+    ms = statistics.median(ts)
+    res["captured_" + form] = {"captured": True, "ms": ms, "trial_ms": ts, "builds_per_s": builds / (ms / 1e3),
+                               "state_steps_per_s": ssteps / (ms / 1e3),
+                               "kernel_nodes": launches,
+                               "note": "one CUDA graph holding lb_run_instances for the d<=9 instances (context "
+                                       "with 4096-slice chunks) and for the d=27 instances (200-slice chunks); "
+                                       "median of the replays"}
+    del g
+    for c in (ctx_small, ctx_big):  # the FP64 arms run uncaptured, as a caller would
+        lb.lb_set_max_squarings(c, -1)
+
+    # FP64: batched (lb_run_instances) against per-instance launches, per
+    # d class on a stated sample, extrapolated by the class's instance count
+    samp = {3: 64, 9: 32, 27: 2}
+    by_d = collections.defaultdict(list)
+    for i, x in enumerate(inst):
+        by_d[x["d"]].append(i)
+
+    def per_instance(idx, prec):
+        for i in idx:
+            x = inst[i]
+            S = len(x["u"])
+            n = x["d"] * x["d"]
+            ctx = ctx_small if n <= 81 else ctx_big
+            P = torch.empty((S, n, n), dtype=torch.complex128, device=dev)
+            lb.lb_expm_pade(ctx, arg[i]["Lbase"], arg[i]["Ldrv"], us[i], dt, P, prec=prec)
+            lb.lb_propagate_batch(ctx, P, st[i], steps_per_slice=1, prec=prec)
+
+    fp = {}
+    for prec in ("fp64_hermitian", "fp64"):
+        tot_batched, tot_loop, classes = 0.0, 0.0, {}
+        for d, idx in sorted(by_d.items()):
+            k = min(samp[d], len(idx))
+            sample = idx[:k]
+            scale = len(idx) / k
+            # batched: the whole class for d <= 9 (cheap), the sample at d = 27
+            bidx = idx if d <= 9 else sample
+            bscale = 1.0 if d <= 9 else scale
+            reset(bidx)
+            run_all(prec, bidx if d <= 9 else [], [] if d <= 9 else bidx)  # warm-up
+            tb = []
+            for _ in range(3):
+                reset(bidx)
+                tb.append(ev_ms(lambda: run_all(prec, bidx if d <= 9 else [], [] if d <= 9 else bidx)))
+            tb = statistics.median(tb) * bscale
+            reset(sample)
+            per_instance(sample[:1], prec)  # warm-up
+            reset(sample)
+            t0 = time.perf_counter()
+            per_instance(sample, prec)
+            torch.cuda.synchronize()
+            tl = (time.perf_counter() - t0) * 1e3 * scale
+            classes["d%d" % d] = {"instances": len(idx), "batched_ms": tb, "per_instance_ms": tl,
+                                  "speedup": tl / tb,
+                                  "sample": ("all %d" % len(idx) if d <= 9 else "%d of %d, x%.1f" % (k, len(idx), scale))
+                                  + " batched; %d of %d per instance, x%.1f" % (k, len(idx), scale)}
+            tot_batched += tb
+            tot_loop += tl
+        fp[prec] = {"batched_ms": tot_batched, "per_instance_ms": tot_loop, "speedup": tot_loop / tot_batched,
+                    "classes": classes}
+    lb.lb_sync_status(ctx_small)
+    lb.lb_sync_status(ctx_big)
+    res["fp64_forms"] = fp
+    res["speedup_fp64_hermitian_batched_vs_per_instance_fp64"] = (fp["fp64"]["per_instance_ms"]
+                                                                 / fp["fp64_hermitian"]["batched_ms"])
+    res["speedup_captured_%s_vs_per_instance_fp64" % form] = fp["fp64"]["per_instance_ms"] / ms
+    res["note"] = ("per-instance arms: one lb_expm_pade + lb_propagate_batch call pair per instance through the "
+                   "Python binding, timed with the host clock on a sample per d class and scaled by the class's "
+                   "instance count; batched FP64 at d=27 likewise on a sample (every d=27 build is FP64-LU-bound, "
+                   "so its time is linear in the count)")
+    ctx_small.close()
     return res
 
 
@@ -1081,7 +1168,8 @@ def run_ours(args):
     }
     line["other_workloads"] = other_workloads(lb, accounting, dev, stream, fp64_peak=fp64_peak, fp32_peak=fp32_peak,
                                               bf16_peak=bf16_peak)
-    line["other_workloads"]["mixed_instances"] = mixed_instances(lb, ctx, P, dev, stream, 128)
+    line["other_workloads"]["mixed_instances"] = mixed_instances(lb, ctx, dev, stream, args.instances,
+                                                                 5 if args.steps >= 10 else 2)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, 6)
     if rank == 0:

@@ -86,13 +86,14 @@ def test_squaring_bound_exceeded_is_reported(lbm):
     assert ei.value.name == "LB_EUNSUPPORTED"
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "fp32_hermitian"])
 def test_captured_mixed_instances_replay(lbm, prec):
     """24 instances of the mixed-size batch (d = 3 / 9 / 27, 50 slices,
     1..64 states) captured in one graph: the replay equals the uncaptured
     call bit for bit, and every instance's final states match the oracle
     (its Taylor route through the 50 slices): 1e-12 relative per state in
-    FP64, the stated split-BF16 bound 1e-4 absolute per state."""
+    FP64, the stated bounds (split-BF16 1e-4, FP32 1e-5) absolute per state
+    in the reduced forms (fp32_hermitian is the form the bench captures)."""
     from oracle import expmv as E
 
     dev = torch.device("cuda:0")
@@ -108,7 +109,7 @@ def test_captured_mixed_instances_replay(lbm, prec):
     s0 = [put(x["states"]) for x in inst]
     arg = [dict(Lbase=gens[x["nq"]][0], Ldrv=gens[x["nq"]][1], u=put(x["u"]), states=s0[i].clone())
            for i, x in enumerate(inst)]
-    renorm = prec != "fp64"
+    renorm = not prec.startswith("fp64")
     lbm.lb_run_instances(ctx, arg, 0.1, prec=prec, renorm_trace=renorm)
     lbm.lb_sync_status(ctx)
     ref = [a["states"].clone() for a in arg]
@@ -131,9 +132,9 @@ def test_captured_mixed_instances_replay(lbm, prec):
         if prec == "fp64":
             err = np.max(np.linalg.norm(got - exact, axis=1) / np.linalg.norm(exact, axis=1))
             assert err <= 1e-12, (x["d"], err)
-        else:
+        else:  # the stated bounds: split-BF16 1e-4, FP32 1e-5 (absolute per state)
             err = np.max(np.linalg.norm(got - exact, axis=1))
-            assert err <= 1e-4, (x["d"], err)
+            assert err <= (1e-4 if prec == "bf16x3" else 1e-5), (x["d"], err)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])

@@ -496,7 +496,8 @@ def _instance_set(seed, spec):
     return out
 
 
-@pytest.mark.parametrize("prec,tol,kind", [("fp64", 1e-12, "rel"), ("fp32", 2e-6, "rel"), ("bf16x3", 1e-4, "abs")])
+@pytest.mark.parametrize("prec,tol,kind", [("fp64", 1e-12, "rel"), ("fp32", 2e-6, "rel"), ("bf16x3", 1e-4, "abs"),
+                                           ("fp64_hermitian", 1e-12, "rel"), ("fp32_hermitian", 2e-6, "rel")])
 def test_run_instances_matches_oracle(lbm, dev, prec, tol, kind):
     """Mixed d = 3 / 9 / 27 instances in one call, with chunks that hold
     several whole instances (max_slices = 6), 1 to 64 states per instance
@@ -516,7 +517,7 @@ def test_run_instances_matches_oracle(lbm, dev, prec, tol, kind):
                  steps_per_slice=x["steps"])
         keep.append((Lb, Ld, t))
         arg.append(t)
-    lbm.lb_run_instances(ctx, arg, 0.1, prec=prec, renorm_trace=(prec != "fp64"))
+    lbm.lb_run_instances(ctx, arg, 0.1, prec=prec, renorm_trace=not prec.startswith("fp64"))
     lbm.lb_sync_status(ctx)
     for x, (Lb, Ld, t) in zip(inst, keep):
         Ps = O.slice_propagators(Lb, Ld, x["u"], 0.1)
