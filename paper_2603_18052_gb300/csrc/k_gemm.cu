@@ -290,8 +290,8 @@ namespace {
 // A launch "shape" is the GEMM family, its precision, the number of problems
 // and each problem's (M, N, K, batch, opB, beta).  In tuning mode (set for
 // the calling host thread only, by lb_autotune) every launch times each
-// candidate tile configuration (CUDA events, host wait) and records the
-// fastest for its shape; afterwards launches of a recorded shape use it, and
+// candidate tile configuration (one untimed and three timed runs, CUDA
+// events, host wait) and records the fastest for its shape; afterwards launches of a recorded shape use it, and
 // other shapes use the caller's tile-count heuristic.
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
@@ -329,16 +329,18 @@ cudaError_t tuned_launch(const TuneKey& key, int ncand, int heuristic, TuneCand 
   for (int c = 0; c < ncand; c++) {
     cudaError_t e = run(c, args, st);  // warm-up
     if (e != cudaSuccess) return e;
-    if (cudaEventRecord(ev.e0, st) != cudaSuccess) return cudaErrorUnknown;
-    e = run(c, args, st);
-    if (e != cudaSuccess) return e;
-    if (cudaEventRecord(ev.e1, st) != cudaSuccess || cudaEventSynchronize(ev.e1) != cudaSuccess)
-      return cudaErrorUnknown;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
-    if (ms < best) {
-      best = ms;
-      besti = c;
+    for (int rep = 0; rep < 3; rep++) {  // the fastest of three timed runs
+      if (cudaEventRecord(ev.e0, st) != cudaSuccess) return cudaErrorUnknown;
+      e = run(c, args, st);
+      if (e != cudaSuccess) return e;
+      if (cudaEventRecord(ev.e1, st) != cudaSuccess || cudaEventSynchronize(ev.e1) != cudaSuccess)
+        return cudaErrorUnknown;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+      if (ms < best) {
+        best = ms;
+        besti = c;
+      }
     }
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
