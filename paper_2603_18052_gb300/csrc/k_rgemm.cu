@@ -119,17 +119,25 @@ __device__ __forceinline__ void store_out(const RGemmProblem<T>& P, long long b,
   }
 }
 
-template <typename T, int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
+// Resident CTAs per SM the register allocation is held to: 1 x 1 thread
+// tiles (small problems, many tiles) keep enough CTAs for every tile to be
+// resident at once; larger thread tiles two.
+template <int TM, int TN>
+constexpr int rgemm_min_ctas() {
+  return TM * TN == 1 ? 6 : 2;
+}
+
+template <typename T, int BM, int BN, int TM, int TN, bool DB>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), rgemm_min_ctas<TM, TN>())
     rgemm_kernel(const __grid_constant__ RGroup<T> g) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int BK = 16;
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;  // tile elements each thread stages
   static_assert(LA * NT == BM * BK && LB * NT == BK * BN, "tile must divide over the threads");
-  // two shared-memory stages: the next K block is fetched into registers
+  // DB: two shared-memory stages, the next K block fetched into registers
   // while the current one is multiplied, then stored into the other stage
-  __shared__ __align__(16) T As[2][BK][BM];
-  __shared__ __align__(16) T Bs[2][BK][BN];
+  __shared__ __align__(16) T As[DB ? 2 : 1][BK][BM];
+  __shared__ __align__(16) T Bs[DB ? 2 : 1][BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN);
   const int ty = tid / (BN / TN);
@@ -224,13 +232,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
       }
     };
 
-    fetch(0);
-    stash(0);
-    __syncthreads();
-    int st = 0;
-    for (int k0 = 0; k0 < K; k0 += BK) {
-      const bool more = k0 + BK < K;
-      if (more) fetch(k0 + BK);  // loads in flight during the products below
+    auto multiply = [&](int st) {
 #pragma unroll
       for (int k = 0; k < BK; k++) {
         T a[TM], bb[TN];
@@ -241,9 +243,28 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN), 2)
 #pragma unroll
           for (int j = 0; j < TN; j++) acc[i][j] = fma_t(a[i], bb[j], acc[i][j]);
       }
-      if (more) stash(st ^ 1);
+    };
+    if (DB) {
+      fetch(0);
+      stash(0);
       __syncthreads();
-      st ^= 1;
+      int st = 0;
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) fetch(k0 + BK);  // loads in flight during the products below
+        multiply(st);
+        if (more) stash(st ^ 1);
+        __syncthreads();
+        st ^= 1;
+      }
+    } else {  // one stage: fewer registers, more resident CTAs
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        fetch(k0);
+        stash(0);
+        __syncthreads();
+        multiply(0);
+        __syncthreads();
+      }
     }
 
 #pragma unroll
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(256) sparse_flags_kernel(int n, int S, const T
   }
 }
 
-template <typename T, int BM, int BN, int TM, int TN>
+template <typename T, int BM, int BN, int TM, int TN, bool DB>
 cudaError_t launch_rcfg(const RGemmProblem<T>* probs, int nprob, int sm_count, cudaStream_t st) {
   RGroup<T> g;
   g.nprob = nprob;
@@ -364,13 +385,13 @@ cudaError_t launch_rcfg(const RGemmProblem<T>* probs, int nprob, int sm_count, c
   static int occ = -1;  // resident CTAs per SM for this configuration
   if (occ < 0) {
     int o = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, rgemm_kernel<T, BM, BN, TM, TN>, NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, rgemm_kernel<T, BM, BN, TM, TN, DB>, NT, 0);
     if (e != cudaSuccess) return e;
     occ = std::max(1, o);
   }
   const long long grid = std::min<long long>(acc, (long long)sm_count * occ);
   count_launch();
-  rgemm_kernel<T, BM, BN, TM, TN><<<(unsigned)grid, NT, 0, st>>>(g);
+  rgemm_kernel<T, BM, BN, TM, TN, DB><<<(unsigned)grid, NT, 0, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -417,19 +438,20 @@ cudaError_t rrun(int cand, const void* a, cudaStream_t st) {
 cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
   typedef cudaError_t (*fn)(const RGemmProblem<double>*, int, int, cudaStream_t);
-  static const fn cands[3] = {launch_rcfg<double, 16, 16, 1, 1>, launch_rcfg<double, 32, 32, 2, 2>,
-                              launch_rcfg<double, 64, 64, 4, 4>};
-  // 32 x 32 tiles when there are enough of them to balance the persistent
-  // grid, else 16 x 16
+  static const fn cands[5] = {launch_rcfg<double, 16, 16, 1, 1, false>, launch_rcfg<double, 32, 32, 2, 2, true>,
+                              launch_rcfg<double, 64, 64, 4, 4, true>, launch_rcfg<double, 16, 16, 1, 1, true>,
+                              launch_rcfg<double, 32, 32, 2, 2, false>};
+  // 32 x 32 tiles (two stages) when there are enough of them to balance the
+  // persistent grid, else 16 x 16 (one stage, more resident CTAs)
   const long long t32 = rtiles(probs, nprob, 32, 32);
   const RArgs<double> a{cands, probs, nprob, sm_count};
-  return tuned_launch(rshape_key(probs, nprob), 3, t32 >= 8LL * sm_count ? 1 : 0, rrun<double>, &a, st);
+  return tuned_launch(rshape_key(probs, nprob), 5, t32 >= 8LL * sm_count ? 1 : 0, rrun<double>, &a, st);
 }
 
 cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
   typedef cudaError_t (*fn)(const RGemmProblem<float>*, int, int, cudaStream_t);
-  static const fn cands[2] = {launch_rcfg<float, 32, 32, 2, 2>, launch_rcfg<float, 64, 64, 4, 4>};
+  static const fn cands[2] = {launch_rcfg<float, 32, 32, 2, 2, true>, launch_rcfg<float, 64, 64, 4, 4, true>};
   const long long t64 = rtiles(probs, nprob, 64, 64);
   const RArgs<float> a{cands, probs, nprob, sm_count};
   return tuned_launch(rshape_key(probs, nprob), 2, t64 >= 2LL * sm_count ? 1 : 0, rrun<float>, &a, st);
