@@ -256,6 +256,28 @@ lb_status lb_grape_grad(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, co
                         void* stream);
 
 /*
+ * lb_grape_grad_batch -- lb_grape_grad for K independent problems in one
+ * call (the many GRAPE optimisations of a training set for the warm-start
+ * network, Sec. 2.5):
+ *   problem k has the base generator Lbase + k * lbase_stride (n x n;
+ *   lbase_stride = 0 shares one, else lbase_stride >= n*n), the shared
+ *   drive generator Ldrv, the controls u[k * nslices + s], the start and
+ *   target operators X0[k], Xtarget[k] (B x n each, stored one problem after
+ *   another); fidelity_out[k] and grad_out[k * nslices + s] are that
+ *   problem's F and dF/du[s] as lb_grape_grad defines them.
+ *   prec = LB_FP64: exactly the arithmetic of lb_grape_grad.  LB_FP32: the
+ *   Pade products and their derivatives in FP32 (FP32 operands and
+ *   accumulation); LU, solve, squarings, chains and reductions FP64.
+ * Limits: as lb_grape_grad, and K * nslices <= max_slices,
+ * K * B <= max_batch, K <= 65535 (LB_EUNSUPPORTED beyond).  Reads the largest
+ * squaring count back to the host (not capturable).
+ */
+lb_status lb_grape_grad_batch(lb_ctx* ctx, int n, int K, int nslices, const lb_c64* Lbase, long long lbase_stride,
+                              const lb_c64* Ldrv, const double* u, double dt, int steps_per_slice, int B,
+                              const lb_c64* X0, const lb_c64* Xtarget, lb_precision prec, double* fidelity_out,
+                              double* grad_out, void* stream);
+
+/*
  * lb_run_instances -- many independent problems of mixed size in one call:
  * for every instance i, its slice propagators
  *   P_{i,s} = exp((Lbase_i + u_i[s] Ldrv_i) dt)      (Eq. 5, Algorithm 1)

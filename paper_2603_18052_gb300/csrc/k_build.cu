@@ -85,10 +85,11 @@ __global__ void assemble_kernel(int d, const z64* __restrict__ H, int K, const z
 // Column absolute sums of A_s = (Lbase + u_s Ldrv) dt, max-reduced per slice.
 // grid: (ceil(n / blockDim), S).  Threads own columns, loop over rows
 // (coalesced: a warp reads 32 consecutive columns of one row).
-__global__ void colnorm_kernel(int n, const z64* __restrict__ Lb, const z64* __restrict__ Ld,
+__global__ void colnorm_kernel(int n, int S, const z64* __restrict__ Lb, const z64* __restrict__ Ld,
                                const double* __restrict__ u, double dt,
                                unsigned long long* __restrict__ norm_bits) {
-  const int s = blockIdx.y;
+  // slices s = blockIdx.y, blockIdx.y + gridDim.y, ... (gridDim.y <= 65535)
+  for (int s = blockIdx.y; s < S; s += gridDim.y) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   double sum = 0.0;
   if (c < n) {
@@ -118,6 +119,8 @@ __global__ void colnorm_kernel(int n, const z64* __restrict__ Lb, const z64* __r
     double v = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) atomicMax(norm_bits + s, (unsigned long long)__double_as_longlong(v));
+  }
+  __syncthreads();  // red[] is reused by the next slice
   }
 }
 
@@ -374,9 +377,9 @@ cudaError_t launch_slice_prepare(int n, int S, const z64* Lbase, const z64* Ldrv
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(sc + S, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  dim3 g1((n + 127) / 128, S);
+  dim3 g1((n + 127) / 128, S < 65535 ? S : 65535);
   count_launch();
-  colnorm_kernel<<<g1, 128, 0, st>>>(n, Lbase, Ldrv, u, dt, norm_bits);
+  colnorm_kernel<<<g1, 128, 0, st>>>(n, S, Lbase, Ldrv, u, dt, norm_bits);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launch();

@@ -13,7 +13,12 @@
 //   forward chain X_t = P X_{t-1}, adjoint chain Lam_{t-1} = P^+ Lam_t,
 //   F = Re sum <Xt, X_T> / B,  g_s = sum_{t in s} Re <Lam_t, dP_s X_{t-1}> / B.
 // The gradient of slice s is a GEMM of the stacked states of its steps with
-// dP_s^T followed by a deterministic reduction.  All FP64.
+// dP_s^T followed by a deterministic reduction.  All FP64, except that
+// lb_grape_grad_batch may run the Pade products and their derivatives in
+// FP32.  lb_grape_grad_batch does K independent problems (own base
+// generator, controls, start and target operators; shared drive) in one
+// differentiated build of all K * nslices slices and one multi-problem
+// launch per chain.
 #include "lb_internal.cuh"
 
 #include <algorithm>
@@ -83,8 +88,12 @@ struct GrapeWs {
   z64 *E, *M2, *M4, *M6, *dZ1, *dZ2, *dV, *dW, *R, *dR, *T1, *T2, *RHS, *Y3, *Xh, *Lh, *Yg, *S0, *S1;
 };
 
+// History buffers: room for the longest chain of one call with the most
+// states (S slices x 20 steps, up to 64 states), capped at 2^27 complex
+// values (2 GiB) each; a call that needs more returns LB_EUNSUPPORTED.
+constexpr size_t kHistCap = size_t(1) << 27;
 size_t hist_elems(int nG, int Bg, int S) {
-  return ((size_t)S * kGrapeMaxStepsPerSlice + 1) * Bg * nG;
+  return std::min(((size_t)S * kGrapeMaxStepsPerSlice + 1) * Bg * nG, kHistCap);
 }
 
 GrapeWs carve(lb_ctx* c) {
@@ -147,38 +156,49 @@ using namespace lb;
 
 // P_s = exp(A_s) and dP_s = d/du_s exp((Lbase + u_s Ldrv) dt) into w.R and
 // w.dR for the S slices (the differentiated Pade build described above).
+// Gs (optional): the S slice generators already formed (Lbase_k + u Ldrv of
+// several problems); Ld is then only the direction of the derivative.
+// prec = LB_FP32: the Pade products and their derivatives in FP32 (FP32
+// operands and accumulation, FP64 epilogue); the LU, the solve and the
+// squarings stay FP64.
 static lb_status frechet_build(lb_ctx* c, int n, int S, const z64* Lb, const z64* Ld, const double* u, double dt,
-                        GrapeWs& w, cudaStream_t st) {
+                        GrapeWs& w, cudaStream_t st, const z64* Gs = nullptr, lb_precision prec = LB_FP64) {
   const long long nn = (long long)n * n;
   const double* b = c->pade_b;
+  typedef cudaError_t (*gemm_fn)(const ZGemmProblem*, int, int, cudaStream_t);
+  const gemm_fn zgemm_prod = prec == LB_FP32 ? zgemm_f32 : zgemm_f64;
     // scaled A and E, s per slice
-    LB_CUDA(launch_slice_prepare(n, S, Lb, Ld, u, dt, c->A, c->norm_bits, c->sc, nullptr, nullptr, c->err_dev,
-                                 c->sm_count, st));
+    if (Gs != nullptr)
+      LB_CUDA(launch_slice_prepare(n, S, Gs, nullptr, nullptr, dt, c->A, c->norm_bits, c->sc, nullptr, nullptr,
+                                   c->err_dev, c->sm_count, st));
+    else
+      LB_CUDA(launch_slice_prepare(n, S, Lb, Ld, u, dt, c->A, c->norm_bits, c->sc, nullptr, nullptr, c->err_dev,
+                                   c->sm_count, st));
     LB_CUDA(cudaMemcpyAsync(c->scmax_host, c->sc + S, sizeof(int), cudaMemcpyDeviceToHost, st));
     LB_CUDA(cudaEventRecord(c->ev_scmax, st));
     LB_CUDA(launch_scale_bcast(n, S, Ld, dt, c->sc, w.E, st));
     // powers and their derivatives
     ZGemmProblem p = sq(n, S, c->A, c->A, c->A2);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A, w.E, w.M2);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, w.E, c->A, w.M2);
     p.beta = 1.0;
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A2, c->A2, c->A4);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A2, w.M2, w.M4);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, w.M2, c->A2, w.M4);
     p.beta = 1.0;
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A4, c->A2, c->A6);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A4, w.M2, w.M6);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, w.M4, c->A2, w.M6);
     p.beta = 1.0;
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[12], b[10], b[8], c->Z1, st));
     LB_CUDA(launch_lincomb3((int)nn, S, c->A6, c->A4, c->A2, b[13], b[11], b[9], c->Z2, st));
     LB_CUDA(launch_lincomb3((int)nn, S, w.M6, w.M4, w.M2, b[12], b[10], b[8], w.dZ1, st));
@@ -198,24 +218,24 @@ static lb_status frechet_build(lb_ctx* c, int n, int S, const z64* Lb, const z64
     g4[1] = with3(sq(n, S, c->A6, c->Z2, c->W), c->A6, c->A4, c->A2, b[7], b[5], b[3], b[1]);
     g4[2] = with3(sq(n, S, c->A6, w.dZ1, w.dV), w.M6, w.M4, w.M2, b[6], b[4], b[2], 0.0);
     g4[3] = with3(sq(n, S, c->A6, w.dZ2, w.dW), w.M6, w.M4, w.M2, b[7], b[5], b[3], 0.0);
-    LB_CUDA(zgemm_f64(g4, 4, c->sm_count, st));
+    LB_CUDA(zgemm_prod(g4, 4, c->sm_count, st));
     ZGemmProblem g2[2];
     g2[0] = sq(n, S, w.M6, c->Z1, w.dV);
     g2[0].beta = 1.0;
     g2[1] = sq(n, S, w.M6, c->Z2, w.dW);
     g2[1].beta = 1.0;
-    LB_CUDA(zgemm_f64(g2, 2, c->sm_count, st));
+    LB_CUDA(zgemm_prod(g2, 2, c->sm_count, st));
     // Mx = V - A W' ;  dU = E W' + A dW' (in T1)
     p = sq(n, S, c->A, c->W, c->Mx);
     p.alpha = -1.0;
     p.nterms = 1;
     p.X[0] = c->V; p.sX[0] = nn; p.coef[0] = 1.0;
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, w.E, c->W, w.T1);
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     p = sq(n, S, c->A, w.dW, w.T1);
     p.beta = 1.0;
-    LB_CUDA(zgemm_f64(&p, 1, c->sm_count, st));
+    LB_CUDA(zgemm_prod(&p, 1, c->sm_count, st));
     // RHS = [V + U | dV + dU | dV - dU]  (n x 3n per slice), V + U = 2V - Mx
     const long long ld3 = 3LL * n, s3 = 3 * nn;
     LB_CUDA(launch_combine(n, S, 2.0, c->V, n, nn, -1.0, c->Mx, n, nn, w.RHS, ld3, s3, st));
@@ -267,6 +287,10 @@ extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* 
   if (c->max_n > kGrapeMaxN || n > kGrapeMaxN || B > kGrapeMaxB || nslices > c->max_slices ||
       steps_per_slice > kGrapeMaxStepsPerSlice)
     return LB_EUNSUPPORTED;
+  {
+    const int nG = std::min(c->max_n, kGrapeMaxN), Bg = std::min(c->max_batch, kGrapeMaxB);
+    if (((size_t)nslices * steps_per_slice + 1) * B * n > hist_elems(nG, Bg, c->max_slices)) return LB_EUNSUPPORTED;
+  }
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != c->device) cudaSetDevice(c->device);
@@ -302,6 +326,84 @@ extern "C" lb_status lb_grape_grad(lb_ctx* c, int n, int nslices, const lb_c64* 
   }();
   if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
   return rs;
+}
+
+namespace lb {
+namespace {
+// G[k S + s] = Lbase_k + u[k S + s] Ldrv  (Lbase_k = Lbase + k lb_stride)
+__global__ void gen_batch_kernel(int n, int S, long long total, const z64* __restrict__ Lb, long long lb_stride,
+                                 const z64* __restrict__ Ld, const double* __restrict__ u, z64* __restrict__ G) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long sl = e / nn, o = e - sl * nn, k = sl / S;
+    const z64 a = Lb[k * lb_stride + o], d = Ld[o];
+    const double us = u[sl];
+    G[e] = make_double2(fma(us, d.x, a.x), fma(us, d.y, a.y));
+  }
+}
+}  // namespace
+}  // namespace lb
+
+extern "C" lb_status lb_grape_grad_batch(lb_ctx* c, int n, int K, int nslices, const lb_c64* Lbase,
+                                         long long lbase_stride, const lb_c64* Ldrv, const double* u, double dt,
+                                         int steps_per_slice, int B, const lb_c64* X0, const lb_c64* Xtarget,
+                                         lb_precision prec, double* fidelity_out, double* grad_out, void* stream) {
+  if (c == nullptr || Lbase == nullptr || Ldrv == nullptr || u == nullptr || X0 == nullptr ||
+      Xtarget == nullptr || fidelity_out == nullptr || grad_out == nullptr)
+    return LB_EINVAL;
+  if (n < 1 || n > c->max_n || K < 1 || nslices < 1 || steps_per_slice < 1 || B < 1 || lbase_stride < 0 ||
+      !std::isfinite(dt) || (prec != LB_FP64 && prec != LB_FP32))
+    return LB_EINVAL;
+  int d = 1;
+  while (d * d < n) d++;
+  if (d * d != n) return LB_EINVAL;
+  const long long nn = (long long)n * n;
+  if (lbase_stride != 0 && lbase_stride < nn) return LB_EINVAL;
+  if (c->max_n > lb::kGrapeMaxN || B > lb::kGrapeMaxB || (long long)K * nslices > c->max_slices ||
+      (long long)K * B > c->max_batch || steps_per_slice > lb::kGrapeMaxStepsPerSlice || K > 65535)
+    return LB_EUNSUPPORTED;
+  {
+    const int nG = std::min(c->max_n, lb::kGrapeMaxN), Bg = std::min(c->max_batch, lb::kGrapeMaxB);
+    if ((size_t)K * nslices * steps_per_slice * B * n > hist_elems(nG, Bg, c->max_slices)) return LB_EUNSUPPORTED;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return LB_EUNSUPPORTED;  // reads the squaring count back to the host
+  lb::DeviceGuard guard(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = nslices, m = steps_per_slice, SK = K * nslices;
+  const long long bn = (long long)B * n, T = (long long)S * m;
+  GrapeWs w = carve(c);
+  const z64* Ld = (const z64*)Ldrv;
+  // every problem's slice generators, then the differentiated build of all
+  // K * nslices slices at once
+  const long long total = nn * SK;
+  lb::count_launch();
+  lb::gen_batch_kernel<<<grid_for(total), 256, 0, st>>>(n, S, total, (const z64*)Lbase, lbase_stride, Ld, u,
+                                                         c->Ginst);
+  LB_CUDA(cudaGetLastError());
+  lb_status fb = frechet_build(c, n, SK, nullptr, Ld, nullptr, dt, w, st, c->Ginst, prec);
+  if (fb != LB_OK) return fb;
+  // forward and adjoint chains of every problem, compact history
+  z64* fwd = c->Rtmp;
+  z64* adj = c->Xh;
+  LB_CUDA(cudaMemcpyAsync(fwd, X0, sizeof(z64) * bn * K, cudaMemcpyDeviceToDevice, st));
+  LB_CUDA(launch_propagate_resident_f64_multi(n, K, S, w.R, m, B, fwd, 0, w.Xh, c->sm_count, st));
+  LB_CUDA(cudaMemcpyAsync(adj, Xtarget, sizeof(z64) * bn * K, cudaMemcpyDeviceToDevice, st));
+  LB_CUDA(launch_propagate_resident_f64_multi(n, K, S, w.R, m, B, adj, 1, w.Lh, c->sm_count, st));
+  // Yg[k S + s] = (stacked X_{t-1}, t in slice s of problem k) dP^T
+  ZGemmProblem y;
+  y.M = (int)(m * B); y.N = n; y.K = n;
+  y.A = w.Xh; y.lda = n; y.sA = m * bn;
+  y.B = w.dR; y.ldb = n; y.sB = nn; y.opB = 1;
+  y.C = w.Yg; y.ldc = n; y.sC = m * bn;
+  y.batch = SK;
+  LB_CUDA(zgemm_f64(&y, 1, c->sm_count, st));
+  LB_CUDA(launch_redot(SK, m * bn, w.Lh, m * bn, w.Yg, m * bn, 1.0 / B, grad_out, st));
+  LB_CUDA(launch_redot(K, bn, (const z64*)Xtarget, bn, fwd, bn, 1.0 / B, fidelity_out, st));
+  (void)T;
+  return LB_OK;
 }
 
 namespace lb {

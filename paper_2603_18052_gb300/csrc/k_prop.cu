@@ -33,9 +33,14 @@ size_t resident_f32_smem(int n, int chunk) {
 // adjoint: apply P^+ (load conj(P[j][i]) as row i) with the slices in reverse
 // order.  hist (optional): the states before the first step and after every
 // step, indexed t = 0..T forward or T - k after k adjoint steps.
+// Several independent problems (blockIdx.y = problem k): its propagators at
+// P + k p_stride, states at states + k x_stride, history at hist + k h_stride.
+// hcompact: the history keeps only what the gradient reads, T entries per
+// problem: forward X_0 .. X_{T-1} at t, adjoint Lam_1 .. Lam_T at t - 1.
 __global__ void __launch_bounds__(kResThreads)
     prop_resident_f64_kernel(int n, int nslices, const z64* __restrict__ P, int steps_per_slice, int B,
-                             int chunk, z64* __restrict__ states, int adjoint, z64* __restrict__ hist) {
+                             int chunk, z64* __restrict__ states, int adjoint, z64* __restrict__ hist,
+                             long long p_stride, long long x_stride, long long h_stride, int hcompact) {
   extern __shared__ __align__(16) double sm[];
   double* Pr = sm;
   double* Pi = Pr + n * n;
@@ -47,6 +52,9 @@ __global__ void __launch_bounds__(kResThreads)
   double* yi = yr + chunk * n;
   const int b0 = blockIdx.x * chunk;
   if (b0 >= B) return;
+  P += blockIdx.y * p_stride;
+  states += blockIdx.y * x_stride;
+  if (hist != nullptr) hist += blockIdx.y * h_stride;
   const int nb = min(chunk, B - b0);
   const int tid = threadIdx.x;
   const long long nn = (long long)n * n;
@@ -59,9 +67,15 @@ __global__ void __launch_bounds__(kResThreads)
   const int work = nb * n;
   const long long T = (long long)nslices * steps_per_slice;
   long long hidx = adjoint ? T : 0;
-  if (hist != nullptr)
+  // where the state after hidx steps goes in the history (-1: not kept)
+  auto hpos = [&](long long h) -> long long {
+    if (!hcompact) return h;
+    if (adjoint) return h >= 1 ? h - 1 : -1;
+    return h <= T - 1 ? h : -1;
+  };
+  if (hist != nullptr && hpos(hidx) >= 0)
     for (int e = tid; e < work; e += blockDim.x)
-      hist[(hidx * B + b0) * n + e] = states[(long long)b0 * n + e];
+      hist[(hpos(hidx) * B + b0) * n + e] = states[(long long)b0 * n + e];
   for (int si = 0; si < nslices; si++) {
     const int s = adjoint ? nslices - 1 - si : si;
     __syncthreads();
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(kResThreads)
         xr[e] = r;
         xi[e] = im;
         xs[e] = r + im;
-        if (hist != nullptr) hist[(hidx * B + b0) * n + e] = make_double2(r, im);
+        if (hist != nullptr && hpos(hidx) >= 0) hist[(hpos(hidx) * B + b0) * n + e] = make_double2(r, im);
       }
       __syncthreads();
     }
@@ -422,7 +436,28 @@ cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P,
   const int grid = (B + chunk - 1) / chunk;
   count_launch();
   prop_resident_f64_kernel<<<grid, kResThreads, smem, st>>>(n, nslices, P, steps_per_slice, B, chunk,
-                                                            states, adjoint, hist);
+                                                            states, adjoint, hist, 0, 0, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_resident_f64_multi(int n, int K, int nslices, const z64* P, int steps_per_slice, int B,
+                                                z64* states, int adjoint, z64* hist, int sm_count, cudaStream_t st) {
+  if (K < 1 || K > 65535) return cudaErrorInvalidValue;
+  const long long nn = (long long)n * n, T = (long long)nslices * steps_per_slice;
+  int chunk = std::max(1, std::min(B, (B * K + sm_count - 1) / sm_count));
+  size_t smem = resident_f64_smem(n, chunk);
+  while (smem > 227 * 1024 && chunk > 1) {
+    chunk = (chunk + 1) / 2;
+    smem = resident_f64_smem(n, chunk);
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = set_smem_once((const void*)prop_resident_f64_kernel, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((B + chunk - 1) / chunk, K);
+  count_launch();
+  prop_resident_f64_kernel<<<grid, kResThreads, smem, st>>>(n, nslices, P, steps_per_slice, B, chunk, states,
+                                                            adjoint, hist, nslices * nn, (long long)B * n,
+                                                            T * B * n, 1);
   return cudaGetLastError();
 }
 

@@ -391,6 +391,13 @@ cudaError_t launch_propagate_resident_f64_hist(int n, int nslices, const z64* P,
                                                z64* states, int adjoint, z64* hist, int sm_count,
                                                cudaStream_t st);
 
+// The same chain for K independent problems in one launch (problem k: its
+// nslices propagators at P + k nslices n^2, its B states at states + k B n),
+// with the compact history (T = nslices * steps_per_slice entries per
+// problem at hist + k T B n: forward X_0 .. X_{T-1}, adjoint Lam_1 .. Lam_T).
+cudaError_t launch_propagate_resident_f64_multi(int n, int K, int nslices, const z64* P, int steps_per_slice, int B,
+                                                z64* states, int adjoint, z64* hist, int sm_count, cudaStream_t st);
+
 // dst[s](ld_d, col off_d) = c0 X0[s](ld_0, off_0) + c1 X1[s](ld_1, off_1), n x n blocks.
 cudaError_t launch_combine(int n, int S, double c0, const z64* X0, long long ld0, long long s0, double c1,
                            const z64* X1, long long ld1, long long s1, z64* dst, long long ldd, long long sd,

@@ -46,6 +46,7 @@ EXPORTED = (
     "lb_expm_pade",
     "lb_propagate_batch",
     "lb_grape_grad",
+    "lb_grape_grad_batch",
     "lb_propagate_batch_static",
     "lb_run_instances",
     "lb_mlp_forward",
@@ -158,6 +159,8 @@ def lib():
     L.lb_adam_step_f64.argtypes = [ll, vp, vp, vp, vp, f64, f64, f64, f64, i32, i32, vp]
     L.lb_grape_grad.restype = i32
     L.lb_grape_grad.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, i32, vp, vp, vp, vp, vp]
+    L.lb_grape_grad_batch.restype = i32
+    L.lb_grape_grad_batch.argtypes = [vp, i32, i32, i32, vp, ll, vp, vp, f64, i32, i32, vp, vp, i32, vp, vp, vp]
     L.lb_expmv.restype = i32
     L.lb_expmv.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, ctypes.POINTER(ctypes.c_int), vp]
     L.lb_expmv_hermitian.restype = i32
@@ -347,6 +350,28 @@ def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelit
                                _ptr(fidelity_out, torch.float64, "fidelity_out", (1,)),
                                _ptr(grad_out, torch.float64, "grad_out", (S,)), _stream(stream)),
            "lb_grape_grad")
+
+
+def lb_grape_grad_batch(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelity_out, grad_out, prec="fp64",
+                        stream=None):
+    """K problems at once: Lbase (n, n) shared or (K, n, n) per problem, Ldrv
+    (n, n) shared, u (K, S), X0 / Xtarget (K, B, n); fidelity_out (K,),
+    grad_out (K, S)."""
+    c128 = torch.complex128
+    K, S = u.shape
+    n = Ldrv.shape[0]
+    B = X0.shape[1]
+    if Lbase.dim() == 2:
+        lbp, stride = _ptr(Lbase, c128, "Lbase", (n, n)), 0
+    else:
+        lbp, stride = _ptr(Lbase, c128, "Lbase", (K, n, n)), n * n
+    _check(lib().lb_grape_grad_batch(ctx.handle, n, K, S, lbp, stride, _ptr(Ldrv, c128, "Ldrv", (n, n)),
+                                     _ptr(u, torch.float64, "u", (K, S)), float(dt), int(steps_per_slice), B,
+                                     _ptr(X0, c128, "X0", (K, B, n)), _ptr(Xtarget, c128, "Xtarget", (K, B, n)),
+                                     PRECISIONS.get(prec, prec),
+                                     _ptr(fidelity_out, torch.float64, "fidelity_out", (K,)),
+                                     _ptr(grad_out, torch.float64, "grad_out", (K, S)), _stream(stream)),
+           "lb_grape_grad_batch")
 
 
 def lb_expm_frechet(ctx, Lbase, Ldrv, u, dt, P_out, dP_out, stream=None):

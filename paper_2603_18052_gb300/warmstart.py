@@ -16,7 +16,9 @@ F_avg = (d_c F + 1) / (d_c + 1), with F = Re sum_b <X_target,b, X_T,b> / d_c^2
 over the d_c^2 basis operators |i><j|.
 
 Every arithmetic step runs in the library's kernels; this module only moves
-tensors and loops.
+tensors and loops.  `experiment_batched` runs the experiment at the
+configured scale: thousands of GRAPE optimisations advance together, one
+lb_grape_grad_batch call per iteration for all of them.
 """
 
 import argparse
@@ -121,6 +123,48 @@ def grape(ctx, prob, u0, target=0.999, max_iter=300, lr=0.01, history=None):
         lb.lb_adam_step_f64(u, g, m, v, it, lr=lr, ascend=True)
     torch.cuda.synchronize()
     return it, best, time.perf_counter() - t0
+
+
+def grape_batch(ctx, probs, U, target, max_iter=300, lr=0.01, prec="fp64"):
+    """Plain GRAPE (Adam ascent of F) for K problems of one size at once:
+    one lb_grape_grad_batch call and one lb_adam_step_f64 over all K x
+    NSLICES controls per iteration.  U (K, NSLICES, device float64) holds the
+    starting controls and receives, for every problem that reached F_avg >=
+    target, the control of the iteration where it first did (the last one
+    otherwise).  Returns (iterations per problem: the first iteration at the
+    target, or max_iter; best F_avg per problem; seconds of the batch)."""
+    K = len(probs)
+    dev = U.device
+    Lb = torch.stack([p.Lb for p in probs]).contiguous()
+    X0 = torch.stack([p.X0 for p in probs]).contiguous()
+    Xt = torch.stack([p.Xt for p in probs]).contiguous()
+    dc = probs[0].dc
+    g, m, v = torch.zeros_like(U), torch.zeros_like(U), torch.zeros_like(U)
+    F = torch.zeros(K, dtype=torch.float64, device=dev)
+    iters = np.full(K, max_iter)
+    best = np.full(K, -1.0)
+    done = np.zeros(K, dtype=bool)
+    saved = U.clone()
+    t0 = time.perf_counter()
+    for it in range(1, max_iter + 1):
+        lb.lb_grape_grad_batch(ctx, Lb, probs[0].Ld, U, DT, 1, X0, Xt, F, g, prec=prec)
+        fa = (dc * F.cpu().numpy() + 1.0) / (dc + 1.0)
+        best = np.maximum(best, fa)
+        new = (fa >= target) & ~done
+        if new.any():
+            idx = torch.from_numpy(np.nonzero(new)[0]).to(dev)
+            saved[idx] = U[idx]
+            iters[new] = it
+            done |= new
+            if done.all():
+                break
+        lb.lb_adam_step_f64(U, g, m, v, it, lr=lr, ascend=True)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    if done.any():
+        idx = torch.from_numpy(np.nonzero(done)[0]).to(dev)
+        U[idx] = saved[idx]
+    return iters, best, secs
 
 
 def random_u(seed, dev):
@@ -257,6 +301,103 @@ def experiment(nq=1, n_train=128, n_test=8, max_iter=300, target=0.999, seed=0x5
                 target_reached_plain=sum(r["random_best"] >= target for r in rows), tests=rows)
 
 
+def iteration_seconds(ctx, prob, reps=20):
+    """Wall time of one plain-GRAPE iteration of a single problem (one
+    lb_grape_grad call and one Adam step), the median of `reps`: the
+    per-instance time the batched runs' iteration counts are converted
+    with."""
+    u = random_u(1, prob.Lb.device)
+    g, m, v = torch.zeros_like(u), torch.zeros_like(u), torch.zeros_like(u)
+    F = torch.zeros(1, dtype=torch.float64, device=u.device)
+    ts = []
+    for r in range(reps + 2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lb.lb_grape_grad(ctx, prob.Lb, prob.Ld, u, DT, 1, prob.X0, prob.Xt, F, g)
+        F.item()
+        lb.lb_adam_step_f64(u, g, m, v, r + 1, lr=0.01, ascend=True)
+        torch.cuda.synchronize()
+        if r >= 2:
+            ts.append(time.perf_counter() - t0)
+    return float(np.median(ts))
+
+
+def experiment_batched(n_train=(20000, 1024), n_test=100, max_iter=300, targets=(0.999, 0.96),
+                       batch=(2048, 128), precs=("fp64", "fp32"), seed=0x5EED0004, dev=None, epochs=60,
+                       train_batch=256, log=print):
+    """The warm-start experiment at the configured scale, with every GRAPE run
+    batched (lb_grape_grad_batch): n_train[i] library-generated GRAPE
+    solutions at d = 3 and d = 9 (batches of batch[i] problems, products in
+    precs[i]), one network trained on both sizes (d is an input), then per
+    size n_test held-out problems solved from a random start and from the
+    network's proposal (FP64), both to the threshold targets[i] fixed before
+    the runs.  Reports iteration counts (medians and the share of problems
+    reaching the threshold) and wall times per instance (iterations x the
+    measured time of one single-problem iteration)."""
+    dev = dev or torch.device("cuda:0")
+    X, Y = [], []
+    res = dict(nslices=NSLICES, dt=DT, max_iter=max_iter, sizes={})
+    for nq, ntr, K, prec, target in zip((1, 2), n_train, batch, precs, targets):
+        d = 3 ** nq
+        ctx = lb.Context(dev.index or 0, max_n=d * d, max_batch=(2 ** nq) ** 2 * K, max_slices=K * NSLICES)
+        t0 = time.perf_counter()
+        its, bests = [], []
+        for b0 in range(0, ntr, K):
+            k = min(K, ntr - b0)
+            probs = sample_problems(ctx, stream_seed(seed, "train%d_%d" % (nq, b0)), k, nq, dev)
+            U = torch.stack([random_u(stream_seed(seed, "u%d_%d" % (nq, b0 + i)), dev) for i in range(k)]).contiguous()
+            it, best, _ = grape_batch(ctx, probs, U, target, max_iter=max_iter, prec=prec)
+            its.extend(it.tolist())
+            bests.extend(best.tolist())
+            X.extend(p.features() for p in probs)
+            Y.extend((U / U_SCALE).float().cpu().numpy())
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        res["sizes"]["d%d" % d] = dict(d=d, n_train=ntr, target_f_avg=target, batch=K, product_precision=prec,
+                                       dataset_seconds=t_data, dataset_median_iters=float(np.median(its)),
+                                       dataset_median_best=float(np.median(bests)),
+                                       dataset_reached=int(np.sum(np.array(bests) >= target)))
+        log("d=%d dataset: %d GRAPE solutions in %.1f s (%d reached %.3g)" % (d, ntr, t_data,
+                                                                         res["sizes"]["d%d" % d]["dataset_reached"],
+                                                                         target))
+        ctx.close()
+    net = WarmStartNet(dev)
+    Xd = torch.from_numpy(np.array(X, dtype=np.float32)).to(dev)
+    Yd = torch.from_numpy(np.array(Y, dtype=np.float32)).to(dev)
+    t1 = time.perf_counter()
+    losses = net.train(Xd, Yd, epochs=epochs, batch=train_batch)
+    res["train_seconds"] = time.perf_counter() - t1
+    res["train_samples"] = int(Xd.shape[0])
+    res["loss_first_last"] = [losses[0], losses[-1]]
+    log("training: %d samples, %d epochs in %.1f s, loss %.4g -> %.4g" % (Xd.shape[0], epochs, res["train_seconds"],
+                                                                        losses[0], losses[-1]))
+    for nq, target in zip((1, 2), targets):
+        d = 3 ** nq
+        ctx = lb.Context(dev.index or 0, max_n=d * d, max_batch=(2 ** nq) ** 2 * n_test, max_slices=n_test * NSLICES)
+        probs = sample_problems(ctx, stream_seed(seed, "test%d" % nq), n_test, nq, dev)
+        U_r = torch.stack([random_u(stream_seed(seed, "test_u%d_%d" % (nq, i)), dev) for i in range(n_test)])
+        it_r, best_r, s_r = grape_batch(ctx, probs, U_r.contiguous(), target, max_iter=max_iter)
+        feats = torch.from_numpy(np.array([p.features() for p in probs])).to(dev)
+        U_w = (net.predict(feats).double() * U_SCALE).contiguous()
+        it_w, best_w, s_w = grape_batch(ctx, probs, U_w, target, max_iter=max_iter)
+        t_it = iteration_seconds(ctx, probs[0])
+        ok_r, ok_w = best_r >= target, best_w >= target
+        r = res["sizes"]["d%d" % d]
+        r.update(n_test=n_test, threshold=target, seconds_per_iteration=t_it,
+                 random_reached=int(ok_r.sum()), warm_reached=int(ok_w.sum()),
+                 median_random_iters=float(np.median(it_r)), median_warm_iters=float(np.median(it_w)),
+                 median_random_seconds=float(np.median(it_r)) * t_it,
+                 median_warm_seconds=float(np.median(it_w)) * t_it,
+                 batched_seconds_random=s_r, batched_seconds_warm=s_w,
+                 median_random_best=float(np.median(best_r)), median_warm_best=float(np.median(best_w)),
+                 plain_reached_0999=int((best_r >= 0.999).sum()))
+        log("d=%d test: threshold %.4g  warm median %g it (%d/%d reached)  random median %g it (%d/%d reached)"
+            % (d, target, r["median_warm_iters"], r["warm_reached"], n_test, r["median_random_iters"],
+               r["random_reached"], n_test))
+        ctx.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description="warm-start GRAPE experiment")
     ap.add_argument("--nq", type=int, default=1)
@@ -266,7 +407,19 @@ def main():
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--target", type=float, default=0.999)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--batched", action="store_true",
+                    help="the configured scale: batched GRAPE at d = 3 and 9, one network for both")
+    ap.add_argument("--train3", type=int, default=20000)
+    ap.add_argument("--train9", type=int, default=1024)
     a = ap.parse_args()
+    if a.batched:
+        res = experiment_batched(n_train=(a.train3, a.train9), n_test=a.test, max_iter=a.max_iter,
+                                 epochs=a.epochs)
+        print(json.dumps(res))
+        if a.out:
+            os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+            json.dump(res, open(a.out, "w"), indent=1)
+        return
     res = experiment(nq=a.nq, n_train=a.train, n_test=a.test, max_iter=a.max_iter, target=a.target,
                      epochs=a.epochs)
     print(json.dumps({k: v for k, v in res.items() if k != "tests"}))

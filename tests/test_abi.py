@@ -47,6 +47,8 @@ def test_null_arguments_are_rejected_without_a_device(L):
     assert L.lb_expm_pade(None, 9, 1, vp(8), None, None, 0.1, 0, vp(8), None, None) == 1
     assert L.lb_propagate_batch(None, 9, 1, vp(8), 1, 1, vp(8), 0, 0, None) == 1
     assert L.lb_grape_grad(None, 9, 1, vp(8), vp(8), vp(8), 0.1, 1, 1, vp(8), vp(8), vp(8), vp(8), None) == 1
+    assert L.lb_grape_grad_batch(None, 9, 2, 1, vp(8), 0, vp(8), vp(8), 0.1, 1, 1, vp(8), vp(8), 0, vp(8), vp(8),
+                                 None) == 1
     assert L.lb_sync_status(None, None) == 1
     assert L.lb_selftest_wait_timeout(None, 1000, None) == 1
     assert L.lb_expm_frechet(None, 9, 1, vp(8), vp(8), vp(8), 0.1, vp(8), vp(8), None) == 1

@@ -350,6 +350,64 @@ def test_grape_matches_oracle(lbm, dev, nq, S, m, dtscale):
     assert np.max(np.abs(g - g_ref)) <= 1e-9 * max(1e-6, np.max(np.abs(g_ref))), (g, g_ref)
 
 
+@pytest.mark.parametrize("nq,K,S,m,prec,tol", [(1, 5, 7, 1, "fp64", 1e-9), (1, 3, 4, 3, "fp64", 1e-9),
+                                                (2, 3, 5, 2, "fp64", 1e-9), (1, 4, 6, 1, "fp32", 1e-5),
+                                                (2, 2, 3, 1, "fp32", 1e-5)])
+def test_grape_batch_matches_oracle(lbm, dev, nq, K, S, m, prec, tol):
+    """K problems with their own base generators (jump rates), controls and
+    targets in one call, each against the oracle's F and gradient (Van Loan
+    block Frechet derivative): FP64 as lb_grape_grad (F within 1e-12,
+    gradient within 1e-9 of max |g|); FP32 products: within 1e-5 of max |g|
+    (products of operands rounded to 2^-24 relative, n terms each)."""
+    from workloads import transmon_chain
+
+    models = [transmon_chain(nq, gamma1=1e-3 * (k + 1), gamma_phi=5e-4 / (k + 1)) for k in range(K)]
+    Lbs = np.array([O.lindbladian(mm.H0, mm.jumps) for mm in models])
+    Ld = O.drive_generator(models[0].X)
+    n = Lbs.shape[1]
+    us, X0s, Xts, refs = [], [], [], []
+    for k in range(K):
+        _, _, u, dt, X0, Xt = _gate_problem(nq, S, 1000 + 17 * k)
+        us.append(u)
+        X0s.append(X0)
+        Xts.append(np.roll(Xt, k, axis=0))  # a different target per problem
+        refs.append(O.grape_fidelity_grad(Lbs[k], Ld, u, dt, m, X0s[-1], Xts[-1]))
+    ctx = lbm.Context(0, max_n=n, max_batch=4 * K, max_slices=K * S)
+    Fo = torch.zeros(K, dtype=torch.float64, device=dev)
+    go = torch.zeros((K, S), dtype=torch.float64, device=dev)
+    lbm.lb_grape_grad_batch(ctx, _t(Lbs, dev), _t(Ld, dev), _t(np.array(us), dev), dt, m, _t(np.array(X0s), dev),
+                            _t(np.array(Xts), dev), Fo, go, prec=prec)
+    lbm.lb_sync_status(ctx)
+    F, g = Fo.cpu().numpy(), go.cpu().numpy()
+    for k in range(K):
+        F_ref, g_ref = refs[k]
+        assert abs(F[k] - F_ref) <= max(tol, 1e-12) * max(1.0, abs(F_ref)), (k, F[k], F_ref)
+        assert np.max(np.abs(g[k] - g_ref)) <= tol * max(1e-6, np.max(np.abs(g_ref))), (k, g[k], g_ref)
+
+
+def test_grape_batch_shared_base_equals_single_calls(lbm, dev):
+    """A shared base generator (stride 0): every problem equals its own
+    lb_grape_grad call to rounding."""
+    K, S = 4, 6
+    Lb, Ld, _, dt, X0, Xt = _gate_problem(1, S, 1200)
+    n = Lb.shape[0]
+    us = np.array([0.3 * normal(1300 + k, S) for k in range(K)])
+    ctx = lbm.Context(0, max_n=n, max_batch=4 * K, max_slices=K * S)
+    Fo = torch.zeros(K, dtype=torch.float64, device=dev)
+    go = torch.zeros((K, S), dtype=torch.float64, device=dev)
+    X0b = np.repeat(X0[None], K, axis=0)
+    Xtb = np.repeat(Xt[None], K, axis=0)
+    lbm.lb_grape_grad_batch(ctx, _t(Lb, dev), _t(Ld, dev), _t(us, dev), dt, 1, _t(X0b, dev), _t(Xtb, dev), Fo, go)
+    lbm.lb_sync_status(ctx)
+    for k in range(K):
+        F1 = torch.zeros(1, dtype=torch.float64, device=dev)
+        g1 = torch.zeros(S, dtype=torch.float64, device=dev)
+        lbm.lb_grape_grad(ctx, _t(Lb, dev), _t(Ld, dev), _t(us[k], dev), dt, 1, _t(X0, dev), _t(Xt, dev), F1, g1)
+        lbm.lb_sync_status(ctx)
+        assert abs(Fo[k].item() - F1.item()) <= 1e-13
+        assert np.max(np.abs(go[k].cpu().numpy() - g1.cpu().numpy())) <= 1e-12 * max(1e-6, g1.abs().max().item())
+
+
 def test_grape_rejects_large_contexts(lbm, dev):
     ctx = lbm.Context(0, max_n=729, max_batch=4, max_slices=2)
     z = torch.zeros((9, 9), dtype=torch.complex128, device=dev)
