@@ -274,6 +274,18 @@ cudaError_t launch_cfg(const ZGemmProblem* probs, int nprob, int sm_count, cudaS
   return cudaGetLastError();
 }
 
+// Padded output area of BM x BN tiles over the problems' real output area:
+// large tiles on small matrices (9 x 9, 81 x 81) compute mostly zeros.
+double pad_ratio(const ZGemmProblem* probs, int nprob, int BM, int BN) {
+  double padded = 0.0, real = 0.0;
+  for (int i = 0; i < nprob; i++) {
+    if (probs[i].M <= 0 || probs[i].N <= 0) continue;
+    padded += (double)((probs[i].M + BM - 1) / BM * BM) * ((probs[i].N + BN - 1) / BN * BN) * probs[i].batch;
+    real += (double)probs[i].M * probs[i].N * probs[i].batch;
+  }
+  return real > 0.0 ? padded / real : 1.0;
+}
+
 long long count_tiles(const ZGemmProblem* probs, int nprob, int BM, int BN) {
   long long acc = 0;
   for (int i = 0; i < nprob; i++)
@@ -392,18 +404,22 @@ cudaError_t zgemm_f64(const ZGemmProblem* probs, int nprob, int sm_count, cudaSt
   static const cfg_fn cands[3] = {launch_cfg<double, 16, 16, 1, 1, true>, launch_cfg<double, 32, 32, 2, 2, true>,
                                   launch_cfg<double, 64, 64, 4, 4, true>};
   // heuristic: 32x32 tiles when there are enough of them to balance the
-  // persistent grid, else 16x16 tiles
+  // persistent grid and they pad little more than 16x16 tiles, else 16x16
   const long long t32 = count_tiles(probs, nprob, 32, 32);
+  const bool big = t32 >= 8LL * sm_count &&
+                   pad_ratio(probs, nprob, 32, 32) <= 1.25 * pad_ratio(probs, nprob, 16, 16);
   const ZArgs a{cands, probs, nprob, sm_count};
-  return tuned_launch(zshape_key(64, probs, nprob), 3, t32 >= 8LL * sm_count ? 1 : 0, zrun, &a, st);
+  return tuned_launch(zshape_key(64, probs, nprob), 3, big ? 1 : 0, zrun, &a, st);
 }
 
 cudaError_t zgemm_f32(const ZGemmProblem* probs, int nprob, int sm_count, cudaStream_t st) {
   if (nprob <= 0 || nprob > 4) return cudaErrorInvalidValue;
   static const cfg_fn cands[2] = {launch_cfg<float, 32, 32, 2, 2, false>, launch_cfg<float, 64, 64, 4, 4, false>};
   const long long t64 = count_tiles(probs, nprob, 64, 64);
+  const bool big = t64 >= 4LL * sm_count &&
+                   pad_ratio(probs, nprob, 64, 64) <= 1.25 * pad_ratio(probs, nprob, 32, 32);
   const ZArgs a{cands, probs, nprob, sm_count};
-  return tuned_launch(zshape_key(32, probs, nprob), 2, t64 >= 4LL * sm_count ? 1 : 0, zrun, &a, st);
+  return tuned_launch(zshape_key(32, probs, nprob), 2, big ? 1 : 0, zrun, &a, st);
 }
 
 }  // namespace lb

@@ -396,6 +396,17 @@ cudaError_t launch_rcfg(const RGemmProblem<T>* probs, int nprob, int sm_count, c
 }
 
 template <typename T>
+double rpad(const RGemmProblem<T>* probs, int nprob, int BM, int BN) {
+  double padded = 0.0, real = 0.0;
+  for (int i = 0; i < nprob; i++) {
+    if (probs[i].M <= 0 || probs[i].N <= 0) continue;
+    padded += (double)((probs[i].M + BM - 1) / BM * BM) * ((probs[i].N + BN - 1) / BN * BN) * probs[i].batch;
+    real += (double)probs[i].M * probs[i].N * probs[i].batch;
+  }
+  return real > 0.0 ? padded / real : 1.0;
+}
+
+template <typename T>
 long long rtiles(const RGemmProblem<T>* probs, int nprob, int BM, int BN) {
   long long acc = 0;
   for (int i = 0; i < nprob; i++)
@@ -444,8 +455,9 @@ cudaError_t rgemm_f64(const RGemmProblem<double>* probs, int nprob, int sm_count
   // 32 x 32 tiles (two stages) when there are enough of them to balance the
   // persistent grid, else 16 x 16 (one stage, more resident CTAs)
   const long long t32 = rtiles(probs, nprob, 32, 32);
+  const bool big = t32 >= 8LL * sm_count && rpad(probs, nprob, 32, 32) <= 1.25 * rpad(probs, nprob, 16, 16);
   const RArgs<double> a{cands, probs, nprob, sm_count};
-  return tuned_launch(rshape_key(probs, nprob), 5, t32 >= 8LL * sm_count ? 1 : 0, rrun<double>, &a, st);
+  return tuned_launch(rshape_key(probs, nprob), 5, big ? 1 : 0, rrun<double>, &a, st);
 }
 
 cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count, cudaStream_t st) {
@@ -453,8 +465,9 @@ cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count,
   typedef cudaError_t (*fn)(const RGemmProblem<float>*, int, int, cudaStream_t);
   static const fn cands[2] = {launch_rcfg<float, 32, 32, 2, 2, true>, launch_rcfg<float, 64, 64, 4, 4, true>};
   const long long t64 = rtiles(probs, nprob, 64, 64);
+  const bool big = t64 >= 2LL * sm_count && rpad(probs, nprob, 64, 64) <= 1.25 * rpad(probs, nprob, 32, 32);
   const RArgs<float> a{cands, probs, nprob, sm_count};
-  return tuned_launch(rshape_key(probs, nprob), 2, t64 >= 2LL * sm_count ? 1 : 0, rrun<float>, &a, st);
+  return tuned_launch(rshape_key(probs, nprob), 2, big ? 1 : 0, rrun<float>, &a, st);
 }
 
 template <typename T, int NQ>
