@@ -55,8 +55,13 @@ typedef enum {
                             Hermiticity-preserving generators and propagators (every
                             Lindbladian and its exponential are); see lb_expm_pade and
                             lb_propagate_batch */
-  LB_FP32_HERMITIAN = 4  /* lb_expm_pade: the real-coordinate build with FP32 Pade
+  LB_FP32_HERMITIAN = 4, /* lb_expm_pade: the real-coordinate build with FP32 Pade
                             products; lb_propagate_batch: the same as LB_FP32 */
+  LB_FP64_SLICED = 5     /* LB_FP64_HERMITIAN with the dense FP64 products (squarings,
+                            propagation steps) on the BF16 tensor cores through exact
+                            slices (Ozaki scheme, see lb_gemm_f64_sliced): FP64
+                            operands and results, error of the size of an FP64
+                            product's rounding */
 } lb_precision;
 
 typedef struct lb_ctx lb_ctx;
@@ -188,6 +193,8 @@ lb_status lb_assemble(lb_ctx* ctx, int d, const lb_c64* H, int K, const lb_c64* 
  *           variant runs the six Pade products and the near-I squarings in
  *           FP32; LU, solve and the other squarings stay FP64.  n must be a
  *           square (else LB_EINVAL).
+ *           LB_FP64_SLICED: LB_FP64_HERMITIAN with the squarings as sliced
+ *           FP64 products (lb_gemm_f64_sliced) for n > 81.
  *   P_out : nslices x n x n
  *   s_out : nslices ints (device) receiving sc, or NULL
  * The LU takes no pivots: at theta = 0.25 the matrix V - U is strictly
@@ -225,10 +232,37 @@ lb_status lb_expm_pade(lb_ctx* ctx, int n, int nslices, const lb_c64* Lbase, con
  *   matrices of up to max_slices slices in the context's scratch.
  *   renorm_trace is ignored, as for LB_FP64.
  *   prec = LB_FP32_HERMITIAN runs the LB_FP32 form.
+ *   prec = LB_FP64_SLICED: LB_FP64_HERMITIAN with the per-step real product
+ *   for n > 81 and B > 8 as a sliced FP64 product (lb_gemm_f64_sliced).
  */
 lb_status lb_propagate_batch(lb_ctx* ctx, int n, int nslices, const lb_c64* P, int steps_per_slice,
                              int B, lb_c64* states, lb_precision prec, int renorm_trace,
                              void* stream);
+
+/*
+ * lb_gemm_f64_sliced -- C = alpha A B + beta C for a batch of real FP64
+ * matrices, computed on the BF16 tensor cores through exact slices (the
+ * Ozaki scheme: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012).  The
+ * building block of the LB_FP64_SLICED form (the dense products of Algorithm
+ * 1's squarings and Algorithm 2's steps on the real coordinates); the paper
+ * computes these products in FP64, which this reproduces to the size of an
+ * FP64 product's rounding.  Each row of A and each column of B is written as
+ * nine signed base-64 digits against its own power-of-two exponent; the
+ * digit products of equal weight are summed exactly in FP32 on the tensor
+ * cores and combined in integer arithmetic; the one rounding is to FP64.
+ * Error: |C - A B| <= K 2^(e_r + f_c) 2^-54 (13/4) for row r, column c,
+ * where 2^e_r > max_k |A[r][k]| and 2^f_c > max_k |B[k][c]|.
+ *   A : batch x M x K, row-major, leading dimension lda, batch stride sA
+ *   B : batch x K x N, row-major, ldb, sB
+ *   C : batch x M x N, row-major, ldc, sC (may alias A or B: both are
+ *       consumed before C is written)
+ * All pointers device memory owned by the caller; 1 <= K <= 1488 (else
+ * LB_EINVAL); the batch is processed in chunks that fit the context's
+ * scratch.  Non-finite inputs give unspecified results.
+ */
+lb_status lb_gemm_f64_sliced(lb_ctx* ctx, int M, int N, int K, int batch, const double* A, long long lda,
+                             long long sA, const double* B, long long ldb, long long sB, double* C, long long ldc,
+                             long long sC, double alpha, double beta, void* stream);
 
 /*
  * lb_grape_grad -- fidelity of a piecewise-constant control and its gradient

@@ -25,13 +25,15 @@
 // memory; otherwise each writes its partial to global scratch and the CTA
 // that takes the last ticket (atomic, no waiting) sums them.  Either way the
 // partials are added in split order, so the result does not depend on
-// arrival order.
+// arrival order.  A chain of at least two steps whose split CTAs form
+// clusters runs as one persistent launch (chain32_persist_kernel below).
 #include "lb_internal.cuh"
 
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 
 namespace lb {
@@ -336,6 +338,252 @@ __global__ void __launch_bounds__(1024 / TM, 2)
   if (tid == 0) cnt[tile] = 0u;  // ready for the next launch
 }
 
+// ---------------------------------------------------------------------------
+// Persistent chain: every step of the chain in one launch.  Each CTA keeps
+// its output tile and K split for all steps; the split CTAs of a tile form a
+// cluster and reduce through distributed shared memory as in the per-step
+// kernel; between steps a grid-wide barrier (one counter, bounded wait)
+// makes the step's states visible before any CTA reads them, and the next
+// step's first D^T stages are fetched before the barrier.  The grid is at
+// most two CTAs per SM and is launched cooperatively where possible, so all
+// CTAs are resident.  A barrier that waits longer than about 2 s sets the
+// timeout bit of the error word and every CTA returns.
+constexpr long long kBarWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <bool RENORM, int TM>
+__global__ void __launch_bounds__(1024 / TM, 2)
+    chain32_persist_kernel(ChainDims g, int kps, const float* __restrict__ Dt0, long long dstride,
+                           int steps_per_slice, int nsteps, float* __restrict__ Ra, float* __restrict__ Rb,
+                           unsigned* __restrict__ bar, unsigned int* __restrict__ err) {
+  constexpr int NT = 1024 / TM;
+  constexpr int NQ = NT / CB;
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float2 cs[CB];
+  __shared__ float2 trp[NQ][CB];
+  __shared__ int timed_out;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * CB, m0 = blockIdx.y * CB, z = blockIdx.z, splits = gridDim.z;
+  const int kt0 = z * kps;
+  const int kt1 = min(g.Kp / CK, kt0 + kps);
+  const int nkt = kt1 - kt0;
+  const long long pA = (long long)g.Kp * g.Bp, pB = (long long)g.Kp * g.Np;
+  const unsigned nctas = gridDim.x * gridDim.y * gridDim.z;
+  const int w = tid >> 5, l = tid & 31;
+  const int am = TM == 4 ? (w >> 2) * 32 + (l & 7) * 4 : (w >> 1) * 32 + (l & 3) * 8;
+  const int bn = TM == 4 ? (w & 3) * 16 + (l >> 3) * 4 : (w & 1) * 32 + (l >> 2) * 4;
+  const float* Dt = Dt0;
+  auto loadA = [&](const float* Rt, int stage, int kt) {
+    float* sA = sm + stage * STAGE_FLOATS;
+    const int k0 = kt * CK;
+    for (int c = tid; c < NPL * CK * (CB / 4); c += NT) {
+      const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
+      cp16(sA + (p * CK + r) * CB + 4 * q, Rt + p * pA + (long long)(k0 + r) * g.Bp + m0 + 4 * q);
+    }
+  };
+  auto loadB = [&](int stage, int kt) {
+    float* sB = sm + stage * STAGE_FLOATS + OPER_FLOATS;
+    const int k0 = kt * CK;
+    for (int c = tid; c < NPL * CK * (CB / 4); c += NT) {
+      const int p = c / (CK * (CB / 4)), r = (c / (CB / 4)) % CK, q = c % (CB / 4);
+      cp16(sB + (p * CK + r) * CB + 4 * q, Dt + p * pB + (long long)(k0 + r) * g.Np + j0 + 4 * q);
+    }
+  };
+  // the first step's D^T stages
+#pragma unroll
+  for (int s = 0; s < CSTAGE - 1; s++)
+    if (s < nkt) loadB(s, kt0 + s);
+  for (int t = 0; t < nsteps; t++) {
+    const float* Rt = (t & 1) ? Rb : Ra;
+    float* Ot = (t & 1) ? Ra : Rb;
+#pragma unroll
+    for (int s = 0; s < CSTAGE - 1; s++) {
+      if (s < nkt) loadA(Rt, s, kt0 + s);
+      cp_commit();
+    }
+    if (RENORM) {
+      const int b = m0 + (tid & (CB - 1)), q0 = tid / CB;
+      float tr = 0.f, ti = 0.f;
+      if (b < g.B) {
+#pragma unroll
+        for (int u = 0; u < 32 / NQ; u++) {
+          const int i = q0 + NQ * u;
+          if (i < g.d) {
+            const long long k = (long long)i * (g.d + 1) * g.Bp + b;
+            tr += __ldcg(Rt + k);
+            ti += __ldcg(Rt + pA + k);
+          }
+        }
+      }
+      trp[q0][tid & (CB - 1)] = make_float2(tr, ti);
+    }
+    float t1[TM][4], t2[TM][4], t3[TM][4];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) t1[i][j] = t2[i][j] = t3[i][j] = 0.f;
+    for (int it = 0; it < nkt; it++) {
+      cp_wait<CSTAGE - 2>();
+      __syncthreads();
+      {
+        const int nx = it + CSTAGE - 1;
+        if (nx < nkt) {
+          loadA(Rt, nx % CSTAGE, kt0 + nx);
+          loadB(nx % CSTAGE, kt0 + nx);
+        }
+        cp_commit();
+      }
+      const float* sA = sm + (it % CSTAGE) * STAGE_FLOATS;
+      const float* sB = sA + OPER_FLOATS;
+      constexpr int QA = TM / 4;
+      float4 fa[2][NPL][QA], fb[2][NPL];
+#pragma unroll
+      for (int p = 0; p < NPL; p++) {
+#pragma unroll
+        for (int h = 0; h < QA; h++) fa[0][p][h] = *(const float4*)(sA + (p * CK) * CB + am + 4 * h);
+        fb[0][p] = *(const float4*)(sB + (p * CK) * CB + bn);
+      }
+#pragma unroll
+      for (int k = 0; k < CK; k++) {
+        const int cur = k & 1;
+        if (k + 1 < CK) {
+#pragma unroll
+          for (int p = 0; p < NPL; p++) {
+#pragma unroll
+            for (int h = 0; h < QA; h++)
+              fa[cur ^ 1][p][h] = *(const float4*)(sA + (p * CK + k + 1) * CB + am + 4 * h);
+            fb[cur ^ 1][p] = *(const float4*)(sB + (p * CK + k + 1) * CB + bn);
+          }
+        }
+        float ar[TM], ai[TM], as[TM];
+#pragma unroll
+        for (int h = 0; h < QA; h++) {
+          ar[4 * h] = fa[cur][0][h].x; ar[4 * h + 1] = fa[cur][0][h].y;
+          ar[4 * h + 2] = fa[cur][0][h].z; ar[4 * h + 3] = fa[cur][0][h].w;
+          ai[4 * h] = fa[cur][1][h].x; ai[4 * h + 1] = fa[cur][1][h].y;
+          ai[4 * h + 2] = fa[cur][1][h].z; ai[4 * h + 3] = fa[cur][1][h].w;
+        }
+#pragma unroll
+        for (int i = 0; i < TM; i++) as[i] = ar[i] + ai[i];
+        const float br[4] = {fb[cur][0].x, fb[cur][0].y, fb[cur][0].z, fb[cur][0].w};
+        const float bi[4] = {fb[cur][1].x, fb[cur][1].y, fb[cur][1].z, fb[cur][1].w};
+        const float bs[4] = {br[0] + bi[0], br[1] + bi[1], br[2] + bi[2], br[3] + bi[3]};
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            t1[i][j] = fmaf(ar[i], br[j], t1[i][j]);
+            t2[i][j] = fmaf(ai[i], bi[j], t2[i][j]);
+            t3[i][j] = fmaf(as[i], bs[j], t3[i][j]);
+          }
+      }
+    }
+    cp_wait<0>();
+    __syncthreads();
+    if (tid < CB) {
+      float2 c = make_float2(0.f, 0.f);
+      if (m0 + tid < g.B) {
+        if (RENORM) {
+          float tr = 0.f, ti = 0.f;
+#pragma unroll
+          for (int q = 0; q < NQ; q++) {
+            tr += trp[q][tid].x;
+            ti += trp[q][tid].y;
+          }
+          const float m2 = tr * tr + ti * ti;
+          c = make_float2(tr / m2, -ti / m2);
+        } else {
+          c = make_float2(1.f, 0.f);
+        }
+      }
+      cs[tid] = c;
+    }
+    // partial tile in the (idle) ring; CTA r of the cluster finishes its
+    // share of the tile's rows over all partials, in split order
+    float* Ps = sm;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+      for (int h = 0; h < TM / 4; h++) {
+        float4 qr, qi;
+        qr.x = t1[4 * h][j] - t2[4 * h][j];
+        qr.y = t1[4 * h + 1][j] - t2[4 * h + 1][j];
+        qr.z = t1[4 * h + 2][j] - t2[4 * h + 2][j];
+        qr.w = t1[4 * h + 3][j] - t2[4 * h + 3][j];
+        qi.x = t3[4 * h][j] - t1[4 * h][j] - t2[4 * h][j];
+        qi.y = t3[4 * h + 1][j] - t1[4 * h + 1][j] - t2[4 * h + 1][j];
+        qi.z = t3[4 * h + 2][j] - t1[4 * h + 2][j] - t2[4 * h + 2][j];
+        qi.w = t3[4 * h + 3][j] - t1[4 * h + 3][j] - t2[4 * h + 3][j];
+        *(float4*)(Ps + (bn + j) * CB + am + 4 * h) = qr;
+        *(float4*)(Ps + CB * CB + (bn + j) * CB + am + 4 * h) = qi;
+      }
+    cl.sync();
+    {
+      const int rank = (int)cl.block_rank();
+      const int rows = (CB + splits - 1) / splits;
+      const int jl0 = rank * rows, jl1 = min(CB, jl0 + rows);
+      const float* src[8];
+#pragma unroll
+      for (int zz = 0; zz < 8; zz++) src[zz] = zz < splits ? cl.map_shared_rank(Ps, zz) : Ps;
+      for (int q = tid; q < (jl1 - jl0) * (CB / 4); q += NT) {
+        const int jl = jl0 + q / (CB / 4), b4 = (q % (CB / 4)) * 4;
+        float4 sr = make_float4(0.f, 0.f, 0.f, 0.f), si = sr;
+#pragma unroll
+        for (int zz = 0; zz < 8; zz++) {
+          if (zz < splits) {
+            sr = f4add(sr, *(const float4*)(src[zz] + jl * CB + b4));
+            si = f4add(si, *(const float4*)(src[zz] + CB * CB + jl * CB + b4));
+          }
+        }
+        chain_finish(g, Rt, Ot, cs + b4, j0 + jl, m0 + b4, sr, si);
+      }
+    }
+    cl.sync();  // the partials stay readable until every CTA of the cluster is done
+    if (t + 1 == nsteps) break;
+    // the next step's D^T stages (written before the chain), then the grid
+    // barrier: every tile of O_t written before anyone reads it.  Each CTA
+    // arrives; rank 0 of the cluster waits for all and hands its verdict to
+    // the cluster, so a timeout ends whole clusters (no CTA is left waiting
+    // at a cluster barrier for one that returned).
+    Dt = Dt0 + (long long)((t + 1) / steps_per_slice) * dstride;
+#pragma unroll
+    for (int s = 0; s < CSTAGE - 1; s++)
+      if (s < nkt) loadB(s, kt0 + s);
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(bar, 1u);
+      if (cl.block_rank() == 0) {
+        const unsigned target = (unsigned)(t + 1) * nctas;
+        int to = 0;
+        if (ld_acquire_u32(bar) < target) {
+          const long long c0 = clock64();
+          while (ld_acquire_u32(bar) < target) {
+            if (clock64() - c0 > kBarWaitCycles) {
+              to = 1;
+              atomicOr(err, ERR_TIMEOUT);
+              break;
+            }
+          }
+        }
+        __threadfence();
+        for (int r = 0; r < splits; r++) *cl.map_shared_rank(&timed_out, r) = to;
+      }
+    }
+    cl.sync();
+    if (timed_out) {
+      cp_wait<0>();
+      return;
+    }
+  }
+}
+
 // D^T planes of S propagators: Dt[s][p][k][j] = (P_s - I)[j][k], zero padding.
 __global__ void chain32_dplanes_kernel(int n, int Kp, int Np, const z64* __restrict__ P, float* __restrict__ Dt) {
   __shared__ float tr[32][33], ti[32][33];
@@ -435,16 +683,16 @@ __global__ void chain32_states_out_kernel(int n, int d, int B, int Kp, int Bp, i
 int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 // Whether `tiles` clusters of `splits` CTAs of this kernel can be resident at
-// once (queried once per kernel and cluster size).
-bool cluster_fits(void (*kern)(ChainDims, int, const float*, const float*, float*, float*, unsigned*, int),
-                  bool renorm, int splits, int tiles) {
+// once (queried once per kernel, device and cluster size).
+template <typename Kern>
+bool cluster_fits(Kern kern, int splits, int tiles) {
   constexpr int NT = 1024 / kChainTM;
   static std::mutex mu;
-  static std::map<std::pair<int, int>, int> cache;
+  static std::map<std::tuple<const void*, int, int>, int> cache;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_pair(dev * 16 + (renorm ? 8 : 0), splits);
+  const auto key = std::make_tuple((const void*)kern, dev, splits);
   auto it = cache.find(key);
   if (it == cache.end()) {
     cudaLaunchConfig_t cfg = {};
@@ -459,7 +707,8 @@ bool cluster_fits(void (*kern)(ChainDims, int, const float*, const float*, float
     cfg.attrs = &a;
     cfg.numAttrs = 1;
     int num = 0;
-    if (cudaOccupancyMaxActiveClusters(&num, (const void*)kern, &cfg) != cudaSuccess) {
+    if (set_smem_once((const void*)kern, STEP_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&num, (const void*)kern, &cfg) != cudaSuccess) {
       cudaGetLastError();
       num = 0;
     }
@@ -505,6 +754,84 @@ cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt,
   return cudaGetLastError();
 }
 
+bool launch_chain32_persist(int n, int B, int renorm, const float* Dt, long long dstride, int steps_per_slice,
+                            int nsteps, float* Ra, float* Rb, unsigned* bar, unsigned int* err, int sm_count,
+                            cudaStream_t st, cudaError_t* status) {
+  *status = cudaSuccess;
+  ChainDims g;
+  g.n = n;
+  g.d = chain_isqrt(n);
+  g.B = B;
+  g.Kp = rup(n, CK);
+  g.Np = rup(n, CB);
+  g.Bp = rup(B, CB);
+  const int tilesN = g.Np / CB, tilesM = g.Bp / CB, tiles = tilesN * tilesM;
+  const int ktiles = g.Kp / CK;
+  if (nsteps < 2 || tiles >= sm_count) return false;
+  void (*kern)(ChainDims, int, const float*, long long, int, int, float*, float*, unsigned*, unsigned int*) =
+      renorm ? chain32_persist_kernel<true, kChainTM> : chain32_persist_kernel<false, kChainTM>;
+  // the widest K split (at most two CTAs per SM, four K blocks per split)
+  // whose clusters all fit at once
+  int splits = 0, kps = 0;
+  for (int want = std::max(1, std::min({2 * sm_count / tiles, ktiles / 4, 8})); want >= 2; want--) {
+    kps = (ktiles + want - 1) / want;
+    const int sp = (ktiles + kps - 1) / kps;
+    if (sp >= 2 && tiles * sp <= 2 * sm_count && cluster_fits(kern, sp, tiles)) {
+      splits = sp;
+      break;
+    }
+  }
+  if (splits < 2) return false;
+  // whether a cooperative cluster launch of this kernel was accepted on this
+  // device: tried outside stream capture only (a refused launch would end a
+  // capture), remembered for captures
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int>, int> accepted;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple((const void*)kern, dev, splits);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = accepted.find(key);
+    if (it != accepted.end() && it->second == 0) return false;
+    if (it == accepted.end() && cap != cudaStreamCaptureStatusNone) return false;
+  }
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) {
+    *status = e;
+    return true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tilesN, tilesM, splits);
+  cfg.blockDim = dim3(1024 / kChainTM);
+  cfg.dynamicSmemBytes = STEP_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = splits;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  e = cudaLaunchKernelEx(&cfg, kern, g, kps, Dt, dstride, steps_per_slice, nsteps, Ra, Rb, bar, err);
+  std::lock_guard<std::mutex> lk(mu);
+  if (e != cudaSuccess) {  // refused (not in a capture, see above): per-step launches from now on
+    cudaGetLastError();
+    accepted[key] = 0;
+    return false;
+  }
+  accepted[key] = 1;
+  count_launch();
+  return true;
+}
+
 cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
                                 unsigned* cnt, int sm_count, bool pdl, cudaStream_t st) {
   ChainDims g;
@@ -536,7 +863,7 @@ cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const
   cudaLaunchAttribute attr[2];
   int na = 0;
   // the split CTAs of a tile as one cluster, if that many clusters fit at once
-  const bool cluster = splits > 1 && cluster_fits(kern, renorm, splits, tiles);
+  const bool cluster = splits > 1 && cluster_fits(kern, splits, tiles);
   if (cluster) {
     attr[na].id = cudaLaunchAttributeClusterDimension;
     attr[na].val.clusterDim.x = 1;

@@ -162,13 +162,13 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add((size_t)max_batch * max_n * zb);                      // Rtmp
   add((size_t)max_batch * max_n * zb);                      // Xh
   const size_t plane_elems = (size_t)max_n * (size_t)plane_ld(max_n);
-  for (int i = 0; i < 9; i++) add((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));  // split planes
+  add(38 * plane_elems * S * sizeof(__nv_bfloat16));  // split planes (6 + 8 x 4), sliced-FP64 scratch
   for (int i = 0; i < 2; i++) add(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
   const size_t dpl = std::max(chain32_dplane_floats(max_n), 2 * nn) * S;
   add(dpl * sizeof(float));                                 // Dpl (Dr, Di inside)
   for (int i = 0; i < 2; i++) add(chain32_state_floats(max_n, max_batch) * sizeof(float));  // C32a, C32b
   add(chain32_part_floats(prop.multiProcessorCount) * sizeof(float));                       // part32
-  add((size_t)prop.multiProcessorCount * sizeof(unsigned));                                 // cnt32
+  add((size_t)(prop.multiProcessorCount + 1) * sizeof(unsigned));                           // cnt32, barrier
   add(nn * S * zb);                                          // Ginst
   add(nn * S * zb);                                          // Pinst
   add(inst_table_bytes());                                   // instance tables
@@ -205,8 +205,10 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
   c->Xh = Z((size_t)max_batch * max_n);
+  c->oz_bytes = 38 * plane_elems * S * sizeof(__nv_bfloat16);
+  c->oz_scratch = ar.take(c->oz_bytes);
   for (int i = 0; i < 9; i++)
-    c->sp[i] = (__nv_bfloat16*)ar.take((i == 0 ? 6 : 4) * plane_elems * S * sizeof(__nv_bfloat16));
+    c->sp[i] = (__nv_bfloat16*)c->oz_scratch + (i == 0 ? 0 : 6 + 4 * (i - 1)) * plane_elems * S;
   for (int i = 0; i < 2; i++)
     c->spR[i] = (__nv_bfloat16*)ar.take(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
   c->Dpl = (float*)ar.take(dpl * sizeof(float));
@@ -215,7 +217,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->C32a = (float*)ar.take(chain32_state_floats(max_n, max_batch) * sizeof(float));
   c->C32b = (float*)ar.take(chain32_state_floats(max_n, max_batch) * sizeof(float));
   c->part32 = (float*)ar.take(chain32_part_floats(c->sm_count) * sizeof(float));
-  c->cnt32 = (unsigned*)ar.take((size_t)c->sm_count * sizeof(unsigned));
+  c->cnt32 = (unsigned*)ar.take((size_t)(c->sm_count + 1) * sizeof(unsigned));
   c->Ginst = Z(nn * S);
   c->Pinst = Z(nn * S);
   c->inst_tab_bytes = inst_table_bytes();
@@ -662,7 +664,7 @@ lb_status lb_expm_pade(lb_ctx* c, int n, int nslices, const lb_c64* Lbase, const
   if (n < 1 || n > c->max_n || nslices < 0) return LB_EINVAL;
   if (Ldrv != nullptr && u == nullptr) return LB_EINVAL;
   if (!std::isfinite(dt)) return LB_EINVAL;
-  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN;
+  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN || prec == LB_FP64_SLICED;
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && !herm) return LB_EINVAL;
   if (herm && !is_square(n, nullptr)) return LB_EINVAL;
   if (nslices == 0) return LB_OK;
@@ -694,7 +696,7 @@ lb_status lb_propagate_batch(lb_ctx* c, int n, int nslices, const lb_c64* P, int
   if (n < 1 || n > c->max_n || !is_square(n, &d)) return LB_EINVAL;
   if (nslices < 0 || steps_per_slice < 0 || B < 1 || B > c->max_batch) return LB_EINVAL;
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN &&
-      prec != LB_FP32_HERMITIAN)
+      prec != LB_FP32_HERMITIAN && prec != LB_FP64_SLICED)
     return LB_EINVAL;
   if (prec == LB_FP32_HERMITIAN) prec = LB_FP32;  // the propagation of the FP32 forms is the same
   if (nslices == 0 || steps_per_slice == 0) return LB_OK;
@@ -712,7 +714,7 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   int d = 0;
   is_square(n, &d);
   const long long nn = (long long)n * n;
-  if (prec == LB_FP64_HERMITIAN) {
+  if (prec == LB_FP64_HERMITIAN || prec == LB_FP64_SLICED) {
     int C = 0, K = 0;
     const bool lat = herm_lat_split(n, &C, &K);
     if (lat || herm_resident_fits(n)) {
@@ -728,7 +730,7 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
       }
       return LB_OK;
     }
-    return propagate_herm_large(c, n, nslices, Pz, steps_per_slice, B, X, st);
+    return propagate_herm_large(c, n, nslices, Pz, steps_per_slice, B, X, prec == LB_FP64_SLICED, st);
   }
   if (prec == LB_FP64) {
     const bool gemv = gemv_f64_preferred(n, B);
@@ -831,6 +833,18 @@ lb_status propagate_impl(lb_ctx* c, int n, int nslices, const z64* Pz, int steps
   for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
     const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
     LB_CUDA(launch_chain32_dplanes(n, S, Pz + s0 * nn, c->Dpl, st));
+    // the chunk's steps in one persistent launch where the shape allows
+    cudaError_t pe = cudaSuccess;
+    if (launch_chain32_persist(n, B, renorm_trace, c->Dpl, (long long)dpl, steps_per_slice, S * steps_per_slice, cur,
+                               nxt, c->cnt32 + c->sm_count, c->err_dev, c->sm_count, st, &pe)) {
+      LB_CUDA(pe);
+      if ((S * steps_per_slice) & 1) {
+        float* t1 = cur;
+        cur = nxt;
+        nxt = t1;
+      }
+      continue;
+    }
     for (int s = 0; s < S; s++)
       for (int t = 0; t < steps_per_slice; t++) {
         const bool pdl = s > 0 || t > 0;  // the first step of a chunk follows the D^T conversion

@@ -97,7 +97,9 @@ struct lb_ctx {
   int* kmix = nullptr;  // max_slices
   lb::z64* G = nullptr;  // d x d Gram matrix for assembly
   // --- split-BF16 planes for the tensor-core products (per slice 4 x n x ld) ---
-  __nv_bfloat16* sp[9] = {};
+  __nv_bfloat16* sp[9] = {};  // split-BF16 planes; all nine share one region, also the sliced-FP64 scratch
+  void* oz_scratch = nullptr;
+  size_t oz_bytes = 0;
   __nv_bfloat16* spR[2] = {};  // state planes, 4 x max_batch x ld each
   // --- propagation ---
   lb::z64* Rtmp = nullptr;  // max_batch x max_n
@@ -106,7 +108,7 @@ struct lb_ctx {
   float* Dpl = nullptr;                // FP32 D^T planes of the chain, per slice chain32_dplane_floats
   float *C32a = nullptr, *C32b = nullptr;  // FP32 state planes, chain32_state_floats(max_n, max_batch)
   float* part32 = nullptr;             // split-K partial tiles, chain32_part_floats(sm_count)
-  unsigned* cnt32 = nullptr;           // split-K tickets, sm_count (zero between launches)
+  unsigned* cnt32 = nullptr;           // split-K tickets, sm_count (zero between launches), then a barrier counter
   // --- many-instance batching (lb_run_instances) ---
   lb::z64* Ginst = nullptr;  // per-slice generators, max_slices x max_n^2
   lb::z64* Pinst = nullptr;  // their propagators
@@ -317,7 +319,7 @@ cudaError_t launch_lu_diag_real(int n, int S, int k0, int kb, const double* M, d
 lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
                           lb_precision prec, z64* P, int* s_out, cudaStream_t st);
 lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
-                               cudaStream_t st);
+                               bool sliced, cudaStream_t st);
 // Stage-timer events of one build chunk (null when timing is off).
 lb_status stage_events_begin(lb_ctx* c, cudaStream_t st, cudaEvent_t** ev_out);
 
@@ -365,6 +367,14 @@ size_t chain32_part_floats(int sm_count);
 cudaError_t launch_chain32_dplanes(int n, int S, const z64* P, float* Dt, cudaStream_t st);
 cudaError_t launch_chain32_states_in(int n, int B, const z64* X, float* Rt, cudaStream_t st);
 cudaError_t launch_chain32_states_out(int n, int B, int renorm, const float* Rt, z64* X, cudaStream_t st);
+// The whole chain in one persistent launch (nsteps steps, slice t /
+// steps_per_slice of the D^T planes at Dt + slice * dstride; states ping-pong
+// between Ra and Rb, the result in Ra if nsteps is even, else in Rb; bar: a
+// scratch counter).  false: not possible for this shape (nothing queued), use
+// per-step launches.  *status: a CUDA error met after the decision.
+bool launch_chain32_persist(int n, int B, int renorm, const float* Dt, long long dstride, int steps_per_slice,
+                            int nsteps, float* Ra, float* Rb, unsigned* bar, unsigned int* err, int sm_count,
+                            cudaStream_t st, cudaError_t* status);
 // pdl: launch with programmatic stream serialisation (only when the
 // previous launch on the stream is another step of the same chain)
 cudaError_t launch_chain32_step(int n, int B, int renorm, const float* Dt, const float* Rt, float* Ot, float* part,
@@ -447,6 +457,29 @@ struct TcProblem {
   unsigned int* err = nullptr;
 };
 cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
+
+// FP64 product C = alpha A B + beta C through exact BF16 slices on the
+// tensor cores (k_ozaki.cu).  A(m, k) of batch element b at
+// A[b sA + m a_sm + k a_sk], B(k, n) at B[b sB + k b_sk + n b_sn], C
+// row-major with leading dimension ldc.  C may alias A or B (both are
+// consumed into slices before C is written).  K <= kOzMaxK.
+constexpr int kOzSlices = 9;    // base-64 digits per operand row / column (54 bits)
+constexpr int kOzMaxK = 1488;   // every group sum exact in FP32 up to this K
+struct OzGemm {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const double* A = nullptr; long long a_sm = 0, a_sk = 1, sA = 0;
+  const double* B = nullptr; long long b_sk = 0, b_sn = 1, sB = 0;
+  double* C = nullptr; long long ldc = 0, sC = 0;
+  double alpha = 1.0, beta = 0.0;
+  // optional batch mask: batch element b is skipped when active[b] <= active_iter
+  const int* active = nullptr; int active_iter = 0;
+  const int* EA = nullptr; const int* EB = nullptr;  // row / column exponents (set by ozgemm_f64)
+  unsigned int* err = nullptr;
+};
+long long oz_kpad(int K);
+// scratch for one call: the slice planes of both operands and the exponents
+size_t oz_scratch_bytes(int M, int N, int K, int batch);
+cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st);
 // Z = c0 X0 + c1 X1 + c2 X2 (FP32) written as the two-piece planes of Z^T
 cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* X1, const float2* X2, float c0,
                                   float c1, float c2, __nv_bfloat16* dst, long long ldd, long long plane,

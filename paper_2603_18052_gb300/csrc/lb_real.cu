@@ -158,6 +158,44 @@ lb_status skip_product(lb_ctx* c, RGemmProblem<T> p, const int* flag, cudaStream
   return LB_OK;
 }
 
+// C = alpha A B + beta C through the sliced FP64 product, in chunks of
+// batch elements that fit the context's scratch.
+lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
+  int chunk = p.batch;
+  while (chunk > 1 && oz_scratch_bytes(p.M, p.N, p.K, chunk) > c->oz_bytes) chunk = (chunk + 1) / 2;
+  if (oz_scratch_bytes(p.M, p.N, p.K, chunk) > c->oz_bytes) {
+    // one batch element does not fit: blocks of rows of A and C (multiples
+    // of the 128-row tile), each batch element in turn
+    int rows = (p.M + 127) / 128 * 128;
+    while (rows > 128 && oz_scratch_bytes(rows, p.N, p.K, 1) > c->oz_bytes) rows = (rows / 2 + 127) / 128 * 128;
+    if (oz_scratch_bytes(rows, p.N, p.K, 1) > c->oz_bytes) return LB_EINVAL;
+    for (int b0 = 0; b0 < p.batch; b0++)
+      for (int m0 = 0; m0 < p.M; m0 += rows) {
+        OzGemm q = p;
+        q.batch = 1;
+        q.M = std::min(rows, p.M - m0);
+        q.A = p.A + (long long)b0 * p.sA + (long long)m0 * p.a_sm;
+        q.B = p.B + (long long)b0 * p.sB;
+        q.C = p.C + (long long)b0 * p.sC + (long long)m0 * p.ldc;
+        if (p.active != nullptr) q.active = p.active + b0;
+        q.err = c->err_dev;
+        LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st));
+      }
+    return LB_OK;
+  }
+  for (int b0 = 0; b0 < p.batch; b0 += chunk) {
+    OzGemm q = p;
+    q.batch = std::min(chunk, p.batch - b0);
+    q.A = p.A + (long long)b0 * p.sA;
+    q.B = p.B + (long long)b0 * p.sB;
+    q.C = p.C + (long long)b0 * p.sC;
+    if (p.active != nullptr) q.active = p.active + b0;
+    q.err = c->err_dev;
+    LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st));
+  }
+  return LB_OK;
+}
+
 #define LB_TRY(x)                     \
   do {                                \
     lb_status r_ = (x);               \
@@ -203,7 +241,7 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
   const long long max_nnz = (long long)(kSparseDensity * (double)nn);
   int* flagA = c->spflag;                     // A row-sparse
   int* flagA2 = c->spflag + c->max_slices;    // A^2 row-sparse
-  if (prec == LB_FP64_HERMITIAN) {
+  if (prec == LB_FP64_HERMITIAN || prec == LB_FP64_SLICED) {
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
     LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
@@ -342,7 +380,20 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
   // squarings; in the FP32 form the leading ones, whose operand is still
   // near I (kmix[s] of them), run as R^2 = 2R - I + D D with D = R - I and
   // only D D in FP32; the rest are FP64
-  for (int it = 0; it < smax; it++) {
+  for (int it = 0; it < smax && prec == LB_FP64_SLICED; it++) {
+    // in place: both operands are sliced before R is overwritten, and the
+    // slices whose squarings are done are skipped whole
+    OzGemm q;
+    q.M = q.N = q.K = n;
+    q.batch = S;
+    q.A = N; q.a_sm = n; q.a_sk = 1; q.sA = nn;
+    q.B = N; q.b_sk = n; q.b_sn = 1; q.sB = nn;
+    q.C = N; q.ldc = n; q.sC = nn;
+    q.active = c->sc;
+    q.active_iter = it;
+    LB_TRY(oz_product(c, q, st));
+  }
+  for (int it = 0; it < smax && prec != LB_FP64_SLICED; it++) {
     RGemmProblem<double> q = rsq(n, S, N, N, T2);
     q.active = c->sc;
     q.active_iter = it;
@@ -375,7 +426,7 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
 // ping-pong buffers, one real product per step (a few-state product for
 // B <= 8), and the states written back exactly Hermitian.
 lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int steps_per_slice, int B, z64* X,
-                               cudaStream_t st) {
+                               bool sliced, cudaStream_t st) {
   int d = 1;
   while (d * d < n) d++;
   const long long nn = (long long)n * n;
@@ -390,6 +441,14 @@ lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int 
       for (int t = 0; t < steps_per_slice; t++) {
         if (B <= kGemvMaxB) {
           LB_CUDA(launch_dgemv_f64(n, B, R + s * nn, n, cur, n, nxt, n, 1.0, nullptr, 0, st));
+        } else if (sliced) {
+          // next = cur R_s^T as a sliced FP64 product
+          OzGemm q;
+          q.M = B; q.N = n; q.K = n;
+          q.A = cur; q.a_sm = n; q.a_sk = 1;
+          q.B = R + s * nn; q.b_sk = 1; q.b_sn = n;
+          q.C = nxt; q.ldc = n;
+          LB_TRY(oz_product(c, q, st));
         } else {
           // next[b][a] = sum_k R_s[a][k] cur[b][k]  ->  next = cur R_s^T
           RGemmProblem<double> q;
@@ -410,3 +469,22 @@ lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int 
 }
 
 }  // namespace lb
+
+extern "C" lb_status lb_gemm_f64_sliced(lb_ctx* c, int M, int N, int K, int batch, const double* A, long long lda,
+                                        long long sA, const double* B, long long ldb, long long sB, double* C,
+                                        long long ldc, long long sC, double alpha, double beta, void* stream) {
+  using namespace lb;
+  if (c == nullptr || A == nullptr || B == nullptr || C == nullptr) return LB_EINVAL;
+  if (M < 0 || N < 0 || batch < 0 || K < 1 || K > kOzMaxK) return LB_EINVAL;
+  if (lda < K || ldb < N || ldc < N) return LB_EINVAL;
+  if (M == 0 || N == 0 || batch == 0) return LB_OK;
+  DeviceGuard g(c->device);
+  OzGemm q;
+  q.M = M; q.N = N; q.K = K; q.batch = batch;
+  q.A = A; q.a_sm = lda; q.a_sk = 1; q.sA = sA;
+  q.B = B; q.b_sk = ldb; q.b_sn = 1; q.sB = sB;
+  q.C = C; q.ldc = ldc; q.sC = sC;
+  q.alpha = alpha;
+  q.beta = beta;
+  return oz_product(c, q, (cudaStream_t)stream);
+}

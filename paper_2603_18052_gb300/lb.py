@@ -14,9 +14,9 @@ import torch
 
 from . import _build
 
-LB_FP64, LB_FP32, LB_BF16X3, LB_FP64_HERMITIAN, LB_FP32_HERMITIAN = 0, 1, 2, 3, 4
+LB_FP64, LB_FP32, LB_BF16X3, LB_FP64_HERMITIAN, LB_FP32_HERMITIAN, LB_FP64_SLICED = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16x3": LB_BF16X3, "fp64_hermitian": LB_FP64_HERMITIAN,
-              "fp32_hermitian": LB_FP32_HERMITIAN}
+              "fp32_hermitian": LB_FP32_HERMITIAN, "fp64_sliced": LB_FP64_SLICED}
 
 _STATUS = {
     0: "LB_OK",
@@ -45,6 +45,7 @@ EXPORTED = (
     "lb_assemble",
     "lb_expm_pade",
     "lb_propagate_batch",
+    "lb_gemm_f64_sliced",
     "lb_grape_grad",
     "lb_grape_grad_batch",
     "lb_propagate_batch_static",
@@ -135,6 +136,9 @@ def lib():
     L.lb_expm_pade.argtypes = [vp, i32, i32, vp, vp, vp, f64, i32, vp, vp, vp]
     L.lb_propagate_batch.restype = i32
     L.lb_propagate_batch.argtypes = [vp, i32, i32, vp, i32, i32, vp, i32, i32, vp]
+    L.lb_gemm_f64_sliced.restype = i32
+    i64 = ctypes.c_longlong
+    L.lb_gemm_f64_sliced.argtypes = [vp, i32, i32, i32, i32, vp, i64, i64, vp, i64, i64, vp, i64, i64, f64, f64, vp]
     L.lb_propagate_batch_static.restype = i32
     L.lb_propagate_batch_static.argtypes = [i32, i32, vp, i32, i32, vp, vp]
     L.lb_expm_frechet.restype = i32
@@ -335,6 +339,19 @@ def lb_propagate_batch(ctx, P, states, steps_per_slice=1, prec="fp64", renorm_tr
                                     _ptr(states, c128, "states", (B, n)), PRECISIONS.get(prec, prec),
                                     int(bool(renorm_trace)), _stream(stream)),
            "lb_propagate_batch")
+
+
+def lb_gemm_f64_sliced(ctx, A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha A B + beta C for float64 (batch, M, K) x (batch, K, N) ->
+    (batch, M, N) (or 2-D), row-major contiguous, via exact BF16 slices."""
+    f = torch.float64
+    A3, B3, C3 = (x if x.dim() == 3 else x.unsqueeze(0) for x in (A, B, C))
+    nb, M, K = A3.shape
+    N = B3.shape[2]
+    _check(lib().lb_gemm_f64_sliced(ctx.handle, M, N, K, nb, _ptr(A3, f, "A", (nb, M, K)), K, M * K,
+                                    _ptr(B3, f, "B", (nb, K, N)), N, K * N, _ptr(C3, f, "C", (nb, M, N)), N, M * N,
+                                    float(alpha), float(beta), _stream(stream)),
+           "lb_gemm_f64_sliced")
 
 
 def lb_grape_grad(ctx, Lbase, Ldrv, u, dt, steps_per_slice, X0, Xtarget, fidelity_out, grad_out, stream=None):

@@ -297,6 +297,31 @@ def test_propagate_fp32_d27_200_steps(lbm, dev):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("B,renorm", [(256, True), (37, False)])
+def test_propagate_fp32_d27_persistent(lbm, dev, B, renorm):
+    """The d = 27 FP32 chain with many steps runs as one persistent launch
+    (grid barrier between steps) rather than one launch per step: 60 steps
+    over 3 slices take at most a handful of launches, match the oracle chain
+    (1e-5 absolute Frobenius per state) and repeat bit for bit (the barrier
+    counter is reset per launch)."""
+    w = make_workload("d27_chain", B=B, nslices=3)
+    Ps = _slice_props(w, w["u"])
+    ref = O.propagate_chain(Ps, w["states"], 20)
+    ctx = lbm.Context(0, max_n=729, max_batch=B, max_slices=3)
+    out = []
+    for _ in range(2):
+        R = _t(w["states"], dev)
+        n0 = lbm.lb_launch_count()
+        lbm.lb_propagate_batch(ctx, _t(Ps, dev), R, steps_per_slice=20, prec="fp32", renorm_trace=renorm)
+        lbm.lb_sync_status(ctx)
+        launches = lbm.lb_launch_count() - n0
+        assert launches <= 8, launches
+        out.append(R.cpu().numpy())
+        err = np.max(np.linalg.norm(out[-1] - ref, axis=1))
+        assert err <= 1e-5, err
+    assert np.array_equal(out[0], out[1])
+
+
 def test_zero_steps_and_slices_leave_states(lbm, dev):
     w = make_workload("d3_single", B=3)
     Ps = _slice_props(w, np.array([0.05]))
