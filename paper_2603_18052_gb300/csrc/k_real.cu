@@ -176,16 +176,19 @@ __global__ void herm_to_complex_kernel(int n, int d, int S, const double* __rest
 // Real diagonal block of the blocked LU without pivot search, one CTA per
 // slice: factors the kb x kb block at (k0, k0) of M[s] in shared memory,
 // writes its upper factor into Uf[s] and the inverses of the unit-lower and
-// upper factors into Linv and Uinv (nb x nb, zero outside kb x kb).  A pivot
-// of modulus below 1e-300 (or non-finite) sets the error word.
+// upper factors into Linv and Uinv (NB x NB, zero outside kb x kb).  A pivot
+// of modulus below 1e-300 (or non-finite) sets the error word.  NB = 32 or
+// 64; the triangular inverses sum each entry in 256 / NB partial sums.
+template <int NB>
 __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb, const double* __restrict__ M,
                                                            double* __restrict__ Uf, double* __restrict__ Linv,
                                                            long long sLinv, double* __restrict__ Uinv,
                                                            long long sUinv, unsigned int* err) {
-  constexpr int NB = kLuNb;
-  __shared__ double a[NB][NB + 1];
-  __shared__ double x[NB][NB + 1];
-  __shared__ double part[8][NB];
+  constexpr int NP = 256 / NB;
+  extern __shared__ double lu_smem[];
+  double(*a)[NB + 1] = (double(*)[NB + 1])lu_smem;
+  double(*x)[NB + 1] = (double(*)[NB + 1])(lu_smem + NB * (NB + 1));
+  double(*part)[NB] = (double(*)[NB])(lu_smem + 2 * NB * (NB + 1));
   __shared__ double rinv_s;
   const int s = blockIdx.x;
   const long long nn = (long long)n * n;
@@ -217,19 +220,19 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
     }
     __syncthreads();
   }
-  const int c = tid & 31, p = tid >> 5;  // column, partial-sum group (8 groups)
+  const int c = tid % NB, p = tid / NB;  // column, partial-sum group
   // Linv: X = L^{-1}, L unit lower; X[i][c] = d_ic - sum_{j<i} L[i][j] X[j][c]
   for (int e = tid; e < NB * NB; e += blockDim.x) x[e / NB][e % NB] = 0.0;
   __syncthreads();
   for (int i = 0; i < kb; i++) {
     double acc = 0.0;
     if (c < kb)
-      for (int j = p; j < i; j += 8) acc = fma(-a[i][j], x[j][c], acc);
+      for (int j = p; j < i; j += NP) acc = fma(-a[i][j], x[j][c], acc);
     part[p][c] = acc;
     __syncthreads();
     if (p == 0 && c < kb) {
       double v = i == c ? 1.0 : 0.0;
-      for (int q = 0; q < 8; q++) v += part[q][c];
+      for (int q = 0; q < NP; q++) v += part[q][c];
       x[i][c] = v;
     }
     __syncthreads();
@@ -243,12 +246,12 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
   for (int i = kb - 1; i >= 0; i--) {
     double acc = 0.0;
     if (c < kb)
-      for (int j = i + 1 + p; j < kb; j += 8) acc = fma(-a[i][j], x[j][c], acc);
+      for (int j = i + 1 + p; j < kb; j += NP) acc = fma(-a[i][j], x[j][c], acc);
     part[p][c] = acc;
     __syncthreads();
     if (p == 0 && c < kb) {
       double v = i == c ? 1.0 : 0.0;
-      for (int q = 0; q < 8; q++) v += part[q][c];
+      for (int q = 0; q < NP; q++) v += part[q][c];
       const double dd = a[i][i];
       x[i][c] = (fabs(dd) >= 1e-300 && isfinite(dd)) ? v / dd : v;
     }
@@ -261,6 +264,11 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
     const int i = e / kb, j = e - (e / kb) * kb;
     Ufs[(long long)(k0 + i) * n + (k0 + j)] = (j >= i) ? a[i][j] : 0.0;
   }
+}
+
+template <int NB>
+constexpr size_t lu_diag_smem() {
+  return (size_t)(2 * NB * (NB + 1) + (256 / NB) * NB) * sizeof(double);
 }
 
 }  // namespace
@@ -339,9 +347,19 @@ cudaError_t launch_herm_to_complex(int n, int d, int S, const double* R, z64* P,
 }
 
 cudaError_t launch_lu_diag_real(int n, int S, int k0, int kb, const double* M, double* Uf, double* Linv,
-                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st) {
+                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st,
+                                int nb) {
+  if (nb == 64) {
+    constexpr size_t sm = lu_diag_smem<64>();
+    cudaError_t e = set_smem_once((const void*)lu_diag_real_kernel<64>, sm);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    lu_diag_real_kernel<64><<<S, 256, sm, st>>>(n, k0, kb, M, Uf, Linv, sLinv, Uinv, sUinv, err);
+    return cudaGetLastError();
+  }
+  if (nb != kLuNb) return cudaErrorInvalidValue;
   count_launch();
-  lu_diag_real_kernel<<<S, 256, 0, st>>>(n, k0, kb, M, Uf, Linv, sLinv, Uinv, sUinv, err);
+  lu_diag_real_kernel<kLuNb><<<S, 256, lu_diag_smem<kLuNb>(), st>>>(n, k0, kb, M, Uf, Linv, sLinv, Uinv, sUinv, err);
   return cudaGetLastError();
 }
 

@@ -162,7 +162,13 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add((size_t)max_batch * max_n * zb);                      // Rtmp
   add((size_t)max_batch * max_n * zb);                      // Xh
   const size_t plane_elems = (size_t)max_n * (size_t)plane_ld(max_n);
-  add(38 * plane_elems * S * sizeof(__nv_bfloat16));  // split planes (6 + 8 x 4), sliced-FP64 scratch
+  // split planes (6 + 8 x 4); also the sliced-FP64 scratch: both operands of
+  // a squaring of all slices, or the propagators' and the states' slices
+  const size_t oz_need = std::max(oz_scratch_bytes(max_n, max_n, max_n, max_slices),
+                                  oz_sliced_bytes(max_n, max_n, max_slices, kOzBNSmall) +
+                                      oz_sliced_bytes(max_batch, max_n, 1, kOzTileM));
+  const size_t sp_bytes = std::max(38 * plane_elems * S * sizeof(__nv_bfloat16), oz_need);
+  add(sp_bytes);
   for (int i = 0; i < 2; i++) add(4 * (size_t)max_batch * plane_ld(max_n) * sizeof(__nv_bfloat16));
   const size_t dpl = std::max(chain32_dplane_floats(max_n), 2 * nn) * S;
   add(dpl * sizeof(float));                                 // Dpl (Dr, Di inside)
@@ -205,7 +211,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
   c->Xh = Z((size_t)max_batch * max_n);
-  c->oz_bytes = 38 * plane_elems * S * sizeof(__nv_bfloat16);
+  c->oz_bytes = sp_bytes;
   c->oz_scratch = ar.take(c->oz_bytes);
   for (int i = 0; i < 9; i++)
     c->sp[i] = (__nv_bfloat16*)c->oz_scratch + (i == 0 ? 0 : 6 + 4 * (i - 1)) * plane_elems * S;

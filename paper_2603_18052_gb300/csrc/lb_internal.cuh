@@ -21,6 +21,7 @@ enum : unsigned int {
 
 constexpr int kMaxN = 729;
 constexpr int kLuNb = 32;  // LU block size
+constexpr int kLuNbSliced = 64;  // LU block size of the sliced-product schedule
 
 typedef double2 z64;
 
@@ -312,8 +313,10 @@ cudaError_t launch_real_copy_active(long long nn, int S, const double* src, doub
                                     int sm_count, cudaStream_t st);
 // P[s] (complex superoperator) from R[s] (its real-coordinate matrix)
 cudaError_t launch_herm_to_complex(int n, int d, int S, const double* R, z64* P, int sm_count, cudaStream_t st);
+// nb: the block size, 32 (kLuNb) or 64
 cudaError_t launch_lu_diag_real(int n, int S, int k0, int kb, const double* M, double* Uf, double* Linv,
-                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st);
+                                long long sLinv, double* Uinv, long long sUinv, unsigned int* err, cudaStream_t st,
+                                int nb = kLuNb);
 // The real-coordinate propagator build (lb_expm_pade with a Hermitian
 // precision) and the real-coordinate propagation for n > 81 (lb_real.cu).
 lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* Ldrv, const double* u, double dt,
@@ -476,8 +479,26 @@ struct OzGemm {
   const int* EA = nullptr; const int* EB = nullptr;  // row / column exponents (set by ozgemm_f64)
   unsigned int* err = nullptr;
 };
-long long oz_kpad(int K);
-// scratch for one call: the slice planes of both operands and the exponents
+constexpr int kOzBN = 48;       // columns of C per CTA (B tile rows)
+constexpr int kOzBNSmall = 16;  // the narrow tile, for products with few output tiles
+constexpr int kOzTileM = 128;   // rows of C per CTA (A tile rows)
+// An operand in slices: digit planes in the tile-blocked layout of
+// k_ozaki.cu (tile_rows = 128 for A, kOzBN for B) and one exponent per row.
+struct OzSliced {
+  __nv_bfloat16* Q = nullptr;
+  int* E = nullptr;
+  int rows = 0, K = 0, batch = 0, tile_rows = 0;
+};
+size_t oz_sliced_bytes(int rows, int K, int batch, int tile_rows);
+OzSliced oz_carve(void* base, int rows, int K, int batch, int tile_rows);
+OzSliced oz_view(const OzSliced& o, int b);  // batch element b alone
+// rows r of X (element (r, k) of batch element b at X[b sb + r sr + k sk]) in slices
+cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, const OzSliced& o, const int* active,
+                     int active_iter, cudaStream_t st);
+// C = alpha A B + beta C from sliced A (M rows) and sliced B^T (N rows); p's
+// A, B pointers are not used
+cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, cudaStream_t st);
+// scratch for one call of ozgemm_f64: the slices of both operands
 size_t oz_scratch_bytes(int M, int N, int K, int batch);
 cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st);
 // Z = c0 X0 + c1 X1 + c2 X2 (FP32) written as the two-piece planes of Z^T

@@ -133,6 +133,78 @@ lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, 
   return LB_OK;
 }
 
+// C = alpha A B + beta C through the sliced FP64 product, in chunks of
+// batch elements that fit the context's scratch (defined below).
+lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
+
+// The same factorisation and solve with every product sliced (the
+// LB_FP64_SLICED form), on a right-looking schedule: at block step k the
+// diagonal block (up to date with all earlier steps) is factored and
+// inverted, the block row of U and block column of L follow from the block
+// inverses, block row k of Y = L^{-1} N follows from Linv_k, and the
+// trailing matrix and the right-hand sides below the block are updated by
+// two products of K = 64.  The back substitution runs bottom up: block row
+// k of the solution is Uinv_k Y_k, and the rows above are updated by it.
+// Every product is one sliced launch over all slices.
+lb_status lu_solve_sliced_real(lb_ctx* c, int n, int S, double* Mx, double* N, double* Uf, double* Y, double* Lp,
+                               double* inv, cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  // 64-wide blocks from n = 128 (their inverses in `inv`, which holds
+  // 2 n^2 S doubles), else the 32-wide blocks of the context's buffers
+  const int nb = n >= 128 ? kLuNbSliced : kLuNb, nbk = (n + nb - 1) / nb;
+  const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
+  double* Linv = nb == kLuNb ? (double*)c->Linv : inv;                           // S x nb x nb
+  double* Uinv = nb == kLuNb ? (double*)c->Uinv : inv + (long long)S * sLinv;  // S x nbk x nb x nb
+  // C (ld n, one per slice) = alpha A B + beta C; A(m, k) at A + m lda + k,
+  // B(k, j) at B + k ldb + j
+  auto prod = [&](int M, int Ncol, int K, const double* A, long long lda, long long sA, const double* B,
+                  long long ldb, long long sB, double* C, double alpha, double beta) -> lb_status {
+    OzGemm q;
+    q.M = M; q.N = Ncol; q.K = K; q.batch = S;
+    q.A = A; q.a_sm = lda; q.a_sk = 1; q.sA = sA;
+    q.B = B; q.b_sk = ldb; q.b_sn = 1; q.sB = sB;
+    q.C = C; q.ldc = n; q.sC = nn;
+    q.alpha = alpha;
+    q.beta = beta;
+    return oz_product(c, q, st);
+  };
+  for (int k = 0; k < nbk; k++) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, r0 = k0 + kb, rest = n - r0;
+    double* Uinv_k = Uinv + (long long)k * nb * nb;
+    LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st, nb));
+    lb_status r = LB_OK;
+    if (rest > 0) {
+      // U[k0:r0, r0:] = Linv_k Mx[k0:r0, r0:];  L[r0:, k0:r0] = Mx[r0:, k0:r0] Uinv_k
+      r = prod(kb, rest, kb, Linv, nb, sLinv, Mx + (long long)k0 * n + r0, n, nn, Uf + (long long)k0 * n + r0, 1.0,
+               0.0);
+      if (r == LB_OK)
+        r = prod(rest, kb, kb, Mx + (long long)r0 * n + k0, n, nn, Uinv_k, nb, sUinv, Lp + (long long)r0 * n + k0,
+                 1.0, 0.0);
+    }
+    // Y[k0:r0, :] = Linv_k N[k0:r0, :]
+    if (r == LB_OK)
+      r = prod(kb, n, kb, Linv, nb, sLinv, N + (long long)k0 * n, n, nn, Y + (long long)k0 * n, 1.0, 0.0);
+    if (r == LB_OK && rest > 0) {
+      // Mx[r0:, r0:] -= L[r0:, k0:r0] U[k0:r0, r0:];  N[r0:, :] -= L[r0:, k0:r0] Y[k0:r0, :]
+      r = prod(rest, rest, kb, Lp + (long long)r0 * n + k0, n, nn, Uf + (long long)k0 * n + r0, n, nn,
+               Mx + (long long)r0 * n + r0, -1.0, 1.0);
+      if (r == LB_OK)
+        r = prod(rest, n, kb, Lp + (long long)r0 * n + k0, n, nn, Y + (long long)k0 * n, n, nn, N + (long long)r0 * n,
+                 -1.0, 1.0);
+    }
+    if (r != LB_OK) return r;
+  }
+  for (int k = nbk - 1; k >= 0; k--) {
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb;
+    double* Uinv_k = Uinv + (long long)k * nb * nb;
+    // X[k0:r0, :] = Uinv_k Y[k0:r0, :] (into N);  Y[:k0, :] -= U[:k0, k0:r0] X[k0:r0, :]
+    lb_status r = prod(kb, n, kb, Uinv_k, nb, sUinv, Y + (long long)k0 * n, n, nn, N + (long long)k0 * n, 1.0, 0.0);
+    if (r == LB_OK && k0 > 0) r = prod(k0, n, kb, Uf + k0, n, nn, N + (long long)k0 * n, n, nn, Y, -1.0, 1.0);
+    if (r != LB_OK) return r;
+  }
+  return LB_OK;
+}
+
 // Density below which a power of A is multiplied as a row-sparse left
 // operand (the zero-skip of the paper's Pade products, Sec. 3.1): the low
 // powers of a local Lindbladian's real form have a few percent of nonzeros
@@ -368,7 +440,10 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
   if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
   // (V - U) R = (V + U), FP64.  U, Y, L reuse A2, A4, A6.
   {
-    lb_status r = lu_solve_blocked_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6, st);
+    lb_status r = prec == LB_FP64_SLICED
+                      ? lu_solve_sliced_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6,
+                                             (double*)c->Z2, st)
+                      : lu_solve_blocked_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6, st);
     if (r != LB_OK) return r;
   }
   if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
@@ -434,21 +509,36 @@ lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int 
   double* cur = (double*)c->Rtmp;
   double* nxt = cur + (long long)B * n;
   LB_CUDA(launch_herm_coords_in(n, d, B, X, cur, c->sm_count, st));
-  for (int s0 = 0; s0 < nslices; s0 += c->max_slices) {
-    const int S = (nslices - s0 < c->max_slices) ? nslices - s0 : c->max_slices;
+  sliced = sliced && B > kGemvMaxB;
+  // sliced products: the slices of the chunk's R_s (B operands, narrow
+  // tiles: a product has few output tiles) and of the states in the
+  // context's scratch; chunks of at most max_slices slices that fit there
+  const size_t xs_bytes = oz_sliced_bytes(B, n, 1, kOzTileM);
+  int chunk = c->max_slices;
+  while (sliced && chunk > 1 && xs_bytes + oz_sliced_bytes(n, n, chunk, kOzBNSmall) > c->oz_bytes) chunk = (chunk + 1) / 2;
+  if (sliced && xs_bytes + oz_sliced_bytes(n, n, chunk, kOzBNSmall) > c->oz_bytes) return LB_EINVAL;
+  for (int s0 = 0; s0 < nslices; s0 += chunk) {
+    const int S = (nslices - s0 < chunk) ? nslices - s0 : chunk;
     LB_CUDA(launch_herm_matrix(n, d, S, P + s0 * nn, R, c->sm_count, st));
+    OzSliced Rs, Xs;
+    if (sliced) {
+      Rs = oz_carve(c->oz_scratch, n, n, S, kOzBNSmall);
+      Xs = oz_carve((uint8_t*)c->oz_scratch + oz_sliced_bytes(n, n, S, kOzBNSmall), B, n, 1, kOzTileM);
+      LB_CUDA(oz_slice(R, n, 1, nn, Rs, nullptr, 0, st));  // row c of R_s = column c of R_s^T
+    }
     for (int s = 0; s < S; s++)
       for (int t = 0; t < steps_per_slice; t++) {
         if (B <= kGemvMaxB) {
           LB_CUDA(launch_dgemv_f64(n, B, R + s * nn, n, cur, n, nxt, n, 1.0, nullptr, 0, st));
         } else if (sliced) {
-          // next = cur R_s^T as a sliced FP64 product
+          // next = cur R_s^T: the states in slices, then the product with the
+          // slices of R_s made once for the chunk
+          LB_CUDA(oz_slice(cur, n, 1, 0, Xs, nullptr, 0, st));
           OzGemm q;
           q.M = B; q.N = n; q.K = n;
-          q.A = cur; q.a_sm = n; q.a_sk = 1;
-          q.B = R + s * nn; q.b_sk = 1; q.b_sn = n;
           q.C = nxt; q.ldc = n;
-          LB_TRY(oz_product(c, q, st));
+          q.err = c->err_dev;
+          LB_CUDA(oz_multiply(Xs, oz_view(Rs, s), q, st));
         } else {
           // next[b][a] = sum_k R_s[a][k] cur[b][k]  ->  next = cur R_s^T
           RGemmProblem<double> q;
