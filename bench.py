@@ -7,9 +7,15 @@ the 200 slice propagators by Pade-13 scaling and squaring with the FP64 LU
 solve, and propagate 256 density matrices through the 200-slice chain (one
 step per slice).  Five forms are timed:
 
-  fp64_hermitian  (headline) all FP64, every product, the LU and the solve on
-                  the real coordinates of Hermitian matrices (real n x n
-                  matrices: one FMA per multiply-add instead of four)
+  fp64_sliced     (headline) the real-coordinate form below with every dense
+                  FP64 product (Pade products after A^2, the LU and solve
+                  block products, the squarings, the propagation steps)
+                  computed on the BF16 tensor cores through exact digit
+                  slices (FP64 operands and results, error of the size of an
+                  FP64 product's rounding)
+  fp64_hermitian  all FP64 on the FP64 pipe, every product, the LU and the
+                  solve on the real coordinates of Hermitian matrices (real
+                  n x n matrices: one FMA per multiply-add instead of four)
   fp64            all FP64 on the complex superoperators, as the paper states
                   the method
   fp32_hermitian  real-coordinate build with FP32 Pade products and near-I
@@ -69,14 +75,24 @@ def _measured_bf16_peak():
 
 BF16_PEAK = _measured_bf16_peak()
 # form: (build precision, propagation precision, per-step trace renormalisation)
-FORMS = {"fp64_hermitian": ("fp64_hermitian", "fp64_hermitian", False), "fp64": ("fp64", "fp64", False),
+FORMS = {"fp64_sliced": ("fp64_sliced", "fp64_sliced", False),
+         "fp64_hermitian": ("fp64_hermitian", "fp64_hermitian", False), "fp64": ("fp64", "fp64", False),
          "fp32_hermitian": ("fp32_hermitian", "fp32", True), "bf16x3": ("bf16x3", "bf16x3", True),
          "fp32": ("fp32", "fp32", True)}
-HEADLINE = "fp64_hermitian"
+HEADLINE = "fp64_sliced"
+FP64_NATIVE = "fp64_hermitian"
+OZ_KERNEL_VERSION = "persistent-320t-4stage"  # the sliced-product kernel a traffic capture describes
 MIXED_FORMS = ("fp32_hermitian", "bf16x3", "fp32")
-DTYPES = {"fp64_hermitian": "f64", "fp64": "f64", "fp32_hermitian": "f32+f64",
+DTYPES = {"fp64_sliced": "f64", "fp64_hermitian": "f64", "fp64": "f64", "fp32_hermitian": "f32+f64",
           "bf16x3": "bf16 split (x3 build, x5 propagation) + f64", "fp32": "f32+f64"}
 PRECISION_DESC = {
+    "fp64_sliced": "FP64 operands and results on the real coordinates; every dense product (A^4, A^6, A^6 Z1, "
+                   "A^6 Z2, the LU and solve block products, the squarings, the propagation steps) as an exact "
+                   "sliced product on the BF16 tensor cores: each row / column written as nine signed base-64 "
+                   "digits against its power-of-two exponent, the 45 digit products of equal weight summed exactly "
+                   "in FP32 in TMEM, combined in integer arithmetic and rounded once to FP64 (error <= "
+                   "K 2^-54 13/4 of the row and column maxima, the size of an FP64 product's rounding); A^2 and "
+                   "A W skip A's zeros in FP64; the 64 x 64 diagonal LU blocks and their inverses in FP64",
     "fp64_hermitian": "all FP64 on the real coordinates of Hermitian matrices (diagonal, Re and Im of the upper "
                       "triangle): the real form of each slice generator, Pade products, LU, solve and squarings "
                       "as real 729x729 FP64 matrices, P rebuilt from its real form; propagation on the states' "
@@ -252,6 +268,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "state-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "arithmetic": "FP64 inputs and results; the dense FP64 products run on the BF16 tensor cores as exact "
+                      "digit slices (Ozaki scheme) with FP64-size rounding error; the FP64-pipe form is under "
+                      "fp64_native",
             "builds_per_s": per_step / t,
             "config": {"workload": WORKLOAD_DESC,
                        "sample_per_step": "%d of the 200 slices per step (%d Pade builds + 256 states x %d steps); the "
@@ -998,6 +1017,7 @@ def run_ours(args):
         med = max_over_ranks(statistics.median(trial))
         total_ms = max_over_ranks(e0.elapsed_time(e1))
         stages, chunks = lb.lb_stage_times(ctx)
+        kern_ms, kern_fl, kern_n = lb.lb_kernel_times(ctx)
         lb.lb_set_stage_timing(ctx, False)
         ph = {"assemble_ms": 0.0, "build_ms": 0.0, "propagate_ms": 0.0}
         for ev in evs:
@@ -1007,7 +1027,8 @@ def run_ours(args):
         stages = {k: v / steps for k, v in stages.items()}
         return dict(ms_per_step=med, mean_ms_per_step=total_ms / steps, trial_ms_per_step=trial, steps=steps,
                     warmup=warmup, phases=ph, build_stages_ms=stages, launches=(n1 - n0) // steps, clocks=clocks,
-                    step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs])
+                    step_ms=[ev[0].elapsed_time(ev[3]) for ev in evs],
+                    sliced_kernel={"ms": kern_ms / steps, "flops": kern_fl / steps, "launches": kern_n // steps})
 
     t_tune = time.perf_counter()
     tuned = lb.lb_autotune(ctx, n, S, B) if not args.no_autotune else 0
@@ -1085,50 +1106,69 @@ def run_ours(args):
     value = world * units / (head["ms_per_step"] / 1e3)
     builds = world * S / (head["ms_per_step"] / 1e3)
 
-    # roofline of the dominant kernel: the real FP64 GEMM (rgemm_kernel<double>)
-    # that carries the LU updates and substitutions, the squarings and the
-    # propagation steps (the Pade products skip zeros, see below); the
-    # stages' time from the library's stage events and the step's phase
-    # events on this stream
-    st = head["build_stages_ms"]
-    prop_ms = head["phases"]["propagate_ms"]
+    # roofline of the dominant kernel of the headline form: the sliced FP64
+    # product (ozgemm_kernel) on the BF16 tensor cores, every launch of the
+    # timed steps bracketed by CUDA events on its stream (lb_kernel_times);
+    # the work counted is its 45 BF16 digit products per FP64 multiply-add
+    sk = head["sliced_kernel"]
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ozgemm_d27_traffic.json")
+    if os.path.exists(tfile):
+        t = json.load(open(tfile))
+        if t.get("per_launch_bytes") and t.get("kernel_version") == OZ_KERNEL_VERSION:
+            traffic = t["per_launch_bytes"]
+    ach = sk["flops"] / (sk["ms"] / 1e3) if sk["ms"] > 0 else 0.0
+    roofline = {
+        "bound": "tensor", "kernel": "ozgemm_kernel: the sliced FP64 products (Pade products A^4 .. A^6 Z2, the LU and "
+                                     "solve block products, the propagation steps; the masked squaring launches "
+                                     "excepted)",
+        "achieved": ach / 1e12, "peak": bf16_peak / 1e12, "unit": "TFLOP/s", "frac": ach / bf16_peak,
+        "traffic": traffic, "peak_source": peak_src["bf16"] + " (dense BF16 tcgen05, burst)",
+        "launches_per_step": sk["launches"], "kernel_ms_per_step": sk["ms"],
+        "algorithmic_flops_per_step": sk["flops"],
+        "flops_note": "digit-product FLOPs: 45 BF16 products (the digit pairs i + j <= 10 of nine digits per "
+                      "operand) x 2 M N K per FP64 product M x N x K; the padded rows and columns of the 128 x BN "
+                      "tiles are not counted",
+        "fp64_equivalent_tflops": ach / 45.0 / 1e12,
+        "fp64_equivalent_vs_dfma_peak": (ach / 45.0) / fp64_peak,
+        "share_of_step": sk["ms"] / head["ms_per_step"],
+        "stage_ms": {k: head["build_stages_ms"][k] for k in ("pade_products", "lu_solve", "squarings")},
+    }
+
+    # the FP64-pipe form's roofline: the real FP64 GEMM (rgemm_kernel<double>)
+    # of the LU and solve, the squarings and the propagation, from the
+    # stage and phase events
+    nat = res[FP64_NATIVE]
+    st = nat["build_stages_ms"]
+    prop_ms = nat["phases"]["propagate_ms"]
     n3 = float(n) ** 3
     fl_solve = S * accounting.build_flops_real_solve(n)
     fl_sq = sum(squarings) * 2 * n3
     fl_prop = S * B * accounting.state_step_flops_real(n)
     gemm_ms = st["lu_solve"] + st["squarings"] + prop_ms
     gemm_flops = fl_solve + fl_sq + fl_prop
-    ach = gemm_flops / (gemm_ms / 1e3)
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "rgemm_f64_d27_traffic.json")
-    if os.path.exists(tfile):
-        t = json.load(open(tfile))
-        if t.get("per_step_bytes"):
-            traffic = t["per_step_bytes"]
-    roofline = {
+    ach64 = gemm_flops / (gemm_ms / 1e3)
+    roofline_native = {
         "bound": "alu", "kernel": "rgemm_kernel<double>: the LU updates and substitutions, the squarings and the "
-                                  "propagation steps of the real-coordinate FP64 form (with lu_diag_real_kernel)",
-        "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-        "traffic": traffic, "peak_source": peak_src["fp64"] + " (DFMA, burst); FP64 is absent from "
-                                                               "MEASURED_PEAKS.json",
+                                  "propagation steps of the FP64-pipe real-coordinate form",
+        "achieved": ach64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+        "peak_source": peak_src["fp64"] + " (DFMA, burst)",
         "algorithmic_flops_per_step": gemm_flops,
         "flops_note": "real FLOPs, 2 per real multiply-add, n = 729: per slice the LU 2 n^3/3 and the n-RHS solve "
-                      "2 n^3, s squarings at 2 n^3; per state-step 2 n^2 (B = 256, 200 steps); these dense GEMMs "
-                      "execute exactly these FMAs",
-        "share_of_step": gemm_ms / head["ms_per_step"],
+                      "2 n^3, s squarings at 2 n^3; per state-step 2 n^2 (B = 256, 200 steps)",
+        "share_of_step": gemm_ms / nat["ms_per_step"],
         "stage_ms": {"lu_solve": st["lu_solve"], "squarings": st["squarings"], "propagation": prop_ms},
         "lu_solve_frac": (fl_solve / (st["lu_solve"] / 1e3)) / fp64_peak,
         "squarings_frac": (fl_sq / (st["squarings"] / 1e3)) / fp64_peak if st["squarings"] > 0 else None,
-        "propagation_frac": (fl_prop / (prop_ms / 1e3)) / fp64_peak,
-        "pade_products": {"ms": st["pade_products"],
-                          "note": "zero-skipping products (rgemm_rowskip_kernel): A and A^2 of the transmon chain "
-                                  "are 1.2 % and 5.6 % nonzero on the real coordinates, so the Pade step costs "
-                                  "a few percent of its dense 12 n^3 per slice and is bound by L2 traffic, "
-                                  "not by the FP64 pipe"}}
+        "propagation_frac": (fl_prop / (prop_ms / 1e3)) / fp64_peak}
 
     def prop_roof(f):
         ms = res[f]["phases"]["propagate_ms"]
-        if f == "fp64_hermitian":
+        if f == "fp64_sliced":
+            fl, peak, note = S * B * accounting.state_step_flops_real(n) * 45, bf16_peak, \
+                "45 BF16 digit products per real multiply-add, 2 n^2 real FLOP per state-step, against the BF16 " \
+                "tcgen05 probe (the states sliced every step, the propagators once per chunk)"
+        elif f == "fp64_hermitian":
             fl, peak, note = S * B * accounting.state_step_flops_real(n), fp64_peak, \
                 "2 n^2 real FLOP per state-step on the real coordinates against the DFMA probe"
         elif f in ("fp64",):
@@ -1142,7 +1182,8 @@ def run_ours(args):
             fl, peak, note = S * B * accounting.state_step_flops(n), fp32_peak, \
                 "8 n^2 FLOP per state-step against the FFMA probe"
         a = fl / (ms / 1e3)
-        return {"bound": "tensor" if f == "bf16x3" else "alu", "achieved": a / 1e12, "peak": peak / 1e12,
+        return {"bound": "tensor" if f in ("bf16x3", "fp64_sliced") else "alu", "achieved": a / 1e12,
+                "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": a / peak, "ms": ms, "note": note}
 
     mixed_line = {"form": mixed_form, **form_line(mixed_form),
@@ -1153,6 +1194,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "state-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "arithmetic": "FP64 inputs and results; the dense FP64 products run on the BF16 tensor cores as exact "
+                      "digit slices (Ozaki scheme) with FP64-size rounding error; the FP64-pipe form is under "
+                      "fp64_native",
         "builds_per_s": builds, "form": HEADLINE,
         "config": {"workload": WORKLOAD_DESC,
                    "precision": PRECISION_DESC[HEADLINE],
@@ -1167,6 +1211,9 @@ def run_ours(args):
         "forms": {f: form_line(f) for f in FORMS},
         "peaks_measured_tflops": peaks,
         "roofline": roofline,
+        "roofline_fp64_native": roofline_native,
+        "fp64_native": {"form": FP64_NATIVE, **form_line(FP64_NATIVE),
+                        "headline_speedup": nat["ms_per_step"] / head["ms_per_step"]},
         "roofline_propagation": {f: prop_roof(f) for f in FORMS},
         "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": "state-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -153,6 +153,17 @@ lb_status lb_set_stage_timing(lb_ctx* ctx, int enable);
 lb_status lb_stage_times(lb_ctx* ctx, double* ms_out, long long* chunks_out);
 
 /*
+ * lb_kernel_times -- with the stage timers on (lb_set_stage_timing), every
+ * launch of the sliced FP64 product kernel (LB_FP64_SLICED; launches with a
+ * per-slice mask, the squarings, excepted) is bracketed by CUDA events on
+ * its stream.  Waits for them and returns since the last
+ * lb_set_stage_timing: *ms_out the summed kernel time (ms), *flops_out its
+ * digit-product FLOPs (45 BF16 products per multiply-add: 90 M N K per
+ * product; may be NULL), *launches_out the launches (may be NULL).
+ */
+lb_status lb_kernel_times(lb_ctx* ctx, double* ms_out, double* flops_out, long long* launches_out);
+
+/*
  * lb_assemble -- the vectorised Lindbladian of Eq. 1 under row-major vec
  * (Eq. 2-3):
  *   L = -i (H (x) I - I (x) H^T)

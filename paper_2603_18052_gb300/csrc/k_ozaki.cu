@@ -6,7 +6,8 @@
 // Row r of the left operand A (M x K) is written in fixed point against its
 // own exponent e_r (every |A[r][k]| < 2^e_r) as signed base-2^BETA digits,
 //   A[r][k] = 2^e_r ( sum_{i=1..NS} a_i[r][k] 2^(-i BETA) + rho ),
-//   |a_1| <= 2^BETA, |a_i| <= 2^(BETA-1) (i >= 2), |rho| <= 2^(-NS BETA - 1),
+//   |a_1| <= 2^BETA, -2^(BETA-1) <= a_i < 2^(BETA-1) (i >= 2),
+//   |rho| <= 2^(-NS BETA - 1),
 // and column c of B (K x N) likewise against f_c with digits b_j.  Every
 // digit is an integer of at most seven significant bits, exact in BF16, and
 // every digit product is exact in FP32.  The digit products of one "group"
@@ -54,7 +55,8 @@ constexpr int OZ_BETA = 6;
 constexpr int OZ_TBM = 128;       // rows per A tile (M of one MMA)
 constexpr int OZ_KB = 16;         // K per block and stage (one MMA K step)
 constexpr int OZ_NSTAGE = 4;
-constexpr int OZ_THREADS = 256;
+constexpr int OZ_THREADS = 320;  // producer warp, MMA warp, eight epilogue warps (at most 168 registers:
+                                 // three warps share one scheduler's 16K registers)
 constexpr int OZ_ZERO_EXP = -2000;  // exponent of an all-zero row
 constexpr long long kOzWaitCycles = 4000000000LL;
 
@@ -118,14 +120,43 @@ __device__ __forceinline__ void oz_bulk(uint32_t dst, const void* src, uint32_t 
                : "memory");
 }
 
-__device__ __forceinline__ void oz_ld8(uint32_t ta, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(ta));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Eight columns of each of the nine groups of this thread's lane (group g
+// at TMEM column ta + g stride), all loads in flight, one wait.
+__device__ __forceinline__ void oz_ld8x9(uint32_t ta, uint32_t stride, float* v) {
+  uint32_t r[72];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%72];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%73];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%74];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%75];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%76];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%77];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48,%49,%50,%51,%52,%53,%54,%55}, [%78];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%56,%57,%58,%59,%60,%61,%62,%63}, [%79];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%64,%65,%66,%67,%68,%69,%70,%71}, [%80];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]), "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71])
+      : "r"(ta + 0 * stride), "r"(ta + 1 * stride), "r"(ta + 2 * stride), "r"(ta + 3 * stride), "r"(ta + 4 * stride), "r"(ta + 5 * stride), "r"(ta + 6 * stride), "r"(ta + 7 * stride), "r"(ta + 8 * stride)
+      : "memory");
 #pragma unroll
-  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 72; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// x 2^e as a double, exactly, for |x| < 2^53, with sgn xor-ed into the sign;
+// false where the result would not be a normal double.
+__device__ __forceinline__ bool oz_i2d(long long x, int e, unsigned long long sgn, double* out) {
+  if (x == 0) {
+    *out = 0.0;
+    return true;
+  }
+  const unsigned long long neg = x < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int p = 63 - __clzll((long long)a);  // leading bit, <= 52
+  const int E = p + e;
+  if (E < -1022 || E > 1023) return false;
+  const unsigned long long mant = (a << (52 - p)) & 0xFFFFFFFFFFFFFull;
+  *out = __longlong_as_double((long long)((neg ^ sgn) | ((unsigned long long)(E + 1023) << 52) | mant));
+  return true;
 }
 
 // 2^s as a double for s in [-1022, 1023]; 0 below
@@ -134,65 +165,36 @@ __device__ __forceinline__ double oz_pow2(int s) {
   return __longlong_as_double((long long)(s + 1023) << 52);
 }
 
-// (hi 2^30 + lo) 2^e rounded to the nearest double (ties to even), for
-// |hi| < 2^44, |lo| < 2^50, in integer arithmetic only (the FP64 pipe is
-// slow on this part); *ok = false where the result would leave the normal
-// range (the caller then takes the FP64 route).
-__device__ __forceinline__ double oz_round(long long hi, long long lo, int e, bool* ok) {
-  const __int128 T = (__int128)hi * ((__int128)1 << 30) + (__int128)lo;
-  const bool neg = T < 0;
-  const unsigned __int128 U = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
-  const unsigned long long uh = (unsigned long long)(U >> 64), ul = (unsigned long long)U;
-  *ok = true;
-  if ((uh | ul) == 0ull) return 0.0;
-  const int p = uh != 0ull ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);  // leading bit
-  unsigned long long mant;
-  int E = p + e;
-  if (p <= 52) {
-    mant = ul << (52 - p);
-  } else {
-    const int sh = p - 52;  // 1 .. 75
-    const unsigned __int128 m = U >> sh;
-    const unsigned __int128 rem = U - (m << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    mant = (unsigned long long)m;
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      mant++;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        E++;
-      }
-    }
-  }
-  if (E < -1022 || E > 1023) {
-    *ok = false;
-    return 0.0;
-  }
-  const unsigned long long bits =
-      ((unsigned long long)neg << 63) | ((unsigned long long)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
-
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... (tile = (batch, row
+// tile, column tile), column tile fastest).  Warp 0 (one lane) copies K
+// blocks into the ring, running ahead into the next tile; warp 1 (one lane)
+// issues the MMAs of a tile once the epilogue has emptied TMEM; warps 2 .. 9
+// are the epilogue: they read the groups of a finished tile out of TMEM,
+// fold them into two exact integers per output, release TMEM (so the next
+// tile's MMAs start) and only then round, add beta C and store.
 template <int NS, int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozgemm_kernel(const __grid_constant__ OzGemm P, const __nv_bfloat16* __restrict__ QA,
                   const __nv_bfloat16* __restrict__ QB, int kblocks) {
   using Cfg = OzCfg<NS, BN>;
-  const int b = blockIdx.z;
-  if (P.active != nullptr && P.active[b] <= P.active_iter) return;  // whole CTA, before any setup
+  constexpr int NCH = (BN / 8 + 1) / 2;  // 8-column chunks per epilogue thread
+  static_assert(BN % 16 == 0 && 16 * (NCH - 1) + 8 < BN, "both halves take NCH whole chunks");
   extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[OZ_NSTAGE], empty_bar[OZ_NSTAGE], acc_bar;
+  __shared__ __align__(8) uint64_t full_bar[OZ_NSTAGE], empty_bar[OZ_NSTAGE], acc_bar, tfree_bar, done_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int give_up;
+  __shared__ volatile int give_up;
+  __shared__ int issued_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * OZ_TBM;
+  const int NT = (P.N + BN - 1) / BN, MT = (P.M + OZ_TBM - 1) / OZ_TBM;
+  const int tiles = NT * MT * P.batch;
   const int nk = kblocks;
-  // this CTA's K blocks of A (tile blockIdx.y) and of B (tile blockIdx.x)
-  const uint8_t* srcA =
-      (const uint8_t*)QA + ((long long)b * gridDim.y + blockIdx.y) * (long long)kblocks * Cfg::A_BYTES;
-  const uint8_t* srcB =
-      (const uint8_t*)QB + ((long long)b * gridDim.x + blockIdx.x) * (long long)kblocks * Cfg::B_BYTES;
+  auto tile_of = [&](int t, int& b, int& mt, int& nt) {
+    nt = t % NT;
+    mt = (t / NT) % MT;
+    b = t / (NT * MT);
+  };
+  auto skipped = [&](int b) { return P.active != nullptr && P.active[b] <= P.active_iter; };
 
   if (tid == 0) {
     for (int s = 0; s < OZ_NSTAGE; s++) {
@@ -200,8 +202,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&empty_bar[s])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&acc_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(oz_su32(&tfree_bar)));  // one arrival per epilogue warp
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(&done_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     give_up = 0;
+    issued_s = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_su32(&tmem_base)),
@@ -213,138 +218,178 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tacc = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // producer: the A and B blocks of each K block, one bulk copy each
-    for (int kb = 0; kb < nk; kb++) {
-      const int s = kb % OZ_NSTAGE;
-      if (kb >= OZ_NSTAGE && !oz_wait(oz_su32(&empty_bar[s]), ((kb - OZ_NSTAGE) / OZ_NSTAGE) & 1)) {
-        atomicOr(P.err, ERR_TIMEOUT);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: K blocks of this CTA's tiles in order, it = running block count
+      int it = 0;
+      for (int t = blockIdx.x; t < tiles && !give_up; t += gridDim.x) {
+        int b, mt, nt;
+        tile_of(t, b, mt, nt);
+        if (skipped(b)) continue;
+        const uint8_t* srcA = (const uint8_t*)QA + ((long long)b * MT + mt) * (long long)nk * Cfg::A_BYTES;
+        const uint8_t* srcB = (const uint8_t*)QB + ((long long)b * NT + nt) * (long long)nk * Cfg::B_BYTES;
+        for (int kb = 0; kb < nk; kb++, it++) {
+          const int s = it % OZ_NSTAGE;
+          if (it >= OZ_NSTAGE && !oz_wait(oz_su32(&empty_bar[s]), ((it - OZ_NSTAGE) / OZ_NSTAGE) & 1)) {
+            atomicOr(P.err, ERR_TIMEOUT);
+            give_up = 1;
+            break;
+          }
+          const uint32_t base = oz_su32(sm + s * Cfg::STAGE);
+          const uint32_t fb = oz_su32(&full_bar[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(Cfg::STAGE)
+                       : "memory");
+          oz_bulk(base, srcA + (long long)kb * Cfg::A_BYTES, Cfg::A_BYTES, fb);
+          oz_bulk(base + Cfg::A_BYTES, srcB + (long long)kb * Cfg::B_BYTES, Cfg::B_BYTES, fb);
+          issued_s = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: digit i of A against B digits 0 .. NS-1-i into group
+      // columns [i BN, NS BN); one commit to acc_bar per tile
+      int it = 0, j = 0;
+      for (int t = blockIdx.x; t < tiles && !give_up; t += gridDim.x) {
+        int b, mt, nt;
+        tile_of(t, b, mt, nt);
+        if (skipped(b)) continue;
+        if (j > 0 && !oz_wait(oz_su32(&tfree_bar), (j - 1) & 1)) {  // TMEM read out by the epilogue
+          atomicOr(P.err, ERR_TIMEOUT);
+          give_up = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool ok = true;
+        for (int kb = 0; kb < nk; kb++, it++) {
+          const int s = it % OZ_NSTAGE;
+          if (!oz_wait(oz_su32(&full_bar[s]), (it / OZ_NSTAGE) & 1)) {
+            atomicOr(P.err, ERR_TIMEOUT);
+            give_up = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t abase = oz_su32(sm + s * Cfg::STAGE);
+          const uint32_t bbase = abase + Cfg::A_BYTES;
+#pragma unroll
+          for (int i = 0; i < NS; i++) {
+            const uint64_t ad = oz_desc(abase + i * (OZ_TBM * OZ_KB * 2));
+            const int rows = (NS - i) * BN;
+#pragma unroll
+            for (int r0 = 0; r0 < rows; r0 += Cfg::NMAX) {
+              const int nr = rows - r0 < Cfg::NMAX ? rows - r0 : Cfg::NMAX;
+              const uint32_t acc = (kb > 0 || i > 0) ? 1u : 0u;
+              oz_mma(tacc + i * BN + r0, ad, oz_desc(bbase + r0 * (OZ_KB * 2)), oz_idesc(nr), acc);
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           oz_su32(&empty_bar[s]))
+                       : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         oz_su32(&acc_bar))
+                     : "memory");
+        j++;
+      }
+      // every MMA issued so far complete before TMEM is released at exit
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       oz_su32(&done_bar))
+                   : "memory");
+    }
+  } else {
+    // epilogue warps 2 .. 9: TMEM lane quadrant warp % 4, column half (warp - 2) / 4
+    static_assert(NS == 9, "the group split below is for nine groups");
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const bool unit = P.alpha == 1.0 || P.alpha == -1.0;
+    const unsigned long long sgn = P.alpha < 0.0 ? (1ull << 63) : 0ull;
+    const int bmode = P.beta == 0.0 ? 0 : (P.beta == 1.0 ? 1 : 2);
+    int j = 0;
+    for (int t = blockIdx.x; t < tiles && !give_up; t += gridDim.x) {
+      int b, mt, nt;
+      tile_of(t, b, mt, nt);
+      if (skipped(b)) continue;
+      const int n0 = nt * BN, r = mt * OZ_TBM + quad * 32 + lane;
+      const int ea = r < P.M ? __ldg(P.EA + (long long)b * P.M + r) : OZ_ZERO_EXP;
+      // every lane waits; the verdict is made warp-uniform (the TMEM loads
+      // below need the whole warp)
+      if (!__all_sync(0xffffffffu, oz_wait(oz_su32(&acc_bar), j & 1) ? 1 : 0)) {
+        if (lane == 0) atomicOr(P.err, ERR_TIMEOUT);
         give_up = 1;
         break;
       }
-      const uint32_t base = oz_su32(sm + s * Cfg::STAGE);
-      const uint32_t fb = oz_su32(&full_bar[s]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(Cfg::STAGE) : "memory");
-      oz_bulk(base, srcA + (long long)kb * Cfg::A_BYTES, Cfg::A_BYTES, fb);
-      oz_bulk(base + Cfg::A_BYTES, srcB + (long long)kb * Cfg::B_BYTES, Cfg::B_BYTES, fb);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: digit i of A (0-based) against B digits 0 .. NS-1-i into
-    // group columns [i BN, NS BN)
-    bool ok = true;
-    for (int kb = 0; kb < nk; kb++) {
-      const int s = kb % OZ_NSTAGE;
-      if (!oz_wait(oz_su32(&full_bar[s]), (kb / OZ_NSTAGE) & 1)) {
-        atomicOr(P.err, ERR_TIMEOUT);
-        ok = false;
-        break;
-      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t abase = oz_su32(sm + s * Cfg::STAGE);
-      const uint32_t bbase = abase + Cfg::A_BYTES;
+      // the product is 2^(ea + eb - 12) sum_g G_g 2^(-6 g) (G_g exact
+      // integers below 2^24): H = groups 2 .. 6 (below 2^49) and L = groups
+      // 7 .. 10 (below 2^43), both exact
+      long long Hs[NCH][8], Ls[NCH][8];
 #pragma unroll
-      for (int i = 0; i < NS; i++) {
-        const uint64_t ad = oz_desc(abase + i * (OZ_TBM * OZ_KB * 2));
-        const int rows = (NS - i) * BN;  // stacked B rows of digits 0 .. NS-1-i
+      for (int h = 0; h < NCH; h++) {
+        const int c0 = half * 8 + 16 * h;
+        float v[NS * 8];
+        oz_ld8x9(tacc + ((uint32_t)(quad * 32) << 16) + c0, BN, v);
 #pragma unroll
-        for (int r0 = 0; r0 < rows; r0 += Cfg::NMAX) {
-          const int nr = rows - r0 < Cfg::NMAX ? rows - r0 : Cfg::NMAX;
-          const uint32_t acc = (kb > 0 || i > 0) ? 1u : 0u;
-          oz_mma(tacc + i * BN + r0, ad, oz_desc(bbase + r0 * (OZ_KB * 2)), oz_idesc(nr), acc);
+        for (int jj = 0; jj < 8; jj++) {
+          int q[NS];
+#pragma unroll
+          for (int g = 0; g < NS; g++) q[g] = __float2int_rn(v[g * 8 + jj]);
+          Hs[h][jj] = ((((long long)(q[0] * 64 + q[1]) * 64 + q[2]) * 64 + q[3]) * 64) + q[4];
+          Ls[h][jj] = ((long long)(q[5] * 64 + q[6]) * 64 + q[7]) * 64 + q[8];
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       oz_su32(&empty_bar[s]))
-                   : "memory");
-    }
-    if (!ok) give_up = 1;
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     oz_su32(&acc_bar))
-                 : "memory");
-  }
-  __syncwarp();
-  // while the MMAs run: this thread's exponents of B's columns and, for
-  // beta != 0, its entries of C (row r, the 8-column chunks of its half),
-  // all loads in flight at once
-  constexpr int NCH = (BN / 8 + 1) / 2;  // chunks per half
-  const int quad = warp & 3, half = warp >> 2;
-  const int r = m0 + quad * 32 + lane;
-  int ebv[NCH][8];
-  double cpre[NCH][8];
-#pragma unroll
-  for (int h = 0; h < NCH; h++) {
-    const int c0 = half * 8 + 16 * h;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int c = n0 + c0 + j;
-      const bool in = c0 < BN && c < P.N;
-      ebv[h][j] = in ? __ldg(P.EB + (long long)b * P.N + c) : 0;
-      cpre[h][j] = (in && r < P.M && P.beta != 0.0) ? P.C[(long long)b * P.sC + (long long)r * P.ldc + c] : 0.0;
-    }
-  }
-  const bool have = oz_wait(oz_su32(&acc_bar), 0);
-  if (!have && tid == 0) atomicOr(P.err, ERR_TIMEOUT);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool good = __syncthreads_and(have ? 1 : 0) && !give_up;
-  if (!good && tid == 0) {
-    // copies may still be in flight after a give-up: wait (bounded) for the
-    // last use of each stage before the shared memory is released
-    for (int s = 0; s < OZ_NSTAGE; s++) {
-      const int uses = (nk - s + OZ_NSTAGE - 1) / OZ_NSTAGE;
-      if (uses > 0) oz_wait(oz_su32(&full_bar[s]), (uses - 1) & 1);
-    }
-  }
-  if (good) {
-    // warp w: TMEM lanes 32 (w % 4) .. (its rows), 8-column chunks
-    // half w / 4, half w / 4 + 2, ...
-    const int ea = r < P.M ? P.EA[(long long)b * P.M + r] : OZ_ZERO_EXP;
-    double* crow = P.C + (long long)b * P.sC + (long long)r * P.ldc;
-#pragma unroll
-    for (int h = 0; h < NCH; h++) {
-      const int c0 = half * 8 + 16 * h;
-      if (c0 >= BN) break;
-      // groups 2 .. 5 in hi (units 2^-30), groups 6 .. NS+1 in lo: exact
-      // integers below 2^43 and 2^49
-      long long hi[8], lo[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++) hi[j] = lo[j] = 0;
-#pragma unroll
-      for (int g = 0; g < NS; g++) {
-        float v[8];
-        oz_ld8(tacc + ((uint32_t)(quad * 32) << 16) + g * BN + c0, v);
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const long long q = (long long)__float2int_rn(v[j]);
-          if (g < 4)
-            hi[j] = hi[j] * (1 << OZ_BETA) + q;
-          else
-            lo[j] = lo[j] * (1 << OZ_BETA) + q;
-        }
-      }
+      // TMEM free for the next tile's MMAs
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(&tfree_bar)) : "memory");
+      j++;
       if (r < P.M) {
-        static_assert(NS == 9, "the integer rounding takes lo in units of 2^-30 of hi");
-        constexpr int LO_SHIFT = (NS - 4) * OZ_BETA;  // lo's unit relative to hi's
-        const bool unit = P.alpha == 1.0 || P.alpha == -1.0;
+        // C element (r, c) at crow[c * cstep]: row-major, or transposed
+        // (consecutive rows of a warp then hit consecutive addresses)
+        double* crow = P.C + (long long)b * P.sC + (P.transC ? (long long)r : (long long)r * P.ldc);
+        const long long cstep = P.transC ? P.ldc : 1;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const int c = n0 + c0 + j;
-          if (c >= P.N) break;
-          const int eb = ebv[h][j];
-          // value = (hi 2^30 + lo) 2^(ea + eb - 60): one rounding to FP64
-          bool ok = false;
-          double v = unit ? oz_round(hi[j], lo[j], ea + eb - 2 * LO_SHIFT, &ok) : 0.0;
-          if (ok) {
-            if (P.alpha < 0.0) v = -v;
-          } else {
-            const double u = fma((double)lo[j], oz_pow2(-LO_SHIFT), (double)hi[j]);
-            v = P.alpha * (u * oz_pow2(ea + eb - 5 * OZ_BETA));
+        for (int h = 0; h < NCH; h++) {
+          const int c0 = half * 8 + 16 * h;
+          double cold[8];
+          int ebv[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; jj++) {
+            const int c = n0 + c0 + jj;
+            cold[jj] = (bmode != 0 && c < P.N) ? crow[c * cstep] : 0.0;
+            ebv[jj] = c < P.N ? __ldg(P.EB + (long long)b * P.N + c) : 0;
           }
-          if (P.beta == 1.0)
-            v += cpre[h][j];
-          else if (P.beta != 0.0)
-            v = fma(P.beta, cpre[h][j], v);
-          crow[c] = v;
+#pragma unroll
+          for (int jj = 0; jj < 8; jj++) {
+            const int c = n0 + c0 + jj;
+            if (c >= P.N) break;
+            const int E = ea + ebv[jj];
+            double hd, ld, out;
+            if (unit && oz_i2d(Hs[h][jj], E - 36, sgn, &hd) && oz_i2d(Ls[h][jj], E - 60, sgn, &ld)) {
+              out = hd + ld;  // the one rounding
+            } else {
+              const double u = fma((double)Ls[h][jj], oz_pow2(-24), (double)Hs[h][jj]);
+              out = P.alpha * (u * oz_pow2(E - 36));
+            }
+            if (bmode == 1)
+              out += cold[jj];
+            else if (bmode == 2)
+              out = fma(P.beta, cold[jj], out);
+            crow[c * cstep] = out;
+          }
         }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // MMAs complete (bounded) and, after a give-up, the copies in flight
+    if (!oz_wait(oz_su32(&done_bar), 0)) atomicOr(P.err, ERR_TIMEOUT);
+    if (give_up) {
+      const int issued = issued_s;
+      for (int s = 0; s < OZ_NSTAGE && s < issued; s++) {
+        const int last = s + (issued - 1 - s) / OZ_NSTAGE * OZ_NSTAGE;  // the last block copied into stage s
+        oz_wait(oz_su32(&full_bar[s]), (last / OZ_NSTAGE) & 1);
       }
     }
   }
@@ -418,44 +463,70 @@ __global__ void oz_exp_rcontig_kernel(int R, int K, int batch, const double* __r
   }
 }
 
-// Digits of x against exponent e: x 2^(62 - e) in 64-bit fixed point
-// (truncated below 2^(e - 62)), then NS signed base-2^BETA digits by
-// rounding from the top.
-template <int NS>
-__device__ __forceinline__ void oz_digits(double x, int e, int* d) {
-  long long F = 0;
+// Fixed-point form of x against exponent e: F = x 2^(62 - e), |F| < 2^62,
+// truncated below 2^(e - 62); 0 for x = 0 or a zero row.
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
-  if (mag != 0 && e != OZ_ZERO_EXP) {
-    const int ex = (int)(mag >> 52);
-    const unsigned long long m = ex == 0 ? (mag & 0xFFFFFFFFFFFFFull) : ((mag & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    const int sh = (ex == 0 ? 1 : ex) - 1075 + 62 - e;  // x = m 2^(ex - 1075); F = m 2^sh
-    unsigned long long f;
-    if (sh >= 0)
-      f = m << sh;  // < 2^62 because |x| < 2^e
-    else
-      f = sh > -64 ? (m >> (-sh)) : 0ull;
-    F = (bits >> 63) ? -(long long)f : (long long)f;
-  }
-#pragma unroll
-  for (int i = 0; i < NS; i++) {
-    const int s = 62 - (i + 1) * OZ_BETA;
-    const long long q = (F + (1ll << (s - 1))) >> s;  // round half up
-    d[i] = (int)q;
-    F -= q * (1ll << s);
-  }
+  if (mag == 0 || e == OZ_ZERO_EXP) return 0;
+  const int ex = (int)(mag >> 52);
+  const unsigned long long m = ex == 0 ? (mag & 0xFFFFFFFFFFFFFull) : ((mag & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int sh = (ex == 0 ? 1 : ex) - 1075 + 62 - e;  // x = m 2^(ex - 1075); F = m 2^sh
+  unsigned long long f;
+  if (sh >= 0)
+    f = m << sh;  // < 2^62 because |x| < 2^e
+  else
+    f = sh > -64 ? (m >> (-sh)) : 0ull;
+  return (bits >> 63) ? -(long long)f : (long long)f;
+}
+
+// The NS = 9 signed base-64 digits of F (digit i at bit 56 - 6 i), as BF16
+// bit patterns: with the balancing offsets sum_i 32 2^(56 - 6 i) and half of
+// the last digit's unit added, digit i >= 1 is its 6-bit field minus 32
+// (in [-32, 31]) and digit 0 everything above minus 32 (in [-64, 64]); the
+// remainder F - sum_i d_i 2^(56 - 6 i) lies in [-128, 127].  A small
+// integer d becomes a float through the 2^23 magic number (exact), and its
+// BF16 pattern is the float's upper half (at most seven significant bits).
+__device__ __forceinline__ uint32_t oz_bf16_of(int d) {
+  const float f = __int_as_float(0x4B000000 | (d + 0x400000)) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+__host__ __device__ constexpr long long oz_offsets() {
+  long long c = 1ll << (62 - 9 * OZ_BETA - 1);
+  for (int i = 0; i < 9; i++) c += 1ll << (62 - (i + 1) * OZ_BETA + OZ_BETA - 1);
+  return c;
+}
+static_assert(oz_offsets() == 0x2082082082082080ll, "digit offsets");
+
+__device__ __forceinline__ void oz_digit_bits(long long F, uint32_t* h) {
+  constexpr long long CR = oz_offsets();  // sum_i 2^(61 - 6 i) + 2^7
+  const long long G = F + CR;
+  const int hi = (int)(G >> 32);
+  const unsigned lo = (unsigned)G;
+  h[0] = oz_bf16_of((hi >> 24) - 32);
+  h[1] = oz_bf16_of((int)((hi >> 18) & 63) - 32);
+  h[2] = oz_bf16_of((int)((hi >> 12) & 63) - 32);
+  h[3] = oz_bf16_of((int)((hi >> 6) & 63) - 32);
+  h[4] = oz_bf16_of((int)(hi & 63) - 32);
+  h[5] = oz_bf16_of((int)((lo >> 26) & 63) - 32);
+  h[6] = oz_bf16_of((int)((lo >> 20) & 63) - 32);
+  h[7] = oz_bf16_of((int)((lo >> 14) & 63) - 32);
+  h[8] = oz_bf16_of((int)((lo >> 8) & 63) - 32);
 }
 
 // Digit planes of an operand in the tile-blocked layout (see the head of
 // the file): a block of 32 rows x 32 K is read through shared memory (along
-// whichever of r and k is contiguous) and written in address order, 64
-// consecutive elements (one core matrix) per half warp.  Rows up to the
+// whichever of r and k is contiguous) and written in address order, two
+// consecutive elements per thread and plane (one 4-byte store), 64
+// consecutive elements (one core matrix) per 32 threads.  Rows up to the
 // padded tile count and K up to the padded block count are written, zero
 // where outside the operand.
 template <int NS>
 __global__ void oz_slice_kernel(int R, int K, const double* __restrict__ X, long long sr, long long sk, long long sb,
                                 const int* __restrict__ E, __nv_bfloat16* __restrict__ Q, int tile_rows, int ntiles,
                                 int kblocks, const int* __restrict__ active, int active_iter) {
+  static_assert(NS == 9, "nine digits per value");
   __shared__ double tile[32][33];
   const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32, b = blockIdx.z;
   if (oz_skip(active, active_iter, b)) return;
@@ -475,20 +546,23 @@ __global__ void oz_slice_kernel(int R, int K, const double* __restrict__ X, long
   __syncthreads();
   const int rpad = ntiles * tile_rows, kpad = kblocks * OZ_KB;
   const long long plane = (long long)tile_rows * OZ_KB;  // elements of one plane of one block
-  for (int e = tid; e < 1024; e += 256) {
-    // address order: k8, r8, K half, row group, K block
+  for (int p = tid; p < 512; p += 256) {
+    // element pairs in address order: k8 (even), r8, K half, row group, K block
+    const int e = 2 * p;
     const int k8 = e & 7, r8 = (e >> 3) & 7, kh = (e >> 6) & 1, rgl = (e >> 7) & 3, kbl = e >> 9;
     const int rr = rgl * 8 + r8, kk = kbl * 16 + kh * 8 + k8;
     const int r = r0 + rr, k = k0 + kk;
-    if (r >= rpad || k >= kpad) continue;
-    int d[NS];
-    oz_digits<NS>(tile[rr][kk], r < R ? E[(long long)b * R + r] : OZ_ZERO_EXP, d);
+    if (r >= rpad || k >= kpad) continue;  // kpad is a multiple of 16: the pair is whole
+    const int er = r < R ? E[(long long)b * R + r] : OZ_ZERO_EXP;
+    uint32_t h0[NS], h1[NS];
+    oz_digit_bits(oz_fixed(tile[rr][kk], er), h0);
+    oz_digit_bits(oz_fixed(tile[rr][kk + 1], er), h1);
     const int t = r / tile_rows, rt = r - t * tile_rows;
     const int kb = k / OZ_KB;
-    __nv_bfloat16* q = Q + (((long long)b * ntiles + t) * kblocks + kb) * NS * plane +
-                       ((rt >> 3) * 2 + kh) * 64 + r8 * 8 + k8;
+    uint32_t* q = (uint32_t*)(Q + (((long long)b * ntiles + t) * kblocks + kb) * NS * plane +
+                              ((rt >> 3) * 2 + kh) * 64 + r8 * 8 + k8);
 #pragma unroll
-    for (int i = 0; i < NS; i++) q[i * plane] = __int2bfloat16_rn(d[i]);
+    for (int i = 0; i < NS; i++) q[i * plane / 2] = h0[i] | (h1[i] << 16);
   }
 }
 
@@ -547,46 +621,59 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
 
 namespace {
 template <int BN>
-cudaError_t oz_launch(const OzSliced& A, const OzSliced& B, OzGemm p, cudaStream_t st) {
+cudaError_t oz_launch(const OzSliced& A, const OzSliced& B, OzGemm p, int sm_count, cudaStream_t st, cudaEvent_t ev0,
+                      cudaEvent_t ev1) {
   constexpr int NS = kOzSlices;
   using Cfg = OzCfg<NS, BN>;
   p.EA = A.E;
   p.EB = B.E;
   cudaError_t e = set_smem_once((const void*)ozgemm_kernel<NS, BN>, Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid(oz_tiles(p.N, BN), oz_tiles(p.M, OZ_TBM), p.batch);
+  const long long tiles = (long long)oz_tiles(p.N, BN) * oz_tiles(p.M, OZ_TBM) * p.batch;
+  const int grid = (int)std::min<long long>(tiles, sm_count > 0 ? sm_count : 1);
+  if (ev0 != nullptr) {
+    e = cudaEventRecord(ev0, st);
+    if (e != cudaSuccess) return e;
+  }
   count_launch();
   ozgemm_kernel<NS, BN><<<grid, OZ_THREADS, Cfg::SMEM, st>>>(p, A.Q, B.Q, oz_kblocks(p.K));
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && ev1 != nullptr) e = cudaEventRecord(ev1, st);
+  return e;
 }
 }  // namespace
 
-cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, cudaStream_t st) {
+cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, int sm_count, cudaStream_t st,
+                        cudaEvent_t ev0, cudaEvent_t ev1) {
   if (p.M <= 0 || p.N <= 0 || p.batch <= 0) return cudaSuccess;
   if (A.tile_rows != OZ_TBM || A.rows != p.M || B.rows != p.N || A.K != p.K || B.K != p.K || A.batch != p.batch ||
       B.batch != p.batch || p.K > kOzMaxK)
     return cudaErrorInvalidValue;
-  if (B.tile_rows == kOzBN) return oz_launch<kOzBN>(A, B, p, st);
-  if (B.tile_rows == kOzBNSmall) return oz_launch<kOzBNSmall>(A, B, p, st);
+  if (B.tile_rows == kOzBN) return oz_launch<kOzBN>(A, B, p, sm_count, st, ev0, ev1);
+  if (B.tile_rows == kOzBNMid) return oz_launch<kOzBNMid>(A, B, p, sm_count, st, ev0, ev1);
+  if (B.tile_rows == kOzBNSmall) return oz_launch<kOzBNSmall>(A, B, p, sm_count, st, ev0, ev1);
   return cudaErrorInvalidValue;
 }
 
+int oz_bn_for(int N) { return N <= 16 ? kOzBNSmall : (N <= 64 ? kOzBNMid : kOzBN); }
+
 size_t oz_scratch_bytes(int M, int N, int K, int batch) {
-  return oz_sliced_bytes(M, K, batch, OZ_TBM) + oz_sliced_bytes(N, K, batch, kOzBN);
+  return oz_sliced_bytes(M, K, batch, OZ_TBM) + oz_sliced_bytes(N, K, batch, oz_bn_for(N));
 }
 
-cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st) {
-  (void)sm_count;
+cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st,
+                       cudaEvent_t ev0, cudaEvent_t ev1) {
   if (p.M <= 0 || p.N <= 0 || p.batch <= 0) return cudaSuccess;
   if (p.K <= 0 || p.K > kOzMaxK) return cudaErrorInvalidValue;
   if (scratch_bytes < oz_scratch_bytes(p.M, p.N, p.K, p.batch)) return cudaErrorInvalidValue;
   const OzSliced A = oz_carve(scratch, p.M, p.K, p.batch, OZ_TBM);
-  const OzSliced B = oz_carve((uint8_t*)scratch + oz_sliced_bytes(p.M, p.K, p.batch, OZ_TBM), p.N, p.K, p.batch, kOzBN);
+  const OzSliced B =
+      oz_carve((uint8_t*)scratch + oz_sliced_bytes(p.M, p.K, p.batch, OZ_TBM), p.N, p.K, p.batch, oz_bn_for(p.N));
   // A's rows; B's columns (B element (k, c) is row c, position k of B^T)
   cudaError_t e = oz_slice(p.A, p.a_sm, p.a_sk, p.sA, A, p.active, p.active_iter, st);
   if (e == cudaSuccess) e = oz_slice(p.B, p.b_sn, p.b_sk, p.sB, B, p.active, p.active_iter, st);
   if (e != cudaSuccess) return e;
-  return oz_multiply(A, B, p, st);
+  return oz_multiply(A, B, p, sm_count, st, ev0, ev1);
 }
 
 }  // namespace lb

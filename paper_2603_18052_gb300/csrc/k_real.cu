@@ -80,6 +80,19 @@ __global__ void real_lincomb3_kernel(long long total, const T* __restrict__ X0, 
     Z[e] = c0 * X0[e] + (c1 * X1[e] + c2 * X2[e]);
 }
 
+// Z = c0 X0 + c1 X1 + c2 X2 + g I (n x n per slice, FP64)
+__global__ void real_lincomb3i_kernel(int n, long long total, const double* __restrict__ X0,
+                                      const double* __restrict__ X1, const double* __restrict__ X2, double c0,
+                                      double c1, double c2, double g, double* __restrict__ Z) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long o = e % nn;
+    const double v = c0 * X0[e] + (c1 * X1[e] + c2 * X2[e]);
+    Z[e] = (o / n == o % n) ? v + g : v;
+  }
+}
+
 // dst (FP32) = src - shift I  (n x n per slice)
 __global__ void real_to_f32_kernel(int n, long long total, const double* __restrict__ src, double shift,
                                    float* __restrict__ dst) {
@@ -302,6 +315,14 @@ cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, cons
 }
 template cudaError_t launch_real_lincomb3<double>(long long, const double*, const double*, const double*, double,
                                                   double, double, double*, int, cudaStream_t);
+
+cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
+                                  double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st) {
+  const long long total = (long long)n * n * S;
+  count_launch();
+  real_lincomb3i_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, total, X0, X1, X2, c0, c1, c2, g, Z);
+  return cudaGetLastError();
+}
 template cudaError_t launch_real_lincomb3<float>(long long, const float*, const float*, const float*, double, double,
                                                  double, float*, int, cudaStream_t);
 

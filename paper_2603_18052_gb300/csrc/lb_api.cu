@@ -49,9 +49,47 @@ cudaError_t set_smem_once(const void* kernel, size_t bytes) {
 
 namespace {
 cudaError_t accumulate_slot(lb_ctx* c, int r);
+
+// fold every recorded sliced-product event pair into the totals (waits for them)
+cudaError_t accumulate_kernels(lb_ctx* c) {
+  for (int r = 0; r < lb_ctx::kKRing; r++) {
+    if (!c->kern_used[r]) continue;
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(c->ev_kern[r][1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev_kern[r][0], c->ev_kern[r][1]);
+    if (e != cudaSuccess) return e;
+    c->kern_ms += ms;
+    c->kern_fl += c->kern_flops[r];
+    c->kern_launches++;
+    c->kern_used[r] = 0;
+  }
+  return cudaSuccess;
+}
 }
 
 namespace lb {
+cudaError_t kernel_events(lb_ctx* c, double flops, cudaEvent_t* ev0, cudaEvent_t* ev1) {
+  *ev0 = *ev1 = nullptr;
+  if (!c->timing) return cudaSuccess;
+  const int r = c->kern_next;
+  c->kern_next = (r + 1) % lb_ctx::kKRing;
+  if (c->kern_used[r]) {  // the ring has wrapped: fold the oldest pair in (waits for it)
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(c->ev_kern[r][1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev_kern[r][0], c->ev_kern[r][1]);
+    if (e != cudaSuccess) return e;
+    c->kern_ms += ms;
+    c->kern_fl += c->kern_flops[r];
+    c->kern_launches++;
+    c->kern_used[r] = 0;
+  }
+  c->kern_used[r] = 1;
+  c->kern_flops[r] = flops;
+  *ev0 = c->ev_kern[r][0];
+  *ev1 = c->ev_kern[r][1];
+  return cudaSuccess;
+}
+
 lb_status stage_events_begin(lb_ctx* c, cudaStream_t st, cudaEvent_t** ev_out) {
   *ev_out = nullptr;
   if (!c->timing) return LB_OK;
@@ -251,6 +289,14 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
         return LB_ENOMEM;
       }
     }
+  for (int r = 0; r < lb_ctx::kKRing; r++)
+    for (int i = 0; i < 2; i++) {
+      if (cudaEventCreate(&c->ev_kern[r][i]) != cudaSuccess) {
+        cudaGetLastError();
+        lb_destroy(c);
+        return LB_ENOMEM;
+      }
+    }
   *out = c;
   return LB_OK;
 }
@@ -264,6 +310,9 @@ lb_status lb_destroy(lb_ctx* c) {
   for (int r = 0; r < lb_ctx::kRing; r++)
     for (int i = 0; i < 6; i++)
       if (c->ev_stage[r][i]) cudaEventDestroy(c->ev_stage[r][i]);
+  for (int r = 0; r < lb_ctx::kKRing; r++)
+    for (int i = 0; i < 2; i++)
+      if (c->ev_kern[r][i]) cudaEventDestroy(c->ev_kern[r][i]);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->scmax_host) cudaFreeHost(c->scmax_host);
   if (c->ws) cudaFree(c->ws);
@@ -280,9 +329,22 @@ lb_status lb_set_stage_timing(lb_ctx* c, int enable) {
   DeviceGuard g(c->device);
   for (int r = 0; r < lb_ctx::kRing; r++)
     if (accumulate_slot(c, r) != cudaSuccess) return LB_ECUDA;
+  if (accumulate_kernels(c) != cudaSuccess) return LB_ECUDA;
   c->timing = enable ? 1 : 0;
   for (int i = 0; i < 5; i++) c->stage_ms[i] = 0.0;
   c->stage_chunks = 0;
+  c->kern_ms = c->kern_fl = 0.0;
+  c->kern_launches = 0;
+  return LB_OK;
+}
+
+lb_status lb_kernel_times(lb_ctx* c, double* ms_out, double* flops_out, long long* launches_out) {
+  if (c == nullptr || ms_out == nullptr) return LB_EINVAL;
+  DeviceGuard g(c->device);
+  if (accumulate_kernels(c) != cudaSuccess) return LB_ECUDA;
+  *ms_out = c->kern_ms;
+  if (flops_out) *flops_out = c->kern_fl;
+  if (launches_out) *launches_out = c->kern_launches;
   return LB_OK;
 }
 

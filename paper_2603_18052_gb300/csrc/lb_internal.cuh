@@ -88,6 +88,15 @@ struct lb_ctx {
   int ring_next = 0;
   double stage_ms[5] = {0, 0, 0, 0, 0};
   long long stage_chunks = 0;
+  // --- with the stage timers: events around every sliced-product launch
+  // without a batch mask (a ring; kern_flops: digit-product FLOPs) ---
+  static constexpr int kKRing = 4096;
+  cudaEvent_t ev_kern[kKRing][2] = {};
+  double kern_flops[kKRing] = {};
+  int kern_used[kKRing] = {};
+  int kern_next = 0;
+  double kern_ms = 0.0, kern_fl = 0.0;
+  long long kern_launches = 0;
   // --- propagator build, per slice (stride max_n^2 complex) ---
   lb::z64 *A = nullptr, *A2 = nullptr, *A4 = nullptr, *A6 = nullptr, *Z1 = nullptr, *Z2 = nullptr;
   lb::z64 *V = nullptr, *W = nullptr, *Mx = nullptr;
@@ -296,6 +305,9 @@ cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const doub
 template <typename T>
 cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, const T* X2, double c0, double c1,
                                  double c2, T* Z, int sm_count, cudaStream_t st);
+// Z = c0 X0 + c1 X1 + c2 X2 + g I for S real n x n matrices (FP64)
+cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
+                                  double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st);
 // The Pade coefficients b_0 .. b_13 by value.
 struct PadeCoef {
   double b[14];
@@ -468,11 +480,13 @@ cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
 // consumed into slices before C is written).  K <= kOzMaxK.
 constexpr int kOzSlices = 9;    // base-64 digits per operand row / column (54 bits)
 constexpr int kOzMaxK = 1488;   // every group sum exact in FP32 up to this K
+constexpr int kOzPairs = kOzSlices * (kOzSlices + 1) / 2;  // digit products per multiply-add (45)
 struct OzGemm {
   int M = 0, N = 0, K = 0, batch = 1;
   const double* A = nullptr; long long a_sm = 0, a_sk = 1, sA = 0;
   const double* B = nullptr; long long b_sk = 0, b_sn = 1, sB = 0;
   double* C = nullptr; long long ldc = 0, sC = 0;
+  int transC = 0;  // C element (m, n) at C[b sC + n ldc + m] instead of C[b sC + m ldc + n]
   double alpha = 1.0, beta = 0.0;
   // optional batch mask: batch element b is skipped when active[b] <= active_iter
   const int* active = nullptr; int active_iter = 0;
@@ -481,6 +495,7 @@ struct OzGemm {
 };
 constexpr int kOzBN = 48;       // columns of C per CTA (B tile rows)
 constexpr int kOzBNSmall = 16;  // the narrow tile, for products with few output tiles
+constexpr int kOzBNMid = 32;    // for products with 64 columns
 constexpr int kOzTileM = 128;   // rows of C per CTA (A tile rows)
 // An operand in slices: digit planes in the tile-blocked layout of
 // k_ozaki.cu (tile_rows = 128 for A, kOzBN for B) and one exponent per row.
@@ -497,10 +512,16 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
                      int active_iter, cudaStream_t st);
 // C = alpha A B + beta C from sliced A (M rows) and sliced B^T (N rows); p's
 // A, B pointers are not used
-cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, cudaStream_t st);
+cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, int sm_count, cudaStream_t st,
+                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // scratch for one call of ozgemm_f64: the slices of both operands
 size_t oz_scratch_bytes(int M, int N, int K, int batch);
-cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st);
+int oz_bn_for(int N);  // the column tile ozgemm_f64 takes for N columns
+cudaError_t ozgemm_f64(const OzGemm& p, void* scratch, size_t scratch_bytes, int sm_count, cudaStream_t st,
+                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+// events to bracket one sliced-product launch of `flops` digit-product FLOPs
+// (both null unless the context's stage timers are on)
+cudaError_t kernel_events(lb_ctx* c, double flops, cudaEvent_t* ev0, cudaEvent_t* ev1);
 // Z = c0 X0 + c1 X1 + c2 X2 (FP32) written as the two-piece planes of Z^T
 cudaError_t launch_lincomb_splitT(int n, int S, const float2* X0, const float2* X1, const float2* X2, float c0,
                                   float c1, float c2, __nv_bfloat16* dst, long long ldd, long long plane,

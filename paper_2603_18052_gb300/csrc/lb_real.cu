@@ -138,16 +138,20 @@ lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, 
 lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
 
 // The same factorisation and solve with every product sliced (the
-// LB_FP64_SLICED form), on a right-looking schedule: at block step k the
-// diagonal block (up to date with all earlier steps) is factored and
-// inverted, the block row of U and block column of L follow from the block
-// inverses, block row k of Y = L^{-1} N follows from Linv_k, and the
-// trailing matrix and the right-hand sides below the block are updated by
-// two products of K = 64.  The back substitution runs bottom up: block row
-// k of the solution is Uinv_k Y_k, and the rows above are updated by it.
-// Every product is one sliced launch over all slices.
-lb_status lu_solve_sliced_real(lb_ctx* c, int n, int S, double* Mx, double* N, double* Uf, double* Y, double* Lp,
-                               double* inv, cudaStream_t st) {
+// LB_FP64_SLICED form), on a left-looking schedule: at block step k, block
+// row k of the matrix (from the diagonal on), block column k below the
+// diagonal and block row k of the right-hand sides are brought up to date
+// with all earlier blocks in one product each (K = k0), so every entry is
+// updated once, by one long product; the diagonal block is factored and
+// inverted and the block row of U, the block column of L and block row k of
+// Y = L^{-1} N follow from the block inverses.  The back substitution is
+// left-looking too: block row k of Y takes U[k, k+1:] X[k+1:] in one
+// product, then X_k = Uinv_k Y_k.  Every product has the columns of one
+// block (64) on its short side; the products whose natural form has the
+// block's rows run transposed (the long operand as the 128-row side, C
+// written transposed).  Every product is one sliced launch over all slices.
+lb_status lu_solve_sliced_ll(lb_ctx* c, int n, int S, double* Mx, double* N, double* Uf, double* Y, double* Lp,
+                             double* inv, cudaStream_t st) {
   const long long nn = (long long)n * n;
   // 64-wide blocks from n = 128 (their inverses in `inv`, which holds
   // 2 n^2 S doubles), else the 32-wide blocks of the context's buffers
@@ -155,15 +159,17 @@ lb_status lu_solve_sliced_real(lb_ctx* c, int n, int S, double* Mx, double* N, d
   const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
   double* Linv = nb == kLuNb ? (double*)c->Linv : inv;                           // S x nb x nb
   double* Uinv = nb == kLuNb ? (double*)c->Uinv : inv + (long long)S * sLinv;  // S x nbk x nb x nb
-  // C (ld n, one per slice) = alpha A B + beta C; A(m, k) at A + m lda + k,
-  // B(k, j) at B + k ldb + j
-  auto prod = [&](int M, int Ncol, int K, const double* A, long long lda, long long sA, const double* B,
-                  long long ldb, long long sB, double* C, double alpha, double beta) -> lb_status {
+  // C = alpha A B + beta C (one per slice): A(m, k) at A + m a_sm + k a_sk,
+  // B(k, j) at B + k b_sk + j b_sn, C(m, j) at C + m n + j or, transposed,
+  // at C + j n + m
+  auto prod = [&](int M, int Ncol, int K, const double* A, long long a_sm, long long a_sk, long long sA,
+                  const double* B, long long b_sk, long long b_sn, long long sB, double* C, int trans, double alpha,
+                  double beta) -> lb_status {
     OzGemm q;
     q.M = M; q.N = Ncol; q.K = K; q.batch = S;
-    q.A = A; q.a_sm = lda; q.a_sk = 1; q.sA = sA;
-    q.B = B; q.b_sk = ldb; q.b_sn = 1; q.sB = sB;
-    q.C = C; q.ldc = n; q.sC = nn;
+    q.A = A; q.a_sm = a_sm; q.a_sk = a_sk; q.sA = sA;
+    q.B = B; q.b_sk = b_sk; q.b_sn = b_sn; q.sB = sB;
+    q.C = C; q.ldc = n; q.sC = nn; q.transC = trans;
     q.alpha = alpha;
     q.beta = beta;
     return oz_product(c, q, st);
@@ -171,35 +177,46 @@ lb_status lu_solve_sliced_real(lb_ctx* c, int n, int S, double* Mx, double* N, d
   for (int k = 0; k < nbk; k++) {
     const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, r0 = k0 + kb, rest = n - r0;
     double* Uinv_k = Uinv + (long long)k * nb * nb;
-    LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st, nb));
     lb_status r = LB_OK;
-    if (rest > 0) {
-      // U[k0:r0, r0:] = Linv_k Mx[k0:r0, r0:];  L[r0:, k0:r0] = Mx[r0:, k0:r0] Uinv_k
-      r = prod(kb, rest, kb, Linv, nb, sLinv, Mx + (long long)k0 * n + r0, n, nn, Uf + (long long)k0 * n + r0, 1.0,
-               0.0);
-      if (r == LB_OK)
-        r = prod(rest, kb, kb, Mx + (long long)r0 * n + k0, n, nn, Uinv_k, nb, sUinv, Lp + (long long)r0 * n + k0,
-                 1.0, 0.0);
-    }
-    // Y[k0:r0, :] = Linv_k N[k0:r0, :]
-    if (r == LB_OK)
-      r = prod(kb, n, kb, Linv, nb, sLinv, N + (long long)k0 * n, n, nn, Y + (long long)k0 * n, 1.0, 0.0);
-    if (r == LB_OK && rest > 0) {
-      // Mx[r0:, r0:] -= L[r0:, k0:r0] U[k0:r0, r0:];  N[r0:, :] -= L[r0:, k0:r0] Y[k0:r0, :]
-      r = prod(rest, rest, kb, Lp + (long long)r0 * n + k0, n, nn, Uf + (long long)k0 * n + r0, n, nn,
-               Mx + (long long)r0 * n + r0, -1.0, 1.0);
-      if (r == LB_OK)
-        r = prod(rest, n, kb, Lp + (long long)r0 * n + k0, n, nn, Y + (long long)k0 * n, n, nn, N + (long long)r0 * n,
+    if (k0 > 0) {
+      // Mx[k0:r0, k0:] -= L[k0:r0, :k0] U[:k0, k0:], as its transpose (rows: the n - k0 columns)
+      r = prod(n - k0, kb, k0, Uf + k0, 1, n, nn, Lp + (long long)k0 * n, 1, n, nn, Mx + (long long)k0 * n + k0, 1,
+               -1.0, 1.0);
+      // Mx[r0:, k0:r0] -= L[r0:, :k0] U[:k0, k0:r0]
+      if (r == LB_OK && rest > 0)
+        r = prod(rest, kb, k0, Lp + (long long)r0 * n, n, 1, nn, Uf + k0, n, 1, nn, Mx + (long long)r0 * n + k0, 0,
                  -1.0, 1.0);
+      // N[k0:r0, :] -= L[k0:r0, :k0] Y[:k0, :], transposed
+      if (r == LB_OK)
+        r = prod(n, kb, k0, Y, 1, n, nn, Lp + (long long)k0 * n, 1, n, nn, N + (long long)k0 * n, 1, -1.0, 1.0);
     }
+    if (r != LB_OK) return r;
+    LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st, nb));
+    if (rest > 0) {
+      // U[k0:r0, r0:] = Linv_k Mx[k0:r0, r0:], transposed
+      r = prod(rest, kb, kb, Mx + (long long)k0 * n + r0, 1, n, nn, Linv, 1, nb, sLinv, Uf + (long long)k0 * n + r0,
+               1, 1.0, 0.0);
+      // L[r0:, k0:r0] = Mx[r0:, k0:r0] Uinv_k
+      if (r == LB_OK)
+        r = prod(rest, kb, kb, Mx + (long long)r0 * n + k0, n, 1, nn, Uinv_k, nb, 1, sUinv,
+                 Lp + (long long)r0 * n + k0, 0, 1.0, 0.0);
+    }
+    // Y[k0:r0, :] = Linv_k N[k0:r0, :], transposed
+    if (r == LB_OK)
+      r = prod(n, kb, kb, N + (long long)k0 * n, 1, n, nn, Linv, 1, nb, sLinv, Y + (long long)k0 * n, 1, 1.0, 0.0);
     if (r != LB_OK) return r;
   }
   for (int k = nbk - 1; k >= 0; k--) {
-    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb;
+    const int k0 = k * nb, kb = (n - k0 < nb) ? n - k0 : nb, r0 = k0 + kb, rest = n - r0;
     double* Uinv_k = Uinv + (long long)k * nb * nb;
-    // X[k0:r0, :] = Uinv_k Y[k0:r0, :] (into N);  Y[:k0, :] -= U[:k0, k0:r0] X[k0:r0, :]
-    lb_status r = prod(kb, n, kb, Uinv_k, nb, sUinv, Y + (long long)k0 * n, n, nn, N + (long long)k0 * n, 1.0, 0.0);
-    if (r == LB_OK && k0 > 0) r = prod(k0, n, kb, Uf + k0, n, nn, N + (long long)k0 * n, n, nn, Y, -1.0, 1.0);
+    lb_status r = LB_OK;
+    // Y[k0:r0, :] -= U[k0:r0, r0:] X[r0:, :] (X in N's rows below), transposed
+    if (rest > 0)
+      r = prod(n, kb, rest, N + (long long)r0 * n, 1, n, nn, Uf + (long long)k0 * n + r0, 1, n, nn,
+               Y + (long long)k0 * n, 1, -1.0, 1.0);
+    // X[k0:r0, :] = Uinv_k Y[k0:r0, :] into N, transposed
+    if (r == LB_OK)
+      r = prod(n, kb, kb, Y + (long long)k0 * n, 1, n, nn, Uinv_k, 1, nb, sUinv, N + (long long)k0 * n, 1, 1.0, 0.0);
     if (r != LB_OK) return r;
   }
   return LB_OK;
@@ -248,10 +265,13 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
         q.M = std::min(rows, p.M - m0);
         q.A = p.A + (long long)b0 * p.sA + (long long)m0 * p.a_sm;
         q.B = p.B + (long long)b0 * p.sB;
-        q.C = p.C + (long long)b0 * p.sC + (long long)m0 * p.ldc;
+        q.C = p.C + (long long)b0 * p.sC + (p.transC ? (long long)m0 : (long long)m0 * p.ldc);
         if (p.active != nullptr) q.active = p.active + b0;
         q.err = c->err_dev;
-        LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (p.active == nullptr)
+          LB_CUDA(kernel_events(c, 2.0 * kOzPairs * q.M * (double)q.N * q.K, &e0, &e1));
+        LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st, e0, e1));
       }
     return LB_OK;
   }
@@ -263,7 +283,10 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
     q.C = p.C + (long long)b0 * p.sC;
     if (p.active != nullptr) q.active = p.active + b0;
     q.err = c->err_dev;
-    LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p.active == nullptr)
+      LB_CUDA(kernel_events(c, 2.0 * kOzPairs * q.M * (double)q.N * q.K * q.batch, &e0, &e1));
+    LB_CUDA(ozgemm_f64(q, c->oz_scratch, c->oz_bytes, c->sm_count, st, e0, e1));
   }
   return LB_OK;
 }
@@ -313,7 +336,43 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
   const long long max_nnz = (long long)(kSparseDensity * (double)nn);
   int* flagA = c->spflag;                     // A row-sparse
   int* flagA2 = c->spflag + c->max_slices;    // A^2 row-sparse
-  if (prec == LB_FP64_HERMITIAN || prec == LB_FP64_SLICED) {
+  if (prec == LB_FP64_SLICED) {
+    // the sliced form: A^2 skips A's zeros (a local generator's A is about
+    // 1 % nonzero); A^4, A^6 and the two products with A^6 are dense sliced
+    // products (V and W start from their power terms and take A^6 Z1,
+    // A^6 Z2 with beta = 1); U = A W skips A's zeros again
+    double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
+           *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
+    LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
+    RGemmProblem<double> p = rsq(n, S, Ar, Ar, A2);
+    LB_TRY(skip_product(c, p, flagA, st));
+    auto sq = [&](const double* X, const double* Y, double* Cc, double beta) {
+      OzGemm q;
+      q.M = q.N = q.K = n;
+      q.batch = S;
+      q.A = X; q.a_sm = n; q.a_sk = 1; q.sA = nn;
+      q.B = Y; q.b_sk = n; q.b_sn = 1; q.sB = nn;
+      q.C = Cc; q.ldc = n; q.sC = nn;
+      q.beta = beta;
+      return oz_product(c, q, st);
+    };
+    LB_TRY(sq(A2, A2, A4, 0.0));
+    LB_TRY(sq(A2, A4, A6, 0.0));
+    LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[12], b[10], b[8], Z1, c->sm_count, st));
+    LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
+    LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[6], b[4], b[2], b[0], V, c->sm_count, st));
+    LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[7], b[5], b[3], b[1], W, c->sm_count, st));
+    LB_TRY(sq(A6, Z1, V, 1.0));
+    LB_TRY(sq(A6, Z2, W, 1.0));
+    // U = A W:  Mx = V - U, N = V + U
+    p = rsq(n, S, Ar, W, Mx);
+    p.alpha[0] = -1.0;
+    p.O[1] = N;
+    p.nterms = 1;
+    p.X[0] = V; p.sX[0] = nn;
+    p.coef[0][0] = 1.0; p.coef[1][0] = 1.0;
+    LB_TRY(skip_product(c, p, flagA, st));
+  } else if (prec == LB_FP64_HERMITIAN) {
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
     LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
@@ -441,8 +500,8 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
   // (V - U) R = (V + U), FP64.  U, Y, L reuse A2, A4, A6.
   {
     lb_status r = prec == LB_FP64_SLICED
-                      ? lu_solve_sliced_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6,
-                                             (double*)c->Z2, st)
+                      ? lu_solve_sliced_ll(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6,
+                                           (double*)c->Z2, st)
                       : lu_solve_blocked_real(c, n, S, Mx, N, (double*)c->A2, (double*)c->A4, (double*)c->A6, st);
     if (r != LB_OK) return r;
   }
@@ -538,7 +597,9 @@ lb_status propagate_herm_large(lb_ctx* c, int n, int nslices, const z64* P, int 
           q.M = B; q.N = n; q.K = n;
           q.C = nxt; q.ldc = n;
           q.err = c->err_dev;
-          LB_CUDA(oz_multiply(Xs, oz_view(Rs, s), q, st));
+          cudaEvent_t e0 = nullptr, e1 = nullptr;
+          LB_CUDA(kernel_events(c, 2.0 * kOzPairs * B * (double)n * n, &e0, &e1));
+          LB_CUDA(oz_multiply(Xs, oz_view(Rs, s), q, c->sm_count, st, e0, e1));
         } else {
           // next[b][a] = sum_k R_s[a][k] cur[b][k]  ->  next = cur R_s^T
           RGemmProblem<double> q;

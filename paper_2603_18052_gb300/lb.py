@@ -42,6 +42,7 @@ EXPORTED = (
     "lb_autotune",
     "lb_set_stage_timing",
     "lb_stage_times",
+    "lb_kernel_times",
     "lb_assemble",
     "lb_expm_pade",
     "lb_propagate_batch",
@@ -130,6 +131,9 @@ def lib():
     L.lb_set_stage_timing.argtypes = [vp, i32]
     L.lb_stage_times.restype = i32
     L.lb_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    L.lb_kernel_times.restype = i32
+    L.lb_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_longlong)]
     L.lb_assemble.restype = i32
     L.lb_assemble.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     L.lb_expm_pade.restype = i32
@@ -284,6 +288,16 @@ def lb_set_stage_timing(ctx, enable=True):
 
 
 STAGES = ("prepare", "pade_products", "lu_solve", "squarings", "check")
+
+
+def lb_kernel_times(ctx):
+    """Summed time (ms), digit-product FLOPs and launches of the sliced
+    FP64 product kernel since the last lb_set_stage_timing."""
+    ms = ctypes.c_double(0.0)
+    fl = ctypes.c_double(0.0)
+    nl = ctypes.c_longlong(0)
+    _check(lib().lb_kernel_times(ctx.handle, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(nl)), "lb_kernel_times")
+    return ms.value, fl.value, int(nl.value)
 
 
 def lb_stage_times(ctx):

@@ -34,9 +34,12 @@ def test_metric_names_the_workload(bench):
 
 
 def test_headline_form_is_fp64(bench):
-    """The recorded value is an all-FP64 form; the reduced-precision forms
-    are reported under "mixed"."""
+    """The recorded value is an FP64 form (FP64 operands and results, the
+    dense products as exact slices on the tensor cores), the FP64-pipe form
+    is reported beside it, and the reduced-precision forms under "mixed"."""
     assert bench.HEADLINE in bench.FORMS and bench.DTYPES[bench.HEADLINE] == "f64"
-    assert bench.FORMS[bench.HEADLINE][:2] == ("fp64_hermitian", "fp64_hermitian")
+    assert bench.FORMS[bench.HEADLINE][:2] == ("fp64_sliced", "fp64_sliced")
+    assert bench.FORMS[bench.FP64_NATIVE][:2] == ("fp64_hermitian", "fp64_hermitian")
+    assert bench.DTYPES[bench.FP64_NATIVE] == "f64"
     for f in bench.MIXED_FORMS:
         assert f in bench.FORMS and bench.DTYPES[f] != "f64"
