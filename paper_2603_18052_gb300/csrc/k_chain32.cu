@@ -770,18 +770,14 @@ bool launch_chain32_persist(int n, int B, int renorm, const float* Dt, long long
   if (nsteps < 2 || tiles >= sm_count) return false;
   void (*kern)(ChainDims, int, const float*, long long, int, int, float*, float*, unsigned*, unsigned int*) =
       renorm ? chain32_persist_kernel<true, kChainTM> : chain32_persist_kernel<false, kChainTM>;
-  // the widest K split (at most two CTAs per SM, four K blocks per split)
-  // whose clusters all fit at once
-  int splits = 0, kps = 0;
-  for (int want = std::max(1, std::min({2 * sm_count / tiles, ktiles / 4, 8})); want >= 2; want--) {
-    kps = (ktiles + want - 1) / want;
-    const int sp = (ktiles + kps - 1) / kps;
-    if (sp >= 2 && tiles * sp <= 2 * sm_count && cluster_fits(kern, sp, tiles)) {
-      splits = sp;
-      break;
-    }
-  }
-  if (splits < 2) return false;
+  // the per-step launches' K split (at most two CTAs per SM, four K blocks
+  // per split), if its clusters all fit at once; a narrower split gives
+  // each CTA more of the K loop per step and was measured slower than the
+  // per-step launches with the wide split (256 states: 7.2 against 6.5 ms)
+  const int want = std::max(1, std::min({2 * sm_count / tiles, ktiles / 4, 8}));
+  const int kps = (ktiles + want - 1) / want;
+  const int splits = (ktiles + kps - 1) / kps;
+  if (splits < 2 || tiles * splits > 2 * sm_count || !cluster_fits(kern, splits, tiles)) return false;
   // whether a cooperative cluster launch of this kernel was accepted on this
   // device: tried outside stream capture only (a refused launch would end a
   // capture), remembered for captures

@@ -297,7 +297,7 @@ def test_propagate_fp32_d27_200_steps(lbm, dev):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("B,renorm", [(256, True), (37, False)])
+@pytest.mark.parametrize("B,renorm", [(64, True), (37, False)])
 def test_propagate_fp32_d27_persistent(lbm, dev, B, renorm):
     """The d = 27 FP32 chain with many steps runs as one persistent launch
     (grid barrier between steps) rather than one launch per step: 60 steps
