@@ -345,7 +345,7 @@ def mixed_instances(lb, ctx_big, dev, stream, count, trials):
         return a.elapsed_time(b)
 
     def run_all(prec, idx_small, idx_big):
-        renorm = prec not in ("fp64", "fp64_hermitian")
+        renorm = prec not in ("fp64", "fp64_hermitian", "fp64_sliced")
         if idx_small:
             lb.lb_run_instances(ctx_small, [arg[i] for i in idx_small], dt, prec=prec, renorm_trace=renorm)
         if idx_big:
@@ -357,8 +357,9 @@ def mixed_instances(lb, ctx_big, dev, stream, count, trials):
                        % (len(inst), counts[3], counts[9], counts[27], builds, ssteps)
                        + ("" if world == 1 else " (this rank's share of %d, split by cost)" % count)}
 
-    # the whole batch in one captured graph, fastest mixed form
-    form = "fp32_hermitian"
+    # the whole batch in one captured graph, in the fastest form (FP64 via
+    # exact slices)
+    form = "fp64_sliced"
     reset(range(len(inst)))
     run_all(form, small, big)  # warm-up (tables, kernels)
     torch.cuda.synchronize()
@@ -404,7 +405,7 @@ def mixed_instances(lb, ctx_big, dev, stream, count, trials):
             lb.lb_propagate_batch(ctx, P, st[i], steps_per_slice=1, prec=prec)
 
     fp = {}
-    for prec in ("fp64_hermitian", "fp64"):
+    for prec in ("fp64_sliced", "fp64_hermitian", "fp64"):
         tot_batched, tot_loop, classes = 0.0, 0.0, {}
         for d, idx in sorted(by_d.items()):
             k = min(samp[d], len(idx))
@@ -440,10 +441,12 @@ def mixed_instances(lb, ctx_big, dev, stream, count, trials):
     res["fp64_forms"] = fp
     res["speedup_fp64_hermitian_batched_vs_per_instance_fp64"] = (fp["fp64"]["per_instance_ms"]
                                                                  / fp["fp64_hermitian"]["batched_ms"])
+    res["speedup_fp64_sliced_batched_vs_per_instance_fp64"] = (fp["fp64"]["per_instance_ms"]
+                                                              / fp["fp64_sliced"]["batched_ms"])
     res["speedup_captured_%s_vs_per_instance_fp64" % form] = fp["fp64"]["per_instance_ms"] / ms
     res["note"] = ("per-instance arms: one lb_expm_pade + lb_propagate_batch call pair per instance through the "
                    "Python binding, timed with the host clock on a sample per d class and scaled by the class's "
-                   "instance count; batched FP64 at d=27 likewise on a sample (every d=27 build is FP64-LU-bound, "
+                   "instance count; batched FP64 at d=27 likewise on a sample (every d=27 build is LU-bound, "
                    "so its time is linear in the count)")
     ctx_small.close()
     return res

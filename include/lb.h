@@ -337,8 +337,9 @@ lb_status lb_grape_grad_batch(lb_ctx* ctx, int n, int K, int nslices, const lb_c
  *   prec  : precision of the Pade products and of the propagation, as in
  *           lb_expm_pade and lb_propagate_batch (for n <= 81 the reduced
  *           forms propagate in FP32 with D = P - I; the Hermitian forms build
- *           on the real coordinates, LB_FP64_HERMITIAN propagates n <= 81 in
- *           complex FP64 and n > 81 on the real coordinates,
+ *           on the real coordinates, LB_FP64_HERMITIAN and LB_FP64_SLICED
+ *           propagate n <= 81 in complex FP64 and n > 81 on the real
+ *           coordinates (LB_FP64_SLICED with sliced products),
  *           LB_FP32_HERMITIAN propagates in FP32)
  *   renorm_trace : as in lb_propagate_batch (reduced forms only)
  * Limits: n <= max_n; nslices <= max_slices per instance; for n > 81,

@@ -162,9 +162,9 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
                                       int renorm_trace, void* stream) {
   if (c == nullptr || (inst == nullptr && count > 0) || count < 0) return LB_EINVAL;
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_BF16X3 && prec != LB_FP64_HERMITIAN &&
-      prec != LB_FP32_HERMITIAN)
+      prec != LB_FP32_HERMITIAN && prec != LB_FP64_SLICED)
     return LB_EINVAL;
-  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN;
+  const bool herm = prec == LB_FP64_HERMITIAN || prec == LB_FP32_HERMITIAN || prec == LB_FP64_SLICED;
   // propagation precision: the FP32 real-coordinate build propagates in FP32
   const lb_precision pprec = prec == LB_FP32_HERMITIAN ? LB_FP32 : prec;
   long long total_slices = 0, total_items = 0;
@@ -258,8 +258,8 @@ extern "C" lb_status lb_run_instances(lb_ctx* c, const lb_instance* inst, int co
                          : expm_chunk_public(c, n, ch.S, c->Ginst, nullptr, nullptr, dt, prec, c->Pinst, nullptr, st);
       if (r != LB_OK) return r;
       if (n <= 81) {
-        // FP64 and FP64_HERMITIAN: the complex FP64 step (exact for every state)
-        const bool f32 = pprec != LB_FP64 && pprec != LB_FP64_HERMITIAN;
+        // the FP64 forms: the complex FP64 step (exact for every state)
+        const bool f32 = pprec != LB_FP64 && pprec != LB_FP64_HERMITIAN && pprec != LB_FP64_SLICED;
         const size_t smem = worklist_smem(n, 8, f32);
         if (f32) {
           LB_CUDA(set_smem_once((const void*)worklist_kernel<true>, smem));

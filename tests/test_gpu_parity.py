@@ -580,7 +580,8 @@ def _instance_set(seed, spec):
 
 
 @pytest.mark.parametrize("prec,tol,kind", [("fp64", 1e-12, "rel"), ("fp32", 2e-6, "rel"), ("bf16x3", 1e-4, "abs"),
-                                           ("fp64_hermitian", 1e-12, "rel"), ("fp32_hermitian", 2e-6, "rel")])
+                                           ("fp64_hermitian", 1e-12, "rel"), ("fp32_hermitian", 2e-6, "rel"),
+                                           ("fp64_sliced", 1e-12, "rel")])
 def test_run_instances_matches_oracle(lbm, dev, prec, tol, kind):
     """Mixed d = 3 / 9 / 27 instances in one call, with chunks that hold
     several whole instances (max_slices = 6), 1 to 64 states per instance
