@@ -93,6 +93,19 @@ __global__ void real_lincomb3i_kernel(int n, long long total, const double* __re
   }
 }
 
+// dst[s][r][c] = src[s][r][c] for an R x C block of S matrices (leading
+// dimensions and batch strides of their own)
+__global__ void real_copy_block_kernel(int R, int C, long long total, const double* __restrict__ src, long long sld,
+                                       long long ss, double* __restrict__ dst, long long dld, long long ds) {
+  const long long rc = (long long)R * C;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / rc, o = e - s * rc;
+    const int r = (int)(o / C), c = (int)(o - (o / C) * C);
+    dst[s * ds + r * dld + c] = src[s * ss + r * sld + c];
+  }
+}
+
 // dst (FP32) = src - shift I  (n x n per slice)
 __global__ void real_to_f32_kernel(int n, long long total, const double* __restrict__ src, double shift,
                                    float* __restrict__ dst) {
@@ -315,6 +328,15 @@ cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, cons
 }
 template cudaError_t launch_real_lincomb3<double>(long long, const double*, const double*, const double*, double,
                                                   double, double, double*, int, cudaStream_t);
+
+cudaError_t launch_real_copy_block(int R, int C, int S, const double* src, long long sld, long long ss, double* dst,
+                                   long long dld, long long ds, int sm_count, cudaStream_t st) {
+  const long long total = (long long)R * C * S;
+  if (total <= 0) return cudaSuccess;
+  count_launch();
+  real_copy_block_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(R, C, total, src, sld, ss, dst, dld, ds);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
                                   double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st) {

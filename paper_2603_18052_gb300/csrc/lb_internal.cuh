@@ -21,7 +21,7 @@ enum : unsigned int {
 
 constexpr int kMaxN = 729;
 constexpr int kLuNb = 32;  // LU block size
-constexpr int kLuNbSliced = 64;  // LU block size of the sliced-product schedule
+constexpr int kLuNbSliced = 128;  // LU block size of the sliced-product schedule (two 64-wide halves)
 
 typedef double2 z64;
 
@@ -305,6 +305,9 @@ cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const doub
 template <typename T>
 cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, const T* X2, double c0, double c1,
                                  double c2, T* Z, int sm_count, cudaStream_t st);
+// an R x C block of S real matrices (leading dimension, batch stride each)
+cudaError_t launch_real_copy_block(int R, int C, int S, const double* src, long long sld, long long ss, double* dst,
+                                   long long dld, long long ds, int sm_count, cudaStream_t st);
 // Z = c0 X0 + c1 X1 + c2 X2 + g I for S real n x n matrices (FP64)
 cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
                                   double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st);

@@ -137,6 +137,12 @@ lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, 
 // batch elements that fit the context's scratch (defined below).
 lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
 
+#define LB_TRY(x)                     \
+  do {                                \
+    lb_status r_ = (x);               \
+    if (r_ != LB_OK) return r_;       \
+  } while (0)
+
 // The same factorisation and solve with every product sliced (the
 // LB_FP64_SLICED form), on a left-looking schedule: at block step k, block
 // row k of the matrix (from the diagonal on), block column k below the
@@ -150,15 +156,65 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
 // block (64) on its short side; the products whose natural form has the
 // block's rows run transposed (the long operand as the 128-row side, C
 // written transposed).  Every product is one sliced launch over all slices.
+// The diagonal block of the two-level schedule: the kb x kb block (kb <= 128)
+// at (k0, k0) of Mx, up to date with all earlier blocks, factored from two
+// 64-wide halves (the first by lu_diag_real_kernel<64>, the off-diagonal
+// blocks of U and L from its inverses, the second half's Schur complement
+// and its factorisation), and the inverses of its unit-lower and upper
+// factors assembled by the 2 x 2 block formulas
+//   L^{-1} = [[L1^{-1}, 0], [-L2^{-1} L21 L1^{-1}, L2^{-1}]],
+//   U^{-1} = [[U1^{-1}, -U1^{-1} U12 U2^{-1}], [0, U2^{-1}]]
+// into Linv (128 x 128, zeroed here) and Uinv_k (128 x 128, zero on entry).  U's blocks go
+// to Uf, L21 to Lp.  The small products run on the FP64 pipe; `tmp` holds
+// 6 S 64 x 64 doubles.
+lb_status diag_block128(lb_ctx* c, int n, int S, double* Mx, double* Uf, double* Lp, int k0, int kb, double* Linv,
+                        long long sLinv, double* Uinv_k, long long sUinv, double* tmp, cudaStream_t st) {
+  constexpr int H = 64, NB = 128;
+  const long long nn = (long long)n * n, hh = (long long)H * H;
+  const int h0 = kb < H ? kb : H, h1 = kb - h0, k1 = k0 + h0;
+  double *Li1 = tmp, *Ui1 = tmp + S * hh, *Li2 = tmp + 2 * S * hh, *Ui2 = tmp + 3 * S * hh, *T = tmp + 4 * S * hh,
+         *T2 = tmp + 5 * S * hh;
+  LB_CUDA(cudaMemsetAsync(Linv, 0, sizeof(double) * NB * NB * S, st));  // Uinv_k: zeroed by the caller
+  LB_CUDA(launch_lu_diag_real(n, S, k0, h0, Mx, Uf, Li1, hh, Ui1, hh, c->err_dev, st, H));
+  LB_CUDA(launch_real_copy_block(h0, h0, S, Li1, H, hh, Linv, NB, sLinv, c->sm_count, st));
+  LB_CUDA(launch_real_copy_block(h0, h0, S, Ui1, H, hh, Uinv_k, NB, sUinv, c->sm_count, st));
+  if (h1 == 0) return LB_OK;
+  double* U12 = Uf + (long long)k0 * n + k1;
+  double* L21 = Lp + (long long)k1 * n + k0;
+  RGemmProblem<double> pr[2];
+  // U12 = L1^{-1} Mx[k0:k1, k1:k1+h1];  L21 = Mx[k1:k1+h1, k0:k1] U1^{-1}
+  pr[0] = rupd(h0, h1, h0, Li1, H, hh, Mx + (long long)k0 * n + k1, n, nn, U12, n, nn, 1.0, 0.0, S);
+  pr[1] = rupd(h1, h0, h0, Mx + (long long)k1 * n + k0, n, nn, Ui1, H, hh, L21, n, nn, 1.0, 0.0, S);
+  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  // the Schur complement of the second half, then its factorisation
+  RGemmProblem<double> q = rupd(h1, h1, h0, L21, n, nn, U12, n, nn, Mx + (long long)k1 * n + k1, n, nn, -1.0, 1.0, S);
+  LB_CUDA(rgemm_f64(&q, 1, c->sm_count, st));
+  LB_CUDA(launch_lu_diag_real(n, S, k1, h1, Mx, Uf, Li2, hh, Ui2, hh, c->err_dev, st, H));
+  LB_CUDA(launch_real_copy_block(h1, h1, S, Li2, H, hh, Linv + (long long)h0 * NB + h0, NB, sLinv, c->sm_count, st));
+  LB_CUDA(launch_real_copy_block(h1, h1, S, Ui2, H, hh, Uinv_k + (long long)h0 * NB + h0, NB, sUinv, c->sm_count, st));
+  // T = L21 L1^{-1}, T2 = U12 U2^{-1}; then the off-diagonal blocks
+  pr[0] = rupd(h1, h0, h0, L21, n, nn, Li1, H, hh, T, H, hh, 1.0, 0.0, S);
+  pr[1] = rupd(h0, h1, h1, U12, n, nn, Ui2, H, hh, T2, H, hh, 1.0, 0.0, S);
+  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  pr[0] = rupd(h1, h0, h1, Li2, H, hh, T, H, hh, Linv + (long long)h0 * NB, NB, sLinv, -1.0, 0.0, S);
+  pr[1] = rupd(h0, h1, h0, Ui1, H, hh, T2, H, hh, Uinv_k + h0, NB, sUinv, -1.0, 0.0, S);
+  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  return LB_OK;
+}
+
 lb_status lu_solve_sliced_ll(lb_ctx* c, int n, int S, double* Mx, double* N, double* Uf, double* Y, double* Lp,
                              double* inv, cudaStream_t st) {
   const long long nn = (long long)n * n;
-  // 64-wide blocks from n = 128 (their inverses in `inv`, which holds
-  // 2 n^2 S doubles), else the 32-wide blocks of the context's buffers
-  const int nb = n >= 128 ? kLuNbSliced : kLuNb, nbk = (n + nb - 1) / nb;
+  // 128-wide blocks (two 64-wide halves) from n = 256, their inverses and
+  // the halves' scratch in `inv` (which holds 2 n^2 S doubles); else the
+  // 32-wide blocks of the context's buffers
+  const bool two = n >= 256;
+  const int nb = two ? kLuNbSliced : kLuNb, nbk = (n + nb - 1) / nb;
   const long long sLinv = (long long)nb * nb, sUinv = (long long)nbk * nb * nb;
-  double* Linv = nb == kLuNb ? (double*)c->Linv : inv;                           // S x nb x nb
-  double* Uinv = nb == kLuNb ? (double*)c->Uinv : inv + (long long)S * sLinv;  // S x nbk x nb x nb
+  double* Linv = two ? inv : (double*)c->Linv;                            // S x nb x nb
+  double* Uinv = two ? inv + (long long)S * sLinv : (double*)c->Uinv;    // S x nbk x nb x nb
+  double* tmp = inv + (long long)S * (sLinv + sUinv);                     // 6 S 64 x 64 (two-level only)
+  if (two) LB_CUDA(cudaMemsetAsync(Uinv, 0, sizeof(double) * S * sUinv, st));
   // C = alpha A B + beta C (one per slice): A(m, k) at A + m a_sm + k a_sk,
   // B(k, j) at B + k b_sk + j b_sn, C(m, j) at C + m n + j or, transposed,
   // at C + j n + m
@@ -191,7 +247,10 @@ lb_status lu_solve_sliced_ll(lb_ctx* c, int n, int S, double* Mx, double* N, dou
         r = prod(n, kb, k0, Y, 1, n, nn, Lp + (long long)k0 * n, 1, n, nn, N + (long long)k0 * n, 1, -1.0, 1.0);
     }
     if (r != LB_OK) return r;
-    LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st, nb));
+    if (two)
+      LB_TRY(diag_block128(c, n, S, Mx, Uf, Lp, k0, kb, Linv, sLinv, Uinv_k, sUinv, tmp, st));
+    else
+      LB_CUDA(launch_lu_diag_real(n, S, k0, kb, Mx, Uf, Linv, sLinv, Uinv_k, sUinv, c->err_dev, st, nb));
     if (rest > 0) {
       // U[k0:r0, r0:] = Linv_k Mx[k0:r0, r0:], transposed
       r = prod(rest, kb, kb, Mx + (long long)k0 * n + r0, 1, n, nn, Linv, 1, nb, sLinv, Uf + (long long)k0 * n + r0,
@@ -291,11 +350,6 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
   return LB_OK;
 }
 
-#define LB_TRY(x)                     \
-  do {                                \
-    lb_status r_ = (x);               \
-    if (r_ != LB_OK) return r_;       \
-  } while (0)
 
 }  // namespace
 

@@ -163,9 +163,12 @@ def _gen_pair(d, seed, scale):
     return Lb * f, Ld * f
 
 
-@pytest.mark.parametrize("d,S,scale", [(2, 3, 0.2), (3, 3, 3.0), (6, 2, 13.0), (9, 3, 1.7), (11, 2, 0.6)])
+@pytest.mark.parametrize("d,S,scale", [(2, 3, 0.2), (3, 3, 3.0), (6, 2, 13.0), (9, 3, 1.7), (11, 2, 0.6),
+                                       (16, 2, 0.9), (17, 2, 2.0)])
 def test_build_sliced_matches_oracle(lbm, d, S, scale):
-    """Squaring counts 0 to 7: every squaring a sliced product."""
+    """Squaring counts 0 to 7: every squaring a sliced product.  n = 256 and
+    289 take the 128-wide LU blocks (two 64-wide halves; 289 ends in a
+    33-wide block with no second half)."""
     n = d * d
     Lb, Ld = _gen_pair(d, 2500 + d, scale)
     u = np.linspace(-0.3, 0.4, S)
