@@ -137,6 +137,13 @@ lb_status lu_solve_blocked_real(lb_ctx* c, int n, int S, double* Mx, double* N, 
 // batch elements that fit the context's scratch (defined below).
 lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
 
+// C_j = A B_j + beta_j C_j (j = 0, 1; n x n, S slices, row-major) with A
+// sliced once, where both products' slices fit the scratch (else two
+// oz_product calls).  B_1 is sliced after the first product is written, so
+// it may be C_0.
+lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const double* B0, double* C0, double beta0,
+                              const double* B1, double* C1, double beta1, cudaStream_t st);
+
 #define LB_TRY(x)                     \
   do {                                \
     lb_status r_ = (x);               \
@@ -308,6 +315,43 @@ lb_status skip_product(lb_ctx* c, RGemmProblem<T> p, const int* flag, cudaStream
 
 // C = alpha A B + beta C through the sliced FP64 product, in chunks of
 // batch elements that fit the context's scratch.
+lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const double* B0, double* C0, double beta0,
+                              const double* B1, double* C1, double beta1, cudaStream_t st) {
+  const long long nn = (long long)n * n;
+  OzGemm q;
+  q.M = q.N = q.K = n;
+  q.batch = S;
+  q.A = A; q.a_sm = n; q.a_sk = 1; q.sA = nn;
+  q.ldc = n; q.sC = nn;
+  q.err = c->err_dev;
+  const double* Bs[2] = {B0, B1};
+  double* Cs[2] = {C0, C1};
+  const double betas[2] = {beta0, beta1};
+  if (oz_scratch_bytes(n, n, n, S) > c->oz_bytes) {
+    for (int j = 0; j < 2; j++) {
+      OzGemm p = q;
+      p.B = Bs[j]; p.b_sk = n; p.b_sn = 1; p.sB = nn;
+      p.C = Cs[j];
+      p.beta = betas[j];
+      LB_TRY(oz_product(c, p, st));
+    }
+    return LB_OK;
+  }
+  const OzSliced As = oz_carve(c->oz_scratch, n, n, S, kOzTileM);
+  const OzSliced Bsl = oz_carve((uint8_t*)c->oz_scratch + oz_sliced_bytes(n, n, S, kOzTileM), n, n, S, oz_bn_for(n));
+  LB_CUDA(oz_slice(A, n, 1, nn, As, nullptr, 0, st));
+  for (int j = 0; j < 2; j++) {
+    LB_CUDA(oz_slice(Bs[j], 1, n, nn, Bsl, nullptr, 0, st));  // B(k, c) is row c, position k of B^T
+    OzGemm p = q;
+    p.C = Cs[j];
+    p.beta = betas[j];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LB_CUDA(kernel_events(c, 2.0 * kOzPairs * (double)n * n * n * S, &e0, &e1));
+    LB_CUDA(oz_multiply(As, Bsl, p, c->sm_count, st, e0, e1));
+  }
+  return LB_OK;
+}
+
 lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
   int chunk = p.batch;
   while (chunk > 1 && oz_scratch_bytes(p.M, p.N, p.K, chunk) > c->oz_bytes) chunk = (chunk + 1) / 2;
@@ -400,24 +444,15 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
     RGemmProblem<double> p = rsq(n, S, Ar, Ar, A2);
     LB_TRY(skip_product(c, p, flagA, st));
-    auto sq = [&](const double* X, const double* Y, double* Cc, double beta) {
-      OzGemm q;
-      q.M = q.N = q.K = n;
-      q.batch = S;
-      q.A = X; q.a_sm = n; q.a_sk = 1; q.sA = nn;
-      q.B = Y; q.b_sk = n; q.b_sn = 1; q.sB = nn;
-      q.C = Cc; q.ldc = n; q.sC = nn;
-      q.beta = beta;
-      return oz_product(c, q, st);
-    };
-    LB_TRY(sq(A2, A2, A4, 0.0));
-    LB_TRY(sq(A2, A4, A6, 0.0));
+    // A^4 = A^2 A^2 then A^6 = A^2 A^4 (A^2 sliced once; A^4 is complete
+    // before it is sliced as the second product's operand)
+    LB_TRY(oz_product_shared_a(c, n, S, A2, A2, A4, 0.0, A4, A6, 0.0, st));
     LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[12], b[10], b[8], Z1, c->sm_count, st));
     LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
     LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[6], b[4], b[2], b[0], V, c->sm_count, st));
     LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[7], b[5], b[3], b[1], W, c->sm_count, st));
-    LB_TRY(sq(A6, Z1, V, 1.0));
-    LB_TRY(sq(A6, Z2, W, 1.0));
+    // V += A^6 Z1, W += A^6 Z2 with A^6 sliced once
+    LB_TRY(oz_product_shared_a(c, n, S, A6, Z1, V, 1.0, Z2, W, 1.0, st));
     // U = A W:  Mx = V - U, N = V + U
     p = rsq(n, S, Ar, W, Mx);
     p.alpha[0] = -1.0;
