@@ -566,6 +566,65 @@ __global__ void oz_slice_kernel(int R, int K, const double* __restrict__ X, long
   }
 }
 
+// Exponents and digit planes of an operand whose K is contiguous, in one
+// pass: a CTA takes one row group (8 rows) whole.  Each warp reads its row
+// into shared memory and reduces the row's largest magnitude; then the CTA
+// writes the group's digits core matrix by core matrix (two elements per
+// thread and plane, 128 contiguous bytes per 32 threads).  Rows past R (the
+// padding of the last tile) are zero digits.
+template <int NS>
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const double* __restrict__ X, long long sr,
+                                                            long long sb, int* __restrict__ E,
+                                                            __nv_bfloat16* __restrict__ Q, int tile_rows, int ntiles,
+                                                            int kblocks, const int* __restrict__ active,
+                                                            int active_iter) {
+  static_assert(NS == 9, "nine digits per value");
+  extern __shared__ double oz_rows[];
+  __shared__ int es[8];
+  const int b = blockIdx.y, r0 = blockIdx.x * 8;
+  if (oz_skip(active, active_iter, b)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kpad = kblocks * OZ_KB, ld = kpad + 1;
+  {
+    const int r = r0 + warp;
+    const double* x = X + (long long)b * sb + (long long)r * sr;
+    unsigned long long mx = 0;
+    for (int k = lane; k < kpad; k += 32) {
+      const double v = (r < R && k < K) ? __ldg(x + k) : 0.0;
+      oz_rows[warp * ld + k] = v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+      mx = a > mx ? a : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    const int e = r < R ? oz_exp_of(mx) : OZ_ZERO_EXP;
+    if (lane == 0) {
+      es[warp] = e;
+      if (r < R) E[(long long)b * R + r] = e;
+    }
+  }
+  __syncthreads();
+  const int t = r0 / tile_rows, rt = r0 - t * tile_rows;
+  const long long plane = (long long)tile_rows * OZ_KB;
+  __nv_bfloat16* qb = Q + ((long long)b * ntiles + t) * kblocks * NS * plane + (rt >> 3) * 2 * 64;
+  for (int p = threadIdx.x; p < 4 * kpad; p += 256) {
+    // element pairs in address order: k8 (even), r8, K half, K block
+    const int e = 2 * p;
+    const int k8 = e & 7, r8 = (e >> 3) & 7, ci = e >> 6;
+    const int kb = ci >> 1, kh = ci & 1, k = kb * 16 + kh * 8 + k8;
+    const int er = es[r8];
+    uint32_t h0[NS], h1[NS];
+    oz_digit_bits(oz_fixed(oz_rows[r8 * ld + k], er), h0);
+    oz_digit_bits(oz_fixed(oz_rows[r8 * ld + k + 1], er), h1);
+    uint32_t* q = (uint32_t*)(qb + (long long)kb * NS * plane + kh * 64 + r8 * 8 + k8);
+#pragma unroll
+    for (int i = 0; i < NS; i++) q[i * plane / 2] = h0[i] | (h1[i] << 16);
+  }
+}
+
 unsigned oz_grid(long long total, int per) { return (unsigned)((total + per - 1) / per); }
 
 }  // namespace
@@ -601,6 +660,17 @@ OzSliced oz_view(const OzSliced& o, int b) {
 cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, const OzSliced& o, const int* active,
                      int active_iter, cudaStream_t st) {
   if (o.rows <= 0 || o.batch <= 0) return cudaSuccess;
+  const int nt = oz_tiles(o.rows, o.tile_rows), kbl = oz_kblocks(o.K);
+  if (sk == 1 && o.K <= kOzMaxK) {
+    // K contiguous: exponents and digits in one pass, one row group per CTA
+    const size_t smem = (size_t)8 * (kbl * OZ_KB + 1) * sizeof(double);
+    cudaError_t e = set_smem_once((const void*)oz_slice_rows_kernel<kOzSlices>, smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    oz_slice_rows_kernel<kOzSlices><<<dim3((nt * o.tile_rows) / 8, o.batch), 256, smem, st>>>(
+        o.rows, o.K, X, sr, sb, o.E, o.Q, o.tile_rows, nt, kbl, active, active_iter);
+    return cudaGetLastError();
+  }
   const long long rows = (long long)o.rows * o.batch;
   count_launch();
   if (sk == 1)
@@ -611,7 +681,6 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
                                                                                        sb, o.E, active, active_iter);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nt = oz_tiles(o.rows, o.tile_rows), kbl = oz_kblocks(o.K);
   dim3 grid(oz_grid((long long)kbl * OZ_KB, 32), oz_grid((long long)nt * o.tile_rows, 32), o.batch);
   count_launch();
   oz_slice_kernel<kOzSlices><<<grid, 256, 0, st>>>(o.rows, o.K, X, sr, sk, sb, o.E, o.Q, o.tile_rows, nt, kbl, active,
