@@ -1228,7 +1228,7 @@ def run_ours(args):
     line["other_workloads"] = other_workloads(lb, accounting, dev, stream, fp64_peak=fp64_peak, fp32_peak=fp32_peak,
                                               bf16_peak=bf16_peak)
     line["other_workloads"]["mixed_instances"] = mixed_instances(lb, ctx, dev, stream, args.instances,
-                                                                 5 if args.steps >= 10 else 2)
+                                                                 5)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, 6)
     if rank == 0:
