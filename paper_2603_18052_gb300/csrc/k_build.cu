@@ -227,8 +227,11 @@ __global__ void check_finite_kernel(long long count, const z64* __restrict__ x, 
   bool bad = false;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x) {
+    // exponent field all ones (Inf or NaN), tested on the bits: integer
+    // operations only
     const z64 v = x[e];
-    if (!isfinite(v.x) || !isfinite(v.y)) bad = true;
+    const unsigned hx = (unsigned)(__double_as_longlong(v.x) >> 32), hy = (unsigned)(__double_as_longlong(v.y) >> 32);
+    if ((hx & 0x7FF00000u) == 0x7FF00000u || (hy & 0x7FF00000u) == 0x7FF00000u) bad = true;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NONFINITE);
 }

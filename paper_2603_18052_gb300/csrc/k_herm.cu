@@ -36,25 +36,28 @@
 namespace lb {
 namespace {
 
+// a CTA per row a of R[s], its threads along the row
 __global__ void herm_matrix_kernel(int n, int d, int S, const z64* __restrict__ P, double* __restrict__ R) {
-  const long long nn = (long long)n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)S * nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(t / nn);
-    const int a = (int)((t / n) % n), b = (int)(t % n);
-    int k, l, pa, i, j, pb;
+  const long long nn = (long long)n * n, rows = (long long)S * n;
+  for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const long long s = rw / n;
+    const int a = (int)(rw - s * n);
+    int k, l, pa;
     herm_coord(a, d, &k, &l, &pa);
-    herm_coord(b, d, &i, &j, &pb);
     const z64* row = P + s * nn + (long long)(k * d + l) * n;
-    z64 v;
-    if (pb == 0) {
-      v = row[i * d + i];
-    } else {
-      const z64 pij = row[i * d + j], pji = row[j * d + i];
-      v = pb == 1 ? make_double2(pij.x + pji.x, pij.y + pji.y)      // Re rho_ij
-                  : make_double2(-(pij.y - pji.y), pij.x - pji.x);  // Im rho_ij: i (P_ij - P_ji)
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      int i, j, pb;
+      herm_coord(b, d, &i, &j, &pb);
+      z64 v;
+      if (pb == 0) {
+        v = row[i * d + i];
+      } else {
+        const z64 pij = row[i * d + j], pji = row[j * d + i];
+        v = pb == 1 ? make_double2(pij.x + pji.x, pij.y + pji.y)      // Re rho_ij
+                    : make_double2(-(pij.y - pji.y), pij.x - pji.x);  // Im rho_ij: i (P_ij - P_ji)
+      }
+      R[rw * n + b] = pa == 2 ? v.y : v.x;
     }
-    R[t] = pa == 2 ? v.y : v.x;
   }
 }
 
@@ -324,9 +327,8 @@ bool herm_lat_split(int n, int* C, int* K) {
 }
 
 cudaError_t launch_herm_matrix(int n, int d, int S, const z64* P, double* R, int sm_count, cudaStream_t st) {
-  const long long total = (long long)S * n * n;
-  long long blocks = (total + 255) / 256;
-  if (blocks > (long long)sm_count * 8) blocks = (long long)sm_count * 8;
+  long long blocks = (long long)S * n;
+  if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
   count_launch();
   herm_matrix_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, d, S, P, R);
   return cudaGetLastError();

@@ -172,7 +172,7 @@ __device__ __forceinline__ double oz_pow2(int s) {
 // are the epilogue: they read the groups of a finished tile out of TMEM,
 // fold them into two exact integers per output, release TMEM (so the next
 // tile's MMAs start) and only then round, add beta C and store.
-template <int NS, int BN>
+template <int NS, int BN, bool XO>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozgemm_kernel(const __grid_constant__ OzGemm P, const __nv_bfloat16* __restrict__ QA,
                   const __nv_bfloat16* __restrict__ QB, int kblocks) {
@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (r < P.M) {
         // C element (r, c) at crow[c * cstep]: row-major, or transposed
         // (consecutive rows of a warp then hit consecutive addresses)
-        double* crow = P.C + (long long)b * P.sC + (P.transC ? (long long)r : (long long)r * P.ldc);
+        const long long coff = (long long)b * P.sC + (P.transC ? (long long)r : (long long)r * P.ldc);
+        double* crow = (!XO || P.C != nullptr) ? P.C + coff : nullptr;
         const long long cstep = P.transC ? P.ldc : 1;
 #pragma unroll
         for (int h = 0; h < NCH; h++) {
@@ -375,7 +376,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               out += cold[jj];
             else if (bmode == 2)
               out = fma(P.beta, cold[jj], out);
-            crow[c * cstep] = out;
+            if (!XO) {
+              crow[c * cstep] = out;
+            } else {
+              if (crow != nullptr) crow[c * cstep] = out;
+              // the further outputs (row-major only)
+              const long long e = coff + c;
+              const double t1 = P.x.T1 != nullptr ? P.x.T1[e] : 0.0;
+              if (P.x.pm) {
+                P.x.X[0][e] = t1 - out;
+                P.x.X[1][e] = t1 + out;
+              } else {
+                const double t2 = P.x.T2 != nullptr ? P.x.T2[e] : 0.0;
+#pragma unroll
+                for (int w = 0; w < 4; w++) {
+                  if (w >= P.x.nx) break;
+                  double v = P.x.c[w][0] * out + (P.x.c[w][1] * t1 + P.x.c[w][2] * t2);
+                  if (r == c) v += P.x.g[w];
+                  P.x.X[w][e] = v;
+                }
+              }
+            }
           }
         }
       }
@@ -566,14 +587,18 @@ __global__ void oz_slice_kernel(int R, int K, const double* __restrict__ X, long
   }
 }
 
-// Exponents and digit planes of an operand whose K is contiguous, in one
-// pass: a CTA takes one row group (8 rows) whole.  Each warp reads its row
-// into shared memory and reduces the row's largest magnitude; then the CTA
-// writes the group's digits core matrix by core matrix (two elements per
-// thread and plane, 128 contiguous bytes per 32 threads).  Rows past R (the
-// padding of the last tile) are zero digits.
-template <int NS>
-__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const double* __restrict__ X, long long sr,
+// Exponents and digit planes of an operand, in one pass, where either K is
+// contiguous (element (r, k) at X[b sb + r sr + k], RC = false) or the rows
+// are (at X[b sb + r + k sk], RC = true): a CTA takes one row group (8 rows)
+// whole.  With K contiguous each warp reads one row; with the rows
+// contiguous each K position's 8 values (64 bytes) are read by 8
+// consecutive threads.  The values go to shared memory and each row's
+// largest magnitude is reduced; then the CTA writes the group's digits core
+// matrix by core matrix (two elements per thread and plane, 128 contiguous
+// bytes per 32 threads).  Rows past R (the padding of the last tile) are
+// zero digits.
+template <int NS, bool RC>
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const double* __restrict__ X, long long sx,
                                                             long long sb, int* __restrict__ E,
                                                             __nv_bfloat16* __restrict__ Q, int tile_rows, int ntiles,
                                                             int kblocks, const int* __restrict__ active,
@@ -581,13 +606,15 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const 
   static_assert(NS == 9, "nine digits per value");
   extern __shared__ double oz_rows[];
   __shared__ int es[8];
+  __shared__ unsigned long long part[8][8];
   const int b = blockIdx.y, r0 = blockIdx.x * 8;
   if (oz_skip(active, active_iter, b)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kpad = kblocks * OZ_KB, ld = kpad + 1;
-  {
+  if (!RC) {
+    // sx: the row stride
     const int r = r0 + warp;
-    const double* x = X + (long long)b * sb + (long long)r * sr;
+    const double* x = X + (long long)b * sb + (long long)r * sx;
     unsigned long long mx = 0;
     for (int k = lane; k < kpad; k += 32) {
       const double v = (r < R && k < K) ? __ldg(x + k) : 0.0;
@@ -604,6 +631,34 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const 
     if (lane == 0) {
       es[warp] = e;
       if (r < R) E[(long long)b * R + r] = e;
+    }
+  } else {
+    // sx: the K stride; thread t reads row r0 + t % 8 at K positions t / 8 + 32 j
+    const int r8 = threadIdx.x & 7, r = r0 + r8;
+    const double* x = X + (long long)b * sb + r;
+    unsigned long long mx = 0;
+    for (int k = threadIdx.x >> 3; k < kpad; k += 32) {
+      const double v = (r < R && k < K) ? __ldg(x + (long long)k * sx) : 0.0;
+      oz_rows[r8 * ld + k] = v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+      mx = a > mx ? a : mx;
+    }
+    // lanes with the same row: lane % 8 equal
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (lane < 8) part[warp][lane] = mx;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      const int rr = r0 + threadIdx.x;
+      unsigned long long m = 0;
+#pragma unroll
+      for (int w = 0; w < 8; w++) m = part[w][threadIdx.x] > m ? part[w][threadIdx.x] : m;
+      const int e = rr < R ? oz_exp_of(m) : OZ_ZERO_EXP;
+      es[threadIdx.x] = e;
+      if (rr < R) E[(long long)b * R + rr] = e;
     }
   }
   __syncthreads();
@@ -661,14 +716,25 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
                      int active_iter, cudaStream_t st) {
   if (o.rows <= 0 || o.batch <= 0) return cudaSuccess;
   const int nt = oz_tiles(o.rows, o.tile_rows), kbl = oz_kblocks(o.K);
-  if (sk == 1 && o.K <= kOzMaxK) {
-    // K contiguous: exponents and digits in one pass, one row group per CTA
+  if ((sk == 1 || sr == 1) && o.K <= kOzMaxK) {
+    // K or the rows contiguous: exponents and digits in one pass, one row
+    // group per CTA
     const size_t smem = (size_t)8 * (kbl * OZ_KB + 1) * sizeof(double);
-    cudaError_t e = set_smem_once((const void*)oz_slice_rows_kernel<kOzSlices>, smem);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    oz_slice_rows_kernel<kOzSlices><<<dim3((nt * o.tile_rows) / 8, o.batch), 256, smem, st>>>(
-        o.rows, o.K, X, sr, sb, o.E, o.Q, o.tile_rows, nt, kbl, active, active_iter);
+    const dim3 grid((nt * o.tile_rows) / 8, o.batch);
+    cudaError_t e;
+    if (sk == 1) {
+      e = set_smem_once((const void*)oz_slice_rows_kernel<kOzSlices, false>, smem);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      oz_slice_rows_kernel<kOzSlices, false><<<grid, 256, smem, st>>>(o.rows, o.K, X, sr, sb, o.E, o.Q, o.tile_rows,
+                                                                      nt, kbl, active, active_iter);
+    } else {
+      e = set_smem_once((const void*)oz_slice_rows_kernel<kOzSlices, true>, smem);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      oz_slice_rows_kernel<kOzSlices, true><<<grid, 256, smem, st>>>(o.rows, o.K, X, sk, sb, o.E, o.Q, o.tile_rows,
+                                                                     nt, kbl, active, active_iter);
+    }
     return cudaGetLastError();
   }
   const long long rows = (long long)o.rows * o.batch;
@@ -689,14 +755,14 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
 }
 
 namespace {
-template <int BN>
+template <int BN, bool XO>
 cudaError_t oz_launch(const OzSliced& A, const OzSliced& B, OzGemm p, int sm_count, cudaStream_t st, cudaEvent_t ev0,
                       cudaEvent_t ev1) {
   constexpr int NS = kOzSlices;
   using Cfg = OzCfg<NS, BN>;
   p.EA = A.E;
   p.EB = B.E;
-  cudaError_t e = set_smem_once((const void*)ozgemm_kernel<NS, BN>, Cfg::SMEM);
+  cudaError_t e = set_smem_once((const void*)ozgemm_kernel<NS, BN, XO>, Cfg::SMEM);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)oz_tiles(p.N, BN) * oz_tiles(p.M, OZ_TBM) * p.batch;
   const int grid = (int)std::min<long long>(tiles, sm_count > 0 ? sm_count : 1);
@@ -705,7 +771,7 @@ cudaError_t oz_launch(const OzSliced& A, const OzSliced& B, OzGemm p, int sm_cou
     if (e != cudaSuccess) return e;
   }
   count_launch();
-  ozgemm_kernel<NS, BN><<<grid, OZ_THREADS, Cfg::SMEM, st>>>(p, A.Q, B.Q, oz_kblocks(p.K));
+  ozgemm_kernel<NS, BN, XO><<<grid, OZ_THREADS, Cfg::SMEM, st>>>(p, A.Q, B.Q, oz_kblocks(p.K));
   e = cudaGetLastError();
   if (e == cudaSuccess && ev1 != nullptr) e = cudaEventRecord(ev1, st);
   return e;
@@ -718,9 +784,19 @@ cudaError_t oz_multiply(const OzSliced& A, const OzSliced& B, const OzGemm& p, i
   if (A.tile_rows != OZ_TBM || A.rows != p.M || B.rows != p.N || A.K != p.K || B.K != p.K || A.batch != p.batch ||
       B.batch != p.batch || p.K > kOzMaxK)
     return cudaErrorInvalidValue;
-  if (B.tile_rows == kOzBN) return oz_launch<kOzBN>(A, B, p, sm_count, st, ev0, ev1);
-  if (B.tile_rows == kOzBNMid) return oz_launch<kOzBNMid>(A, B, p, sm_count, st, ev0, ev1);
-  if (B.tile_rows == kOzBNSmall) return oz_launch<kOzBNSmall>(A, B, p, sm_count, st, ev0, ev1);
+  if (p.x.nx < 0 || p.x.nx > 4 || (p.x.nx > 0 && p.transC) || (p.C == nullptr && (p.x.nx == 0 || p.beta != 0.0)))
+    return cudaErrorInvalidValue;
+  for (int w = 0; w < p.x.nx; w++)
+    if (p.x.X[w] == nullptr) return cudaErrorInvalidValue;
+  if (p.x.nx > 0) {
+    if (B.tile_rows == kOzBN) return oz_launch<kOzBN, true>(A, B, p, sm_count, st, ev0, ev1);
+    if (B.tile_rows == kOzBNMid) return oz_launch<kOzBNMid, true>(A, B, p, sm_count, st, ev0, ev1);
+    if (B.tile_rows == kOzBNSmall) return oz_launch<kOzBNSmall, true>(A, B, p, sm_count, st, ev0, ev1);
+    return cudaErrorInvalidValue;
+  }
+  if (B.tile_rows == kOzBN) return oz_launch<kOzBN, false>(A, B, p, sm_count, st, ev0, ev1);
+  if (B.tile_rows == kOzBNMid) return oz_launch<kOzBNMid, false>(A, B, p, sm_count, st, ev0, ev1);
+  if (B.tile_rows == kOzBNSmall) return oz_launch<kOzBNSmall, false>(A, B, p, sm_count, st, ev0, ev1);
   return cudaErrorInvalidValue;
 }
 

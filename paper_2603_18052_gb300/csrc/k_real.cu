@@ -60,15 +60,23 @@ __global__ void __launch_bounds__(256) real_gen_norm_kernel(int n, int S, const 
   }
 }
 
-// A_s = G_s / 2^sc[s] (exact power-of-two scaling)
+// A_s = G_s / 2^sc[s] (exact power-of-two scaling); a CTA per row of a
+// slice, its threads along the row
 __global__ void real_scale_kernel(int n, int S, const double* __restrict__ Gb, const double* __restrict__ Gd,
                                   const double* __restrict__ u, double dt, const int* __restrict__ sc,
                                   double* __restrict__ A) {
-  const long long nn = (long long)n * n, total = nn * S;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e / nn);
-    A[e] = ldexp(slice_gen(Gb, Gd, u, s, nn, e - s * nn, dt), -sc[s]);
+  const long long nn = (long long)n * n, rows = (long long)S * n;
+  for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const int s = (int)(rw / n);
+    const long long o0 = (rw - (long long)s * n) * n;
+    // (v dt) 2^-sc is exact scaling of the rounded v dt, so one product by
+    // dt 2^-sc (exact) rounds the same: two FP64 operations per entry
+    const double f = ldexp(dt, -sc[s]);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const long long o = o0 + c;
+      const double v = Gd == nullptr ? Gb[(long long)s * nn + o] : fma(u[s], Gd[o], Gb[o]);
+      A[rw * n + c] = v * f;
+    }
   }
 }
 
@@ -80,16 +88,47 @@ __global__ void real_lincomb3_kernel(long long total, const T* __restrict__ X0, 
     Z[e] = c0 * X0[e] + (c1 * X1[e] + c2 * X2[e]);
 }
 
-// Z = c0 X0 + c1 X1 + c2 X2 + g I (n x n per slice, FP64)
-__global__ void real_lincomb3i_kernel(int n, long long total, const double* __restrict__ X0,
-                                      const double* __restrict__ X1, const double* __restrict__ X2, double c0,
-                                      double c1, double c2, double g, double* __restrict__ Z) {
-  const long long nn = (long long)n * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long o = e % nn;
-    const double v = c0 * X0[e] + (c1 * X1[e] + c2 * X2[e]);
-    Z[e] = (o / n == o % n) ? v + g : v;
+// A_s^2 of a control-affine slice generator A_s = c_s (G_b + u_s G_d),
+// c_s = dt 2^-sc[s], from three slice-independent products:
+//   A_s^2 = c_s^2 (P0 + u_s (P1 + u_s P2)),  P0 = G_b^2, P1 = G_b G_d + G_d G_b, P2 = G_d^2;
+// a CTA per row of a slice, three FP64 operations per entry.
+__global__ void real_affine_square_kernel(int n, int S, const double* __restrict__ P0, const double* __restrict__ P1,
+                                          const double* __restrict__ P2, const double* __restrict__ u, double dt,
+                                          const int* __restrict__ sc, double* __restrict__ A2) {
+  const long long rows = (long long)S * n;
+  for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const int s = (int)(rw / n);
+    const long long o0 = (rw - (long long)s * n) * n;
+    const double cs = ldexp(dt, -sc[s]), f = cs * cs, us = u[s];
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const long long o = o0 + c;
+      A2[rw * n + c] = fma(us, fma(us, P2[o], P1[o]), P0[o]) * f;
+    }
+  }
+}
+
+// The power terms of the [13/13] approximant's two polynomials in one pass
+// over A^6, A^4, A^2 (n x n per slice, FP64):
+//   Z1 = b12 A^6 + b10 A^4 + b8 A^2,   Z2 = b13 A^6 + b11 A^4 + b9 A^2,
+//   V = b6 A^6 + b4 A^4 + b2 A^2 + b0 I,   W = b7 A^6 + b5 A^4 + b3 A^2 + b1 I;
+// a CTA per row of a slice, its threads along the row.  Twelve FP64
+// operations per entry: the FP64 pipe, not the memory, bounds this pass.
+__global__ void real_pade_terms_kernel(int n, int S, const double* __restrict__ A6, const double* __restrict__ A4,
+                                       const double* __restrict__ A2, PadeCoef cf, double* __restrict__ Z1,
+                                       double* __restrict__ Z2, double* __restrict__ V, double* __restrict__ W) {
+  const long long rows = (long long)S * n;
+  for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const int r = (int)(rw % n);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const long long e = rw * n + c;
+      const double p6 = A6[e], p4 = A4[e], p2 = A2[e];
+      Z1[e] = cf.b[12] * p6 + (cf.b[10] * p4 + cf.b[8] * p2);
+      Z2[e] = cf.b[13] * p6 + (cf.b[11] * p4 + cf.b[9] * p2);
+      const double v = cf.b[6] * p6 + (cf.b[4] * p4 + cf.b[2] * p2);
+      const double w = cf.b[7] * p6 + (cf.b[5] * p4 + cf.b[3] * p2);
+      V[e] = c == r ? v + cf.b[0] : v;
+      W[e] = c == r ? w + cf.b[1] : w;
+    }
   }
 }
 
@@ -178,24 +217,27 @@ __device__ __forceinline__ z64 herm_entry(const double* __restrict__ R, int n, i
   return make_double2(re, i < j ? im : -im);
 }
 
+// a CTA per row (i, j) of P[s], its threads along the row
 __global__ void herm_to_complex_kernel(int n, int d, int S, const double* __restrict__ R, z64* __restrict__ P) {
-  const long long nn = (long long)n * n, total = nn * S;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long s = e / nn;
-    const int r = (int)((e - s * nn) / n), c = (int)(e - s * nn - (long long)r * n);
-    const int i = r / d, j = r - (r / d) * d, k = c / d, l = c - (c / d) * d;
+  const long long nn = (long long)n * n, rows = (long long)S * n;
+  for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+    const long long s = rw / n;
+    const int r = (int)(rw - s * n);
+    const int i = r / d, j = r - (r / d) * d;
     const double* Rs = R + s * nn;
-    z64 v;
-    if (k == l) {
-      v = herm_entry(Rs, n, d, i, j, k);
-    } else {
-      const int a = herm_pair_coord(k < l ? k : l, k < l ? l : k, d);
-      const z64 yre = herm_entry(Rs, n, d, i, j, a), yim = herm_entry(Rs, n, d, i, j, a + 1);
-      v = k < l ? make_double2(0.5 * (yre.x + yim.y), 0.5 * (yre.y - yim.x))
-                : make_double2(0.5 * (yre.x - yim.y), 0.5 * (yre.y + yim.x));
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int k = c / d, l = c - (c / d) * d;
+      z64 v;
+      if (k == l) {
+        v = herm_entry(Rs, n, d, i, j, k);
+      } else {
+        const int a = herm_pair_coord(k < l ? k : l, k < l ? l : k, d);
+        const z64 yre = herm_entry(Rs, n, d, i, j, a), yim = herm_entry(Rs, n, d, i, j, a + 1);
+        v = k < l ? make_double2(0.5 * (yre.x + yim.y), 0.5 * (yre.y - yim.x))
+                  : make_double2(0.5 * (yre.x - yim.y), 0.5 * (yre.y + yim.x));
+      }
+      P[rw * n + c] = v;
     }
-    P[e] = v;
   }
 }
 
@@ -313,9 +355,8 @@ cudaError_t launch_real_slice_prepare(int n, int S, const double* Gb, const doub
   if (e != cudaSuccess) return e;
   e = launch_squaring_count(S, norm_bits, sc, kmix, s_out, err, st);
   if (e != cudaSuccess) return e;
-  const long long total = (long long)n * n * S;
   count_launch();
-  real_scale_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, S, Gb, Gd, u, dt, sc, A);
+  real_scale_kernel<<<grid_of((long long)S * n, 1, sm_count), 256, 0, st>>>(n, S, Gb, Gd, u, dt, sc, A);
   return cudaGetLastError();
 }
 
@@ -338,11 +379,22 @@ cudaError_t launch_real_copy_block(int R, int C, int S, const double* src, long 
   return cudaGetLastError();
 }
 
-cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
-                                  double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st) {
-  const long long total = (long long)n * n * S;
+cudaError_t launch_real_affine_square(int n, int S, const double* P0, const double* P1, const double* P2,
+                                      const double* u, double dt, const int* sc, double* A2, int sm_count,
+                                      cudaStream_t st) {
   count_launch();
-  real_lincomb3i_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, total, X0, X1, X2, c0, c1, c2, g, Z);
+  real_affine_square_kernel<<<grid_of((long long)S * n, 1, sm_count), 256, 0, st>>>(n, S, P0, P1, P2, u, dt, sc, A2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_pade_terms(int n, int S, const double* A6, const double* A4, const double* A2,
+                                   const double* b, double* Z1, double* Z2, double* V, double* W, int sm_count,
+                                   cudaStream_t st) {
+  PadeCoef cf;
+  for (int j = 0; j < 14; j++) cf.b[j] = b[j];
+  count_launch();
+  real_pade_terms_kernel<<<grid_of((long long)S * n, 1, sm_count), 256, 0, st>>>(n, S, A6, A4, A2, cf, Z1, Z2, V,
+                                                                                  W);
   return cudaGetLastError();
 }
 template cudaError_t launch_real_lincomb3<float>(long long, const float*, const float*, const float*, double, double,
@@ -383,9 +435,8 @@ cudaError_t launch_real_copy_active(long long nn, int S, const double* src, doub
 }
 
 cudaError_t launch_herm_to_complex(int n, int d, int S, const double* R, z64* P, int sm_count, cudaStream_t st) {
-  const long long total = (long long)n * n * S;
   count_launch();
-  herm_to_complex_kernel<<<grid_of(total, 256, sm_count), 256, 0, st>>>(n, d, S, R, P);
+  herm_to_complex_kernel<<<grid_of((long long)S * n, 1, sm_count), 256, 0, st>>>(n, d, S, R, P);
   return cudaGetLastError();
 }
 

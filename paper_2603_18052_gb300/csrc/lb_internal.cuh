@@ -127,6 +127,7 @@ struct lb_ctx {
   size_t inst_tab_bytes = 0;
   cudaEvent_t ev_tab = nullptr;   // the last table upload
   int* spflag = nullptr;  // 2 x max_slices: sparse-operand flags of the real-coordinate build
+  int* csr = nullptr;     // max_n + 1 row offsets, then up to max_n^2 / 4 column indices: a sparse pattern
   // --- GRAPE (contexts with max_n <= 81) ---
   lb::z64* grape = nullptr;
   size_t grape_bytes = 0;
@@ -197,6 +198,17 @@ cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count,
 // (cudaErrorInvalidValue otherwise).
 template <typename T>
 cudaError_t rgemm_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t st);
+// The same product with A's nonzero pattern (a superset of every batch
+// element's) in compressed rows: cols[rowptr[r] .. rowptr[r + 1]) are the
+// columns of row r, increasing; the same terms in the same order as
+// rgemm_rowskip.  Needs shiftA == 0 besides rgemm_rowskip's conditions.
+template <typename T>
+cudaError_t rgemm_csr(const RGemmProblem<T>& p, const int* rowptr, const int* cols, int sm_count, cudaStream_t st);
+// The union pattern of X0 and X1 (n x n row-major FP64; X1 may be null) into
+// rowptr (n + 1) and cols (up to max_nnz), one launch; flag[0 .. S) = 1 when
+// it has at most max_nnz entries (and is written), else 0.
+cudaError_t launch_csr_union(int n, const double* X0, const double* X1, long long max_nnz, int S, int* rowptr,
+                             int* cols, int* flag, cudaStream_t st);
 // flag[s] = 1 if M[s] (S row-major n x n matrices) has at most max_nnz
 // nonzero entries, else 0.
 template <typename T>
@@ -218,6 +230,8 @@ bool gemv_f64_preferred(int n, int B);
 // diagonal entries, then Re and Im of the upper-triangle entries (k < l) in
 // row-major order.  Coordinate a -> (k, l, part): part 0 = rho_kk (k = l),
 // 1 = Re rho_kl, 2 = Im rho_kl.
+// Coordinates of the upper-triangle rows before row k: sum_{r < k} (d - 1 - r).
+__host__ __device__ inline int herm_row_base(int k, int d) { return k * (2 * d - k - 1) / 2; }
 __host__ __device__ inline void herm_coord(int a, int d, int* k, int* l, int* part) {
   if (a < d) {
     *k = a;
@@ -225,22 +239,21 @@ __host__ __device__ inline void herm_coord(int a, int d, int* k, int* l, int* pa
     *part = 0;
     return;
   }
-  int q = (a - d) >> 1;
+  const int q = (a - d) >> 1;
   *part = 1 + ((a - d) & 1);
-  int r = 0;
-  while (q >= d - 1 - r) {
-    q -= d - 1 - r;
-    r++;
-  }
+  // the row r with herm_row_base(r) <= q < herm_row_base(r + 1): the root of
+  // the quadratic, then corrected by whole steps
+  const float t = (float)(2 * d - 1);
+  int r = (int)(0.5f * (t - sqrtf(fmaxf(t * t - 8.0f * (float)q, 0.0f))));
+  if (r < 0) r = 0;
+  if (r > d - 2) r = d - 2;
+  while (r > 0 && herm_row_base(r, d) > q) r--;
+  while (r < d - 2 && herm_row_base(r + 1, d) <= q) r++;
   *k = r;
-  *l = r + 1 + q;
+  *l = r + 1 + q - herm_row_base(r, d);
 }
 // Index of the Re coordinate of the upper-triangle entry (k, l), k < l.
-__host__ __device__ inline int herm_pair_coord(int k, int l, int d) {
-  int q = 0;
-  for (int r = 0; r < k; r++) q += d - 1 - r;
-  return d + 2 * (q + l - k - 1);
-}
+__host__ __device__ inline int herm_pair_coord(int k, int l, int d) { return d + 2 * (herm_row_base(k, d) + l - k - 1); }
 
 // Hermitian (real-coordinate) FP64 propagation, k_herm.cu: the lane split of
 // the one-warp latency form (false: n above 9), the real transfer matrices of
@@ -308,9 +321,14 @@ cudaError_t launch_real_lincomb3(long long total, const T* X0, const T* X1, cons
 // an R x C block of S real matrices (leading dimension, batch stride each)
 cudaError_t launch_real_copy_block(int R, int C, int S, const double* src, long long sld, long long ss, double* dst,
                                    long long dld, long long ds, int sm_count, cudaStream_t st);
-// Z = c0 X0 + c1 X1 + c2 X2 + g I for S real n x n matrices (FP64)
-cudaError_t launch_real_lincomb3i(int n, int S, const double* X0, const double* X1, const double* X2, double c0,
-                                  double c1, double c2, double g, double* Z, int sm_count, cudaStream_t st);
+// A_s^2 = (dt 2^-sc[s])^2 (P0 + u_s (P1 + u_s P2)) for S slices (P0, P1, P2: n x n)
+cudaError_t launch_real_affine_square(int n, int S, const double* P0, const double* P1, const double* P2,
+                                      const double* u, double dt, const int* sc, double* A2, int sm_count,
+                                      cudaStream_t st);
+// Z1, Z2, V, W of the [13/13] approximant from A^6, A^4, A^2 (b: the 14 coefficients)
+cudaError_t launch_real_pade_terms(int n, int S, const double* A6, const double* A4, const double* A2,
+                                   const double* b, double* Z1, double* Z2, double* V, double* W, int sm_count,
+                                   cudaStream_t st);
 // The Pade coefficients b_0 .. b_13 by value.
 struct PadeCoef {
   double b[14];
@@ -484,6 +502,21 @@ cudaError_t zgemm_tc(const TcProblem& p, cudaStream_t st);
 constexpr int kOzSlices = 9;    // base-64 digits per operand row / column (54 bits)
 constexpr int kOzMaxK = 1488;   // every group sum exact in FP32 up to this K
 constexpr int kOzPairs = kOzSlices * (kOzSlices + 1) / 2;  // digit products per multiply-add (45)
+// Further outputs of a sliced product, formed in its epilogue from the
+// product's element out (after alpha and beta) and two matrices T1, T2 laid
+// out like C (row-major, C's ldc and sC; T1 or T2 may be null, read as 0):
+//   X_w[e] = c[w][0] out + (c[w][1] T1[e] + c[w][2] T2[e]) (+ g[w] where row == column)
+// for w < nx (at most 4); or, with pm set (and nx = 2), X_0 = T1 - out and
+// X_1 = T1 + out (one FP64 operation each).  Not with transC.
+struct OzExtra {
+  int nx = 0;
+  int pm = 0;
+  const double* T1 = nullptr;
+  const double* T2 = nullptr;
+  double* X[4] = {nullptr, nullptr, nullptr, nullptr};
+  double c[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double g[4] = {0, 0, 0, 0};
+};
 struct OzGemm {
   int M = 0, N = 0, K = 0, batch = 1;
   const double* A = nullptr; long long a_sm = 0, a_sk = 1, sA = 0;
@@ -495,6 +528,7 @@ struct OzGemm {
   const int* active = nullptr; int active_iter = 0;
   const int* EA = nullptr; const int* EB = nullptr;  // row / column exponents (set by ozgemm_f64)
   unsigned int* err = nullptr;
+  OzExtra x;  // C may be null when x.nx > 0 (the product itself not stored)
 };
 constexpr int kOzBN = 48;       // columns of C per CTA (B tile rows)
 constexpr int kOzBNSmall = 16;  // the narrow tile, for products with few output tiles

@@ -140,9 +140,9 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st);
 // C_j = A B_j + beta_j C_j (j = 0, 1; n x n, S slices, row-major) with A
 // sliced once, where both products' slices fit the scratch (else two
 // oz_product calls).  B_1 is sliced after the first product is written, so
-// it may be C_0.
+// it may be C_0.  x1 (may be null): further outputs of the second product.
 lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const double* B0, double* C0, double beta0,
-                              const double* B1, double* C1, double beta1, cudaStream_t st);
+                              const double* B1, double* C1, double beta1, const OzExtra* x1, cudaStream_t st);
 
 #define LB_TRY(x)                     \
   do {                                \
@@ -316,10 +316,24 @@ lb_status skip_product(lb_ctx* c, RGemmProblem<T> p, const int* flag, cudaStream
   return LB_OK;
 }
 
+// The same with A's nonzero pattern in compressed rows (flag[s] = 1: the
+// pattern is valid and sparse, the same for every slice).
+lb_status csr_product(lb_ctx* c, RGemmProblem<double> p, const int* flag, const int* rowptr, const int* cols,
+                      cudaStream_t st) {
+  RGemmProblem<double> q = p;
+  q.pick = flag;
+  q.pick_val = 1;
+  LB_CUDA(rgemm_csr(q, rowptr, cols, c->sm_count, st));
+  p.pick = flag;
+  p.pick_val = 0;
+  LB_CUDA(dense_gemm(p, c->sm_count, st));
+  return LB_OK;
+}
+
 // C = alpha A B + beta C through the sliced FP64 product, in chunks of
 // batch elements that fit the context's scratch.
 lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const double* B0, double* C0, double beta0,
-                              const double* B1, double* C1, double beta1, cudaStream_t st) {
+                              const double* B1, double* C1, double beta1, const OzExtra* x1, cudaStream_t st) {
   const long long nn = (long long)n * n;
   OzGemm q;
   q.M = q.N = q.K = n;
@@ -336,6 +350,7 @@ lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const do
       p.B = Bs[j]; p.b_sk = n; p.b_sn = 1; p.sB = nn;
       p.C = Cs[j];
       p.beta = betas[j];
+      if (j == 1 && x1 != nullptr) p.x = *x1;
       LB_TRY(oz_product(c, p, st));
     }
     return LB_OK;
@@ -348,11 +363,22 @@ lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const do
     OzGemm p = q;
     p.C = Cs[j];
     p.beta = betas[j];
+    if (j == 1 && x1 != nullptr) p.x = *x1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LB_CUDA(kernel_events(c, 2.0 * kOzPairs * (double)n * n * n * S, &e0, &e1));
     LB_CUDA(oz_multiply(As, Bsl, p, c->sm_count, st, e0, e1));
   }
   return LB_OK;
+}
+
+// p.C and the further outputs' matrices advanced by off elements
+OzGemm oz_shift_out(const OzGemm& p, long long off) {
+  OzGemm q = p;
+  if (p.C != nullptr) q.C = p.C + off;
+  if (p.x.T1 != nullptr) q.x.T1 = p.x.T1 + off;
+  if (p.x.T2 != nullptr) q.x.T2 = p.x.T2 + off;
+  for (int w = 0; w < p.x.nx; w++) q.x.X[w] = p.x.X[w] + off;
+  return q;
 }
 
 lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
@@ -366,12 +392,11 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
     if (oz_scratch_bytes(rows, p.N, p.K, 1) > c->oz_bytes) return LB_EINVAL;
     for (int b0 = 0; b0 < p.batch; b0++)
       for (int m0 = 0; m0 < p.M; m0 += rows) {
-        OzGemm q = p;
+        OzGemm q = oz_shift_out(p, (long long)b0 * p.sC + (p.transC ? (long long)m0 : (long long)m0 * p.ldc));
         q.batch = 1;
         q.M = std::min(rows, p.M - m0);
         q.A = p.A + (long long)b0 * p.sA + (long long)m0 * p.a_sm;
         q.B = p.B + (long long)b0 * p.sB;
-        q.C = p.C + (long long)b0 * p.sC + (p.transC ? (long long)m0 : (long long)m0 * p.ldc);
         if (p.active != nullptr) q.active = p.active + b0;
         q.err = c->err_dev;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -382,11 +407,10 @@ lb_status oz_product(lb_ctx* c, const OzGemm& p, cudaStream_t st) {
     return LB_OK;
   }
   for (int b0 = 0; b0 < p.batch; b0 += chunk) {
-    OzGemm q = p;
+    OzGemm q = oz_shift_out(p, (long long)b0 * p.sC);
     q.batch = std::min(chunk, p.batch - b0);
     q.A = p.A + (long long)b0 * p.sA;
     q.B = p.B + (long long)b0 * p.sB;
-    q.C = p.C + (long long)b0 * p.sC;
     if (p.active != nullptr) q.active = p.active + b0;
     q.err = c->err_dev;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -441,29 +465,54 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     // the sliced form: A^2 skips A's zeros (a local generator's A is about
     // 1 % nonzero); A^4, A^6 and the two products with A^6 are dense sliced
     // products (V and W start from their power terms and take A^6 Z1,
-    // A^6 Z2 with beta = 1); U = A W skips A's zeros again
+    // A^6 Z2 with beta = 1); U = A W is a dense sliced product.  With a
+    // drive generator, A_s = c_s (G_base + u_s G_drv) and A_s^2 comes from
+    // the three slice-independent products G_base^2, G_base G_drv + G_drv
+    // G_base and G_drv^2 (zero-skipping, on the pattern of G_base and G_drv
+    // together, found once in compressed rows) and one pass over the slices.
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
-    LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
-    RGemmProblem<double> p = rsq(n, S, Ar, Ar, A2);
-    LB_TRY(skip_product(c, p, flagA, st));
+    const bool csr = Gd != nullptr;
+    int *rowptr = c->csr, *cols = c->csr + c->max_n + 1;
+    if (csr)
+      LB_CUDA(launch_csr_union(n, Gb, Gd, max_nnz, S, rowptr, cols, flagA, st));
+    else
+      LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
+    auto sparse_left = [&](const RGemmProblem<double>& q) {
+      return csr ? csr_product(c, q, flagA, rowptr, cols, st) : skip_product(c, q, flagA, st);
+    };
+    if (csr) {
+      double *P0 = Z1, *P1 = Z1 + nn, *P2 = Z2;  // free until the power terms
+      LB_TRY(sparse_left(rsq(n, 1, Gb, Gb, P0)));
+      LB_TRY(sparse_left(rsq(n, 1, Gb, Gd, P1)));
+      RGemmProblem<double> p1 = rsq(n, 1, Gd, Gb, P1);
+      p1.beta[0] = 1.0;
+      LB_TRY(sparse_left(p1));
+      LB_TRY(sparse_left(rsq(n, 1, Gd, Gd, P2)));
+      LB_CUDA(launch_real_affine_square(n, S, P0, P1, P2, u, dt, c->sc, A2, c->sm_count, st));
+    } else {
+      LB_TRY(sparse_left(rsq(n, S, Ar, Ar, A2)));
+    }
     // A^4 = A^2 A^2 then A^6 = A^2 A^4 (A^2 sliced once; A^4 is complete
     // before it is sliced as the second product's operand)
-    LB_TRY(oz_product_shared_a(c, n, S, A2, A2, A4, 0.0, A4, A6, 0.0, st));
-    LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[12], b[10], b[8], Z1, c->sm_count, st));
-    LB_CUDA(launch_real_lincomb3<double>(nn * S, A6, A4, A2, b[13], b[11], b[9], Z2, c->sm_count, st));
-    LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[6], b[4], b[2], b[0], V, c->sm_count, st));
-    LB_CUDA(launch_real_lincomb3i(n, S, A6, A4, A2, b[7], b[5], b[3], b[1], W, c->sm_count, st));
+    LB_TRY(oz_product_shared_a(c, n, S, A2, A2, A4, 0.0, A4, A6, 0.0, nullptr, st));
+    LB_CUDA(launch_real_pade_terms(n, S, A6, A4, A2, b, Z1, Z2, V, W, c->sm_count, st));
     // V += A^6 Z1, W += A^6 Z2 with A^6 sliced once
-    LB_TRY(oz_product_shared_a(c, n, S, A6, Z1, V, 1.0, Z2, W, 1.0, st));
-    // U = A W:  Mx = V - U, N = V + U
-    p = rsq(n, S, Ar, W, Mx);
-    p.alpha[0] = -1.0;
-    p.O[1] = N;
-    p.nterms = 1;
-    p.X[0] = V; p.sX[0] = nn;
-    p.coef[0][0] = 1.0; p.coef[1][0] = 1.0;
-    LB_TRY(skip_product(c, p, flagA, st));
+    LB_TRY(oz_product_shared_a(c, n, S, A6, Z1, V, 1.0, Z2, W, 1.0, nullptr, st));
+    // U = A W as a sliced product (A W is dense), its epilogue forming
+    // Mx = V - U and N = V + U (U itself not stored)
+    OzGemm q;
+    q.M = q.N = q.K = n;
+    q.batch = S;
+    q.A = Ar; q.a_sm = n; q.a_sk = 1; q.sA = nn;
+    q.B = W; q.b_sk = n; q.b_sn = 1; q.sB = nn;
+    q.C = nullptr; q.ldc = n; q.sC = nn;
+    q.x.nx = 2;
+    q.x.pm = 1;
+    q.x.T1 = V;
+    q.x.X[0] = Mx;
+    q.x.X[1] = N;
+    LB_TRY(oz_product(c, q, st));
   } else if (prec == LB_FP64_HERMITIAN) {
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
