@@ -59,6 +59,7 @@ constexpr int OZ_THREADS = 320;  // producer warp, MMA warp, eight epilogue warp
                                  // three warps share one scheduler's 16K registers)
 constexpr int OZ_ZERO_EXP = -2000;  // exponent of an all-zero row
 constexpr long long kOzWaitCycles = 4000000000LL;
+constexpr long long kOzSliceCtas = 304;  // slicing CTAs wanted at least (two per SM of 152)
 
 template <int NS, int BN>
 struct OzCfg {
@@ -596,7 +597,9 @@ __global__ void oz_slice_kernel(int R, int K, const double* __restrict__ X, long
 // largest magnitude is reduced; then the CTA writes the group's digits core
 // matrix by core matrix (two elements per thread and plane, 128 contiguous
 // bytes per 32 threads).  Rows past R (the padding of the last tile) are
-// zero digits.
+// zero digits.  With gridDim.z > 1 (few row groups) the K blocks are shared
+// out over the z CTAs of a group, each reading the whole rows for their
+// exponents.
 template <int NS, bool RC>
 __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const double* __restrict__ X, long long sx,
                                                             long long sb, int* __restrict__ E,
@@ -630,7 +633,7 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const 
     const int e = r < R ? oz_exp_of(mx) : OZ_ZERO_EXP;
     if (lane == 0) {
       es[warp] = e;
-      if (r < R) E[(long long)b * R + r] = e;
+      if (r < R && blockIdx.z == 0) E[(long long)b * R + r] = e;
     }
   } else {
     // sx: the K stride; thread t reads row r0 + t % 8 at K positions t / 8 + 32 j
@@ -658,14 +661,16 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int R, int K, const 
       for (int w = 0; w < 8; w++) m = part[w][threadIdx.x] > m ? part[w][threadIdx.x] : m;
       const int e = rr < R ? oz_exp_of(m) : OZ_ZERO_EXP;
       es[threadIdx.x] = e;
-      if (rr < R) E[(long long)b * R + rr] = e;
+      if (rr < R && blockIdx.z == 0) E[(long long)b * R + rr] = e;
     }
   }
   __syncthreads();
   const int t = r0 / tile_rows, rt = r0 - t * tile_rows;
   const long long plane = (long long)tile_rows * OZ_KB;
   __nv_bfloat16* qb = Q + ((long long)b * ntiles + t) * kblocks * NS * plane + (rt >> 3) * 2 * 64;
-  for (int p = threadIdx.x; p < 4 * kpad; p += 256) {
+  const int kb0 = (int)((long long)kblocks * blockIdx.z / gridDim.z),
+            kb1 = (int)((long long)kblocks * (blockIdx.z + 1) / gridDim.z);
+  for (int p = kb0 * 64 + threadIdx.x; p < kb1 * 64; p += 256) {
     // element pairs in address order: k8 (even), r8, K half, K block
     const int e = 2 * p;
     const int k8 = e & 7, r8 = (e >> 3) & 7, ci = e >> 6;
@@ -720,7 +725,9 @@ cudaError_t oz_slice(const double* X, long long sr, long long sk, long long sb, 
     // K or the rows contiguous: exponents and digits in one pass, one row
     // group per CTA
     const size_t smem = (size_t)8 * (kbl * OZ_KB + 1) * sizeof(double);
-    const dim3 grid((nt * o.tile_rows) / 8, o.batch);
+    const long long groups = (long long)(nt * o.tile_rows) / 8 * o.batch;
+    const int zs = (int)std::max<long long>(1, std::min<long long>(kbl, (kOzSliceCtas + groups - 1) / groups));
+    const dim3 grid((nt * o.tile_rows) / 8, o.batch, zs);
     cudaError_t e;
     if (sk == 1) {
       e = set_smem_once((const void*)oz_slice_rows_kernel<kOzSlices, false>, smem);

@@ -108,11 +108,13 @@ __global__ void real_affine_square_kernel(int n, int S, const double* __restrict
 }
 
 // The power terms of the [13/13] approximant's two polynomials in one pass
-// over A^6, A^4, A^2 (n x n per slice, FP64):
-//   Z1 = b12 A^6 + b10 A^4 + b8 A^2,   Z2 = b13 A^6 + b11 A^4 + b9 A^2,
-//   V = b6 A^6 + b4 A^4 + b2 A^2 + b0 I,   W = b7 A^6 + b5 A^4 + b3 A^2 + b1 I;
-// a CTA per row of a slice, its threads along the row.  Twelve FP64
-// operations per entry: the FP64 pipe, not the memory, bounds this pass.
+// over A^6, A^4, A^2 (n x n per slice, FP64), with the A^6 terms of V and W
+// moved into the matrices A^6 multiplies (A^6 Z1 = A^6 (Z1 - b6 I) + b6 A^6):
+//   Z1 = b12 A^6 + b10 A^4 + b8 A^2 + b6 I,   Z2 = b13 A^6 + b11 A^4 + b9 A^2 + b7 I,
+//   V = b4 A^4 + b2 A^2 + b0 I,   W = b5 A^4 + b3 A^2 + b1 I,
+// so that V + A^6 Z1 and W + A^6 Z2 are the approximant's polynomials; a
+// CTA per row of a slice, its threads along the row.  Ten FP64 operations
+// per entry: the FP64 pipe, not the memory, bounds this pass.
 __global__ void real_pade_terms_kernel(int n, int S, const double* __restrict__ A6, const double* __restrict__ A4,
                                        const double* __restrict__ A2, PadeCoef cf, double* __restrict__ Z1,
                                        double* __restrict__ Z2, double* __restrict__ V, double* __restrict__ W) {
@@ -122,12 +124,15 @@ __global__ void real_pade_terms_kernel(int n, int S, const double* __restrict__ 
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const long long e = rw * n + c;
       const double p6 = A6[e], p4 = A4[e], p2 = A2[e];
-      Z1[e] = cf.b[12] * p6 + (cf.b[10] * p4 + cf.b[8] * p2);
-      Z2[e] = cf.b[13] * p6 + (cf.b[11] * p4 + cf.b[9] * p2);
-      const double v = cf.b[6] * p6 + (cf.b[4] * p4 + cf.b[2] * p2);
-      const double w = cf.b[7] * p6 + (cf.b[5] * p4 + cf.b[3] * p2);
-      V[e] = c == r ? v + cf.b[0] : v;
-      W[e] = c == r ? w + cf.b[1] : w;
+      const double z1 = cf.b[12] * p6 + (cf.b[10] * p4 + cf.b[8] * p2);
+      const double z2 = cf.b[13] * p6 + (cf.b[11] * p4 + cf.b[9] * p2);
+      const double v = cf.b[4] * p4 + cf.b[2] * p2;
+      const double w = cf.b[5] * p4 + cf.b[3] * p2;
+      const bool dg = c == r;
+      Z1[e] = dg ? z1 + cf.b[6] : z1;
+      Z2[e] = dg ? z2 + cf.b[7] : z2;
+      V[e] = dg ? v + cf.b[0] : v;
+      W[e] = dg ? w + cf.b[1] : w;
     }
   }
 }
@@ -210,31 +215,56 @@ __global__ void real_copy_active_kernel(long long nn, int S, const double* __res
 //           and H2 = -i (E_kl - E_lk)/2 (Im coordinate -1/2), so
 //           P(E_kl) = Y(R_re)/2 - i Y(R_im)/2
 //   k > l:  E_kl = H1 - i H2 for the pair (l, k): P(E_kl) = Y(R_re)/2 + i Y(R_im)/2
-__device__ __forceinline__ z64 herm_entry(const double* __restrict__ R, int n, int d, int i, int j, int col) {
-  if (i == j) return make_double2(R[(long long)i * n + col], 0.0);
-  const int a = herm_pair_coord(i < j ? i : j, i < j ? j : i, d);
-  const double re = R[(long long)a * n + col], im = R[(long long)(a + 1) * n + col];
-  return make_double2(re, i < j ? im : -im);
+// and entry (i, j) of Y(r) is r_i (i = j), r_re + i r_im (i < j) or
+// r_re - i r_im (i > j) for the coordinates of (min, max).
+// x / 2: the exponent field lowered by one (no FP64 operation) where x and
+// its half are normal; a product otherwise
+__device__ __forceinline__ double half_of(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex > 1 && ex < 0x7FF) return __longlong_as_double(b - (1ll << 52));
+  return 0.5 * x;
 }
+__device__ __forceinline__ double neg_of(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63)); }
 
-// a CTA per row (i, j) of P[s], its threads along the row
+// a CTA per row (i, j) of P[s], its threads along the row.  With Re / Im
+// rows ra, ra + 1 of R for (i, j) (sign sg = +1 for i < j, -1 for i > j) and
+// the coordinate pair a, a + 1 of (k, l):
+//   k = l:  P = (R[ra][k], sg R[ra+1][k])
+//   k < l:  P = ((R[ra][a] + sg R[ra+1][a+1]) / 2, (sg R[ra+1][a] - R[ra][a+1]) / 2)
+//   k > l:  P = ((R[ra][a] - sg R[ra+1][a+1]) / 2, (sg R[ra+1][a] + R[ra][a+1]) / 2)
+// (for i = j the R[ra+1] terms are absent): at most one FP64 addition per
+// real number, the halving and the signs on the bits.
 __global__ void herm_to_complex_kernel(int n, int d, int S, const double* __restrict__ R, z64* __restrict__ P) {
   const long long nn = (long long)n * n, rows = (long long)S * n;
   for (long long rw = blockIdx.x; rw < rows; rw += gridDim.x) {
     const long long s = rw / n;
     const int r = (int)(rw - s * n);
     const int i = r / d, j = r - (r / d) * d;
-    const double* Rs = R + s * nn;
+    const bool diag = i == j, up = i < j;
+    const int ra = diag ? i : herm_pair_coord(up ? i : j, up ? j : i, d);
+    const double* re = R + s * nn + (long long)ra * n;
+    const double* im = re + n;  // used only off the diagonal
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int k = c / d, l = c - (c / d) * d;
       z64 v;
       if (k == l) {
-        v = herm_entry(Rs, n, d, i, j, k);
+        v.x = re[k];
+        v.y = diag ? 0.0 : (up ? im[k] : neg_of(im[k]));
       } else {
         const int a = herm_pair_coord(k < l ? k : l, k < l ? l : k, d);
-        const z64 yre = herm_entry(Rs, n, d, i, j, a), yim = herm_entry(Rs, n, d, i, j, a + 1);
-        v = k < l ? make_double2(0.5 * (yre.x + yim.y), 0.5 * (yre.y - yim.x))
-                  : make_double2(0.5 * (yre.x - yim.y), 0.5 * (yre.y + yim.x));
+        const double x0 = re[a], x1 = re[a + 1];
+        if (diag) {
+          v.x = half_of(x0);
+          v.y = half_of(k < l ? neg_of(x1) : x1);
+        } else {
+          double y0 = im[a], y1 = im[a + 1];
+          if (!up) {
+            y0 = neg_of(y0);
+            y1 = neg_of(y1);
+          }
+          v = k < l ? make_double2(half_of(x0 + y1), half_of(y0 - x1)) : make_double2(half_of(x0 - y1), half_of(y0 + x1));
+        }
       }
       P[rw * n + c] = v;
     }

@@ -343,16 +343,16 @@ __global__ void __launch_bounds__(256) rgemm_rowskip_kernel(const __grid_constan
   }
 }
 
-// The same product with A's nonzero pattern given in compressed rows
-// (rowptr, cols: the column indices of row r in increasing order at
-// cols[rowptr[r] .. rowptr[r + 1])), a superset of every batch element's
-// nonzeros: one warp per output row, the row's pattern read 32 entries at a
-// time, an entry that is zero in this batch element skipped, so the terms
-// and their order are those of rgemm_rowskip_kernel.  Two rows of B are in
-// flight at a time.
+// The same product with A's nonzero pattern given by rows (the column
+// indices of row r in increasing order at cols[rowbeg[r] .. rowend[r])), a
+// superset of every batch element's nonzeros: one warp per output row, the
+// row's pattern read 32 entries at a time, an entry that is zero in this
+// batch element skipped, so the terms and their order are those of
+// rgemm_rowskip_kernel.  Two rows of B are in flight at a time.
 template <typename T, int NQ>
 __global__ void __launch_bounds__(256) rgemm_csr_kernel(const __grid_constant__ RGemmProblem<T> P,
-                                                        const int* __restrict__ rowptr, const int* __restrict__ cols) {
+                                                        const int* __restrict__ rowbeg, const int* __restrict__ rowend,
+                                                        const int* __restrict__ cols) {
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) rgemm_csr_kernel(const __grid_constant__ 
     T acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; q++) acc[q] = T(0);
-    const int j0 = rowptr[gm], j1 = rowptr[gm + 1];
+    const int j0 = rowbeg[gm], j1 = rowend[gm];
     for (int jb = j0; jb < j1; jb += 32) {
       int k = 0;
       T v = T(0);
@@ -412,62 +412,39 @@ __global__ void __launch_bounds__(256) rgemm_csr_kernel(const __grid_constant__ 
   }
 }
 
-// The union nonzero pattern of two n x n matrices (X1 may be null) in
-// compressed rows, one CTA: a warp per row counts its nonzeros (ballots),
-// one warp scans the counts, then each row's column indices are written in
-// increasing order.  With more than max_nnz nonzeros the pattern is not
-// written and flag[0 .. S) = 0, else 1.
-__global__ void __launch_bounds__(1024) csr_union_kernel(int n, const double* __restrict__ X0,
-                                                         const double* __restrict__ X1, long long max_nnz, int S,
-                                                         int* __restrict__ rowptr, int* __restrict__ cols,
-                                                         int* __restrict__ flag) {
+// The union nonzero pattern of two n x n matrices (X1 may be null) by rows:
+// a warp per row writes the row's column indices, increasing, at
+// cols[r n ..] (ballots over 32 columns at a time), rowbeg[r] = r n,
+// rowend[r] = r n + its count, and adds the count to *total.
+__global__ void __launch_bounds__(256) csr_rows_kernel(int n, const double* __restrict__ X0,
+                                                       const double* __restrict__ X1, int* __restrict__ rowbeg,
+                                                       int* __restrict__ rowend, int* __restrict__ cols,
+                                                       unsigned long long* __restrict__ total) {
   constexpr unsigned kFull = 0xffffffffu;
-  extern __shared__ int csr_cnt[];  // n + 1
-  __shared__ int ok_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  auto nz = [&](int r, int k) {
-    const long long o = (long long)r * n + k;
-    return X0[o] != 0.0 || (X1 != nullptr && X1[o] != 0.0);
-  };
-  for (int r = warp; r < n; r += nwarp) {
-    int c = 0;
-    for (int k0 = 0; k0 < n; k0 += 32) c += __popc(__ballot_sync(kFull, k0 + lane < n && nz(r, k0 + lane)));
-    if (lane == 0) csr_cnt[r] = c;
+  const int lane = threadIdx.x & 31;
+  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (r >= n) return;
+  const long long base = (long long)r * n;
+  int pos = 0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int k = k0 + lane;
+    const bool z = k < n && (X0[base + k] != 0.0 || (X1 != nullptr && X1[base + k] != 0.0));
+    const unsigned m = __ballot_sync(kFull, z);
+    if (z) cols[base + pos + __popc(m & ((1u << lane) - 1u))] = k;
+    pos += __popc(m);
   }
-  __syncthreads();
-  if (warp == 0) {
-    // exclusive scan of the counts, 32 at a time
-    int run = 0;
-    for (int r0 = 0; r0 < n; r0 += 32) {
-      const int x = r0 + lane < n ? csr_cnt[r0 + lane] : 0;
-      int inc = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
-      }
-      if (r0 + lane < n) rowptr[r0 + lane] = run + inc - x;
-      run += __shfl_sync(kFull, inc, 31);
-    }
-    if (lane == 0) {
-      rowptr[n] = run;
-      ok_s = (long long)run <= max_nnz ? 1 : 0;
-    }
+  if (lane == 0) {
+    rowbeg[r] = (int)base;
+    rowend[r] = (int)base + pos;
+    atomicAdd(total, (unsigned long long)pos);
   }
-  __syncthreads();
-  const int ok = ok_s;
-  for (int s = threadIdx.x; s < S; s += blockDim.x) flag[s] = ok;
-  if (!ok) return;
-  __threadfence_block();
-  for (int r = warp; r < n; r += nwarp) {
-    int pos = rowptr[r];
-    for (int k0 = 0; k0 < n; k0 += 32) {
-      const bool z = k0 + lane < n && nz(r, k0 + lane);
-      const unsigned m = __ballot_sync(kFull, z);
-      if (z) cols[pos + __popc(m & ((1u << lane) - 1u))] = k0 + lane;
-      pos += __popc(m);
-    }
-  }
+}
+
+// flag[0 .. S) = 1 when the pattern has at most max_nnz entries, else 0
+__global__ void csr_flags_kernel(const unsigned long long* __restrict__ total, long long max_nnz, int S,
+                                 int* __restrict__ flag) {
+  const int ok = *total <= (unsigned long long)max_nnz ? 1 : 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) flag[s] = ok;
 }
 
 // Counts of nonzero entries per matrix, one CTA per matrix, then the flag.
@@ -622,7 +599,8 @@ cudaError_t rgemm_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t s
   return launch_rowskip<T, 23>(p, sm_count, st);
 }
 template <typename T, int NQ>
-cudaError_t launch_csr(const RGemmProblem<T>& p, const int* rowptr, const int* cols, int sm_count, cudaStream_t st) {
+cudaError_t launch_csr(const RGemmProblem<T>& p, const int* rowbeg, const int* rowend, const int* cols, int sm_count,
+                       cudaStream_t st) {
   static int occ = -1;
   if (occ < 0) {
     int o = 0;
@@ -633,27 +611,32 @@ cudaError_t launch_csr(const RGemmProblem<T>& p, const int* rowptr, const int* c
   const long long warps = (long long)p.batch * p.M;
   const long long grid = std::min<long long>((warps + 7) / 8, (long long)sm_count * occ);
   count_launch();
-  rgemm_csr_kernel<T, NQ><<<(unsigned)grid, 256, 0, st>>>(p, rowptr, cols);
+  rgemm_csr_kernel<T, NQ><<<(unsigned)grid, 256, 0, st>>>(p, rowbeg, rowend, cols);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t rgemm_csr(const RGemmProblem<T>& p, const int* rowptr, const int* cols, int sm_count, cudaStream_t st) {
+cudaError_t rgemm_csr(const RGemmProblem<T>& p, const int* rowbeg, const int* rowend, const int* cols, int sm_count,
+                      cudaStream_t st) {
   if (p.transB != 0 || p.shiftA != 0.0 || p.shiftB != 0.0 || p.N > 736 || p.N < 1) return cudaErrorInvalidValue;
   if (p.M < 1 || p.batch < 1) return cudaSuccess;
-  if (p.N <= 128) return launch_csr<T, 4>(p, rowptr, cols, sm_count, st);
-  if (p.N <= 256) return launch_csr<T, 8>(p, rowptr, cols, sm_count, st);
-  return launch_csr<T, 23>(p, rowptr, cols, sm_count, st);
+  if (p.N <= 128) return launch_csr<T, 4>(p, rowbeg, rowend, cols, sm_count, st);
+  if (p.N <= 256) return launch_csr<T, 8>(p, rowbeg, rowend, cols, sm_count, st);
+  return launch_csr<T, 23>(p, rowbeg, rowend, cols, sm_count, st);
 }
-template cudaError_t rgemm_csr<double>(const RGemmProblem<double>&, const int*, const int*, int, cudaStream_t);
+template cudaError_t rgemm_csr<double>(const RGemmProblem<double>&, const int*, const int*, const int*, int,
+                                       cudaStream_t);
 
-cudaError_t launch_csr_union(int n, const double* X0, const double* X1, long long max_nnz, int S, int* rowptr,
-                             int* cols, int* flag, cudaStream_t st) {
-  const size_t smem = sizeof(int) * (size_t)(n + 1);
-  cudaError_t e = set_smem_once((const void*)csr_union_kernel, smem);
+cudaError_t launch_csr_union(int n, const double* X0, const double* X1, long long max_nnz, int S, CsrPattern pat,
+                             int* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(pat.total, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   count_launch();
-  csr_union_kernel<<<1, 1024, smem, st>>>(n, X0, X1, max_nnz, S, rowptr, cols, flag);
+  csr_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, X0, X1, pat.rowbeg, pat.rowend, pat.cols, pat.total);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launch();
+  csr_flags_kernel<<<1, 256, 0, st>>>(pat.total, max_nnz, S, flag);
   return cudaGetLastError();
 }
 

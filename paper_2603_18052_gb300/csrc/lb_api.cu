@@ -196,7 +196,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   add((S + 1) * sizeof(int));                               // sc
   add(S * sizeof(int));                                     // kmix
   add(2 * S * sizeof(int));                                 // spflag
-  add(((size_t)max_n + 1 + nn / 4) * sizeof(int));        // csr
+  add((2 * (size_t)max_n + 2 + nn) * sizeof(int));        // csr
   add(sizeof(z64) * 64 * 64);                               // G
   add((size_t)max_batch * max_n * zb);                      // Rtmp
   add((size_t)max_batch * max_n * zb);                      // Xh
@@ -247,7 +247,7 @@ lb_status lb_create(lb_ctx** out, int device, int max_n, int max_batch, int max_
   c->sc = (int*)ar.take((S + 1) * sizeof(int));
   c->kmix = (int*)ar.take(S * sizeof(int));
   c->spflag = (int*)ar.take(2 * S * sizeof(int));
-  c->csr = (int*)ar.take(((size_t)max_n + 1 + nn / 4) * sizeof(int));
+  c->csr = (int*)ar.take((2 * (size_t)max_n + 2 + nn) * sizeof(int));
   c->G = Z(64 * 64);
   c->Rtmp = Z((size_t)max_batch * max_n);
   c->Xh = Z((size_t)max_batch * max_n);

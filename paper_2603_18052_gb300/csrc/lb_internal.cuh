@@ -127,7 +127,7 @@ struct lb_ctx {
   size_t inst_tab_bytes = 0;
   cudaEvent_t ev_tab = nullptr;   // the last table upload
   int* spflag = nullptr;  // 2 x max_slices: sparse-operand flags of the real-coordinate build
-  int* csr = nullptr;     // max_n + 1 row offsets, then up to max_n^2 / 4 column indices: a sparse pattern
+  int* csr = nullptr;     // a sparse pattern: count (2 ints), row starts, row ends (max_n each), columns (max_n^2)
   // --- GRAPE (contexts with max_n <= 81) ---
   lb::z64* grape = nullptr;
   size_t grape_bytes = 0;
@@ -198,17 +198,25 @@ cudaError_t rgemm_f32(const RGemmProblem<float>* probs, int nprob, int sm_count,
 // (cudaErrorInvalidValue otherwise).
 template <typename T>
 cudaError_t rgemm_rowskip(const RGemmProblem<T>& p, int sm_count, cudaStream_t st);
+// A nonzero pattern by rows: the columns of row r, increasing, at
+// cols[rowbeg[r] .. rowend[r]); total counts them.
+struct CsrPattern {
+  int* rowbeg = nullptr;
+  int* rowend = nullptr;
+  int* cols = nullptr;
+  unsigned long long* total = nullptr;
+};
 // The same product with A's nonzero pattern (a superset of every batch
-// element's) in compressed rows: cols[rowptr[r] .. rowptr[r + 1]) are the
-// columns of row r, increasing; the same terms in the same order as
+// element's) given by rows; the same terms in the same order as
 // rgemm_rowskip.  Needs shiftA == 0 besides rgemm_rowskip's conditions.
 template <typename T>
-cudaError_t rgemm_csr(const RGemmProblem<T>& p, const int* rowptr, const int* cols, int sm_count, cudaStream_t st);
-// The union pattern of X0 and X1 (n x n row-major FP64; X1 may be null) into
-// rowptr (n + 1) and cols (up to max_nnz), one launch; flag[0 .. S) = 1 when
-// it has at most max_nnz entries (and is written), else 0.
-cudaError_t launch_csr_union(int n, const double* X0, const double* X1, long long max_nnz, int S, int* rowptr,
-                             int* cols, int* flag, cudaStream_t st);
+cudaError_t rgemm_csr(const RGemmProblem<T>& p, const int* rowbeg, const int* rowend, const int* cols, int sm_count,
+                      cudaStream_t st);
+// The union pattern of X0 and X1 (n x n row-major FP64; X1 may be null)
+// into pat (row r's columns at cols[r n ..]); flag[0 .. S) = 1 when it has at
+// most max_nnz entries, else 0.
+cudaError_t launch_csr_union(int n, const double* X0, const double* X1, long long max_nnz, int S, CsrPattern pat,
+                             int* flag, cudaStream_t st);
 // flag[s] = 1 if M[s] (S row-major n x n matrices) has at most max_nnz
 // nonzero entries, else 0.
 template <typename T>

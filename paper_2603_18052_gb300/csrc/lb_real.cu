@@ -316,14 +316,13 @@ lb_status skip_product(lb_ctx* c, RGemmProblem<T> p, const int* flag, cudaStream
   return LB_OK;
 }
 
-// The same with A's nonzero pattern in compressed rows (flag[s] = 1: the
-// pattern is valid and sparse, the same for every slice).
-lb_status csr_product(lb_ctx* c, RGemmProblem<double> p, const int* flag, const int* rowptr, const int* cols,
-                      cudaStream_t st) {
+// The same with A's nonzero pattern given by rows (flag[s] = 1: the pattern
+// is sparse, the same for every slice).
+lb_status csr_product(lb_ctx* c, RGemmProblem<double> p, const int* flag, const CsrPattern& pat, cudaStream_t st) {
   RGemmProblem<double> q = p;
   q.pick = flag;
   q.pick_val = 1;
-  LB_CUDA(rgemm_csr(q, rowptr, cols, c->sm_count, st));
+  LB_CUDA(rgemm_csr(q, pat.rowbeg, pat.rowend, pat.cols, c->sm_count, st));
   p.pick = flag;
   p.pick_val = 0;
   LB_CUDA(dense_gemm(p, c->sm_count, st));
@@ -469,17 +468,21 @@ lb_status expm_chunk_herm(lb_ctx* c, int n, int S, const z64* Lbase, const z64* 
     // drive generator, A_s = c_s (G_base + u_s G_drv) and A_s^2 comes from
     // the three slice-independent products G_base^2, G_base G_drv + G_drv
     // G_base and G_drv^2 (zero-skipping, on the pattern of G_base and G_drv
-    // together, found once in compressed rows) and one pass over the slices.
+    // together, found once by rows) and one pass over the slices.
     double *A2 = (double*)c->A2, *A4 = (double*)c->A4, *A6 = (double*)c->A6, *Z1 = (double*)c->Z1,
            *Z2 = (double*)c->Z2, *V = (double*)c->V, *W = (double*)c->W;
     const bool csr = Gd != nullptr;
-    int *rowptr = c->csr, *cols = c->csr + c->max_n + 1;
+    CsrPattern pat;
+    pat.total = (unsigned long long*)c->csr;
+    pat.rowbeg = c->csr + 2;
+    pat.rowend = pat.rowbeg + c->max_n;
+    pat.cols = pat.rowend + c->max_n;
     if (csr)
-      LB_CUDA(launch_csr_union(n, Gb, Gd, max_nnz, S, rowptr, cols, flagA, st));
+      LB_CUDA(launch_csr_union(n, Gb, Gd, max_nnz, S, pat, flagA, st));
     else
       LB_CUDA(launch_sparse_flags<double>(n, S, Ar, max_nnz, flagA, c->sm_count, st));
     auto sparse_left = [&](const RGemmProblem<double>& q) {
-      return csr ? csr_product(c, q, flagA, rowptr, cols, st) : skip_product(c, q, flagA, st);
+      return csr ? csr_product(c, q, flagA, pat, st) : skip_product(c, q, flagA, st);
     };
     if (csr) {
       double *P0 = Z1, *P1 = Z1 + nn, *P2 = Z2;  // free until the power terms
