@@ -150,6 +150,19 @@ lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const do
     if (r_ != LB_OK) return r_;       \
   } while (0)
 
+// C = alpha A B + beta C of a small real product (no transposed B, one
+// output) as a sliced FP64 product
+lb_status oz_small(lb_ctx* c, const RGemmProblem<double>& r, cudaStream_t st) {
+  OzGemm q;
+  q.M = r.M; q.N = r.N; q.K = r.K; q.batch = r.batch;
+  q.A = r.A; q.a_sm = r.lda; q.a_sk = 1; q.sA = r.sA;
+  q.B = r.B; q.b_sk = r.ldb; q.b_sn = 1; q.sB = r.sB;
+  q.C = r.O[0]; q.ldc = r.ldc; q.sC = r.sC;
+  q.alpha = r.alpha[0];
+  q.beta = r.beta[0];
+  return oz_product(c, q, st);
+}
+
 // The diagonal block of the two-level schedule: the kb x kb block (kb <= 128)
 // at (k0, k0) of Mx, up to date with all earlier blocks, factored from two
 // 64-wide halves (the first by lu_diag_real_kernel<64>, the off-diagonal
@@ -159,8 +172,8 @@ lb_status oz_product_shared_a(lb_ctx* c, int n, int S, const double* A, const do
 //   L^{-1} = [[L1^{-1}, 0], [-L2^{-1} L21 L1^{-1}, L2^{-1}]],
 //   U^{-1} = [[U1^{-1}, -U1^{-1} U12 U2^{-1}], [0, U2^{-1}]]
 // into Linv (128 x 128, zeroed here) and Uinv_k (128 x 128, zero on entry).  U's blocks go
-// to Uf, L21 to Lp.  The small products run on the FP64 pipe; `tmp` holds
-// 6 S 64 x 64 doubles.
+// to Uf, L21 to Lp.  The seven 64 x 64 x 64 products are sliced FP64
+// products too; `tmp` holds 6 S 64 x 64 doubles.
 lb_status diag_block128(lb_ctx* c, int n, int S, double* Mx, double* Uf, double* Lp, int k0, int kb, double* Linv,
                         long long sLinv, double* Uinv_k, long long sUinv, double* tmp, cudaStream_t st) {
   constexpr int H = 64, NB = 128;
@@ -179,20 +192,23 @@ lb_status diag_block128(lb_ctx* c, int n, int S, double* Mx, double* Uf, double*
   // U12 = L1^{-1} Mx[k0:k1, k1:k1+h1];  L21 = Mx[k1:k1+h1, k0:k1] U1^{-1}
   pr[0] = rupd(h0, h1, h0, Li1, H, hh, Mx + (long long)k0 * n + k1, n, nn, U12, n, nn, 1.0, 0.0, S);
   pr[1] = rupd(h1, h0, h0, Mx + (long long)k1 * n + k0, n, nn, Ui1, H, hh, L21, n, nn, 1.0, 0.0, S);
-  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  LB_TRY(oz_small(c, pr[0], st));
+  LB_TRY(oz_small(c, pr[1], st));
   // the Schur complement of the second half, then its factorisation
   RGemmProblem<double> q = rupd(h1, h1, h0, L21, n, nn, U12, n, nn, Mx + (long long)k1 * n + k1, n, nn, -1.0, 1.0, S);
-  LB_CUDA(rgemm_f64(&q, 1, c->sm_count, st));
+  LB_TRY(oz_small(c, q, st));
   LB_CUDA(launch_lu_diag_real(n, S, k1, h1, Mx, Uf, Li2, hh, Ui2, hh, c->err_dev, st, H));
   LB_CUDA(launch_real_copy_block(h1, h1, S, Li2, H, hh, Linv + (long long)h0 * NB + h0, NB, sLinv, c->sm_count, st));
   LB_CUDA(launch_real_copy_block(h1, h1, S, Ui2, H, hh, Uinv_k + (long long)h0 * NB + h0, NB, sUinv, c->sm_count, st));
   // T = L21 L1^{-1}, T2 = U12 U2^{-1}; then the off-diagonal blocks
   pr[0] = rupd(h1, h0, h0, L21, n, nn, Li1, H, hh, T, H, hh, 1.0, 0.0, S);
   pr[1] = rupd(h0, h1, h1, U12, n, nn, Ui2, H, hh, T2, H, hh, 1.0, 0.0, S);
-  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  LB_TRY(oz_small(c, pr[0], st));
+  LB_TRY(oz_small(c, pr[1], st));
   pr[0] = rupd(h1, h0, h1, Li2, H, hh, T, H, hh, Linv + (long long)h0 * NB, NB, sLinv, -1.0, 0.0, S);
   pr[1] = rupd(h0, h1, h0, Ui1, H, hh, T2, H, hh, Uinv_k + h0, NB, sUinv, -1.0, 0.0, S);
-  LB_CUDA(rgemm_f64(pr, 2, c->sm_count, st));
+  LB_TRY(oz_small(c, pr[0], st));
+  LB_TRY(oz_small(c, pr[1], st));
   return LB_OK;
 }
 
