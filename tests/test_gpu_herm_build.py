@@ -115,12 +115,13 @@ def test_expm_herm_per_slice_generators_and_chunking(lbm, dev):
         assert _relf(Pg[s], O.expm_pade13(gens[s] * 0.5)) <= 1e-12
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64_hermitian", 1e-12), ("fp32_hermitian", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64_hermitian", 1e-12), ("fp32_hermitian", 1e-6), ("fp64_sliced", 1e-12)])
 def test_expm_herm_sparse_and_dense_slices(lbm, dev, prec, tol):
     """Slices whose powers of A are sparse (a dephasing generator: the real
     form is 2 x 2 block diagonal, so A and A^2 take the zero-skipping
     products) alternate with dense random generators in one call; every
-    slice against the oracle."""
+    slice against the oracle.  In the sliced form (one generator per slice,
+    no drive) A^2 is the per-slice zero-skipping product and the rest sliced."""
     d, S = 4, 6
     n = d * d
     rng_h = _rand_c(1800, (d, d))

@@ -153,13 +153,14 @@ def test_expm_fp32_products(lbm, dev):
     assert err <= 1e-6, err
 
 
-def test_expm_nonfinite_input_is_reported(lbm, dev):
+@pytest.mark.parametrize("prec", ["fp64", "fp64_hermitian", "fp64_sliced"])
+def test_expm_nonfinite_input_is_reported(lbm, dev, prec):
     n = 9
     Lb = np.zeros((n, n), dtype=complex)
     Lb[2, 3] = np.nan
     ctx = lbm.Context(0, max_n=n, max_batch=1, max_slices=1)
     P = torch.empty((1, n, n), dtype=torch.complex128, device=dev)
-    lbm.lb_expm_pade(ctx, _t(Lb[None], dev), None, None, 0.1, P)
+    lbm.lb_expm_pade(ctx, _t(Lb[None], dev), None, None, 0.1, P, prec=prec)
     with pytest.raises(lbm.LBError) as ei:
         lbm.lb_sync_status(ctx)
     assert ei.value.name == "LB_ENONFINITE"
