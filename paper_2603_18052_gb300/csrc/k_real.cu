@@ -285,9 +285,11 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
   constexpr int NP = 256 / NB;
   extern __shared__ double lu_smem[];
   double(*a)[NB + 1] = (double(*)[NB + 1])lu_smem;
-  double(*x)[NB + 1] = (double(*)[NB + 1])(lu_smem + NB * (NB + 1));
-  double(*part)[NB] = (double(*)[NB])(lu_smem + 2 * NB * (NB + 1));
-  __shared__ double rinv_s;
+  double(*xl)[NB + 1] = (double(*)[NB + 1])(lu_smem + NB * (NB + 1));
+  double(*xu)[NB + 1] = (double(*)[NB + 1])(lu_smem + 2 * NB * (NB + 1));
+  double(*pl)[NB] = (double(*)[NB])(lu_smem + 3 * NB * (NB + 1));
+  double(*pu)[NB] = (double(*)[NB])(lu_smem + 3 * NB * (NB + 1) + NP * NB);
+  double* rdiag = lu_smem + 3 * NB * (NB + 1) + 2 * NP * NB;  // 1 / U[j][j] (1 where the pivot is unusable)
   const int s = blockIdx.x;
   const long long nn = (long long)n * n;
   const double* Ms = M + s * nn;
@@ -302,13 +304,13 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
       const double p = a[j][j];
       if (!(fabs(p) >= 1e-300) || !isfinite(p)) {
         atomicOr(err, isfinite(p) ? ERR_SINGULAR : ERR_NONFINITE);
-        rinv_s = 1.0;
+        rdiag[j] = 1.0;
       } else {
-        rinv_s = 1.0 / p;
+        rdiag[j] = 1.0 / p;
       }
     }
     __syncthreads();
-    const double rinv = rinv_s;
+    const double rinv = rdiag[j];
     for (int i = j + 1 + tid; i < kb; i += blockDim.x) a[i][j] *= rinv;
     __syncthreads();
     const int w = kb - j - 1;
@@ -318,45 +320,44 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
     }
     __syncthreads();
   }
+  // the two triangular inverses row by row, one row of each per round:
+  //   L^{-1} (L unit lower), forward:  X[i][c] = d_ic - sum_{j<i} L[i][j] X[j][c]
+  //   U^{-1}, backward:  X[i][c] = (d_ic - sum_{j>i} U[i][j] X[j][c]) / U[i][i]
+  // (the division as a product with the pivot's reciprocal from the
+  // factorisation); each entry's sum in NP partial sums of a fixed order
   const int c = tid % NB, p = tid / NB;  // column, partial-sum group
-  // Linv: X = L^{-1}, L unit lower; X[i][c] = d_ic - sum_{j<i} L[i][j] X[j][c]
-  for (int e = tid; e < NB * NB; e += blockDim.x) x[e / NB][e % NB] = 0.0;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    xl[e / NB][e % NB] = 0.0;
+    xu[e / NB][e % NB] = 0.0;
+  }
   __syncthreads();
-  for (int i = 0; i < kb; i++) {
-    double acc = 0.0;
-    if (c < kb)
-      for (int j = p; j < i; j += NP) acc = fma(-a[i][j], x[j][c], acc);
-    part[p][c] = acc;
+  for (int t = 0; t < kb; t++) {
+    const int il = t, iu = kb - 1 - t;
+    double accl = 0.0, accu = 0.0;
+    if (c < kb) {
+      for (int j = p; j < il; j += NP) accl = fma(-a[il][j], xl[j][c], accl);
+      for (int j = iu + 1 + p; j < kb; j += NP) accu = fma(-a[iu][j], xu[j][c], accu);
+    }
+    pl[p][c] = accl;
+    pu[p][c] = accu;
     __syncthreads();
     if (p == 0 && c < kb) {
-      double v = i == c ? 1.0 : 0.0;
-      for (int q = 0; q < NP; q++) v += part[q][c];
-      x[i][c] = v;
+      double v = il == c ? 1.0 : 0.0, u = iu == c ? 1.0 : 0.0;
+      for (int q = 0; q < NP; q++) {
+        v += pl[q][c];
+        u += pu[q][c];
+      }
+      xl[il][c] = v;
+      xu[iu][c] = u * rdiag[iu];
     }
     __syncthreads();
   }
   double* Li = Linv + (long long)s * sLinv;
-  for (int e = tid; e < NB * NB; e += blockDim.x) Li[e] = x[e / NB][e % NB];
-  __syncthreads();
-  // Uinv: X = U^{-1}; X[i][c] = (d_ic - sum_{j>i} U[i][j] X[j][c]) / U[i][i]
-  for (int e = tid; e < NB * NB; e += blockDim.x) x[e / NB][e % NB] = 0.0;
-  __syncthreads();
-  for (int i = kb - 1; i >= 0; i--) {
-    double acc = 0.0;
-    if (c < kb)
-      for (int j = i + 1 + p; j < kb; j += NP) acc = fma(-a[i][j], x[j][c], acc);
-    part[p][c] = acc;
-    __syncthreads();
-    if (p == 0 && c < kb) {
-      double v = i == c ? 1.0 : 0.0;
-      for (int q = 0; q < NP; q++) v += part[q][c];
-      const double dd = a[i][i];
-      x[i][c] = (fabs(dd) >= 1e-300 && isfinite(dd)) ? v / dd : v;
-    }
-    __syncthreads();
-  }
   double* Ui = Uinv + (long long)s * sUinv;
-  for (int e = tid; e < NB * NB; e += blockDim.x) Ui[e] = x[e / NB][e % NB];
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    Li[e] = xl[e / NB][e % NB];
+    Ui[e] = xu[e / NB][e % NB];
+  }
   double* Ufs = Uf + s * nn;
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, j = e - (e / kb) * kb;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(256) lu_diag_real_kernel(int n, int k0, int kb
 
 template <int NB>
 constexpr size_t lu_diag_smem() {
-  return (size_t)(2 * NB * (NB + 1) + (256 / NB) * NB) * sizeof(double);
+  return (size_t)(3 * NB * (NB + 1) + 2 * (256 / NB) * NB + NB) * sizeof(double);
 }
 
 }  // namespace
