@@ -38,9 +38,14 @@
 //    i+1 .. NS+1: the accumulator is NS groups x OZ_BN columns of FP32;
 //  * all eight warps read the groups out of TMEM (warp w: lanes 32 (w % 4),
 //    column chunks of half w / 4), combine them and write FP64
-//    C = alpha (A B) + beta C.
+//    C = alpha (A B) + beta C; a variant (XO) also writes further outputs
+//    formed from the product and two matrices laid out like C (OzExtra).
 // Every mbarrier wait is bounded; a wait that gives up sets the error word,
 // the CTA waits (bounded) for its copies in flight and frees its TMEM.
+//
+// The digits are made by oz_slice: one pass per row group (exponents and
+// digits) when K or the rows of the operand are contiguous, else an
+// exponent pass and a pass over 32 x 32 blocks.
 #include "lb_internal.cuh"
 
 #include <cuda_bf16.h>
